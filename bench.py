@@ -1,0 +1,350 @@
+#!/usr/bin/env python3
+"""Throughput of the Shield-MPPI hot path on GB300.
+
+One step = one whole Shield-MPPI control update (Alg. 2 body) of the K = 65536,
+T = 100 problem (elliptical 20 x 12 m track, half-width 2 m): K sampled
+rollouts with the DCBF cost and the softmin update (smppi_step), 10 Armijo
+repair iterations of V+ (smppi_repair), then the disturbed closed-loop step
+and warm start (smppi_apply), all through smppi_shield_update.  The metric is
+rollout-steps/s = K T / (time per update); the line also carries the
+microseconds per update, the roofline of the dominant kernel, the end-to-end
+rate through the host-buffer API and the FP64 oracle timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one process per GPU) every rank runs its own problem
+instance (an independent Philox stream): weak scaling, no collective on the
+data path; rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "rollout-steps/s & µs per MPPI update (batched+adjoint vs plain), % FP32 roofline"
+UNIT = "rollout-steps/s"
+K_ROLL, T_HOR, N_REPAIR = 65536, 100, 10
+# FP32 flops of one rollout step (FMA = 2), hand count of the forward model,
+# noise, track projection and cost; see the design notes.
+F_ALG = 310
+# FP32 peak: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (maximum SM clock)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+L2_FLUSH_BYTES = 256 << 20
+# DRAM traffic per rollout launch from the ncu capture in profiles/, valid only
+# for the kernel source it was taken on (hash of the files that define it).
+ROLLOUT_TRAFFIC = {"sources_sha": None, "bytes_per_launch": None}
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("rollout.cu", "device.cuh", "kernels.cuh"):
+        with open(os.path.join(ROOT, "paper_2302_11719_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# --------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while timing runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def gpu_index(local_rank: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [v for v in vis.split(",") if v.strip()]
+    if ids and all(v.strip().isdigit() for v in ids):
+        return int(ids[local_rank % len(ids)])
+    return local_rank
+
+
+# --------------------------------------------------------------------------
+def oracle_updates(K, T, n_repair, budget_s, nthreads, max_updates=None):
+    """Time whole Shield-MPPI updates of the FP64 oracle (closed loop) on the host."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2302_11719_gb300 import inputs as I
+    O.build()
+    pr = I.throughput_problem(K, T)
+    m = O.Model(pr.params, pr.track)
+    x0 = pr.x0.astype(np.float64)
+    V = pr.V.astype(np.float64)
+    n, t0 = 0, time.perf_counter()
+    times = []
+    while True:
+        a = time.perf_counter()
+        _, Vp = O.mppi_step(m, x0, V, n, 0, nthreads=nthreads)
+        Vs, _, _, _ = O.repair(m, x0, Vp, n_repair)
+        x0 = O.apply(m, x0, Vs[0], n)
+        V = O.shift(m, Vp)
+        times.append(time.perf_counter() - a)
+        n += 1
+        if (max_updates and n >= max_updates) or (not max_updates and
+                                                   time.perf_counter() - t0 > budget_s):
+            break
+    return n, times
+
+
+def cpu_threads() -> int:
+    return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    nth = cpu_threads()
+    # warm-up updates, then the timed ones (full-size updates of the oracle)
+    oracle_updates(K_ROLL, T_HOR, N_REPAIR, 0, nth, max_updates=max(1, args.warmup))
+    n, times = oracle_updates(K_ROLL, T_HOR, N_REPAIR, 0, nth, max_updates=args.steps)
+    total = sum(times)
+    value = K_ROLL * T_HOR * n / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": n, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / n, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nth, "kind": "oracle",
+                         "sample": "%d whole Shield-MPPI updates (K=%d, T=%d, %d repair "
+                                   "iterations) of the FP64 oracle" % (n, K_ROLL, T_HOR,
+                                                                      N_REPAIR)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config():
+    return {"workload": "Shield-MPPI control update, K=%d rollouts, T=%d, %d Armijo repair "
+                        "iterations, closed loop" % (K_ROLL, T_HOR, N_REPAIR),
+            "K": K_ROLL, "T": T_HOR, "n_repair": N_REPAIR,
+            "track": "ellipse 20 x 12 m, half-width 2 m, 1024 points",
+            "model": "6-state dynamic single-track car, dt 0.02 s",
+            "l2": "flushed between timed steps (256 MiB write, outside the timed events)"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_2302_11719_gb300 import inputs as I
+    from paper_2302_11719_gb300 import smppi as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    pr = I.throughput_problem(K_ROLL, T_HOR)
+    ctl = S.Controller(pr.params, pr.track, device=dev)
+    inst = rank
+    x0 = ctl.tensor(pr.x0)
+    V = ctl.tensor(pr.V)
+    Vs = torch.empty_like(V)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    it = 0
+    for _ in range(args.warmup):
+        S.smppi_shield_update(ctl.h, x0, V, Vs, it, inst, N_REPAIR)
+        it += 1
+    st, bits = ctl.sync_status()
+    if st not in (S.OK, S.ERR_STALLED):
+        raise RuntimeError("device status %d (bits %d) in warm-up" % (st, bits))
+
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(gpu_index(local))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    S.smppi_timing(ctl.h, True)
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        e0[i].record()
+        S.smppi_shield_update(ctl.h, x0, V, Vs, it, inst, N_REPAIR)
+        e1[i].record()
+        it += 1
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    S.smppi_timing(ctl.h, False)
+    clocks = sampler.stop()
+    kt = S.smppi_timing_read(ctl.h)
+    step_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
+    total_s = sum(step_ms) / 1e3
+    st, bits = ctl.sync_status()
+    if st not in (S.OK, S.ERR_STALLED):
+        raise RuntimeError("device status %d (bits %d) in the timed region" % (st, bits))
+    if dist:
+        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = world * K_ROLL * T_HOR * args.steps / total_s
+
+    # end to end through the host-buffer entry point (copies in the timed region)
+    hx = torch.from_numpy(pr.x0.copy()).pin_memory()
+    hV = torch.from_numpy(pr.V.copy()).pin_memory()
+    hVs = torch.empty_like(hV).pin_memory()
+    for _ in range(2):
+        S.smppi_shield_update(ctl.h, hx.data_ptr(), hV.data_ptr(), hVs.data_ptr(), it, inst,
+                              N_REPAIR, None, True)
+        it += 1
+    e2e_s = 0.0
+    for i in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        S.smppi_shield_update(ctl.h, hx.data_ptr(), hV.data_ptr(), hVs.data_ptr(), it, inst,
+                              N_REPAIR, None, True)
+        e2e_s += time.perf_counter() - a
+        it += 1
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * K_ROLL * T_HOR * args.steps / e2e_s
+
+    if rank != 0:
+        dist.barrier()
+        dist.destroy_process_group()
+        ctl.close()
+        return 0
+
+    # roofline of the dominant kernel (largest share of the timed kernel time)
+    shares = {k: v[0] for k, v in kt.items() if v[1] > 0}
+    tot_k = sum(shares.values())
+    dominant = max(shares, key=shares.get)
+    roll_ms, roll_n = kt["rollout"]
+    roll_avg_s = roll_ms / roll_n / 1e3
+    achieved = F_ALG * K_ROLL * T_HOR / roll_avg_s / 1e12
+    sha = kernel_sha()
+    traffic = (ROLLOUT_TRAFFIC["bytes_per_launch"]
+               if ROLLOUT_TRAFFIC["sources_sha"] == sha else None)
+    roofline = {"bound": "alu", "kernel": "rollout", "achieved": achieved,
+                "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                "traffic": traffic,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "flops_per_unit": F_ALG, "units_per_launch": K_ROLL * T_HOR,
+                "avg_launch_us": roll_avg_s * 1e6}
+    n_cpu = cpu_threads()
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        n, times = oracle_updates(K_ROLL, T_HOR, N_REPAIR, args.cpu_seconds, n_cpu)
+        cpu = {"value": K_ROLL * T_HOR * n / sum(times), "unit": UNIT, "cores": n_cpu,
+               "kind": "oracle",
+               "sample": "%d whole Shield-MPPI updates (K=%d, T=%d, %d repair iterations) of "
+                         "the FP64 oracle, %.1f s" % (n, K_ROLL, T_HOR, N_REPAIR, sum(times))}
+    launches = sum(v[1] for v in kt.values())
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": workload_config(),
+        "us_per_update": 1e6 * total_s / args.steps,
+        "step_ms_median": statistics.median(step_ms),
+        "wall_s_timed_loop": wall,
+        "kernel_share": {k: round(v / tot_k, 4) for k, v in shares.items()},
+        "kernel_avg_us": {k: 1e3 * v[0] / v[1] for k, v in kt.items() if v[1]},
+        "dominant_kernel": dominant,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * (6 + 2 * T_HOR),
+                "d2h_bytes_per_step": 4 * (6 + 4 * T_HOR)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    ctl.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

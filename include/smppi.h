@@ -1,0 +1,241 @@
+/*
+ * smppi.h -- C ABI of the GB300 (sm_103a) Shield-MPPI hot path.
+ *
+ * Method: Yin, Dawson, Fan, Tsiotras, "Shield Model Predictive Path Integral:
+ * A Computationally Efficient Robust MPC Approach Using Control Barrier
+ * Functions", arXiv 2302.11719.  One Shield-MPPI control update (Alg. 2) is
+ *   1. K Gaussian perturbations of the nominal controls V (Sec. II),
+ *   2. forward simulation of every perturbed sequence through the vehicle
+ *      model x_{k+1} = f(x_k, u_k) (Eq. 1),
+ *   3. trajectory cost with the DCBF penalty on the augmented state
+ *      (Eq. 12, Eq. 17-20; safe set h = w^2 - e_y^2, Eq. 23; running cost
+ *      Eq. 24-25),
+ *   4. the min-shifted softmin control update (Eq. 10-11),
+ *   5. the safety shield: gradient repair of the CBF objective (Eq. 22,
+ *      Alg. 1),
+ *   6. execution of v_0^safe on the (disturbed, Eq. 26) system and the warm
+ *      start V <- V^+.
+ *
+ * Conventions of every entry point:
+ *   - Arrays are float32 (merits: float64), C-contiguous, in DEVICE memory
+ *     unless the argument says host.  The caller owns them; the library never
+ *     frees or keeps a caller pointer beyond the call, except params.track_xy,
+ *     which must stay valid until smppi_destroy.
+ *   - State x = (v_x, v_y, r, X, Y, psi) (6 floats); control u = (delta, a)
+ *     (steer in rad, throttle in [-1, 1]); a control sequence is T x 2.
+ *   - All work is enqueued on the handle's CUDA stream and is asynchronous;
+ *     no entry point synchronises unless it says so.  Argument errors are
+ *     found on the host before anything is enqueued and return SMPPI_ERR_ARG;
+ *     failed CUDA calls return SMPPI_ERR_CUDA.  Conditions found on the device
+ *     (NaN/Inf in a state or cost, a stalled line search) are recorded in a
+ *     device status word that smppi_sync_status reads.  smppi_last_error gives
+ *     a one-line message for the last failure on the handle.
+ *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key = seed and
+ *     counter = (k, t >> 1, iter, stream | instance << 8); even t uses output
+ *     words (0, 1), odd t words (2, 3); Box-Muller on
+ *     u = ((x >> 9) + 1/2) 2^-23.  Stream 0 = MPPI noise, stream 1 = closed-
+ *     loop disturbance (counter (0, 0, n, 1 | instance << 8)).  Noise is
+ *     regenerated where it is used and never stored.
+ *   - Not thread-safe per handle; distinct handles are independent.
+ */
+#ifndef SMPPI_H
+#define SMPPI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SMPPI_OK = 0,
+    SMPPI_ERR_ARG = 1,      /* invalid argument (null pointer, size or value out of range) */
+    SMPPI_ERR_CUDA = 2,     /* a CUDA runtime call or kernel launch failed */
+    SMPPI_ERR_NUMERIC = 3,  /* NaN or Inf in a state, cost or merit (device status) */
+    SMPPI_ERR_TIMEOUT = 4,  /* a bounded device-side wait gave up (device status) */
+    SMPPI_ERR_STALLED = 5,  /* the repair line search accepted no trial step */
+    SMPPI_ERR_NOMEM = 6     /* workspace allocation failed */
+} smppi_status;
+
+/* Device status bits (smppi_sync_status folds them into a status code). */
+#define SMPPI_DEV_NUMERIC 1u
+#define SMPPI_DEV_TIMEOUT 2u
+#define SMPPI_DEV_STALLED 4u
+
+/* Limits of this build. */
+#define SMPPI_MAX_T 512        /* horizon */
+#define SMPPI_MAX_TRACK 2048   /* centreline points (staged in shared memory) */
+
+/*
+ * Problem parameters (host struct, copied at create).  Names follow the paper:
+ * lambda = temperature (Eq. 11); gamma = control-cost weight of Alg. 2
+ * (Eq. 8 has gamma = lambda); alpha = class-kappa rate p(r) = alpha r, the
+ * paper's beta (Eq. 15), so the penalty threshold is (1 - alpha) h(x_{k-1})
+ * (Eq. 17); C_cbf = C of Eq. 17; half_width = w_T of Eq. 23; q_v, v_target,
+ * q_d, C_obs = the running cost q = q_v (v_x - v_target)^2 + q_d e_y^2 / w^2
+ * + C_obs 1(outside) (Eq. 24-25).
+ */
+typedef struct smppi_params {
+    float m, Iz, lf, lr;        /* vehicle: mass, yaw inertia, CoG-axle distances */
+    float B, Ct, g, fx_gain;    /* tyre Fy = Fz sin(Ct atan(B slip)), gravity, rear N per throttle */
+    float dt;                   /* explicit Euler step (s) */
+    float sigma[2];             /* Sigma = diag(sigma^2) of the control noise */
+    float lambda, gamma;
+    int K, T, N_r;              /* rollouts, horizon (<= SMPPI_MAX_T), repair horizon (<= T) */
+    float alpha, C_cbf;
+    float q_v, v_target, q_d, C_obs;
+    float u_min[2], u_max[2];   /* control box */
+    float half_width;
+    float dist_sigma[2];        /* disturbance std on (v_y, r) of Eq. 26 */
+    float ls_s0, ls_c;          /* Armijo: first step ls_s0 / |g|_inf, sufficient decrease ls_c */
+    int ls_max_halvings;        /* trial steps per line search */
+    int checkpoint;             /* adjoint checkpoint interval (0 = ceil(sqrt(T))) */
+    int max_seq;                /* most sequences one repair / cost_grad call handles */
+    int n_track;                /* centreline points, 3..SMPPI_MAX_TRACK */
+    const float* track_xy;      /* DEVICE, n_track x 2: closed centreline polyline */
+    uint64_t seed;              /* Philox key */
+} smppi_params;
+
+typedef struct smppi_handle smppi_handle;
+
+/* Fill *p with the single-problem defaults (m = 21.7, Iz = 1.12, lf = 0.34,
+ * lr = 0.23, B = 4, Ct = 1.5, g = 9.81, fx_gain = 60, dt = 0.02,
+ * sigma = (0.15, 0.3), lambda = gamma = 1, K = 256, T = N_r = 50, alpha = 0.3,
+ * C_cbf = 1000, q = 2 (v_x - 8)^2 + 100 e_y^2 / w^2, box [-0.5, 0.5] x [-1, 1],
+ * w = 2, disturbance 0.3, Armijo 0.1 / 1e-4 / 20, max_seq = 1); track_xy is
+ * left NULL. */
+void smppi_default_params(smppi_params* p);
+
+/* Create a handle: validates p, copies it, allocates the workspace for p->K
+ * rollouts, horizon p->T and p->max_seq repair sequences, and prepares the
+ * segment table of the track on `cuda_stream` (a cudaStream_t; NULL = the
+ * legacy default stream).  On failure *out is NULL. */
+smppi_status smppi_create(const smppi_params* p, void* cuda_stream, smppi_handle** out);
+
+/* Free the workspace after synchronising the handle's stream.  NULL is a no-op. */
+smppi_status smppi_destroy(smppi_handle* h);
+
+/* Message of the last failure on h (or of the last failed create when h is NULL). */
+const char* smppi_last_error(const smppi_handle* h);
+
+/* Synchronise the stream, read and clear the device status word; returns
+ * SMPPI_OK or the first of NUMERIC / TIMEOUT / STALLED that is set.  If
+ * bits_out is not NULL the raw bits are written there (host). */
+smppi_status smppi_sync_status(smppi_handle* h, uint32_t* bits_out);
+
+/*
+ * One MPPI iteration (Alg. 2, sampling loop + OptimalControl; Eq. 10-12, 20).
+ *   x0   [6]        current state
+ *   V    [T x 2]    in: nominal controls v_t; out: V^+ (Eq. 10, clamped to the box)
+ *   iter            Philox counter word (the control-update index)
+ *   instance        Philox counter word (problem index, < 2^24)
+ *   S_out [K]       optional (NULL): per-rollout cost S~ (Eq. 20)
+ *   traj_out [K x (T+1) x 6]  optional (NULL): every sampled trajectory
+ * Rollout costs accumulate in float32; the cross-block min / normaliser merge
+ * of Eq. 11 and the weighted noise sum run in float64.
+ */
+smppi_status smppi_step(smppi_handle* h, const float* x0, float* V, uint32_t iter,
+                        uint32_t instance, float* S_out, float* traj_out);
+
+/* The control update alone (Eq. 10-11) from given rollout costs S [K]: the
+ * noise of iteration (iter, instance) is regenerated.  V [T x 2] in/out as
+ * in smppi_step. */
+smppi_status smppi_update(smppi_handle* h, const float* S, float* V, uint32_t iter,
+                          uint32_t instance);
+
+/*
+ * Deterministic cost and its gradient for n_seq independent sequences
+ * (n_seq <= max_seq), by a reverse-mode adjoint with checkpoints every
+ * `checkpoint` steps (0 = the handle's) and recomputation in the backward
+ * sweep; checkpoint < 0 stores the whole trajectory instead (full tape).
+ *   J(V) = w_run sum_{t=0}^{N} q(x_t) + w_cbf sum_{t=0}^{N-1} C max{(1-alpha) h_t - h_{t+1}, 0}
+ * with x_{t+1} = f(x_t, clamp(v_t)) from x0 (Eq. 1, 17, 23-24); (0, 1) is
+ * the repair objective P = -C x (objective of Eq. 22).
+ *   x0 [n_seq x 6], V [n_seq x T x 2], N <= T (horizon of the sum),
+ *   J_out [n_seq] (float64), grad_out [n_seq x T x 2] (zero for t >= N).
+ * max(0, .) has derivative 0 at a non-positive argument; clamp passes the
+ * derivative on the closed box and blocks it strictly outside.
+ */
+smppi_status smppi_cost_grad(smppi_handle* h, int n_seq, const float* x0, const float* V,
+                             int N, float w_run, float w_cbf, int checkpoint,
+                             double* J_out, float* grad_out);
+
+/*
+ * Safety shield (Alg. 1, Eq. 22) on n_seq independent sequences
+ * (n_seq <= max_seq): n_iters steps on the first N_r controls of each.
+ *   mode 0: V <- clip(V - delta grad P)                      (Alg. 1, fixed step)
+ *   mode 1: projected gradient with Armijo backtracking: s = ls_s0 / |g|_inf,
+ *           accept clip(V - s g) when P' <= P - ls_c g'(V - V'), else halve s
+ *           (ls_max_halvings trials); stop early when P = 0 (already safe).
+ *   x0 [n_seq x 6]; V_in, V_out [n_seq x T x 2] (may alias);
+ *   merit_out [n_seq x (n_iters + 1)] optional (float64): P before each
+ *   iteration and after the last, repeated after an early stop;
+ *   iters_out [n_seq] optional (int32): iterations run per sequence.
+ * A sequence whose line search accepts nothing keeps its last iterate and
+ * sets SMPPI_DEV_STALLED in the status word.  The merit accumulates in float64.
+ */
+smppi_status smppi_repair(smppi_handle* h, int n_seq, const float* x0, const float* V_in,
+                          float* V_out, int n_iters, int mode, float delta,
+                          double* merit_out, int* iters_out);
+
+/*
+ * Closed-loop step (Alg. 2 ExecuteCommand and warm start; Eq. 26):
+ *   x0 [6] in/out:  x0 <- f(x0, clamp(V_exec[0])) + w_n, w_n on stream 1
+ *   V  [T x 2] in/out: V <- shift(V) (drop v_0, repeat v_{T-1})
+ *   V_exec [T x 2]: the sequence whose first control is executed (V^safe)
+ */
+smppi_status smppi_apply(smppi_handle* h, float* x0, float* V, const float* V_exec, uint32_t n,
+                         uint32_t instance);
+
+/*
+ * One whole Shield-MPPI control update (Alg. 2 body) on the handle's stream:
+ * smppi_step, then smppi_repair (mode 1, n_repair iterations) of V^+ into
+ * V_safe, then the closed-loop step (smppi_apply) with n = iter.
+ *   host_buffers = 0: x0 [6], V [T x 2], V_safe [T x 2] are device arrays.
+ *   host_buffers = 1: they are host arrays (pinned memory recommended); the
+ *   update copies x0 and V in and x0, V and V_safe out and synchronises the
+ *   stream before returning.
+ *   merit_out [n_repair + 1] optional, device (or host when host_buffers = 1).
+ */
+smppi_status smppi_shield_update(smppi_handle* h, float* x0, float* V, float* V_safe,
+                                 uint32_t iter, uint32_t instance, int n_repair,
+                                 double* merit_out, int host_buffers);
+
+/* Capture smppi_shield_update(device buffers) into a CUDA graph owned by the
+ * handle and replay it `n_updates` times, iter = iter0 .. iter0 + n_updates-1
+ * (the graph is re-instantiated when the arguments change). */
+smppi_status smppi_shield_loop(smppi_handle* h, float* x0, float* V, float* V_safe,
+                               uint32_t iter0, uint32_t instance, int n_repair, int n_updates);
+
+/*
+ * Per-kernel timing (CUDA events recorded on the handle's stream around each
+ * kernel launch).  smppi_timing(h, 1) starts recording, (h, 0) stops it.
+ * smppi_timing_read synchronises the stream, writes for each kernel kind k <
+ * n_kinds the summed duration in ms (ms_out[k], host) and the number of
+ * launches (count_out[k], host), and resets the record.  Kinds:
+ */
+#define SMPPI_KERNEL_ROLLOUT 0    /* rollouts + costs + block softmin + weighted noise */
+#define SMPPI_KERNEL_MERGE 1      /* cross-block float64 merge -> V+ */
+#define SMPPI_KERNEL_SEG0 2       /* nearest segment of x0 */
+#define SMPPI_KERNEL_REPAIR 3     /* safety shield iterations */
+#define SMPPI_KERNEL_APPLY 4      /* closed-loop step */
+#define SMPPI_KERNEL_COST_GRAD 5  /* cost + adjoint gradient */
+#define SMPPI_KERNEL_KINDS 6
+smppi_status smppi_timing(smppi_handle* h, int enable);
+smppi_status smppi_timing_read(smppi_handle* h, double* ms_out, int* count_out, int n_kinds);
+
+/*
+ * Test access to the device noise generator: for k < K, t < T writes
+ * eps_out[(k T + t) 2 + j] = the control noise of rollout k, step t exactly as
+ * the rollout kernels draw it (stream 0), and, if raw_out is not NULL,
+ * raw_out[(k ceil(T/2) + p) 4 + i] = Philox word i of counter (k, p, iter,
+ * instance << 8).  Both device arrays.
+ */
+smppi_status smppi_debug_noise(smppi_handle* h, uint32_t iter, uint32_t instance, int K, int T,
+                               float* eps_out, uint32_t* raw_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SMPPI_H */

@@ -67,6 +67,8 @@ def lib():
                                       C.c_uint32, C.c_uint32, _dp]
         L.orc_noise.argtypes = [_PP, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, _dp]
         L.orc_disturbance.argtypes = [_PP, C.c_uint32, C.c_uint32, _dp]
+        L.orc_noise_block.argtypes = [_PP, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int, C.c_int,
+                                      _dp]
         L.orc_seg_dist2.argtypes = [_PP, C.c_int, C.c_double, C.c_double]
         L.orc_seg_dist2.restype = C.c_double
         L.orc_track_nearest.argtypes = [_PP, C.c_double, C.c_double, _dp]
@@ -201,7 +203,12 @@ def noise(m: Model, it, instance, k, t):
 def noise_block(m: Model, it, instance, ks, T=None):
     """eps for rollouts ks and steps 0..T-1: (len(ks), T, 2)."""
     T = m.T if T is None else T
+    ks = list(ks)
     out = np.zeros((len(ks), T, 2))
+    if ks and ks == list(range(ks[0], ks[0] + len(ks))):
+        lib().orc_noise_block(m.ptr, int(it), int(instance), int(ks[0]), len(ks), int(T),
+                              out.ctypes.data_as(_dp))
+        return out
     for i, k in enumerate(ks):
         for t in range(T):
             out[i, t] = noise(m, it, instance, k, t)

@@ -153,6 +153,14 @@ void orc_noise(const OrcParams* p, uint32_t iter, uint32_t instance, uint32_t k,
     eps[1] = p->sigma[1] * z[1];
 }
 
+// eps for rollouts k0..k0+nk-1 and steps 0..T-1 into out[(i T + t) 2 + j].
+void orc_noise_block(const OrcParams* p, uint32_t iter, uint32_t instance, uint32_t k0, int nk,
+                     int T, double* out) {
+    for (int i = 0; i < nk; ++i)
+        for (int t = 0; t < T; ++t)
+            orc_noise(p, iter, instance, k0 + (uint32_t)i, (uint32_t)t, out + ((size_t)i * T + t) * 2);
+}
+
 // Additive disturbance w_n of the closed loop (Eq. 26): zero except on v_y
 // and r, drawn on stream 1 with counter (0, 0, n, 1 | instance << 8).
 void orc_disturbance(const OrcParams* p, uint32_t n, uint32_t instance, double w[6]) {
@@ -364,7 +372,9 @@ double orc_rollout(const OrcParams* p, const double x0[6], const double* V, uint
         for (int i = 0; i < 6; ++i) x[i] = xn[i];
         seg = orc_track_follow(p, seg, x[3], x[4], &d2);
         double h = orc_h(p, d2);
-        S += p->gamma * (V[2 * t] * uraw[0] * is0 + V[2 * t + 1] * uraw[1] * is1);
+        // control term of Alg. 2 (absent when gamma = 0, also for a degenerate Sigma)
+        if (p->gamma != 0.0)
+            S += p->gamma * (V[2 * t] * uraw[0] * is0 + V[2 * t + 1] * uraw[1] * is1);
         S += orc_q(p, x, d2) + orc_cbf_penalty(p, h_prev, h);
         h_prev = h;
         if (traj) for (int i = 0; i < 6; ++i) traj[6 * (t + 1) + i] = x[i];

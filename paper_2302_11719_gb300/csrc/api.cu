@@ -1,0 +1,491 @@
+// C ABI of the Shield-MPPI hot path (include/smppi.h): handle, workspace,
+// argument checks and the launch sequence of one control update.
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+using namespace smppi;
+
+struct smppi_handle {
+    smppi_params p;
+    DevParams dp;
+    cudaStream_t st = nullptr;
+    cudaStream_t cap = nullptr;      // private stream for graph capture
+    float4* seg = nullptr;
+    float* inv = nullptr;
+    float* S_ws = nullptr;           // [K] rollout costs
+    float* part_acc = nullptr;       // [nblk][2T]
+    float2* part_mh = nullptr;       // [nblk]
+    int nblk = 0;
+    unsigned* status = nullptr;
+    uint32_t* iter_dev = nullptr;
+    RepairWs rws{};
+    float* d_x0 = nullptr;           // staging for host-buffer updates
+    float* d_V = nullptr;
+    float* d_Vs = nullptr;
+    double* d_merit = nullptr;
+    int merit_cap = 0;
+    cudaGraphExec_t gexec = nullptr;
+    std::string graph_key;
+    std::string err;
+    // per-kernel timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    std::vector<std::array<int, 3>> records;   // kind, start event, end event
+};
+
+namespace {
+
+std::string g_create_err;
+
+smppi_status fail(smppi_handle* h, smppi_status s, const std::string& msg) {
+    if (h) h->err = msg;
+    else g_create_err = msg;
+    return s;
+}
+
+#define CU(h, call)                                                                        \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail((h), SMPPI_ERR_CUDA,                                               \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));               \
+    } while (0)
+
+bool finite_pos(float v) { return std::isfinite(v) && v > 0.0f; }
+
+smppi_status check_params(const smppi_params* p) {
+    auto bad = [](const char* m) { return fail(nullptr, SMPPI_ERR_ARG, m); };
+    if (!p) return bad("params is NULL");
+    if (!finite_pos(p->m) || !finite_pos(p->Iz)) return bad("m and Iz must be > 0");
+    if (!(p->lf >= 0) || !(p->lr >= 0) || !(p->lf + p->lr > 0)) return bad("lf, lr must be >= 0, lf + lr > 0");
+    if (!std::isfinite(p->B) || !std::isfinite(p->Ct) || !std::isfinite(p->g) || !std::isfinite(p->fx_gain))
+        return bad("tyre / gravity / throttle gain must be finite");
+    if (!finite_pos(p->dt)) return bad("dt must be > 0");
+    if (!(p->sigma[0] >= 0 && p->sigma[1] >= 0) || !std::isfinite(p->sigma[0]) || !std::isfinite(p->sigma[1]))
+        return bad("sigma must be finite and >= 0");
+    if (!finite_pos(p->lambda)) return bad("lambda must be > 0");
+    if (!std::isfinite(p->gamma)) return bad("gamma must be finite");
+    if (p->K < 1 || p->K > (1 << 22)) return bad("K must be in [1, 2^22]");
+    if (p->T < 1 || p->T > SMPPI_MAX_T) return bad("T must be in [1, SMPPI_MAX_T]");
+    if (p->N_r < 0 || p->N_r > p->T) return bad("N_r must be in [0, T]");
+    if (!(p->alpha >= 0 && p->alpha <= 1)) return bad("alpha must be in [0, 1]");
+    if (!(p->C_cbf >= 0) || !std::isfinite(p->C_cbf)) return bad("C_cbf must be finite and >= 0");
+    if (!std::isfinite(p->q_v) || !std::isfinite(p->v_target) || !std::isfinite(p->q_d) || !std::isfinite(p->C_obs))
+        return bad("cost weights must be finite");
+    for (int j = 0; j < 2; ++j)
+        if (!(p->u_min[j] <= p->u_max[j]) || !std::isfinite(p->u_min[j]) || !std::isfinite(p->u_max[j]))
+            return bad("u_min <= u_max required");
+    if (!finite_pos(p->half_width)) return bad("half_width must be > 0");
+    if (!(p->dist_sigma[0] >= 0 && p->dist_sigma[1] >= 0)) return bad("dist_sigma must be >= 0");
+    if (!finite_pos(p->ls_s0) || !(p->ls_c >= 0 && p->ls_c < 1)) return bad("ls_s0 > 0, 0 <= ls_c < 1");
+    if (p->ls_max_halvings < 1 || p->ls_max_halvings > 64) return bad("ls_max_halvings in [1, 64]");
+    if (p->checkpoint < 0 || p->checkpoint > SMPPI_MAX_T) return bad("checkpoint in [0, SMPPI_MAX_T]");
+    if (p->max_seq < 1 || p->max_seq > (1 << 20)) return bad("max_seq in [1, 2^20]");
+    if (p->n_track < 3 || p->n_track > SMPPI_MAX_TRACK) return bad("n_track in [3, SMPPI_MAX_TRACK]");
+    if (!p->track_xy) return bad("track_xy is NULL");
+    return SMPPI_OK;
+}
+
+DevParams derive(const smppi_params& p) {
+    DevParams d{};
+    const double m = p.m, lf = p.lf, lr = p.lr, g = p.g;
+    d.lf = p.lf; d.lr = p.lr; d.B = p.B; d.Ct = p.Ct;
+    d.Fzf = (float)(m * g * lr / (lf + lr));
+    d.Fzr = (float)(m * g * lf / (lf + lr));
+    d.fx_gain = p.fx_gain;
+    d.m_inv = (float)(1.0 / m);
+    d.Iz_inv = (float)(1.0 / (double)p.Iz);
+    d.dt = p.dt;
+    d.sig0 = p.sigma[0]; d.sig1 = p.sigma[1];
+    const double s0 = (double)p.sigma[0] * p.sigma[0], s1 = (double)p.sigma[1] * p.sigma[1];
+    d.gis0 = (float)(p.gamma == 0.0f ? 0.0 : p.gamma / s0);
+    d.gis1 = (float)(p.gamma == 0.0f ? 0.0 : p.gamma / s1);
+    d.lam_inv = (float)(1.0 / (double)p.lambda);
+    d.one_m_alpha = (float)(1.0 - (double)p.alpha);
+    d.C_cbf = p.C_cbf;
+    d.q_v = p.q_v; d.v_target = p.v_target;
+    const double w2 = (double)p.half_width * p.half_width;
+    d.qd_w2 = (float)(p.q_d / w2);
+    d.C_obs = p.C_obs;
+    d.w2 = (float)w2;
+    d.umin0 = p.u_min[0]; d.umin1 = p.u_min[1]; d.umax0 = p.u_max[0]; d.umax1 = p.u_max[1];
+    d.dsig0 = p.dist_sigma[0]; d.dsig1 = p.dist_sigma[1];
+    d.ls_s0 = p.ls_s0; d.ls_c = p.ls_c; d.ls_max = p.ls_max_halvings;
+    d.K = p.K; d.T = p.T; d.N_r = p.N_r; d.n_track = p.n_track;
+    d.key0 = (uint32_t)(p.seed & 0xFFFFFFFFull);
+    d.key1 = (uint32_t)(p.seed >> 32);
+    return d;
+}
+
+void free_all(smppi_handle* h) {
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    void* ptrs[] = {h->seg, h->inv, h->S_ws, h->part_acc, h->part_mh, h->status, h->iter_dev,
+                    h->rws.tape, h->rws.Vw, h->rws.G, h->rws.seg0, h->d_x0, h->d_V, h->d_Vs,
+                    h->d_merit};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    if (h->cap) cudaStreamDestroy(h->cap);
+}
+
+template <class P>
+cudaError_t alloc(P** ptr, size_t bytes) {
+    return cudaMalloc(reinterpret_cast<void**>(ptr), bytes < 16 ? 16 : bytes);
+}
+
+// Event pair around one launch when timing is on (never inside a graph capture).
+int tic(smppi_handle* h, cudaStream_t st) {
+    if (!h->timing || st == h->cap) return -1;
+    if (h->ev_used + 2 > h->ev_pool.size()) {
+        for (int i = 0; i < 64; ++i) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return -1;
+            h->ev_pool.push_back(e);
+        }
+    }
+    const int i0 = (int)h->ev_used;
+    h->ev_used += 2;
+    cudaEventRecord(h->ev_pool[i0], st);
+    return i0;
+}
+
+void toc(smppi_handle* h, cudaStream_t st, int kind, int i0) {
+    if (i0 < 0) return;
+    cudaEventRecord(h->ev_pool[i0 + 1], st);
+    h->records.push_back({kind, i0, i0 + 1});
+}
+
+smppi_status check_seq_call(smppi_handle* h, int n_seq) {
+    if (!h) return fail(nullptr, SMPPI_ERR_ARG, "handle is NULL");
+    if (n_seq < 1 || n_seq > h->p.max_seq)
+        return fail(h, SMPPI_ERR_ARG, "n_seq must be in [1, max_seq]");
+    return SMPPI_OK;
+}
+
+smppi_status enqueue_step(smppi_handle* h, cudaStream_t st, const float* x0, float* V,
+                          uint32_t iter, uint32_t instance, float* S_out, float* traj_out,
+                          uint32_t* iter_dev) {
+    const uint32_t ctr3 = (instance << 8) | 0u;
+    int ev = tic(h, st);
+    CU(h, launch_rollout(h->dp, traj_out ? MODE_DUMP : MODE_ROLL, x0, V, h->seg, h->inv, iter,
+                         ctr3, iter_dev, nullptr, S_out ? S_out : h->S_ws, traj_out, h->part_acc,
+                         h->part_mh, h->status, st));
+    toc(h, st, SMPPI_KERNEL_ROLLOUT, ev);
+    ev = tic(h, st);
+    CU(h, launch_merge(h->dp, h->part_acc, h->part_mh, h->nblk, V, h->status, st));
+    toc(h, st, SMPPI_KERNEL_MERGE, ev);
+    return SMPPI_OK;
+}
+
+smppi_status enqueue_repair(smppi_handle* h, cudaStream_t st, int n_seq, const float* x0,
+                            const float* V_in, float* V_out, int n_iters, int mode, float delta,
+                            double* merit_out, int* iters_out) {
+    int ev = tic(h, st);
+    CU(h, launch_seg0(h->dp, h->seg, h->inv, n_seq, x0, h->rws.seg0, st));
+    toc(h, st, SMPPI_KERNEL_SEG0, ev);
+    ev = tic(h, st);
+    CU(h, launch_repair(h->dp, h->seg, h->inv, h->rws, n_seq, x0, V_in, V_out, n_iters, mode,
+                        delta, merit_out, iters_out, h->status, st));
+    toc(h, st, SMPPI_KERNEL_REPAIR, ev);
+    return SMPPI_OK;
+}
+
+smppi_status enqueue_shield(smppi_handle* h, cudaStream_t st, float* x0, float* V, float* Vs,
+                            uint32_t iter, uint32_t instance, int n_repair, double* merit,
+                            uint32_t* iter_dev) {
+    smppi_status s = enqueue_step(h, st, x0, V, iter, instance, nullptr, nullptr, iter_dev);
+    if (s != SMPPI_OK) return s;
+    if (n_repair > 0) {
+        s = enqueue_repair(h, st, 1, x0, V, Vs, n_repair, 1, 0.0f, merit, nullptr);
+        if (s != SMPPI_OK) return s;
+    } else {
+        CU(h, cudaMemcpyAsync(Vs, V, sizeof(float) * 2 * h->p.T, cudaMemcpyDeviceToDevice, st));
+    }
+    const int ev = tic(h, st);
+    CU(h, launch_apply(h->dp, x0, V, Vs, iter, (instance << 8) | 1u, iter_dev, st));
+    toc(h, st, SMPPI_KERNEL_APPLY, ev);
+    return SMPPI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void smppi_default_params(smppi_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->m = 21.7f; p->Iz = 1.12f; p->lf = 0.34f; p->lr = 0.23f;
+    p->B = 4.0f; p->Ct = 1.5f; p->g = 9.81f; p->fx_gain = 60.0f;
+    p->dt = 0.02f;
+    p->sigma[0] = 0.15f; p->sigma[1] = 0.3f;
+    p->lambda = 1.0f; p->gamma = 1.0f;
+    p->K = 256; p->T = 50; p->N_r = 50;
+    p->alpha = 0.3f; p->C_cbf = 1000.0f;
+    p->q_v = 2.0f; p->v_target = 8.0f; p->q_d = 100.0f; p->C_obs = 0.0f;
+    p->u_min[0] = -0.5f; p->u_min[1] = -1.0f; p->u_max[0] = 0.5f; p->u_max[1] = 1.0f;
+    p->half_width = 2.0f;
+    p->dist_sigma[0] = 0.3f; p->dist_sigma[1] = 0.3f;
+    p->ls_s0 = 0.1f; p->ls_c = 1e-4f; p->ls_max_halvings = 20;
+    p->checkpoint = 0;
+    p->max_seq = 1;
+    p->n_track = 0;
+    p->track_xy = nullptr;
+    p->seed = 0;
+}
+
+smppi_status smppi_create(const smppi_params* p, void* cuda_stream, smppi_handle** out) {
+    if (!out) return fail(nullptr, SMPPI_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    smppi_status s = check_params(p);
+    if (s != SMPPI_OK) return s;
+    const size_t smem = rollout_smem_bytes(p->n_track, p->T);
+    if (smem > 200 * 1024)
+        return fail(nullptr, SMPPI_ERR_ARG, "n_track and T need more shared memory than a block has");
+    smppi_handle* h = new smppi_handle();
+    h->p = *p;
+    if (h->p.checkpoint == 0) h->p.checkpoint = (int)std::ceil(std::sqrt((double)p->T));
+    h->dp = derive(h->p);
+    h->st = static_cast<cudaStream_t>(cuda_stream);
+    h->nblk = (p->K + ROLL_BLK - 1) / ROLL_BLK;
+    const int T = p->T, ms = p->max_seq;
+    h->rws.max_seq = ms;
+    h->rws.T = T;
+    h->rws.ck = h->p.checkpoint;
+    h->rws.nslot = T + 2;
+    cudaError_t e = cudaSuccess;
+#define ALLOC(ptr, bytes)                                                   \
+    if (e == cudaSuccess) e = alloc(&(ptr), (bytes));
+    ALLOC(h->seg, sizeof(float4) * p->n_track);
+    ALLOC(h->inv, sizeof(float) * p->n_track);
+    ALLOC(h->S_ws, sizeof(float) * p->K);
+    ALLOC(h->part_acc, sizeof(float) * 2 * T * (size_t)h->nblk);
+    ALLOC(h->part_mh, sizeof(float2) * h->nblk);
+    ALLOC(h->status, sizeof(unsigned));
+    ALLOC(h->iter_dev, sizeof(uint32_t));
+    ALLOC(h->rws.tape, sizeof(float) * (size_t)h->rws.nslot * NFIELD * ms);
+    ALLOC(h->rws.Vw, sizeof(float2) * (size_t)T * ms);
+    ALLOC(h->rws.G, sizeof(float2) * (size_t)T * ms);
+    ALLOC(h->rws.seg0, sizeof(int) * ms);
+    ALLOC(h->d_x0, sizeof(float) * 6);
+    ALLOC(h->d_V, sizeof(float) * 2 * T);
+    ALLOC(h->d_Vs, sizeof(float) * 2 * T);
+#undef ALLOC
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->iter_dev, 0, sizeof(uint32_t), h->st);
+    if (e == cudaSuccess) e = launch_seg_table(p->track_xy, p->n_track, h->seg, h->inv, h->st);
+    if (e != cudaSuccess) {
+        const bool oom = (e == cudaErrorMemoryAllocation);
+        fail(nullptr, oom ? SMPPI_ERR_NOMEM : SMPPI_ERR_CUDA,
+             std::string("smppi_create: ") + cudaGetErrorString(e));
+        free_all(h);
+        delete h;
+        return oom ? SMPPI_ERR_NOMEM : SMPPI_ERR_CUDA;
+    }
+    *out = h;
+    return SMPPI_OK;
+}
+
+smppi_status smppi_destroy(smppi_handle* h) {
+    if (!h) return SMPPI_OK;
+    cudaStreamSynchronize(h->st);
+    free_all(h);
+    delete h;
+    return SMPPI_OK;
+}
+
+const char* smppi_last_error(const smppi_handle* h) {
+    return h ? h->err.c_str() : g_create_err.c_str();
+}
+
+smppi_status smppi_sync_status(smppi_handle* h, uint32_t* bits_out) {
+    if (!h) return fail(nullptr, SMPPI_ERR_ARG, "handle is NULL");
+    unsigned bits = 0;
+    CU(h, cudaStreamSynchronize(h->st));
+    CU(h, cudaMemcpy(&bits, h->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    CU(h, cudaMemset(h->status, 0, sizeof(unsigned)));
+    if (bits_out) *bits_out = bits;
+    if (bits & SMPPI_DEV_NUMERIC) return fail(h, SMPPI_ERR_NUMERIC, "NaN/Inf met on the device");
+    if (bits & SMPPI_DEV_TIMEOUT) return fail(h, SMPPI_ERR_TIMEOUT, "a device wait gave up");
+    if (bits & SMPPI_DEV_STALLED) return fail(h, SMPPI_ERR_STALLED, "repair line search stalled");
+    return SMPPI_OK;
+}
+
+smppi_status smppi_step(smppi_handle* h, const float* x0, float* V, uint32_t iter,
+                        uint32_t instance, float* S_out, float* traj_out) {
+    if (!h) return fail(nullptr, SMPPI_ERR_ARG, "handle is NULL");
+    if (!x0 || !V) return fail(h, SMPPI_ERR_ARG, "x0 and V must not be NULL");
+    if (instance >= (1u << 24)) return fail(h, SMPPI_ERR_ARG, "instance must be < 2^24");
+    return enqueue_step(h, h->st, x0, V, iter, instance, S_out, traj_out, nullptr);
+}
+
+smppi_status smppi_update(smppi_handle* h, const float* S, float* V, uint32_t iter,
+                          uint32_t instance) {
+    if (!h) return fail(nullptr, SMPPI_ERR_ARG, "handle is NULL");
+    if (!S || !V) return fail(h, SMPPI_ERR_ARG, "S and V must not be NULL");
+    if (instance >= (1u << 24)) return fail(h, SMPPI_ERR_ARG, "instance must be < 2^24");
+    CU(h, launch_rollout(h->dp, MODE_FROM_S, nullptr, V, h->seg, h->inv, iter, instance << 8,
+                         nullptr, S, nullptr, nullptr, h->part_acc, h->part_mh, h->status, h->st));
+    CU(h, launch_merge(h->dp, h->part_acc, h->part_mh, h->nblk, V, h->status, h->st));
+    return SMPPI_OK;
+}
+
+smppi_status smppi_cost_grad(smppi_handle* h, int n_seq, const float* x0, const float* V, int N,
+                             float w_run, float w_cbf, int checkpoint, double* J_out,
+                             float* grad_out) {
+    smppi_status s = check_seq_call(h, n_seq);
+    if (s != SMPPI_OK) return s;
+    if (!x0 || !V || !grad_out) return fail(h, SMPPI_ERR_ARG, "x0, V, grad_out must not be NULL");
+    if (N < 0 || N > h->p.T) return fail(h, SMPPI_ERR_ARG, "N must be in [0, T]");
+    if (!std::isfinite(w_run) || !std::isfinite(w_cbf)) return fail(h, SMPPI_ERR_ARG, "weights must be finite");
+    if (checkpoint > h->p.T) return fail(h, SMPPI_ERR_ARG, "checkpoint must be <= T");
+    const int ck = checkpoint == 0 ? h->p.checkpoint : (checkpoint < 0 ? 0 : checkpoint);
+    int ev = tic(h, h->st);
+    CU(h, launch_seg0(h->dp, h->seg, h->inv, n_seq, x0, h->rws.seg0, h->st));
+    toc(h, h->st, SMPPI_KERNEL_SEG0, ev);
+    ev = tic(h, h->st);
+    CU(h, launch_cost_grad(h->dp, h->seg, h->inv, h->rws, n_seq, x0, V, N, w_run, w_cbf, ck, J_out,
+                           grad_out, h->status, h->st));
+    toc(h, h->st, SMPPI_KERNEL_COST_GRAD, ev);
+    return SMPPI_OK;
+}
+
+smppi_status smppi_timing(smppi_handle* h, int enable) {
+    if (!h) return fail(nullptr, SMPPI_ERR_ARG, "handle is NULL");
+    h->timing = enable != 0;
+    return SMPPI_OK;
+}
+
+smppi_status smppi_timing_read(smppi_handle* h, double* ms_out, int* count_out, int n_kinds) {
+    if (!h) return fail(nullptr, SMPPI_ERR_ARG, "handle is NULL");
+    if (n_kinds < 0 || (n_kinds > 0 && (!ms_out || !count_out)))
+        return fail(h, SMPPI_ERR_ARG, "ms_out and count_out must hold n_kinds values");
+    CU(h, cudaStreamSynchronize(h->st));
+    for (int k = 0; k < n_kinds; ++k) {
+        ms_out[k] = 0.0;
+        count_out[k] = 0;
+    }
+    for (const auto& r : h->records) {
+        float ms = 0.0f;
+        CU(h, cudaEventElapsedTime(&ms, h->ev_pool[r[1]], h->ev_pool[r[2]]));
+        if (r[0] < n_kinds) {
+            ms_out[r[0]] += ms;
+            count_out[r[0]] += 1;
+        }
+    }
+    h->records.clear();
+    h->ev_used = 0;
+    return SMPPI_OK;
+}
+
+smppi_status smppi_repair(smppi_handle* h, int n_seq, const float* x0, const float* V_in,
+                          float* V_out, int n_iters, int mode, float delta, double* merit_out,
+                          int* iters_out) {
+    smppi_status s = check_seq_call(h, n_seq);
+    if (s != SMPPI_OK) return s;
+    if (!x0 || !V_in || !V_out) return fail(h, SMPPI_ERR_ARG, "x0, V_in, V_out must not be NULL");
+    if (n_iters < 0 || n_iters > 100000) return fail(h, SMPPI_ERR_ARG, "n_iters must be in [0, 1e5]");
+    if (mode != 0 && mode != 1) return fail(h, SMPPI_ERR_ARG, "mode must be 0 or 1");
+    if (mode == 0 && !(std::isfinite(delta) && delta >= 0)) return fail(h, SMPPI_ERR_ARG, "delta must be >= 0");
+    return enqueue_repair(h, h->st, n_seq, x0, V_in, V_out, n_iters, mode, delta, merit_out,
+                          iters_out);
+}
+
+smppi_status smppi_apply(smppi_handle* h, float* x0, float* V, const float* V_exec, uint32_t n,
+                         uint32_t instance) {
+    if (!h) return fail(nullptr, SMPPI_ERR_ARG, "handle is NULL");
+    if (!x0 || !V || !V_exec) return fail(h, SMPPI_ERR_ARG, "x0, V, V_exec must not be NULL");
+    if (instance >= (1u << 24)) return fail(h, SMPPI_ERR_ARG, "instance must be < 2^24");
+    CU(h, launch_apply(h->dp, x0, V, V_exec, n, (instance << 8) | 1u, nullptr, h->st));
+    return SMPPI_OK;
+}
+
+smppi_status smppi_shield_update(smppi_handle* h, float* x0, float* V, float* V_safe,
+                                 uint32_t iter, uint32_t instance, int n_repair,
+                                 double* merit_out, int host_buffers) {
+    if (!h) return fail(nullptr, SMPPI_ERR_ARG, "handle is NULL");
+    if (!x0 || !V || !V_safe) return fail(h, SMPPI_ERR_ARG, "x0, V, V_safe must not be NULL");
+    if (n_repair < 0 || n_repair > 100000) return fail(h, SMPPI_ERR_ARG, "n_repair must be in [0, 1e5]");
+    if (instance >= (1u << 24)) return fail(h, SMPPI_ERR_ARG, "instance must be < 2^24");
+    if (!host_buffers)
+        return enqueue_shield(h, h->st, x0, V, V_safe, iter, instance, n_repair, merit_out, nullptr);
+    const size_t vb = sizeof(float) * 2 * h->p.T;
+    double* dm = nullptr;
+    if (merit_out && n_repair > 0) {
+        if (h->merit_cap < n_repair + 1) {
+            if (h->d_merit) cudaFree(h->d_merit);
+            h->d_merit = nullptr;
+            h->merit_cap = 0;
+            CU(h, cudaMalloc(&h->d_merit, sizeof(double) * (n_repair + 1)));
+            h->merit_cap = n_repair + 1;
+        }
+        dm = h->d_merit;
+    }
+    CU(h, cudaMemcpyAsync(h->d_x0, x0, sizeof(float) * 6, cudaMemcpyHostToDevice, h->st));
+    CU(h, cudaMemcpyAsync(h->d_V, V, vb, cudaMemcpyHostToDevice, h->st));
+    smppi_status s = enqueue_shield(h, h->st, h->d_x0, h->d_V, h->d_Vs, iter, instance, n_repair,
+                                    dm, nullptr);
+    if (s != SMPPI_OK) return s;
+    CU(h, cudaMemcpyAsync(x0, h->d_x0, sizeof(float) * 6, cudaMemcpyDeviceToHost, h->st));
+    CU(h, cudaMemcpyAsync(V, h->d_V, vb, cudaMemcpyDeviceToHost, h->st));
+    CU(h, cudaMemcpyAsync(V_safe, h->d_Vs, vb, cudaMemcpyDeviceToHost, h->st));
+    if (dm)
+        CU(h, cudaMemcpyAsync(merit_out, dm, sizeof(double) * (n_repair + 1),
+                              cudaMemcpyDeviceToHost, h->st));
+    CU(h, cudaStreamSynchronize(h->st));
+    return SMPPI_OK;
+}
+
+smppi_status smppi_shield_loop(smppi_handle* h, float* x0, float* V, float* V_safe,
+                               uint32_t iter0, uint32_t instance, int n_repair, int n_updates) {
+    if (!h) return fail(nullptr, SMPPI_ERR_ARG, "handle is NULL");
+    if (!x0 || !V || !V_safe) return fail(h, SMPPI_ERR_ARG, "x0, V, V_safe must not be NULL");
+    if (n_repair < 0 || n_repair > 100000 || n_updates < 0)
+        return fail(h, SMPPI_ERR_ARG, "n_repair in [0, 1e5], n_updates >= 0");
+    if (instance >= (1u << 24)) return fail(h, SMPPI_ERR_ARG, "instance must be < 2^24");
+    char key[256];
+    std::snprintf(key, sizeof(key), "%p %p %p %u %u %d", (void*)x0, (void*)V, (void*)V_safe,
+                  iter0, instance, n_repair);
+    if (!h->gexec || h->graph_key != key) {
+        if (h->gexec) {
+            cudaGraphExecDestroy(h->gexec);
+            h->gexec = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        CU(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+        smppi_status s = enqueue_shield(h, h->cap, x0, V, V_safe, iter0, instance, n_repair,
+                                        nullptr, h->iter_dev);
+        cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+        if (s != SMPPI_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        CU(h, e);
+        e = cudaGraphInstantiate(&h->gexec, g, 0);
+        cudaGraphDestroy(g);
+        CU(h, e);
+        h->graph_key = key;
+    }
+    CU(h, cudaMemsetAsync(h->iter_dev, 0, sizeof(uint32_t), h->st));
+    for (int i = 0; i < n_updates; ++i) CU(h, cudaGraphLaunch(h->gexec, h->st));
+    return SMPPI_OK;
+}
+
+smppi_status smppi_debug_noise(smppi_handle* h, uint32_t iter, uint32_t instance, int K, int T,
+                               float* eps_out, uint32_t* raw_out) {
+    if (!h) return fail(nullptr, SMPPI_ERR_ARG, "handle is NULL");
+    if (K < 1 || T < 1 || T > SMPPI_MAX_T) return fail(h, SMPPI_ERR_ARG, "K >= 1, 1 <= T <= SMPPI_MAX_T");
+    if (!eps_out && !raw_out) return fail(h, SMPPI_ERR_ARG, "no output given");
+    if (instance >= (1u << 24)) return fail(h, SMPPI_ERR_ARG, "instance must be < 2^24");
+    CU(h, launch_debug_noise(h->dp, iter, instance << 8, K, T, eps_out, raw_out, h->st));
+    return SMPPI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,74 @@
+"""The C-ABI library builds, loads and exports every entry point include/smppi.h
+declares; host-side argument checks reject bad input before any device work
+(these run without a GPU)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "smppi.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2302_11719_gb300 import build as B
+    path = B.build()
+    return C.CDLL(path)
+
+
+def declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(smppi_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_entry_points():
+    names = declared()
+    for must in ("smppi_create", "smppi_destroy", "smppi_step", "smppi_update", "smppi_repair",
+                 "smppi_cost_grad", "smppi_apply", "smppi_shield_update", "smppi_last_error",
+                 "smppi_sync_status"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_header():
+    from paper_2302_11719_gb300 import smppi
+    assert set(declared()) <= set(smppi._SIGS), set(declared()) - set(smppi._SIGS)
+
+
+def test_default_params_and_host_checks(lib):
+    from paper_2302_11719_gb300 import smppi
+    smppi.load_library(os.path.join(ROOT, "paper_2302_11719_gb300", "libsmppi.so"))
+    p = smppi.default_params()
+    assert p.K == 256 and p.T == 50 and p.N_r == 50
+    assert abs(p.m - 21.7) < 1e-5 and abs(p.lam - 1.0) < 1e-7 and abs(p.alpha - 0.3) < 1e-7
+    assert abs(p.sigma[0] - 0.15) < 1e-7 and abs(p.sigma[1] - 0.3) < 1e-7
+    L = smppi.load_library()
+    h = C.c_void_p()
+    # no track -> argument error, found on the host before any CUDA call
+    assert L.smppi_create(C.byref(p), None, C.byref(h)) == smppi.ERR_ARG
+    assert h.value is None
+    assert b"track" in L.smppi_last_error(None)
+    p.track_xy = 1234          # never dereferenced: the K check fails first
+    p.n_track = 1024
+    for field, bad in (("K", 0), ("T", 0), ("T", 513), ("N_r", 51), ("n_track", 2),
+                       ("n_track", 4096), ("max_seq", 0)):
+        q = smppi.default_params()
+        C.memmove(C.byref(q), C.byref(p), C.sizeof(p))
+        setattr(q, field, bad)
+        assert L.smppi_create(C.byref(q), None, C.byref(h)) == smppi.ERR_ARG, field
+    q = smppi.default_params()
+    C.memmove(C.byref(q), C.byref(p), C.sizeof(p))
+    q.lam = 0.0
+    assert L.smppi_create(C.byref(q), None, C.byref(h)) == smppi.ERR_ARG
+    assert b"lambda" in L.smppi_last_error(None)
+    # calls on a NULL handle are rejected
+    assert L.smppi_step(None, None, None, 0, 0, None, None) == smppi.ERR_ARG
+    assert L.smppi_repair(None, 1, None, None, None, 1, 1, C.c_float(0), None, None) == smppi.ERR_ARG
+    assert L.smppi_destroy(None) == smppi.OK
