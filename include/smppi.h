@@ -215,8 +215,8 @@ smppi_status smppi_shield_loop(smppi_handle* h, float* x0, float* V, float* V_sa
  * n_kinds the summed duration in ms (ms_out[k], host) and the number of
  * launches (count_out[k], host), and resets the record.  Kinds:
  */
-#define SMPPI_KERNEL_ROLLOUT 0    /* rollouts + costs + block softmin + weighted noise */
-#define SMPPI_KERNEL_MERGE 1      /* cross-block float64 merge -> V+ */
+#define SMPPI_KERNEL_ROLLOUT 0    /* rollouts and trajectory costs */
+#define SMPPI_KERNEL_UPDATE 1     /* softmin weights, weighted noise sum, float64 merge -> V+ */
 #define SMPPI_KERNEL_SEG0 2       /* nearest segment of x0 */
 #define SMPPI_KERNEL_REPAIR 3     /* safety shield iterations */
 #define SMPPI_KERNEL_APPLY 4      /* closed-loop step */

@@ -1,5 +1,6 @@
 // C ABI of the Shield-MPPI hot path (include/smppi.h): handle, workspace,
 // argument checks and the launch sequence of one control update.
+#include <algorithm>
 #include <array>
 #include <cmath>
 #include <cstdio>
@@ -19,8 +20,10 @@ struct smppi_handle {
     float4* seg = nullptr;
     float* inv = nullptr;
     float* S_ws = nullptr;           // [K] rollout costs
-    float* part_acc = nullptr;       // [nblk][2T]
-    float2* part_mh = nullptr;       // [nblk]
+    float* blk_min = nullptr;        // [nblk] block minima of S
+    float* part_acc = nullptr;       // [UPD_BLK][2T] update-kernel partials
+    double* part_eta = nullptr;      // [UPD_BLK]
+    unsigned* ticket = nullptr;      // last-block counter of the update launch
     int nblk = 0;
     unsigned* status = nullptr;
     uint32_t* iter_dev = nullptr;
@@ -108,6 +111,9 @@ DevParams derive(const smppi_params& p) {
     d.gis0 = (float)(p.gamma == 0.0f ? 0.0 : p.gamma / s0);
     d.gis1 = (float)(p.gamma == 0.0f ? 0.0 : p.gamma / s1);
     d.lam_inv = (float)(1.0 / (double)p.lambda);
+    // |eps| <= sigma_max sqrt(-2 ln 2^-24) (smallest uniform of the noise generator)
+    const double e_max = std::max(p.sigma[0], p.sigma[1]) * std::sqrt(2.0 * 24.0 * std::log(2.0));
+    d.w_skip = e_max > 0.0 ? (float)(1e-8 / ((double)p.K * e_max)) : 3.0e38f;
     d.one_m_alpha = (float)(1.0 - (double)p.alpha);
     d.C_cbf = p.C_cbf;
     d.q_v = p.q_v; d.v_target = p.v_target;
@@ -121,13 +127,21 @@ DevParams derive(const smppi_params& p) {
     d.K = p.K; d.T = p.T; d.N_r = p.N_r; d.n_track = p.n_track;
     d.key0 = (uint32_t)(p.seed & 0xFFFFFFFFull);
     d.key1 = (uint32_t)(p.seed >> 32);
+    for (int i = 0; i < 10; ++i) {
+        d.rk0[i] = d.key0 + (uint32_t)i * 0x9E3779B9u;
+        d.rk1[i] = d.key1 + (uint32_t)i * 0xBB67AE85u;
+    }
+    d.tyre15 = (p.Ct == 1.5f) ? 1 : 0;
+    d.steer_small = (std::fabs(p.u_min[0]) <= 1.0f && std::fabs(p.u_max[0]) <= 1.0f) ? 1 : 0;
     return d;
 }
 
 void free_all(smppi_handle* h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
-    void* ptrs[] = {h->seg, h->inv, h->S_ws, h->part_acc, h->part_mh, h->status, h->iter_dev,
+    void* ptrs[] = {h->seg, h->inv, h->S_ws, h->blk_min, h->part_acc, h->part_eta, h->ticket,
+                    h->status,
+                    h->iter_dev,
                     h->rws.tape, h->rws.Vw, h->rws.G, h->rws.seg0, h->d_x0, h->d_V, h->d_Vs,
                     h->d_merit};
     for (void* q : ptrs)
@@ -173,26 +187,33 @@ smppi_status enqueue_step(smppi_handle* h, cudaStream_t st, const float* x0, flo
                           uint32_t iter, uint32_t instance, float* S_out, float* traj_out,
                           uint32_t* iter_dev) {
     const uint32_t ctr3 = (instance << 8) | 0u;
+    float* S = S_out ? S_out : h->S_ws;
     int ev = tic(h, st);
-    CU(h, launch_rollout(h->dp, traj_out ? MODE_DUMP : MODE_ROLL, x0, V, h->seg, h->inv, iter,
-                         ctr3, iter_dev, nullptr, S_out ? S_out : h->S_ws, traj_out, h->part_acc,
-                         h->part_mh, h->status, st));
+    CU(h, launch_rollout(h->dp, traj_out != nullptr, x0, V, h->seg, h->inv, iter, ctr3, iter_dev,
+                         S, traj_out, h->blk_min, h->rws.seg0, h->status, st));
     toc(h, st, SMPPI_KERNEL_ROLLOUT, ev);
     ev = tic(h, st);
-    CU(h, launch_merge(h->dp, h->part_acc, h->part_mh, h->nblk, V, h->status, st));
-    toc(h, st, SMPPI_KERNEL_MERGE, ev);
+    CU(h, launch_update(h->dp, S, h->blk_min, h->nblk, V, iter, ctr3, iter_dev, h->part_acc,
+                        h->part_eta, h->ticket, h->status, st));
+    toc(h, st, SMPPI_KERNEL_UPDATE, ev);
     return SMPPI_OK;
 }
 
+// seg0_known: the nearest segment of x0 is already in the workspace (written
+// by the rollout launch of the same update).  ap: optional fused closed loop.
 smppi_status enqueue_repair(smppi_handle* h, cudaStream_t st, int n_seq, const float* x0,
                             const float* V_in, float* V_out, int n_iters, int mode, float delta,
-                            double* merit_out, int* iters_out) {
-    int ev = tic(h, st);
-    CU(h, launch_seg0(h->dp, h->seg, h->inv, n_seq, x0, h->rws.seg0, st));
-    toc(h, st, SMPPI_KERNEL_SEG0, ev);
+                            double* merit_out, int* iters_out, bool seg0_known,
+                            const ApplyArgs& ap) {
+    int ev;
+    if (!seg0_known) {
+        ev = tic(h, st);
+        CU(h, launch_seg0(h->dp, h->seg, h->inv, n_seq, x0, h->rws.seg0, st));
+        toc(h, st, SMPPI_KERNEL_SEG0, ev);
+    }
     ev = tic(h, st);
     CU(h, launch_repair(h->dp, h->seg, h->inv, h->rws, n_seq, x0, V_in, V_out, n_iters, mode,
-                        delta, merit_out, iters_out, h->status, st));
+                        delta, merit_out, iters_out, ap, h->status, st));
     toc(h, st, SMPPI_KERNEL_REPAIR, ev);
     return SMPPI_OK;
 }
@@ -202,14 +223,12 @@ smppi_status enqueue_shield(smppi_handle* h, cudaStream_t st, float* x0, float* 
                             uint32_t* iter_dev) {
     smppi_status s = enqueue_step(h, st, x0, V, iter, instance, nullptr, nullptr, iter_dev);
     if (s != SMPPI_OK) return s;
-    if (n_repair > 0) {
-        s = enqueue_repair(h, st, 1, x0, V, Vs, n_repair, 1, 0.0f, merit, nullptr);
-        if (s != SMPPI_OK) return s;
-    } else {
-        CU(h, cudaMemcpyAsync(Vs, V, sizeof(float) * 2 * h->p.T, cudaMemcpyDeviceToDevice, st));
-    }
+    const ApplyArgs ap{x0, V, iter, (instance << 8) | 1u, iter_dev};
+    if (n_repair > 0)
+        return enqueue_repair(h, st, 1, x0, V, Vs, n_repair, 1, 0.0f, merit, nullptr, true, ap);
+    CU(h, cudaMemcpyAsync(Vs, V, sizeof(float) * 2 * h->p.T, cudaMemcpyDeviceToDevice, st));
     const int ev = tic(h, st);
-    CU(h, launch_apply(h->dp, x0, V, Vs, iter, (instance << 8) | 1u, iter_dev, st));
+    CU(h, launch_apply(h->dp, ap, Vs, st));
     toc(h, st, SMPPI_KERNEL_APPLY, ev);
     return SMPPI_OK;
 }
@@ -263,10 +282,12 @@ smppi_status smppi_create(const smppi_params* p, void* cuda_stream, smppi_handle
 #define ALLOC(ptr, bytes)                                                   \
     if (e == cudaSuccess) e = alloc(&(ptr), (bytes));
     ALLOC(h->seg, sizeof(float4) * p->n_track);
-    ALLOC(h->inv, sizeof(float) * p->n_track);
+    ALLOC(h->inv, sizeof(float) * ((p->n_track + 3) & ~3));   // padded for 16-byte bulk copies
     ALLOC(h->S_ws, sizeof(float) * p->K);
-    ALLOC(h->part_acc, sizeof(float) * 2 * T * (size_t)h->nblk);
-    ALLOC(h->part_mh, sizeof(float2) * h->nblk);
+    ALLOC(h->blk_min, sizeof(float) * h->nblk);
+    ALLOC(h->part_acc, sizeof(float) * 2 * T * (size_t)UPD_BLK);
+    ALLOC(h->part_eta, sizeof(double) * UPD_BLK);
+    ALLOC(h->ticket, sizeof(unsigned));
     ALLOC(h->status, sizeof(unsigned));
     ALLOC(h->iter_dev, sizeof(uint32_t));
     ALLOC(h->rws.tape, sizeof(float) * (size_t)h->rws.nslot * NFIELD * ms);
@@ -280,6 +301,7 @@ smppi_status smppi_create(const smppi_params* p, void* cuda_stream, smppi_handle
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->iter_dev, 0, sizeof(uint32_t), h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->ticket, 0, sizeof(unsigned), h->st);
     if (e == cudaSuccess) e = launch_seg_table(p->track_xy, p->n_track, h->seg, h->inv, h->st);
     if (e != cudaSuccess) {
         const bool oom = (e == cudaErrorMemoryAllocation);
@@ -331,9 +353,10 @@ smppi_status smppi_update(smppi_handle* h, const float* S, float* V, uint32_t it
     if (!h) return fail(nullptr, SMPPI_ERR_ARG, "handle is NULL");
     if (!S || !V) return fail(h, SMPPI_ERR_ARG, "S and V must not be NULL");
     if (instance >= (1u << 24)) return fail(h, SMPPI_ERR_ARG, "instance must be < 2^24");
-    CU(h, launch_rollout(h->dp, MODE_FROM_S, nullptr, V, h->seg, h->inv, iter, instance << 8,
-                         nullptr, S, nullptr, nullptr, h->part_acc, h->part_mh, h->status, h->st));
-    CU(h, launch_merge(h->dp, h->part_acc, h->part_mh, h->nblk, V, h->status, h->st));
+    const int ev = tic(h, h->st);
+    CU(h, launch_update(h->dp, S, nullptr, 0, V, iter, instance << 8, nullptr, h->part_acc,
+                        h->part_eta, h->ticket, h->status, h->st));
+    toc(h, h->st, SMPPI_KERNEL_UPDATE, ev);
     return SMPPI_OK;
 }
 
@@ -394,8 +417,9 @@ smppi_status smppi_repair(smppi_handle* h, int n_seq, const float* x0, const flo
     if (n_iters < 0 || n_iters > 100000) return fail(h, SMPPI_ERR_ARG, "n_iters must be in [0, 1e5]");
     if (mode != 0 && mode != 1) return fail(h, SMPPI_ERR_ARG, "mode must be 0 or 1");
     if (mode == 0 && !(std::isfinite(delta) && delta >= 0)) return fail(h, SMPPI_ERR_ARG, "delta must be >= 0");
+    const ApplyArgs none{nullptr, nullptr, 0u, 0u, nullptr};
     return enqueue_repair(h, h->st, n_seq, x0, V_in, V_out, n_iters, mode, delta, merit_out,
-                          iters_out);
+                          iters_out, false, none);
 }
 
 smppi_status smppi_apply(smppi_handle* h, float* x0, float* V, const float* V_exec, uint32_t n,
@@ -403,7 +427,10 @@ smppi_status smppi_apply(smppi_handle* h, float* x0, float* V, const float* V_ex
     if (!h) return fail(nullptr, SMPPI_ERR_ARG, "handle is NULL");
     if (!x0 || !V || !V_exec) return fail(h, SMPPI_ERR_ARG, "x0, V, V_exec must not be NULL");
     if (instance >= (1u << 24)) return fail(h, SMPPI_ERR_ARG, "instance must be < 2^24");
-    CU(h, launch_apply(h->dp, x0, V, V_exec, n, (instance << 8) | 1u, nullptr, h->st));
+    const ApplyArgs ap{x0, V, n, (instance << 8) | 1u, nullptr};
+    const int ev = tic(h, h->st);
+    CU(h, launch_apply(h->dp, ap, V_exec, h->st));
+    toc(h, h->st, SMPPI_KERNEL_APPLY, ev);
     return SMPPI_OK;
 }
 

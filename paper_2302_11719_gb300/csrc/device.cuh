@@ -6,6 +6,20 @@
 // running cost q (Eq. 24-25); DCBF penalty C max{(1-alpha) h_{k-1} - h_k, 0}
 // (Eq. 17, alpha = the paper's beta of Eq. 15).  No tensor cores: nothing here
 // is a dense contraction; the hot loop is FP32 FMA/ALU/SFU work in registers.
+//
+// Elementary functions on the hot path are written here so that each step
+// costs few instructions while staying within a few ulp:
+//   atan2   -- octant reduction + a degree-8 polynomial in a^2 for atan(a)/a on
+//              [0, 1], coefficients from a Remez (minimax, absolute error)
+//              fit done for this file (max error 1e-7, <= 3 ulp in float32);
+//   tyre    -- for C = 1.5, sin(1.5 atan z) by the half-angle identities
+//              cos t = 1/sqrt(1+z^2), sin(3t/2) = sin t cos(t/2) + cos t sin(t/2)
+//              (no atan, no sin); other C use the library atanf / sinf;
+//   heading -- (cos psi, sin psi) is carried with the state and rotated by the
+//              Euler increment dt r each step (exactly cos / sin of the Euler
+//              psi up to rounding), so no sin / cos of an unbounded angle;
+//   small sin / cos -- Taylor series to x^13 / x^14 for |x| <= 1 (remainder
+//              < 1e-12), the library otherwise.
 #pragma once
 
 #include <cstdint>
@@ -21,6 +35,7 @@ struct DevParams {
     float sig0, sig1;            // noise std
     float gis0, gis1;            // gamma / sigma^2 (control term of Alg. 2)
     float lam_inv;               // 1 / lambda
+    float w_skip;                // weights <= w_skip are left out of the noise sum (<= 1e-8 on V+)
     float one_m_alpha, C_cbf;    // (1 - alpha), C
     float q_v, v_target, qd_w2, C_obs, w2;
     float umin0, umin1, umax0, umax1;
@@ -28,26 +43,36 @@ struct DevParams {
     float ls_s0, ls_c;
     int ls_max;
     int K, T, N_r, n_track;
+    int tyre15;                  // 1 when Ct == 1.5 (half-angle tyre path)
+    int steer_small;             // 1 when |steer| <= 1 on the whole control box
     uint32_t key0, key1;
+    uint32_t rk0[10], rk1[10];   // Philox round keys key + i * Weyl
 };
 
 struct State {
     float vx, vy, r, X, Y, psi;
+    float cp, sp;                // cos psi, sin psi
 };
+
+__device__ __forceinline__ State make_state(const float* x) {
+    State s;
+    s.vx = x[0]; s.vy = x[1]; s.r = x[2]; s.X = x[3]; s.Y = x[4]; s.psi = x[5];
+    sincosf(s.psi, &s.sp, &s.cp);
+    return s;
+}
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of
 //   (c0..c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0))
-// with the key bumped by the Weyl constants between rounds.
+// with the key bumped by the Weyl constants between rounds (round keys are
+// precomputed on the host: rk[i] = key + i W).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+__device__ __forceinline__ uint4 philox10(uint4 c, const DevParams& P) {
 #pragma unroll
     for (int i = 0; i < 10; ++i) {
         const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
         const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
+        c = make_uint4(hi1 ^ c.y ^ P.rk0[i], lo1, hi0 ^ c.w ^ P.rk1[i], lo0);
     }
     return c;
 }
@@ -69,50 +94,120 @@ __device__ __forceinline__ float clampf(float v, float lo, float hi) {
     return fminf(fmaxf(v, lo), hi);
 }
 
+// atan2 by octant reduction and a minimax polynomial for atan(a)/a, a in [0, 1].
+__device__ __forceinline__ float atan2_poly(float y, float x) {
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    const float a = mx > 0.0f ? __fdividef(mn, mx) : 0.0f;
+    const float s = a * a;
+    float p = 2.456725575e-03f;
+    p = fmaf(p, s, -1.440136135e-02f);
+    p = fmaf(p, s, 3.978123143e-02f);
+    p = fmaf(p, s, -7.234857976e-02f);
+    p = fmaf(p, s, 1.049894616e-01f);
+    p = fmaf(p, s, -1.416122913e-01f);
+    p = fmaf(p, s, 1.998590678e-01f);
+    p = fmaf(p, s, -3.333259821e-01f);
+    p = fmaf(p, s, 9.999998808e-01f);
+    float r = a * p;
+    if (ay > ax) r = 1.57079632679f - r;
+    if (x < 0.0f) r = 3.14159265359f - r;
+    return copysignf(r, y);
+}
+
+// sin and cos of |x| <= 1 by Taylor series (remainder < 1e-12).
+__device__ __forceinline__ void sincos_small(float x, float* s, float* c) {
+    const float x2 = x * x;
+    float ps = -1.6059043836821615e-10f;            // -1/13!
+    ps = fmaf(ps, x2, 2.5052108385441720e-08f);      //  1/11!
+    ps = fmaf(ps, x2, -2.7557319223985893e-06f);     // -1/9!
+    ps = fmaf(ps, x2, 1.9841269841269841e-04f);      //  1/7!
+    ps = fmaf(ps, x2, -8.3333333333333333e-03f);     // -1/5!
+    ps = fmaf(ps, x2, 1.6666666666666667e-01f);      //  1/3!
+    *s = fmaf(-ps * x2, x, x);
+    float pc = 1.1470745597729725e-11f;              //  1/14!
+    pc = fmaf(pc, x2, -2.0876756987868099e-09f);     // -1/12!
+    pc = fmaf(pc, x2, 2.7557319223985891e-07f);      //  1/10!
+    pc = fmaf(pc, x2, -2.4801587301587302e-05f);     // -1/8!
+    pc = fmaf(pc, x2, 1.3888888888888889e-03f);      //  1/6!
+    pc = fmaf(pc, x2, -4.1666666666666667e-02f);     // -1/4!
+    pc = fmaf(pc, x2, 0.5f);                         //  1/2!
+    *c = fmaf(-pc, x2, 1.0f);
+}
+
+__device__ __forceinline__ void sincos_any(float x, float* s, float* c) {
+    if (fabsf(x) <= 1.0f) sincos_small(x, s, c);
+    else sincosf(x, s, c);
+}
+
+// Lateral tyre force shape sin(Ct atan(z)) and, if dz != nullptr, its
+// derivative Ct cos(Ct atan z) / (1 + z^2).
+__device__ __forceinline__ float tyre_shape(const DevParams& P, float z, float* dz) {
+    if (P.tyre15) {
+        const float c = rsqrtf(fmaf(z, z, 1.0f));    // cos t, t = atan z
+        const float s = z * c;                       // sin t
+        const float u = fmaf(0.5f, c, 0.5f);         // cos^2(t/2)
+        const float ru = rsqrtf(u);                  // 1 / cos(t/2)
+        if (dz) *dz = 1.5f * ru * fmaf(c, u, -0.5f * s * s) * c * c;   // 1.5 cos(1.5 t) cos^2 t
+        return s * ru * fmaf(0.5f, c, u);            // sin t cos(t/2) + cos t sin(t/2)
+    }
+    const float t = atanf(z);
+    float sn, cs;
+    sincosf(P.Ct * t, &sn, &cs);
+    if (dz) *dz = P.Ct * cs / fmaf(z, z, 1.0f);
+    return sn;
+}
+
 // ---------------------------------------------------------------------------
 // One explicit Euler step of the single-track model (Eq. 1).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void model_step(const DevParams& P, State& x, float d, float a) {
-    const float bf = atan2f(fmaf(P.lf, x.r, x.vy), x.vx);
-    const float br = atan2f(fmaf(-P.lr, x.r, x.vy), x.vx);
-    const float Fyf = P.Fzf * sinf(P.Ct * atanf(P.B * (d - bf)));
-    const float Fyr = P.Fzr * sinf(P.Ct * atanf(P.B * (-br)));
-    float sd, cd, sp, cp;
-    sincosf(d, &sd, &cd);
-    sincosf(x.psi, &sp, &cp);
+    const float bf = atan2_poly(fmaf(P.lf, x.r, x.vy), x.vx);
+    const float br = atan2_poly(fmaf(-P.lr, x.r, x.vy), x.vx);
+    const float Fyf = P.Fzf * tyre_shape(P, P.B * (d - bf), nullptr);
+    const float Fyr = P.Fzr * tyre_shape(P, -P.B * br, nullptr);
+    float sd, cd;
+    if (P.steer_small) sincos_small(d, &sd, &cd);
+    else sincosf(d, &sd, &cd);
     const float Fx = P.fx_gain * a;
     const float dvx = fmaf(Fx - Fyf * sd, P.m_inv, x.vy * x.r);
     const float dvy = fmaf(Fyr + Fyf * cd, P.m_inv, -x.vx * x.r);
     const float dr = (P.lf * Fyf * cd - P.lr * Fyr) * P.Iz_inv;
-    const float dX = x.vx * cp - x.vy * sp;
-    const float dY = x.vx * sp + x.vy * cp;
-    const float dpsi = x.r;
+    const float dX = x.vx * x.cp - x.vy * x.sp;
+    const float dY = x.vx * x.sp + x.vy * x.cp;
+    // heading: psi += dt r, (cos, sin) rotated by the same increment
+    const float dpsi = P.dt * x.r;
+    float sa, ca;
+    sincos_any(dpsi, &sa, &ca);
+    const float cp = x.cp * ca - x.sp * sa;
+    const float sp = x.sp * ca + x.cp * sa;
     x.vx = fmaf(P.dt, dvx, x.vx);
     x.vy = fmaf(P.dt, dvy, x.vy);
     x.r = fmaf(P.dt, dr, x.r);
     x.X = fmaf(P.dt, dX, x.X);
     x.Y = fmaf(P.dt, dY, x.Y);
-    x.psi = fmaf(P.dt, dpsi, x.psi);
+    x.psi += dpsi;
+    x.cp = cp;
+    x.sp = sp;
 }
 
 // Reverse-mode adjoint of model_step at (x, d, a): given lb = dJ/dx_{t+1},
 // overwrite lb with dJ/dx_t through the dynamics and return dJ/du_t in
-// (*gd, *ga).  Hand-derived from the forward formulas above.
+// (*gd, *ga).  Hand-derived from the forward formulas above (cos / sin psi
+// are functions of psi; the adjoint flows through psi only).
 __device__ __forceinline__ void model_step_adjoint(const DevParams& P, const State& x, float d,
                                                    float a, State& lb, float* gd, float* ga) {
     (void)a;
     const float yf = fmaf(P.lf, x.r, x.vy), yr = fmaf(-P.lr, x.r, x.vy);
-    const float bf = atan2f(yf, x.vx), br = atan2f(yr, x.vx);
+    const float bf = atan2_poly(yf, x.vx), br = atan2_poly(yr, x.vx);
     const float af = d - bf, ar = -br;
-    const float phf = atanf(P.B * af), phr = atanf(P.B * ar);
-    float sphf, cphf, sphr, cphr;
-    sincosf(P.Ct * phf, &sphf, &cphf);
-    sincosf(P.Ct * phr, &sphr, &cphr);
-    const float Fyf = P.Fzf * sphf;
-    (void)sphr;
-    float sd, cd, sp, cp;
-    sincosf(d, &sd, &cd);
-    sincosf(x.psi, &sp, &cp);
+    float dphf, dphr;
+    const float Fyf = P.Fzf * tyre_shape(P, P.B * af, &dphf);
+    tyre_shape(P, P.B * ar, &dphr);
+    float sd, cd;
+    if (P.steer_small) sincos_small(d, &sd, &cd);
+    else sincosf(d, &sd, &cd);
+    const float cp = x.cp, sp = x.sp;
     const float dX = x.vx * cp - x.vy * sp;
     const float dY = x.vx * sp + x.vy * cp;
 
@@ -125,7 +220,7 @@ __device__ __forceinline__ void model_step_adjoint(const DevParams& P, const Sta
     o.psi += gY * dX - gX * dY;
     o.r += gpsi;
     // dvx = (Fx - Fyf sd)/m + vy r
-    float Fxb = gvx * P.m_inv;
+    const float Fxb = gvx * P.m_inv;
     float Fyfb = -gvx * sd * P.m_inv;
     float db = -gvx * Fyf * cd * P.m_inv;
     o.vy += gvx * x.r;
@@ -140,9 +235,9 @@ __device__ __forceinline__ void model_step_adjoint(const DevParams& P, const Sta
     Fyfb += gr * P.lf * cd * P.Iz_inv;
     db -= gr * P.lf * Fyf * sd * P.Iz_inv;
     Fyrb -= gr * P.lr * P.Iz_inv;
-    // tyres: Fy = Fz sin(Ct atan(B alpha))
-    const float afb = Fyfb * P.Fzf * P.Ct * cphf * P.B / fmaf(P.B * af, P.B * af, 1.0f);
-    const float arb = Fyrb * P.Fzr * P.Ct * cphr * P.B / fmaf(P.B * ar, P.B * ar, 1.0f);
+    // tyres: Fy = Fz shape(B alpha)
+    const float afb = Fyfb * P.Fzf * dphf * P.B;
+    const float arb = Fyrb * P.Fzr * dphr * P.B;
     db += afb;
     const float bfb = -afb, brb = -arb;
     // slip: b = atan2(y, vx): db/dy = vx / (vx^2 + y^2), db/dvx = -y / (vx^2 + y^2)
@@ -220,6 +315,49 @@ __device__ __forceinline__ float run_cost(const DevParams& P, float vx, float d2
 // DCBF violation (1 - alpha) h_prev - h (penalty C max(., 0), Eq. 17).
 __device__ __forceinline__ float cbf_arg(const DevParams& P, float h_prev, float h) {
     return fmaf(P.one_m_alpha, h_prev, -h);
+}
+
+// ---------------------------------------------------------------------------
+// Bulk (TMA, non-tensor) global -> shared copies completed on an mbarrier.
+// Addresses 16-byte aligned, sizes multiples of 16 bytes.  The wait is
+// bounded: after the limit it reports failure (the caller sets a status bit).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for phase `parity` of the barrier; false if it did not complete in time.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    for (int i = 0; i < (1 << 22); ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
 }
 
 // Warp-level argmin of (d2, index) with lowest index on ties.

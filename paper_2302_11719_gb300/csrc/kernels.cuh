@@ -5,22 +5,31 @@
 
 namespace smppi {
 
-enum { MODE_ROLL = 0, MODE_DUMP = 1, MODE_FROM_S = 2 };
+constexpr int ROLL_BLK = 128;   // rollouts per block of the single-problem kernel
+constexpr int UPD_BLK = 256;    // threads per block of the update kernel (also its max grid)
 
 // Opt a kernel in to more than 48 KB of dynamic shared memory when needed.
 inline cudaError_t ensure_smem(const void* kernel, size_t bytes) {
     if (bytes <= 48 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
-constexpr int ROLL_BLK = 128;   // rollouts per block of the single-problem kernel
 
 size_t rollout_smem_bytes(int n_track, int T);
-cudaError_t launch_rollout(const DevParams& P, int mode, const float* x0, const float* V,
+// Rollouts: S_out [K] and blk_min [ceil(K / ROLL_BLK)]; traj (optional dump);
+// seg0_out (optional): nearest segment of x0.
+cudaError_t launch_rollout(const DevParams& P, bool dump, const float* x0, const float* V,
                            const float4* seg, const float* inv, uint32_t iter, uint32_t ctr3,
-                           const uint32_t* iter_dev, const float* S_in, float* S_out, float* traj, float* part_acc,
-                           float2* part_mh, unsigned* status, cudaStream_t st);
-cudaError_t launch_merge(const DevParams& P, const float* part_acc, const float2* part_mh,
-                         int nblk, float* V, unsigned* status, cudaStream_t st);
+                           const uint32_t* iter_dev, float* S_out, float* traj, float* blk_min,
+                           int* seg0_out, unsigned* status, cudaStream_t st);
+// Grid of the update kernel for K rollouts (<= UPD_BLK blocks).
+int update_grid(int K);
+// Softmin update V <- clamp(V + sum omega eps / sum omega) from S [K].  blk_min
+// (n_min values) may be NULL.  part_acc [grid][2T], part_eta [grid]; ticket:
+// a device counter that is 0 on entry and left 0.
+cudaError_t launch_update(const DevParams& P, const float* S, const float* blk_min, int n_min,
+                          float* V, uint32_t iter, uint32_t ctr3, const uint32_t* iter_dev,
+                          float* part_acc, double* part_eta, unsigned* ticket, unsigned* status,
+                          cudaStream_t st);
 cudaError_t launch_debug_noise(const DevParams& P, uint32_t iter, uint32_t ctr3, int K, int T,
                                float* eps, uint32_t* raw, cudaStream_t st);
 
@@ -37,7 +46,18 @@ struct RepairWs {
     float2* G;                 // [T][max_seq]  gradient
     int* seg0;                 // [max_seq]     nearest segment of x0
 };
-constexpr int NFIELD = 9;      // x (6), segment, h, h of the previous step
+constexpr int NFIELD = 11;     // x (6), cos psi, sin psi, segment, h, h of the previous step
+// Repairs of at most this many sequences run one block per sequence (shared
+// memory, parallel line search); larger batches run one thread per sequence.
+constexpr int REPAIR_BLOCK_MAX_SEQ = 1024;
+
+// Closed-loop step fused into the tail of the repair of sequence 0.
+struct ApplyArgs {
+    float* x0;                 // in/out state (NULL: no closed-loop step)
+    float* V;                  // in/out: shifted V+
+    uint32_t n, ctr3;          // disturbance index and counter word
+    uint32_t* iter_dev;        // graph replays: n += *iter_dev, then ++*iter_dev
+};
 
 cudaError_t launch_seg0(const DevParams& P, const float4* seg, const float* inv, int n_seq,
                         const float* x0, int* seg0, cudaStream_t st);
@@ -48,8 +68,8 @@ cudaError_t launch_cost_grad(const DevParams& P, const float4* seg, const float*
 cudaError_t launch_repair(const DevParams& P, const float4* seg, const float* inv,
                           const RepairWs& ws, int n_seq, const float* x0, const float* V_in,
                           float* V_out, int n_iters, int mode, float delta, double* merit_out,
-                          int* iters_out, unsigned* status, cudaStream_t st);
-cudaError_t launch_apply(const DevParams& P, float* x0, float* V, const float* V_exec, uint32_t n,
-                         uint32_t ctr3, uint32_t* iter_dev, cudaStream_t st);
+                          int* iters_out, const ApplyArgs& ap, unsigned* status, cudaStream_t st);
+cudaError_t launch_apply(const DevParams& P, const ApplyArgs& ap, const float* V_exec,
+                         cudaStream_t st);
 
 }  // namespace smppi

@@ -24,12 +24,14 @@ struct Tape {
     __device__ __forceinline__ void put(int slot, const State& x, int s, float h, float hp) const {
         at(slot, 0) = x.vx; at(slot, 1) = x.vy; at(slot, 2) = x.r;
         at(slot, 3) = x.X; at(slot, 4) = x.Y; at(slot, 5) = x.psi;
-        at(slot, 6) = __int_as_float(s); at(slot, 7) = h; at(slot, 8) = hp;
+        at(slot, 6) = x.cp; at(slot, 7) = x.sp;
+        at(slot, 8) = __int_as_float(s); at(slot, 9) = h; at(slot, 10) = hp;
     }
     __device__ __forceinline__ void get(int slot, State& x, int& s, float& h, float& hp) const {
         x.vx = at(slot, 0); x.vy = at(slot, 1); x.r = at(slot, 2);
         x.X = at(slot, 3); x.Y = at(slot, 4); x.psi = at(slot, 5);
-        s = __float_as_int(at(slot, 6)); h = at(slot, 7); hp = at(slot, 8);
+        x.cp = at(slot, 6); x.sp = at(slot, 7);
+        s = __float_as_int(at(slot, 8)); h = at(slot, 9); hp = at(slot, 10);
     }
 };
 
@@ -111,7 +113,7 @@ __device__ double seq_cost_grad(const DevParams& P, const float4* seg, const flo
     const bool full = ck <= 0;
     const int nck = full ? 1 : (N + ck - 1) / ck;
     const int rb = full ? 0 : nck;  // first slot of the recomputed segment
-    State lam = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    State lam = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int c = nck - 1; c >= 0; --c) {
         const int t0 = full ? 0 : c * ck;
         const int t1 = full ? N : min(t0 + ck, N);
@@ -146,7 +148,7 @@ __device__ double seq_cost_grad(const DevParams& P, const float4* seg, const flo
             int s;
             float h, hp;
             tape.get(i, x, s, h, hp);
-            const float h_next = tape.at(i + 1, 7);
+            const float h_next = tape.at(i + 1, 9);
             const float2 v = Vw[(size_t)t * ms + seq];
             const float2 u = clamp2(P, v);
             float gd, ga;
@@ -160,6 +162,25 @@ __device__ double seq_cost_grad(const DevParams& P, const float4* seg, const flo
         }
     }
     return J;
+}
+
+// Closed-loop step (Alg. 2 ExecuteCommand + warm start, Eq. 26), one thread:
+// x0 <- f(x0, clamp(v_exec)) + w_n, V <- shift(V).
+__device__ void closed_loop_step(const DevParams& P, const ApplyArgs& ap, float2 v_exec) {
+    const uint32_t nn = ap.n + (ap.iter_dev ? *ap.iter_dev : 0u);
+    State x = make_state(ap.x0);
+    model_step(P, x, clampf(v_exec.x, P.umin0, P.umax0), clampf(v_exec.y, P.umin1, P.umax1));
+    const uint4 r = philox10(make_uint4(0u, 0u, nn, ap.ctr3), P);
+    const float2 z = box_muller(r.x, r.y);
+    ap.x0[0] = x.vx;
+    ap.x0[1] = fmaf(P.dsig0, z.x, x.vy);
+    ap.x0[2] = fmaf(P.dsig1, z.y, x.r);
+    ap.x0[3] = x.X;
+    ap.x0[4] = x.Y;
+    ap.x0[5] = x.psi;
+    float2* V = reinterpret_cast<float2*>(ap.V);
+    for (int t = 0; t + 1 < P.T; ++t) V[t] = V[t + 1];
+    if (ap.iter_dev) *ap.iter_dev += 1u;
 }
 
 }  // namespace
@@ -218,8 +239,7 @@ __global__ void __launch_bounds__(REP_BLK) cost_grad_kernel(
     const int T = P.T, ms = ws.max_seq;
     const float2* Vrow = reinterpret_cast<const float2*>(Vg) + (size_t)q * T;
     for (int t = 0; t < T; ++t) ws.Vw[(size_t)t * ms + q] = Vrow[t];
-    State x0 = {x0g[6 * q], x0g[6 * q + 1], x0g[6 * q + 2], x0g[6 * q + 3], x0g[6 * q + 4],
-                x0g[6 * q + 5]};
+    const State x0 = make_state(x0g + 6 * q);
     const Tape tape{ws.tape, ms, q};
     const double J = seq_cost_grad(P, seg, inv, x0, ws.seg0[q], N, T, ws.Vw, ws.G, ms, q, w_run,
                                    w_cbf, ck, tape);
@@ -231,9 +251,9 @@ __global__ void __launch_bounds__(REP_BLK) cost_grad_kernel(
 
 __global__ void __launch_bounds__(REP_BLK) repair_kernel(
     DevParams P, const float4* __restrict__ segg, const float* __restrict__ invg, RepairWs ws,
-    int n_seq, const float* __restrict__ x0g, const float* __restrict__ Vin,
-    float* __restrict__ Vout, int n_iters, int mode, float delta, double* __restrict__ merit_out,
-    int* __restrict__ iters_out, unsigned* __restrict__ status) {
+    int n_seq, const float* __restrict__ x0g, const float* Vin, float* Vout, int n_iters,
+    int mode, float delta, double* __restrict__ merit_out, int* __restrict__ iters_out,
+    ApplyArgs ap, unsigned* __restrict__ status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4* seg = reinterpret_cast<float4*>(smem_raw);
     float* inv = reinterpret_cast<float*>(seg + P.n_track);
@@ -244,8 +264,7 @@ __global__ void __launch_bounds__(REP_BLK) repair_kernel(
     const float2* vin = reinterpret_cast<const float2*>(Vin) + (size_t)q * T;
     float2* vout = reinterpret_cast<float2*>(Vout) + (size_t)q * T;
     for (int t = 0; t < T; ++t) ws.Vw[(size_t)t * ms + q] = vin[t];
-    const State x0 = {x0g[6 * q], x0g[6 * q + 1], x0g[6 * q + 2], x0g[6 * q + 3],
-                      x0g[6 * q + 4], x0g[6 * q + 5]};
+    const State x0 = make_state(x0g + 6 * q);
     const int s0 = ws.seg0[q];
     const Tape tape{ws.tape, ms, q};
     double P0 = forward_cost<false, false>(P, seg, inv, x0, s0, N, ws.Vw, nullptr, 0.0f, ms, q,
@@ -298,35 +317,153 @@ __global__ void __launch_bounds__(REP_BLK) repair_kernel(
     if (stalled) atomicOr(status, SMPPI_DEV_STALLED);
     if (!isfinite(P0)) atomicOr(status, SMPPI_DEV_NUMERIC);
     for (int t = 0; t < T; ++t) vout[t] = ws.Vw[(size_t)t * ms + q];
+    if (q == 0 && ap.x0) closed_loop_step(P, ap, ws.Vw[0]);
 }
 
-// Closed-loop step: x0 <- f(x0, clamp(V_exec[0])) + w_n (Eq. 26); V <- shift(V).
-// With iter_dev (graph replays) the disturbance index is n + *iter_dev and the
-// counter is advanced for the next update.
-__global__ void apply_kernel(DevParams P, float* __restrict__ x0, float* V, const float* V_exec,
-                             uint32_t n, uint32_t ctr3, uint32_t* __restrict__ iter_dev) {
-    __shared__ float2 Vs[SMPPI_MAX_T];
-    const int T = P.T;
-    // V_exec may alias V: read the executed control before V is shifted
-    const float2 v = reinterpret_cast<const float2*>(V_exec)[0];
-    for (int t = threadIdx.x; t < T; t += blockDim.x) Vs[t] = reinterpret_cast<float2*>(V)[t];
+// Safety shield for few sequences: one block per sequence, everything in
+// shared memory (track table staged by a bulk copy, controls, gradient,
+// checkpoint tape), the Armijo trial steps s, s/2, s/4, ... evaluated in
+// parallel by the lanes of warp 0 (lane j: s 2^-j), the largest accepted step
+// taken: the same iterate as sequential backtracking.
+constexpr int REPB_BLK = 64;
+
+__global__ void __launch_bounds__(REPB_BLK) repair_block_kernel(
+    DevParams P, const float4* __restrict__ segg, const float* __restrict__ invg, int inv_pad,
+    const float* __restrict__ x0g, const float* Vin, float* Vout, int n_iters, int mode,
+    float delta, int ck, double* __restrict__ merit_out, int* __restrict__ iters_out, ApplyArgs ap,
+    unsigned* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int T = P.T, N = P.N_r, n = P.n_track;
+    float4* seg = reinterpret_cast<float4*>(smem_raw);
+    float* inv = reinterpret_cast<float*>(seg + n);
+    float2* Vw = reinterpret_cast<float2*>(inv + inv_pad);
+    float2* G = Vw + T;
+    float* tape_s = reinterpret_cast<float*>(G + T);
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ double s_P;
+    __shared__ float s_red[REPB_BLK / 32];
+    __shared__ int s_redi[REPB_BLK / 32];
+    __shared__ int s_seg0;
+    __shared__ float s_step;
+    __shared__ bool s_ok;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int q = blockIdx.x;
+
+    // stage the track (bulk copy) and this sequence's controls
+    if (tid == 0) mbar_init(&bar, 1);
     __syncthreads();
-    for (int t = threadIdx.x; t < T; t += blockDim.x)
-        reinterpret_cast<float2*>(V)[t] = Vs[t + 1 < T ? t + 1 : T - 1];
-    if (threadIdx.x == 0) {
-        const uint32_t nn = n + (iter_dev ? *iter_dev : 0u);
-        State x = {x0[0], x0[1], x0[2], x0[3], x0[4], x0[5]};
-        model_step(P, x, clampf(v.x, P.umin0, P.umax0), clampf(v.y, P.umin1, P.umax1));
-        const uint4 r = philox10(make_uint4(0u, 0u, nn, ctr3), P.key0, P.key1);
-        const float2 z = box_muller(r.x, r.y);
-        x0[0] = x.vx;
-        x0[1] = fmaf(P.dsig0, z.x, x.vy);
-        x0[2] = fmaf(P.dsig1, z.y, x.r);
-        x0[3] = x.X;
-        x0[4] = x.Y;
-        x0[5] = x.psi;
-        if (iter_dev) *iter_dev += 1u;
+    if (tid == 0) {
+        const uint32_t b_seg = (uint32_t)n * 16u, b_inv = (uint32_t)inv_pad * 4u;
+        mbar_expect_tx(&bar, b_seg + b_inv);
+        bulk_g2s(seg, segg, b_seg, &bar);
+        bulk_g2s(inv, invg, b_inv, &bar);
     }
+    const float2* vin = reinterpret_cast<const float2*>(Vin) + (size_t)q * T;
+    for (int t = tid; t < T; t += REPB_BLK) Vw[t] = vin[t];
+    const State x0 = make_state(x0g + 6 * q);
+    if (!mbar_wait_bounded(&bar, 0)) {
+        atomicOr(status, SMPPI_DEV_TIMEOUT);
+        mbar_wait_bounded(&bar, 0);   // give the copy in flight a second chance to land
+        return;
+    }
+    // nearest segment of x0 (lowest index on ties)
+    float bd = 3.0e38f;
+    int bi = 0x7fffffff;
+    for (int i = tid; i < n; i += REPB_BLK) {
+        const float d = seg_d2(seg, inv, i, x0.X, x0.Y);
+        if (d < bd) { bd = d; bi = i; }
+    }
+    warp_argmin(bd, bi);
+    if (lane == 0) { s_red[warp] = bd; s_redi[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+        for (int w = 1; w < REPB_BLK / 32; ++w)
+            if (s_red[w] < bd || (s_red[w] == bd && s_redi[w] < bi)) { bd = s_red[w]; bi = s_redi[w]; }
+        s_seg0 = bi;
+    }
+    __syncthreads();
+    const int s0 = s_seg0;
+    const Tape tape{tape_s, 1, 0};
+    if (tid == 0)
+        s_P = forward_cost<false, false>(P, seg, inv, x0, s0, N, Vw, nullptr, 0.0f, 1, 0, 0.0f,
+                                         1.0f, 0, tape, nullptr);
+    __syncthreads();
+    double P0 = s_P;
+    int it = 0;
+    bool stalled = false;
+    for (; it < n_iters; ++it) {
+        if (tid == 0 && merit_out) merit_out[(size_t)q * (n_iters + 1) + it] = P0;
+        if (P0 == 0.0) break;
+        if (tid == 0) seq_cost_grad(P, seg, inv, x0, s0, N, T, Vw, G, 1, 0, 0.0f, 1.0f, ck, tape);
+        __syncthreads();
+        if (mode == 0) {
+            for (int t = tid; t < N; t += REPB_BLK)
+                Vw[t] = clamp2(P, make_float2(fmaf(-delta, G[t].x, Vw[t].x),
+                                              fmaf(-delta, G[t].y, Vw[t].y)));
+            __syncthreads();
+            if (tid == 0)
+                s_P = forward_cost<false, false>(P, seg, inv, x0, s0, N, Vw, nullptr, 0.0f, 1, 0,
+                                                 0.0f, 1.0f, 0, tape, nullptr);
+            __syncthreads();
+            P0 = s_P;
+            continue;
+        }
+        // |g|_inf
+        float gm = 0.0f;
+        for (int t = tid; t < N; t += REPB_BLK)
+            gm = fmaxf(gm, fmaxf(fabsf(G[t].x), fabsf(G[t].y)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+        if (lane == 0) s_red[warp] = gm;
+        __syncthreads();
+        gm = s_red[0];
+        for (int w = 1; w < REPB_BLK / 32; ++w) gm = fmaxf(gm, s_red[w]);
+        if (!(gm > 0.0f)) { stalled = true; break; }
+        const float s_first = P.ls_s0 / gm;
+        if (warp == 0) {
+            // lane j tries s_first 2^-j (j = lane, lane + 32, ...); keep the smallest accepted j
+            int best = 0x7fffffff;
+            double best_P = 0.0;
+            for (int j = lane; j < P.ls_max; j += 32) {
+                const float sj = ldexpf(s_first, -j);
+                double dec;
+                const double Pt = forward_cost<false, true>(P, seg, inv, x0, s0, N, Vw, G, sj, 1,
+                                                            0, 0.0f, 1.0f, 0, tape, &dec);
+                if (Pt <= P0 - (double)P.ls_c * dec && j < best) { best = j; best_P = Pt; }
+            }
+            int bj = best;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) bj = min(bj, __shfl_xor_sync(0xffffffffu, bj, o));
+            if (best == bj && bj != 0x7fffffff) {   // the owning lane publishes
+                s_P = best_P;
+                s_step = ldexpf(s_first, -bj);
+            }
+            if (lane == 0) s_ok = (bj != 0x7fffffff);
+        }
+        __syncthreads();
+        if (!s_ok) { stalled = true; break; }
+        const float sa = s_step;
+        for (int t = tid; t < N; t += REPB_BLK)
+            Vw[t] = clamp2(P, make_float2(fmaf(-sa, G[t].x, Vw[t].x), fmaf(-sa, G[t].y, Vw[t].y)));
+        __syncthreads();
+        P0 = s_P;
+    }
+    if (tid == 0) {
+        if (merit_out)
+            for (int i = it; i <= n_iters; ++i) merit_out[(size_t)q * (n_iters + 1) + i] = P0;
+        if (iters_out) iters_out[q] = it;
+        if (stalled) atomicOr(status, SMPPI_DEV_STALLED);
+        if (!isfinite(P0)) atomicOr(status, SMPPI_DEV_NUMERIC);
+    }
+    float2* vout = reinterpret_cast<float2*>(Vout) + (size_t)q * T;
+    for (int t = tid; t < T; t += REPB_BLK) vout[t] = Vw[t];
+    if (q == 0 && tid == 0 && ap.x0) closed_loop_step(P, ap, Vw[0]);
+}
+
+// Closed-loop step as its own launch (V_exec may alias ap.V: it is read first).
+__global__ void apply_kernel(DevParams P, ApplyArgs ap, const float* V_exec) {
+    const float2 v = reinterpret_cast<const float2*>(V_exec)[0];
+    closed_loop_step(P, ap, v);
 }
 
 // ----------------------------------------------------------------------------
@@ -360,19 +497,31 @@ cudaError_t launch_cost_grad(const DevParams& P, const float4* seg, const float*
 cudaError_t launch_repair(const DevParams& P, const float4* seg, const float* inv,
                           const RepairWs& ws, int n_seq, const float* x0, const float* V_in,
                           float* V_out, int n_iters, int mode, float delta, double* merit_out,
-                          int* iters_out, unsigned* status, cudaStream_t st) {
+                          int* iters_out, const ApplyArgs& ap, unsigned* status,
+                          cudaStream_t st) {
+    if (n_seq <= REPAIR_BLOCK_MAX_SEQ) {
+        const int inv_pad = (P.n_track + 3) & ~3;
+        const size_t smem = (size_t)P.n_track * 16 + (size_t)inv_pad * 4 + (size_t)P.T * 16 +
+                            (size_t)(P.T + 2) * NFIELD * 4;
+        cudaError_t e = ensure_smem((const void*)repair_block_kernel, smem);
+        if (e != cudaSuccess) return e;
+        repair_block_kernel<<<n_seq, REPB_BLK, smem, st>>>(P, seg, inv, inv_pad, x0, V_in, V_out,
+                                                           n_iters, mode, delta, ws.ck, merit_out,
+                                                           iters_out, ap, status);
+        return cudaGetLastError();
+    }
     const size_t smem = track_smem(P.n_track);
     cudaError_t e = ensure_smem((const void*)repair_kernel, smem);
     if (e != cudaSuccess) return e;
     repair_kernel<<<(n_seq + REP_BLK - 1) / REP_BLK, REP_BLK, smem, st>>>(
-        P, seg, inv, ws, n_seq, x0, V_in, V_out, n_iters, mode, delta, merit_out, iters_out,
+        P, seg, inv, ws, n_seq, x0, V_in, V_out, n_iters, mode, delta, merit_out, iters_out, ap,
         status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_apply(const DevParams& P, float* x0, float* V, const float* V_exec, uint32_t n,
-                         uint32_t ctr3, uint32_t* iter_dev, cudaStream_t st) {
-    apply_kernel<<<1, 128, 0, st>>>(P, x0, V, V_exec, n, ctr3, iter_dev);
+cudaError_t launch_apply(const DevParams& P, const ApplyArgs& ap, const float* V_exec,
+                         cudaStream_t st) {
+    apply_kernel<<<1, 1, 0, st>>>(P, ap, V_exec);
     return cudaGetLastError();
 }
 

@@ -1,17 +1,21 @@
-// MPPI iteration kernels: K sampled rollouts with the DCBF-augmented cost,
-// the min-shifted softmin weights and the weighted noise sum (Alg. 2 sampling
-// loop + OptimalControl; Eq. 10-12, 17-20).
+// MPPI iteration kernels (Alg. 2 sampling loop + OptimalControl; Eq. 10-12,
+// 17-20): K sampled rollouts with the DCBF-augmented cost, then the min-
+// shifted softmin weights and the weighted noise sum.
 //
-// Layout of one launch (K rollouts, horizon T):
-//   grid = ceil(K / BLK) blocks, one thread per rollout.  Shared memory holds
-//   the centreline segment table, the nominal sequence V and the per-warp
-//   partial sums.  Each thread steps its rollout in registers, drawing the
-//   noise from Philox as it goes (never stored).  The block then reduces its
-//   costs to a local minimum m_b and normaliser eta_b = sum exp(-(S - m_b)/lambda)
-//   and, in a second pass over the same rollouts, regenerates the noise and
-//   accumulates sum_k omega_k eps_{k,t} for every t.  A small merge kernel
-//   rescales the per-block partials by exp(-(m_b - m)/lambda) and sums them in
-//   float64 to V+ = clamp(V + A / eta).
+// Launch 1 (rollouts): grid = ceil(K / BLK), one thread per rollout.  Shared
+//   memory holds the centreline segment table and the nominal sequence V.  Each
+//   thread steps its rollout in registers; the noise of the next pair of steps
+//   is drawn from Philox while the current pair is integrated (never stored).
+//   Writes S_k and the block minimum of S.
+// Launch 2 (update): G <= #SMs blocks of UPD_BLK threads.  Every block takes
+//   m = min_k S_k from the block minima, computes omega_k = exp(-(S_k - m)/lambda)
+//   for its contiguous slice of k (all of them enter eta), and regenerates the
+//   noise only of rollouts with omega_k > w_skip = 1e-8 / (K max|eps|): the
+//   dropped terms change V+ by at most K w_skip max|eps| / eta <= 1e-8 (eta >= 1
+//   because the arg-min has weight 1).  With lambda = 1 and the cost spread of
+//   these problems that leaves a small fraction of K.  The last block to
+//   finish (device-scope ticket) sums the non-empty block partials in float64
+//   and writes V+ = clamp(V + A / eta).
 #include "kernels.cuh"
 
 namespace smppi {
@@ -23,11 +27,6 @@ __device__ __forceinline__ float warp_min(float v) {
     for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 }  // namespace
 
@@ -35,7 +34,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 template <int BLK>
 __device__ __forceinline__ void stage_problem(const DevParams& P, const float4* __restrict__ segg,
                                               const float* __restrict__ invg,
-                                              const float* __restrict__ Vg, const State& x0,
+                                              const float* __restrict__ Vg, float X0, float Y0,
                                               float4* seg, float* inv, float2* Vs, int* s_seg0,
                                               float* s_d20, float* red_f, int* red_i) {
     const int tid = threadIdx.x;
@@ -49,7 +48,7 @@ __device__ __forceinline__ void stage_problem(const DevParams& P, const float4* 
     float bd = 3.0e38f;
     int bi = 0x7fffffff;
     for (int i = tid; i < P.n_track; i += BLK) {
-        const float d = seg_d2(seg, inv, i, x0.X, x0.Y);
+        const float d = seg_d2(seg, inv, i, X0, Y0);
         if (d < bd) { bd = d; bi = i; }
     }
     warp_argmin(bd, bi);
@@ -65,14 +64,37 @@ __device__ __forceinline__ void stage_problem(const DevParams& P, const float4* 
     __syncthreads();
 }
 
-// One block of rollouts (MODE_ROLL / MODE_DUMP) or of given costs (MODE_FROM_S).
-template <int BLK, int MODE>
+// One rollout step: perturb, clamp, integrate, project on the track, add cost.
+__device__ __forceinline__ void rollout_step(const DevParams& P, const float4* seg,
+                                             const float* inv, float2 v, float2 z, State& x,
+                                             int& s, float& h_prev, float& acc) {
+    const float u0 = fmaf(P.sig0, z.x, v.x), u1 = fmaf(P.sig1, z.y, v.y);
+    acc = fmaf(P.gis0 * v.x, u0, acc);
+    acc = fmaf(P.gis1 * v.y, u1, acc);
+    model_step(P, x, clampf(u0, P.umin0, P.umax0), clampf(u1, P.umin1, P.umax1));
+    float d2;
+    s = track_follow(seg, inv, P.n_track, s, x.X, x.Y, d2);
+    const float h = P.w2 - d2;
+    acc += run_cost(P, x.vx, d2) + P.C_cbf * fmaxf(cbf_arg(P, h_prev, h), 0.0f);
+    h_prev = h;
+}
+
+template <bool DUMP>
+__device__ __forceinline__ void dump_state(float* traj, int k, int T, int t, const State& x) {
+    if (DUMP) {
+        float* tr = traj + ((size_t)k * (T + 1) + t) * 6;
+        tr[0] = x.vx; tr[1] = x.vy; tr[2] = x.r; tr[3] = x.X; tr[4] = x.Y; tr[5] = x.psi;
+    }
+}
+
+// Launch 1: one thread per rollout.
+template <int BLK, bool DUMP>
 __global__ void __launch_bounds__(BLK) mppi_rollout_kernel(
     DevParams P, const float* __restrict__ x0g, const float* __restrict__ Vg,
     const float4* __restrict__ segg, const float* __restrict__ invg, uint32_t iter,
-    uint32_t ctr3, const uint32_t* __restrict__ iter_dev, const float* __restrict__ S_in,
-    float* __restrict__ S_out, float* __restrict__ traj, float* __restrict__ part_acc,
-    float2* __restrict__ part_mh, unsigned* __restrict__ status) {
+    uint32_t ctr3, const uint32_t* __restrict__ iter_dev, float* __restrict__ S_out,
+    float* __restrict__ traj, float* __restrict__ blk_min, int* __restrict__ seg0_out,
+    unsigned* __restrict__ status) {
     constexpr int NW = BLK / 32;
     if (iter_dev) iter += *iter_dev;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -80,7 +102,6 @@ __global__ void __launch_bounds__(BLK) mppi_rollout_kernel(
     float4* seg = reinterpret_cast<float4*>(smem_raw);
     float* inv = reinterpret_cast<float*>(seg + n);
     float2* Vs = reinterpret_cast<float2*>(inv + n + (n & 1));
-    float* wacc = reinterpret_cast<float*>(Vs + T);  // [NW][2T]
     __shared__ float red_f[NW];
     __shared__ int red_i[NW];
     __shared__ int s_seg0;
@@ -90,155 +111,188 @@ __global__ void __launch_bounds__(BLK) mppi_rollout_kernel(
     const int k = blockIdx.x * BLK + tid;
     const bool active = k < P.K;
 
-    State x = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (MODE != MODE_FROM_S) {
-        x.vx = x0g[0]; x.vy = x0g[1]; x.r = x0g[2]; x.X = x0g[3]; x.Y = x0g[4]; x.psi = x0g[5];
-    }
-
+    stage_problem<BLK>(P, segg, invg, Vg, x0g[3], x0g[4], seg, inv, Vs, &s_seg0, &s_d20, red_f,
+                       red_i);
+    if (blockIdx.x == 0 && tid == 0 && seg0_out) *seg0_out = s_seg0;
     float S = 3.0e38f;
-    if (MODE == MODE_FROM_S) {
-        for (int t = tid; t < T; t += BLK) Vs[t] = reinterpret_cast<const float2*>(Vg)[t];
-        __syncthreads();
-        if (active) S = S_in[k];
-    } else {
-        stage_problem<BLK>(P, segg, invg, Vg, x, seg, inv, Vs, &s_seg0, &s_d20, red_f, red_i);
-        if (active) {
-            int s = s_seg0;
-            float d2 = s_d20;
-            float h_prev = P.w2 - d2;
-            float acc = run_cost(P, x.vx, d2) + P.C_cbf * fmaxf(cbf_arg(P, h_prev, h_prev), 0.0f);
-            if (MODE == MODE_DUMP) {
-                float* tr = traj + (size_t)k * (T + 1) * 6;
-                tr[0] = x.vx; tr[1] = x.vy; tr[2] = x.r; tr[3] = x.X; tr[4] = x.Y; tr[5] = x.psi;
+    if (active) {
+        State x = make_state(x0g);
+        int s = s_seg0;
+        float h_prev = P.w2 - s_d20;
+        float acc = run_cost(P, x.vx, s_d20) + P.C_cbf * fmaxf(cbf_arg(P, h_prev, h_prev), 0.0f);
+        dump_state<DUMP>(traj, k, T, 0, x);
+        // noise of pair 0, then one pair ahead of the integration
+        uint4 r = philox10(make_uint4((uint32_t)k, 0u, iter, ctr3), P);
+        float2 za = box_muller(r.x, r.y), zb = box_muller(r.z, r.w);
+        const int npair = (T + 1) >> 1;
+        for (int p = 0; p < npair; ++p) {
+            const uint4 rn = philox10(make_uint4((uint32_t)k, (uint32_t)(p + 1), iter, ctr3), P);
+            const float2 na = box_muller(rn.x, rn.y), nb = box_muller(rn.z, rn.w);
+            rollout_step(P, seg, inv, Vs[2 * p], za, x, s, h_prev, acc);
+            dump_state<DUMP>(traj, k, T, 2 * p + 1, x);
+            if (2 * p + 1 < T) {
+                rollout_step(P, seg, inv, Vs[2 * p + 1], zb, x, s, h_prev, acc);
+                dump_state<DUMP>(traj, k, T, 2 * p + 2, x);
             }
-            uint4 rnd = make_uint4(0, 0, 0, 0);
-            for (int t = 0; t < T; ++t) {
-                if ((t & 1) == 0)
-                    rnd = philox10(make_uint4((uint32_t)k, (uint32_t)(t >> 1), iter, ctr3), P.key0,
-                                   P.key1);
-                const float2 z = (t & 1) ? box_muller(rnd.z, rnd.w) : box_muller(rnd.x, rnd.y);
-                const float2 v = Vs[t];
-                const float u0 = fmaf(P.sig0, z.x, v.x), u1 = fmaf(P.sig1, z.y, v.y);
-                acc = fmaf(P.gis0 * v.x, u0, acc);
-                acc = fmaf(P.gis1 * v.y, u1, acc);
-                model_step(P, x, clampf(u0, P.umin0, P.umax0), clampf(u1, P.umin1, P.umax1));
-                s = track_follow(seg, inv, n, s, x.X, x.Y, d2);
-                const float h = P.w2 - d2;
-                acc += run_cost(P, x.vx, d2) + P.C_cbf * fmaxf(cbf_arg(P, h_prev, h), 0.0f);
-                h_prev = h;
-                if (MODE == MODE_DUMP) {
-                    float* tr = traj + ((size_t)k * (T + 1) + t + 1) * 6;
-                    tr[0] = x.vx; tr[1] = x.vy; tr[2] = x.r; tr[3] = x.X; tr[4] = x.Y; tr[5] = x.psi;
-                }
-            }
-            S = acc;
-            if (S_out) S_out[k] = S;
-            if (!isfinite(S)) atomicOr(status, SMPPI_DEV_NUMERIC);
+            za = na;
+            zb = nb;
         }
+        S = acc;
+        S_out[k] = S;
+        if (!isfinite(S)) atomicOr(status, SMPPI_DEV_NUMERIC);
     }
-
-    // block minimum and normaliser (Eq. 11 with the block-local shift m_b)
-    float m = warp_min(active ? S : 3.0e38f);
+    const float m = warp_min(active ? S : 3.0e38f);
     if (lane == 0) red_f[warp] = m;
     __syncthreads();
-    float mb = red_f[0];
-#pragma unroll
-    for (int w = 1; w < NW; ++w) mb = fminf(mb, red_f[w]);
-    __syncthreads();
-    const float om = active ? expf((mb - S) * P.lam_inv) : 0.0f;
-    const float es = warp_sum(om);
-    if (lane == 0) red_f[warp] = es;
-    __syncthreads();
     if (tid == 0) {
-        float eta = 0.0f;
-        for (int w = 0; w < NW; ++w) eta += red_f[w];
-        part_mh[blockIdx.x] = make_float2(mb, eta);
-    }
-
-    // second pass: regenerate eps_{k,t} and accumulate omega_k eps_{k,t} (Eq. 10)
-    const bool warp_active = __any_sync(0xffffffffu, om > 0.0f);
-    float* wa = wacc + warp * 2 * T;
-    const int npair = (T + 1) >> 1;
-    for (int p = 0; p < npair; ++p) {
-        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
-        if (warp_active) {
-            const uint4 rnd = philox10(make_uint4((uint32_t)k, (uint32_t)p, iter, ctr3), P.key0, P.key1);
-            const float2 ze = box_muller(rnd.x, rnd.y);
-            const float2 zo = box_muller(rnd.z, rnd.w);
-            a0 = warp_sum(om * P.sig0 * ze.x);
-            a1 = warp_sum(om * P.sig1 * ze.y);
-            a2 = warp_sum(om * P.sig0 * zo.x);
-            a3 = warp_sum(om * P.sig1 * zo.y);
-        }
-        if (lane == 0) {
-            wa[4 * p] = a0;
-            wa[4 * p + 1] = a1;
-            if (2 * p + 1 < T) {
-                wa[4 * p + 2] = a2;
-                wa[4 * p + 3] = a3;
-            }
-        }
-    }
-    __syncthreads();
-    for (int j = tid; j < 2 * T; j += BLK) {
-        float s = 0.0f;
+        float mb = red_f[0];
 #pragma unroll
-        for (int w = 0; w < NW; ++w) s += wacc[w * 2 * T + j];
-        part_acc[(size_t)blockIdx.x * 2 * T + j] = s;
+        for (int w = 1; w < NW; ++w) mb = fminf(mb, red_f[w]);
+        blk_min[blockIdx.x] = mb;
     }
 }
 
-// Merge the per-block partials (float64): m = min_b m_b, scale_b =
-// exp(-(m_b - m)/lambda), eta = sum_b eta_b scale_b, A_j = sum_b acc_bj scale_b,
-// V+_j = clamp(V_j + A_j / eta).  grid = ceil(2T / 32), block = (32, 8).
-__global__ void __launch_bounds__(256) mppi_merge_kernel(DevParams P,
-                                                         const float* __restrict__ part_acc,
-                                                         const float2* __restrict__ part_mh,
-                                                         int nblk, float* __restrict__ V,
-                                                         unsigned* __restrict__ status) {
-    __shared__ float s_m[8];
-    __shared__ double s_d[8][33];
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
-    const int T2 = 2 * P.T;
+// Launch 2: weights, weighted noise sum of the rollouts with non-zero weight,
+// last-block float64 merge.  blk_min may be NULL (then m is the minimum of S).
+__global__ void __launch_bounds__(UPD_BLK) mppi_update_kernel(
+    DevParams P, const float* __restrict__ S, const float* __restrict__ blk_min, int n_min,
+    float* V, uint32_t iter, uint32_t ctr3, const uint32_t* __restrict__ iter_dev,
+    float* __restrict__ part_acc, double* __restrict__ part_eta, unsigned* __restrict__ ticket,
+    unsigned* __restrict__ status) {
+    constexpr int NW = UPD_BLK / 32;
+    if (iter_dev) iter += *iter_dev;
+    __shared__ float red_f[NW];
+    __shared__ double red_d[NW];
+    __shared__ int l_k[UPD_BLK];
+    __shared__ float l_w[UPD_BLK];
+    __shared__ int l_cnt[NW];
+    __shared__ float acc_s[2 * SMPPI_MAX_T];
+    __shared__ bool s_last;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int K = P.K, T = P.T, T2 = 2 * T, npair = (T + 1) >> 1;
+
+    // global minimum of the costs
     float m = 3.0e38f;
-    for (int b = tid; b < nblk; b += 256) m = fminf(m, part_mh[b].x);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (tx == 0) s_m[ty] = m;
-    __syncthreads();
-    m = s_m[0];
-#pragma unroll
-    for (int w = 1; w < 8; ++w) m = fminf(m, s_m[w]);
-    // eta (every block computes it; nblk is small)
-    double eta = 0.0;
-    for (int b = tid; b < nblk; b += 256) {
-        const float2 mh = part_mh[b];
-        eta += (double)mh.y * (double)expf((m - mh.x) * P.lam_inv);
+    if (blk_min) {
+        for (int b = tid; b < n_min; b += UPD_BLK) m = fminf(m, blk_min[b]);
+    } else {
+        for (int k = tid; k < K; k += UPD_BLK) m = fminf(m, S[k]);
     }
+    m = warp_min(m);
+    if (lane == 0) red_f[warp] = m;
+    __syncthreads();
+    m = red_f[0];
+#pragma unroll
+    for (int w = 1; w < NW; ++w) m = fminf(m, red_f[w]);
+
+    // this block's slice of k
+    const int per = (K + gridDim.x - 1) / gridDim.x;
+    const int k_lo = blockIdx.x * per, k_hi = min(K, k_lo + per);
+    // thread (slot c, pair p) accumulates omega eps for pair p over list items c, c + C, ...
+    const int C = UPD_BLK / npair;          // >= 1 because npair <= SMPPI_MAX_T / 2
+    const int c = tid / npair, p = tid % npair;
+    const bool worker = c < C;
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+    float eta_t = 0.0f;
+    for (int kb = k_lo; kb < k_hi; kb += UPD_BLK) {
+        const int k = kb + tid;
+        const float om = (k < k_hi) ? expf((m - S[k]) * P.lam_inv) : 0.0f;
+        eta_t += om;
+        // compact the rollouts whose weight exceeds the skip threshold, in k order
+        const bool take = om > P.w_skip;
+        const unsigned bal = __ballot_sync(0xffffffffu, take);
+        if (lane == 0) l_cnt[warp] = __popc(bal);
+        __syncthreads();
+        int off = 0, tot = 0;
+        for (int w = 0; w < NW; ++w) {
+            if (w < warp) off += l_cnt[w];
+            tot += l_cnt[w];
+        }
+        if (take) {
+            const int pos = off + __popc(bal & ((1u << lane) - 1u));
+            l_k[pos] = k;
+            l_w[pos] = om;
+        }
+        __syncthreads();
+        if (worker) {
+            for (int i = c; i < tot; i += C) {
+                const uint4 r = philox10(make_uint4((uint32_t)l_k[i], (uint32_t)p, iter, ctr3), P);
+                const float2 ze = box_muller(r.x, r.y), zo = box_muller(r.z, r.w);
+                const float w0 = l_w[i] * P.sig0, w1 = l_w[i] * P.sig1;
+                a0 = fmaf(w0, ze.x, a0);
+                a1 = fmaf(w1, ze.y, a1);
+                a2 = fmaf(w0, zo.x, a2);
+                a3 = fmaf(w1, zo.y, a3);
+            }
+        }
+        __syncthreads();
+    }
+    // block normaliser (float64) and per-pair sums over the slots, in slot order
+    double eta = (double)eta_t;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) eta += __shfl_xor_sync(0xffffffffu, eta, o);
-    if (tx == 0) s_d[ty][32] = eta;
+    if (lane == 0) red_d[warp] = eta;
+    for (int j = tid; j < T2; j += UPD_BLK) acc_s[j] = 0.0f;
     __syncthreads();
     eta = 0.0;
-    for (int w = 0; w < 8; ++w) eta += s_d[w][32];
-    const int j = blockIdx.x * 32 + tx;
-    double a = 0.0;
-    if (j < T2) {
-        for (int b = ty; b < nblk; b += 8) {
-            const float sc = expf((m - part_mh[b].x) * P.lam_inv);
-            a += (double)part_acc[(size_t)b * T2 + j] * (double)sc;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) eta += red_d[w];
+    for (int cc = 0; cc < C; ++cc) {
+        if (worker && c == cc) {
+            acc_s[4 * p] += a0;
+            acc_s[4 * p + 1] += a1;
+            if (2 * p + 1 < T) {
+                acc_s[4 * p + 2] += a2;
+                acc_s[4 * p + 3] += a3;
+            }
         }
+        __syncthreads();
     }
-    s_d[ty][tx] = a;
+    float* pa = part_acc + (size_t)blockIdx.x * T2;
+    for (int j = tid; j < T2; j += UPD_BLK) pa[j] = acc_s[j];
+    if (tid == 0) part_eta[blockIdx.x] = eta;
+
+    // the last block merges the non-empty partials in block order (float64)
+    __threadfence();
     __syncthreads();
-    if (ty == 0 && j < T2) {
+    if (tid == 0) s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // list of the blocks with a non-zero normaliser, in block order (G <= UPD_BLK)
+    const int G = gridDim.x;
+    __shared__ double s_eta[UPD_BLK];
+    const double e = (tid < G) ? __ldcg(&part_eta[tid]) : 0.0;
+    const unsigned bal = __ballot_sync(0xffffffffu, e > 0.0);
+    if (lane == 0) l_cnt[warp] = __popc(bal);
+    s_eta[tid] = e;
+    __syncthreads();
+    int off = 0, nz = 0;
+    for (int w = 0; w < NW; ++w) {
+        if (w < warp) off += l_cnt[w];
+        nz += l_cnt[w];
+    }
+    if (e > 0.0) l_k[off + __popc(bal & ((1u << lane) - 1u))] = tid;
+    __syncthreads();
+    double eta_all = 0.0;
+    for (int b = 0; b < G; ++b) eta_all += s_eta[b];
+    for (int j = tid; j < T2; j += UPD_BLK) {
         double A = 0.0;
-        for (int w = 0; w < 8; ++w) A += s_d[w][tx];
+        int i = 0;
+        for (; i + 8 <= nz; i += 8) {      // 8 independent loads in flight, summed in order
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldcg(&part_acc[(size_t)l_k[i + u] * T2 + j]);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) A += (double)v[u];
+        }
+        for (; i < nz; ++i) A += (double)__ldcg(&part_acc[(size_t)l_k[i] * T2 + j]);
         const float lo = (j & 1) ? P.umin1 : P.umin0, hi = (j & 1) ? P.umax1 : P.umax0;
-        const float v = (float)((double)V[j] + A / eta);
+        const float v = (float)((double)V[j] + A / eta_all);
         if (!isfinite(v)) atomicOr(status, SMPPI_DEV_NUMERIC);
         V[j] = clampf(v, lo, hi);
     }
+    if (tid == 0) *ticket = 0u;
 }
 
 // Control noise exactly as the rollout kernels draw it (test access).
@@ -249,7 +303,7 @@ __global__ void debug_noise_kernel(DevParams P, uint32_t iter, uint32_t ctr3, in
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
         const int k = (int)(i / npair), p = (int)(i % npair);
-        const uint4 r = philox10(make_uint4((uint32_t)k, (uint32_t)p, iter, ctr3), P.key0, P.key1);
+        const uint4 r = philox10(make_uint4((uint32_t)k, (uint32_t)p, iter, ctr3), P);
         if (raw) {
             uint32_t* o = raw + i * 4;
             o[0] = r.x; o[1] = r.y; o[2] = r.z; o[3] = r.w;
@@ -273,29 +327,44 @@ __global__ void debug_noise_kernel(DevParams P, uint32_t iter, uint32_t ctr3, in
 // ----------------------------------------------------------------------------
 size_t rollout_smem_bytes(int n_track, int T) {
     return (size_t)n_track * sizeof(float4) + (size_t)(n_track + (n_track & 1)) * sizeof(float) +
-           (size_t)T * sizeof(float2) + (size_t)(ROLL_BLK / 32) * 2 * T * sizeof(float);
+           (size_t)T * sizeof(float2);
 }
 
-cudaError_t launch_rollout(const DevParams& P, int mode, const float* x0, const float* V,
+int update_grid(int K) {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            sms < 1)
+            sms = 1;
+    }
+    const int by_k = (K + UPD_BLK - 1) / UPD_BLK;
+    int g = by_k < sms ? by_k : sms;
+    return g < UPD_BLK ? g : UPD_BLK;   // the merge lists at most UPD_BLK partials
+}
+
+cudaError_t launch_rollout(const DevParams& P, bool dump, const float* x0, const float* V,
                            const float4* seg, const float* inv, uint32_t iter, uint32_t ctr3,
-                           const uint32_t* iter_dev, const float* S_in, float* S_out, float* traj, float* part_acc,
-                           float2* part_mh, unsigned* status, cudaStream_t st) {
+                           const uint32_t* iter_dev, float* S_out, float* traj, float* blk_min,
+                           int* seg0_out, unsigned* status, cudaStream_t st) {
     const int nblk = (P.K + ROLL_BLK - 1) / ROLL_BLK;
     const size_t smem = rollout_smem_bytes(P.n_track, P.T);
-    auto kern = mppi_rollout_kernel<ROLL_BLK, MODE_ROLL>;
-    if (mode == MODE_DUMP) kern = mppi_rollout_kernel<ROLL_BLK, MODE_DUMP>;
-    if (mode == MODE_FROM_S) kern = mppi_rollout_kernel<ROLL_BLK, MODE_FROM_S>;
+    auto kern = dump ? mppi_rollout_kernel<ROLL_BLK, true> : mppi_rollout_kernel<ROLL_BLK, false>;
     cudaError_t e = ensure_smem((const void*)kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<nblk, ROLL_BLK, smem, st>>>(P, x0, V, seg, inv, iter, ctr3, iter_dev, S_in, S_out, traj,
-                                       part_acc, part_mh, status);
+    kern<<<nblk, ROLL_BLK, smem, st>>>(P, x0, V, seg, inv, iter, ctr3, iter_dev, S_out, traj,
+                                       blk_min, seg0_out, status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_merge(const DevParams& P, const float* part_acc, const float2* part_mh,
-                         int nblk, float* V, unsigned* status, cudaStream_t st) {
-    dim3 grid((2 * P.T + 31) / 32), block(32, 8);
-    mppi_merge_kernel<<<grid, block, 0, st>>>(P, part_acc, part_mh, nblk, V, status);
+cudaError_t launch_update(const DevParams& P, const float* S, const float* blk_min, int n_min,
+                          float* V, uint32_t iter, uint32_t ctr3, const uint32_t* iter_dev,
+                          float* part_acc, double* part_eta, unsigned* ticket, unsigned* status,
+                          cudaStream_t st) {
+    mppi_update_kernel<<<update_grid(P.K), UPD_BLK, 0, st>>>(P, S, blk_min, n_min, V, iter, ctr3,
+                                                             iter_dev, part_acc, part_eta, ticket,
+                                                             status);
     return cudaGetLastError();
 }
 
