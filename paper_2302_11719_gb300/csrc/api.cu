@@ -23,6 +23,7 @@ struct smppi_handle {
     float* blk_min = nullptr;        // [nblk] block minima of S
     float* part_acc = nullptr;       // [UPD_BLK][2T] update-kernel partials
     double* part_eta = nullptr;      // [UPD_BLK]
+    int* part_has = nullptr;         // [UPD_BLK]
     unsigned* ticket = nullptr;      // last-block counter of the update launch
     int nblk = 0;
     unsigned* status = nullptr;
@@ -139,7 +140,8 @@ DevParams derive(const smppi_params& p) {
 void free_all(smppi_handle* h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
-    void* ptrs[] = {h->seg, h->inv, h->S_ws, h->blk_min, h->part_acc, h->part_eta, h->ticket,
+    void* ptrs[] = {h->seg, h->inv, h->S_ws, h->blk_min, h->part_acc, h->part_eta, h->part_has,
+                    h->ticket,
                     h->status,
                     h->iter_dev,
                     h->rws.tape, h->rws.Vw, h->rws.G, h->rws.seg0, h->d_x0, h->d_V, h->d_Vs,
@@ -194,7 +196,7 @@ smppi_status enqueue_step(smppi_handle* h, cudaStream_t st, const float* x0, flo
     toc(h, st, SMPPI_KERNEL_ROLLOUT, ev);
     ev = tic(h, st);
     CU(h, launch_update(h->dp, S, h->blk_min, h->nblk, V, iter, ctr3, iter_dev, h->part_acc,
-                        h->part_eta, h->ticket, h->status, st));
+                        h->part_eta, h->part_has, h->ticket, h->status, st));
     toc(h, st, SMPPI_KERNEL_UPDATE, ev);
     return SMPPI_OK;
 }
@@ -287,6 +289,7 @@ smppi_status smppi_create(const smppi_params* p, void* cuda_stream, smppi_handle
     ALLOC(h->blk_min, sizeof(float) * h->nblk);
     ALLOC(h->part_acc, sizeof(float) * 2 * T * (size_t)UPD_BLK);
     ALLOC(h->part_eta, sizeof(double) * UPD_BLK);
+    ALLOC(h->part_has, sizeof(int) * UPD_BLK);
     ALLOC(h->ticket, sizeof(unsigned));
     ALLOC(h->status, sizeof(unsigned));
     ALLOC(h->iter_dev, sizeof(uint32_t));
@@ -355,7 +358,7 @@ smppi_status smppi_update(smppi_handle* h, const float* S, float* V, uint32_t it
     if (instance >= (1u << 24)) return fail(h, SMPPI_ERR_ARG, "instance must be < 2^24");
     const int ev = tic(h, h->st);
     CU(h, launch_update(h->dp, S, nullptr, 0, V, iter, instance << 8, nullptr, h->part_acc,
-                        h->part_eta, h->ticket, h->status, h->st));
+                        h->part_eta, h->part_has, h->ticket, h->status, h->st));
     toc(h, h->st, SMPPI_KERNEL_UPDATE, ev);
     return SMPPI_OK;
 }

@@ -28,7 +28,8 @@ int update_grid(int K);
 // a device counter that is 0 on entry and left 0.
 cudaError_t launch_update(const DevParams& P, const float* S, const float* blk_min, int n_min,
                           float* V, uint32_t iter, uint32_t ctr3, const uint32_t* iter_dev,
-                          float* part_acc, double* part_eta, unsigned* ticket, unsigned* status,
+                          float* part_acc, double* part_eta, int* part_has, unsigned* ticket,
+                          unsigned* status,
                           cudaStream_t st);
 cudaError_t launch_debug_noise(const DevParams& P, uint32_t iter, uint32_t ctr3, int K, int T,
                                float* eps, uint32_t* raw, cudaStream_t st);

@@ -59,7 +59,9 @@ __device__ __forceinline__ void add_direct(const DevParams& P, const float4* seg
 // Forward rollout of u_t = clamp(Vw_t - step G_t) for N steps from x0 (segment s0).
 // Returns J in float64 and, when STORE, fills the tape (every state when
 // ck <= 0, else every ck-th).  dec_out (optional) = sum_t G_t . (Vw_t - u'_t)
-// where u'_t = clip(Vw_t - step G_t) (the Armijo decrease term).
+// where u'_t = clip(Vw_t - step G_t) (the Armijo decrease term).  The terms are
+// summed in float32 over blocks of 16 steps and the block sums in float64
+// (FP64 arithmetic is slow on this part; one FP64 add per 16 steps).
 template <bool STORE, bool TRIAL>
 __device__ double forward_cost(const DevParams& P, const float4* seg, const float* inv,
                                const State& x0, int s0, int N, const float2* Vw, const float2* G,
@@ -69,8 +71,10 @@ __device__ double forward_cost(const DevParams& P, const float4* seg, const floa
     int s = s0;
     float d2 = seg_d2(seg, inv, s, x.X, x.Y);
     float h_prev = P.w2 - d2, h_pp = h_prev;
-    double J = (double)w_run * (double)run_cost(P, x.vx, d2);
+    double J = (double)(w_run * run_cost(P, x.vx, d2));
     double dec = 0.0;
+    float Jf = 0.0f, decf = 0.0f;
+    const float wc = w_cbf * P.C_cbf;
     const bool full = ck <= 0;
     for (int t = 0; t < N; ++t) {
         if (STORE) {
@@ -82,19 +86,27 @@ __device__ double forward_cost(const DevParams& P, const float4* seg, const floa
         if (TRIAL) {
             const float2 g = G[(size_t)t * ms + seq];
             u = clamp2(P, make_float2(fmaf(-step, g.x, v.x), fmaf(-step, g.y, v.y)));
-            dec += (double)g.x * (double)(v.x - u.x) + (double)g.y * (double)(v.y - u.y);
+            decf = fmaf(g.x, v.x - u.x, fmaf(g.y, v.y - u.y, decf));
         } else {
             u = clamp2(P, v);
         }
         model_step(P, x, u.x, u.y);
         s = track_follow(seg, inv, P.n_track, s, x.X, x.Y, d2);
         const float h = P.w2 - d2;
-        if (w_run != 0.0f) J += (double)w_run * (double)run_cost(P, x.vx, d2);
+        if (w_run != 0.0f) Jf = fmaf(w_run, run_cost(P, x.vx, d2), Jf);
         const float a = cbf_arg(P, h_prev, h);
-        if (a > 0.0f) J += (double)w_cbf * (double)P.C_cbf * (double)a;
+        if (a > 0.0f) Jf = fmaf(wc, a, Jf);
         h_pp = h_prev;
         h_prev = h;
+        if ((t & 15) == 15) {
+            J += (double)Jf;
+            dec += (double)decf;
+            Jf = 0.0f;
+            decf = 0.0f;
+        }
     }
+    J += (double)Jf;
+    dec += (double)decf;
     if (STORE && full) tape.put(N, x, s, h_prev, h_pp);
     if (dec_out) *dec_out = dec;
     return J;

@@ -152,20 +152,24 @@ __global__ void __launch_bounds__(BLK) mppi_rollout_kernel(
     }
 }
 
-// Launch 2: weights, weighted noise sum of the rollouts with non-zero weight,
-// last-block float64 merge.  blk_min may be NULL (then m is the minimum of S).
+// Launch 2: weights, weighted noise sum of the rollouts whose weight exceeds
+// w_skip, last-block float64 merge.  blk_min may be NULL (then m = min of S).
+// part_has[b] != 0 when block b's noise sums are not all zero.
+constexpr int UPD_PER_T = 8;                  // slice values per thread in one pass
+constexpr int UPD_LIST = UPD_PER_T * UPD_BLK;  // list of taken rollouts of one pass
+
 __global__ void __launch_bounds__(UPD_BLK) mppi_update_kernel(
     DevParams P, const float* __restrict__ S, const float* __restrict__ blk_min, int n_min,
     float* V, uint32_t iter, uint32_t ctr3, const uint32_t* __restrict__ iter_dev,
-    float* __restrict__ part_acc, double* __restrict__ part_eta, unsigned* __restrict__ ticket,
-    unsigned* __restrict__ status) {
+    float* __restrict__ part_acc, double* __restrict__ part_eta, int* __restrict__ part_has,
+    unsigned* __restrict__ ticket, unsigned* __restrict__ status) {
     constexpr int NW = UPD_BLK / 32;
+    constexpr int PER_T = UPD_PER_T;
     if (iter_dev) iter += *iter_dev;
     __shared__ float red_f[NW];
-    __shared__ double red_d[NW];
-    __shared__ int l_k[UPD_BLK];
-    __shared__ float l_w[UPD_BLK];
-    __shared__ int l_cnt[NW];
+    __shared__ int l_k[UPD_LIST];
+    __shared__ float l_w[UPD_LIST];
+    __shared__ int w_cnt[NW];
     __shared__ float acc_s[2 * SMPPI_MAX_T];
     __shared__ bool s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -185,7 +189,6 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_update_kernel(
 #pragma unroll
     for (int w = 1; w < NW; ++w) m = fminf(m, red_f[w]);
 
-    // this block's slice of k
     const int per = (K + gridDim.x - 1) / gridDim.x;
     const int k_lo = blockIdx.x * per, k_hi = min(K, k_lo + per);
     // thread (slot c, pair p) accumulates omega eps for pair p over list items c, c + C, ...
@@ -194,28 +197,45 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_update_kernel(
     const bool worker = c < C;
     float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
     float eta_t = 0.0f;
-    for (int kb = k_lo; kb < k_hi; kb += UPD_BLK) {
-        const int k = kb + tid;
-        const float om = (k < k_hi) ? expf((m - S[k]) * P.lam_inv) : 0.0f;
-        eta_t += om;
-        // compact the rollouts whose weight exceeds the skip threshold, in k order
-        const bool take = om > P.w_skip;
-        const unsigned bal = __ballot_sync(0xffffffffu, take);
-        if (lane == 0) l_cnt[warp] = __popc(bal);
+    int has = 0;
+    for (int kb = k_lo; kb < k_hi; kb += PER_T * UPD_BLK) {
+        // weights of up to PER_T values per thread (loads issued together), k in order
+        float om[PER_T];
+        int ntake = 0;
+#pragma unroll
+        for (int u = 0; u < PER_T; ++u) {
+            const int k = kb + tid * PER_T + u;
+            om[u] = (k < k_hi) ? expf((m - __ldg(&S[k])) * P.lam_inv) : 0.0f;
+            eta_t += om[u];
+            ntake += om[u] > P.w_skip;
+        }
+        // block prefix sum of the per-thread counts (thread order = k order)
+        int incl = ntake;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) w_cnt[warp] = incl;
         __syncthreads();
-        int off = 0, tot = 0;
+        int off = incl - ntake, tot = 0;
         for (int w = 0; w < NW; ++w) {
-            if (w < warp) off += l_cnt[w];
-            tot += l_cnt[w];
+            if (w < warp) off += w_cnt[w];
+            tot += w_cnt[w];
         }
-        if (take) {
-            const int pos = off + __popc(bal & ((1u << lane) - 1u));
-            l_k[pos] = k;
-            l_w[pos] = om;
+#pragma unroll
+        for (int u = 0; u < PER_T; ++u) {
+            if (om[u] > P.w_skip) {     // tot <= PER_T * UPD_BLK = UPD_LIST: no overflow
+                l_k[off] = kb + tid * PER_T + u;
+                l_w[off] = om[u];
+                ++off;
+            }
         }
         __syncthreads();
+        const int nl = tot;
+        has |= (nl > 0);
         if (worker) {
-            for (int i = c; i < tot; i += C) {
+            for (int i = c; i < nl; i += C) {
                 const uint4 r = philox10(make_uint4((uint32_t)l_k[i], (uint32_t)p, iter, ctr3), P);
                 const float2 ze = box_muller(r.x, r.y), zo = box_muller(r.z, r.w);
                 const float w0 = l_w[i] * P.sig0, w1 = l_w[i] * P.sig1;
@@ -227,55 +247,66 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_update_kernel(
         }
         __syncthreads();
     }
-    // block normaliser (float64) and per-pair sums over the slots, in slot order
-    double eta = (double)eta_t;
+    // block normaliser (float within the block; FP64 math is slow on this part and
+    // is kept to the cross-block merge) and per-pair sums over the slots, in slot order
+    float eta_f = eta_t;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) eta += __shfl_xor_sync(0xffffffffu, eta, o);
-    if (lane == 0) red_d[warp] = eta;
+    for (int o = 16; o > 0; o >>= 1) eta_f += __shfl_xor_sync(0xffffffffu, eta_f, o);
+    if (lane == 0) red_f[warp] = eta_f;
     for (int j = tid; j < T2; j += UPD_BLK) acc_s[j] = 0.0f;
     __syncthreads();
-    eta = 0.0;
+    float eta = 0.0f;
 #pragma unroll
-    for (int w = 0; w < NW; ++w) eta += red_d[w];
-    for (int cc = 0; cc < C; ++cc) {
-        if (worker && c == cc) {
-            acc_s[4 * p] += a0;
-            acc_s[4 * p + 1] += a1;
-            if (2 * p + 1 < T) {
-                acc_s[4 * p + 2] += a2;
-                acc_s[4 * p + 3] += a3;
+    for (int w = 0; w < NW; ++w) eta += red_f[w];
+    if (has) {
+        for (int cc = 0; cc < C; ++cc) {
+            if (worker && c == cc) {
+                acc_s[4 * p] += a0;
+                acc_s[4 * p + 1] += a1;
+                if (2 * p + 1 < T) {
+                    acc_s[4 * p + 2] += a2;
+                    acc_s[4 * p + 3] += a3;
+                }
             }
+            __syncthreads();
         }
-        __syncthreads();
+        float* pa = part_acc + (size_t)blockIdx.x * T2;
+        for (int j = tid; j < T2; j += UPD_BLK) pa[j] = acc_s[j];
     }
-    float* pa = part_acc + (size_t)blockIdx.x * T2;
-    for (int j = tid; j < T2; j += UPD_BLK) pa[j] = acc_s[j];
-    if (tid == 0) part_eta[blockIdx.x] = eta;
+    if (tid == 0) {
+        part_eta[blockIdx.x] = (double)eta;
+        part_has[blockIdx.x] = has;
+    }
 
-    // the last block merges the non-empty partials in block order (float64)
+    // the last block merges the partials in block order (float64)
     __threadfence();
     __syncthreads();
     if (tid == 0) s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    // list of the blocks with a non-zero normaliser, in block order (G <= UPD_BLK)
-    const int G = gridDim.x;
-    __shared__ double s_eta[UPD_BLK];
-    const double e = (tid < G) ? __ldcg(&part_eta[tid]) : 0.0;
-    const unsigned bal = __ballot_sync(0xffffffffu, e > 0.0);
-    if (lane == 0) l_cnt[warp] = __popc(bal);
-    s_eta[tid] = e;
+    const int G = gridDim.x;            // <= UPD_BLK
+    const int hb = (tid < G) ? __ldcg(&part_has[tid]) : 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, hb != 0);
+    if (lane == 0) w_cnt[warp] = __popc(bal);
     __syncthreads();
     int off = 0, nz = 0;
     for (int w = 0; w < NW; ++w) {
-        if (w < warp) off += l_cnt[w];
-        nz += l_cnt[w];
+        if (w < warp) off += w_cnt[w];
+        nz += w_cnt[w];
     }
-    if (e > 0.0) l_k[off + __popc(bal & ((1u << lane) - 1u))] = tid;
+    if (hb) l_k[off + __popc(bal & ((1u << lane) - 1u))] = tid;
+    // eta = sum_b eta_b in float64 by warp 0 (fixed order: lane-strided, then a tree)
+    __shared__ double s_inv_eta;
+    if (warp == 0) {
+        double e_sum = 0.0;
+        for (int b = lane; b < G; b += 32) e_sum += __ldcg(&part_eta[b]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e_sum += __shfl_xor_sync(0xffffffffu, e_sum, o);
+        if (lane == 0) s_inv_eta = 1.0 / e_sum;
+    }
     __syncthreads();
-    double eta_all = 0.0;
-    for (int b = 0; b < G; ++b) eta_all += s_eta[b];
+    const double inv_eta = s_inv_eta;
     for (int j = tid; j < T2; j += UPD_BLK) {
         double A = 0.0;
         int i = 0;
@@ -288,7 +319,7 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_update_kernel(
         }
         for (; i < nz; ++i) A += (double)__ldcg(&part_acc[(size_t)l_k[i] * T2 + j]);
         const float lo = (j & 1) ? P.umin1 : P.umin0, hi = (j & 1) ? P.umax1 : P.umax0;
-        const float v = (float)((double)V[j] + A / eta_all);
+        const float v = (float)fma(A, inv_eta, (double)V[j]);
         if (!isfinite(v)) atomicOr(status, SMPPI_DEV_NUMERIC);
         V[j] = clampf(v, lo, hi);
     }
@@ -360,11 +391,11 @@ cudaError_t launch_rollout(const DevParams& P, bool dump, const float* x0, const
 
 cudaError_t launch_update(const DevParams& P, const float* S, const float* blk_min, int n_min,
                           float* V, uint32_t iter, uint32_t ctr3, const uint32_t* iter_dev,
-                          float* part_acc, double* part_eta, unsigned* ticket, unsigned* status,
-                          cudaStream_t st) {
+                          float* part_acc, double* part_eta, int* part_has, unsigned* ticket,
+                          unsigned* status, cudaStream_t st) {
     mppi_update_kernel<<<update_grid(P.K), UPD_BLK, 0, st>>>(P, S, blk_min, n_min, V, iter, ctr3,
-                                                             iter_dev, part_acc, part_eta, ticket,
-                                                             status);
+                                                             iter_dev, part_acc, part_eta,
+                                                             part_has, ticket, status);
     return cudaGetLastError();
 }
 
