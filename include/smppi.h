@@ -209,6 +209,24 @@ smppi_status smppi_shield_loop(smppi_handle* h, float* x0, float* V, float* V_sa
                                uint32_t iter0, uint32_t instance, int n_repair, int n_updates);
 
 /*
+ * smppi_step without any allocation, for callers that cannot allocate device
+ * memory: control loops that forbid allocation once running, or runtimes that
+ * own every device allocation.  (The paper has no counterpart; this is a
+ * deployment variant of smppi_step.)  Same arguments and results as smppi_step
+ * (no trajectory dump), but no handle: p is validated and used on every call,
+ * and the work is enqueued on `cuda_stream` (a cudaStream_t, NULL = legacy
+ * default stream).  Limits: K <= 65536 (SMPPI_ERR_ARG beyond, with a message
+ * for smppi_last_error(NULL)), T <= SMPPI_MAX_T, n_track <= SMPPI_MAX_TRACK.
+ * Scratch: one fixed 1.4 MB array per GPU inside the library, held until the
+ * process exits.  The first call on a device looks up that array's device
+ * address; make it before any stream capture.  Every call on a device shares
+ * the array and leaves its contents behind; calls that overlap on the GPU
+ * race on it.  Device-side NaN checks are not reported (NaN reaches V).
+ */
+smppi_status smppi_step_noalloc(const smppi_params* p, const float* x0, float* V, uint32_t iter,
+                                uint32_t instance, float* S_out, void* cuda_stream);
+
+/*
  * Per-kernel timing (CUDA events recorded on the handle's stream around each
  * kernel launch).  smppi_timing(h, 1) starts recording, (h, 0) stops it.
  * smppi_timing_read synchronises the stream, writes for each kernel kind k <

@@ -237,6 +237,13 @@ smppi_status enqueue_shield(smppi_handle* h, cudaStream_t st, float* x0, float* 
 
 }  // namespace
 
+// Parameter checks and derived constants for entry points without a handle.
+namespace smppi {
+smppi_status validate_params(const smppi_params* p) { return check_params(p); }
+DevParams derive_params(const smppi_params& p) { return derive(p); }
+smppi_status report_error(smppi_status s, const char* msg) { return fail(nullptr, s, msg); }
+}  // namespace smppi
+
 extern "C" {
 
 void smppi_default_params(smppi_params* p) {

@@ -73,4 +73,11 @@ cudaError_t launch_repair(const DevParams& P, const float4* seg, const float* in
 cudaError_t launch_apply(const DevParams& P, const ApplyArgs& ap, const float* V_exec,
                          cudaStream_t st);
 
+// Host helpers of the C ABI for entry points that have no handle: check a
+// parameter struct, derive the kernel constants, record the message that
+// smppi_last_error(NULL) returns.
+smppi_status validate_params(const smppi_params* p);
+DevParams derive_params(const smppi_params& p);
+smppi_status report_error(smppi_status s, const char* msg);
+
 }  // namespace smppi

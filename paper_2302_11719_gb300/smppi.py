@@ -67,6 +67,7 @@ _SIGS = {
     "smppi_shield_update": ([_vp, _vp, _vp, _vp, _u32, _u32, _i, _vp, _i], _i),
     "smppi_shield_loop": ([_vp, _vp, _vp, _vp, _u32, _u32, _i, _i], _i),
     "smppi_debug_noise": ([_vp, _u32, _u32, _i, _i, _vp, _vp], _i),
+    "smppi_step_noalloc": ([C.POINTER(Params), _vp, _vp, _u32, _u32, _vp, _vp], _i),
     "smppi_timing": ([_vp, _i], _i),
     "smppi_timing_read": ([_vp, C.POINTER(C.c_double), C.POINTER(C.c_int), _i], _i),
 }
@@ -207,6 +208,12 @@ def smppi_shield_loop(h, x0, V, V_safe, iter0, instance=0, n_repair=10, n_update
 def smppi_debug_noise(h, iter, instance, K, T, eps_out=None, raw_out=None):
     _check(load_library().smppi_debug_noise(h, iter, instance, K, T, _ptr(eps_out),
                                             _ptr(raw_out)), h)
+
+
+def smppi_step_noalloc(params: Params, x0, V, iter=0, instance=0, S_out=None, stream=None):
+    """smppi_step without a handle and without allocating (fixed in-library scratch)."""
+    _check(load_library().smppi_step_noalloc(C.byref(params), _ptr(x0), _ptr(V), iter, instance,
+                                             _ptr(S_out), _stream(stream)))
 
 
 def smppi_timing(h, enable: bool):
