@@ -209,6 +209,59 @@ smppi_status smppi_shield_loop(smppi_handle* h, float* x0, float* V, float* V_sa
                                uint32_t iter0, uint32_t instance, int n_repair, int n_updates);
 
 /*
+ * Batched Shield-MPPI: B independent control problems with their own K_i, T_i,
+ * centreline and state; one closed-loop update of all of them (Alg. 2 body per
+ * problem: sampling loop, OptimalControl, SafetyShield, ExecuteCommand on the
+ * disturbed system of Eq. 26, warm start) in ONE persistent launch over a
+ * device work queue of (problem, chunk of rollouts) items.  The block that
+ * finishes a problem's last chunk forms its V+, repairs it and steps its
+ * closed loop while the other blocks keep taking rollout items.
+ */
+typedef struct smppi_instance_desc {
+    int K, T, N_r;              /* rollouts, horizon, repair horizon of this problem */
+    int n_track;                /* centreline points (3..SMPPI_MAX_TRACK) */
+    float half_width;           /* w_T of Eq. 23 */
+    int track_offset;           /* first point of this problem in tracks_xy */
+    int V_offset;               /* first control of this problem in the V / V_safe arrays */
+} smppi_instance_desc;
+
+typedef struct smppi_batch smppi_batch;
+
+/* Create a batch.  `shared` supplies the parameters common to all problems
+ * (model, noise, temperature, cost weights, CBF alpha and C, Armijo settings,
+ * checkpoint, seed); its K, T, N_r, n_track, track_xy, half_width and max_seq
+ * are ignored.  desc [B] (host) describes each problem; tracks_xy (device)
+ * holds all centrelines back to back (2 floats per point), and must stay
+ * valid only during this call.  block_rollouts: rollouts per work item (64,
+ * 128 or 256), or 0 to let the autotuner pick it together with the grid at
+ * the first smppi_batch_step / smppi_batch_loop (it times one update of each
+ * candidate on a scratch copy of the state; the caller's arrays are untouched). */
+smppi_status smppi_batch_create(const smppi_params* shared, int B,
+                                const smppi_instance_desc* desc, const float* tracks_xy,
+                                int block_rollouts, void* cuda_stream, smppi_batch** out);
+smppi_status smppi_batch_destroy(smppi_batch* b);
+const char* smppi_batch_last_error(const smppi_batch* b);
+
+/* One closed-loop Shield-MPPI update of all B problems (device arrays):
+ *   x0 [B x 6] in/out; V in/out (nominal -> warm start shift(V+)); V_safe out
+ *   (the repaired sequences); both indexed by desc[i].V_offset, T_i x 2 each;
+ *   iter: update index (Philox counter word and disturbance index);
+ *   n_repair: Armijo repair iterations per problem (0 = plain MPPI with the
+ *   DCBF cost, V_safe = V+). */
+smppi_status smppi_batch_step(smppi_batch* b, float* x0, float* V, float* V_safe,
+                              uint32_t iter, int n_repair);
+
+/* n_updates closed-loop updates replayed from a CUDA graph (iter = iter0 ..). */
+smppi_status smppi_batch_loop(smppi_batch* b, float* x0, float* V, float* V_safe,
+                              uint32_t iter0, int n_repair, int n_updates);
+
+/* Synchronise the batch stream and read / clear its device status word. */
+smppi_status smppi_batch_sync_status(smppi_batch* b, uint32_t* bits_out);
+
+/* The launch shape in use (after autotuning): rollouts per item and grid size. */
+smppi_status smppi_batch_config(const smppi_batch* b, int* block_rollouts, int* grid);
+
+/*
  * smppi_step without any allocation, for callers that cannot allocate device
  * memory: control loops that forbid allocation once running, or runtimes that
  * own every device allocation.  (The paper has no counterpart; this is a

@@ -360,6 +360,23 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return false;
 }
 
+// One sampled rollout step (Alg. 2 inner loop): u = v + eps, control term
+// gamma v' Sigma^-1 u, x <- f(x, clamp(u)), project on the track, add q and the
+// DCBF penalty (Eq. 12, 17-20).
+__device__ __forceinline__ void rollout_step(const DevParams& P, const float4* seg,
+                                             const float* inv, float2 v, float2 z, State& x,
+                                             int& s, float& h_prev, float& acc) {
+    const float u0 = fmaf(P.sig0, z.x, v.x), u1 = fmaf(P.sig1, z.y, v.y);
+    acc = fmaf(P.gis0 * v.x, u0, acc);
+    acc = fmaf(P.gis1 * v.y, u1, acc);
+    model_step(P, x, clampf(u0, P.umin0, P.umax0), clampf(u1, P.umin1, P.umax1));
+    float d2;
+    s = track_follow(seg, inv, P.n_track, s, x.X, x.Y, d2);
+    const float h = P.w2 - d2;
+    acc += run_cost(P, x.vx, d2) + P.C_cbf * fmaxf(cbf_arg(P, h_prev, h), 0.0f);
+    h_prev = h;
+}
+
 // Warp-level argmin of (d2, index) with lowest index on ties.
 __device__ __forceinline__ void warp_argmin(float& d, int& i) {
 #pragma unroll

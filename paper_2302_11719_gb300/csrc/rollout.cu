@@ -64,21 +64,6 @@ __device__ __forceinline__ void stage_problem(const DevParams& P, const float4* 
     __syncthreads();
 }
 
-// One rollout step: perturb, clamp, integrate, project on the track, add cost.
-__device__ __forceinline__ void rollout_step(const DevParams& P, const float4* seg,
-                                             const float* inv, float2 v, float2 z, State& x,
-                                             int& s, float& h_prev, float& acc) {
-    const float u0 = fmaf(P.sig0, z.x, v.x), u1 = fmaf(P.sig1, z.y, v.y);
-    acc = fmaf(P.gis0 * v.x, u0, acc);
-    acc = fmaf(P.gis1 * v.y, u1, acc);
-    model_step(P, x, clampf(u0, P.umin0, P.umax0), clampf(u1, P.umin1, P.umax1));
-    float d2;
-    s = track_follow(seg, inv, P.n_track, s, x.X, x.Y, d2);
-    const float h = P.w2 - d2;
-    acc += run_cost(P, x.vx, d2) + P.C_cbf * fmaxf(cbf_arg(P, h_prev, h), 0.0f);
-    h_prev = h;
-}
-
 template <bool DUMP>
 __device__ __forceinline__ void dump_state(float* traj, int k, int T, int t, const State& x) {
     if (DUMP) {

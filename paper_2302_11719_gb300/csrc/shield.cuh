@@ -1,0 +1,319 @@
+// Safety-shield building blocks shared by the repair kernels and the batched
+// persistent kernel: the deterministic rollout cost of Eq. 22 (and of the
+// running + CBF cost), its reverse-mode adjoint with checkpointing, the
+// block-level repair of one sequence (Alg. 1 with Armijo backtracking) and the
+// closed-loop step (Alg. 2 ExecuteCommand + warm start, Eq. 26).
+#pragma once
+
+#include "kernels.cuh"
+
+namespace smppi {
+namespace {
+
+struct Tape {
+    float* base;
+    int ms, seq;
+    __device__ __forceinline__ float& at(int slot, int f) const {
+        return base[((size_t)slot * NFIELD + f) * ms + seq];
+    }
+    __device__ __forceinline__ void put(int slot, const State& x, int s, float h, float hp) const {
+        at(slot, 0) = x.vx; at(slot, 1) = x.vy; at(slot, 2) = x.r;
+        at(slot, 3) = x.X; at(slot, 4) = x.Y; at(slot, 5) = x.psi;
+        at(slot, 6) = x.cp; at(slot, 7) = x.sp;
+        at(slot, 8) = __int_as_float(s); at(slot, 9) = h; at(slot, 10) = hp;
+    }
+    __device__ __forceinline__ void get(int slot, State& x, int& s, float& h, float& hp) const {
+        x.vx = at(slot, 0); x.vy = at(slot, 1); x.r = at(slot, 2);
+        x.X = at(slot, 3); x.Y = at(slot, 4); x.psi = at(slot, 5);
+        x.cp = at(slot, 6); x.sp = at(slot, 7);
+        s = __float_as_int(at(slot, 8)); h = at(slot, 9); hp = at(slot, 10);
+    }
+};
+
+__device__ __forceinline__ float2 clamp2(const DevParams& P, float2 v) {
+    return make_float2(clampf(v.x, P.umin0, P.umax0), clampf(v.y, P.umin1, P.umax1));
+}
+
+// Direct derivative of the cost terms at x_t (segment s, h_{t-1}, h_t, h_{t+1}):
+//   w_run dq/dx_t + w_cbf C [act(t-1,t) (-dh_t/dx_t) + act(t,t+1) (1-alpha) dh_t/dx_t],
+// dh/d(X,Y) = -2 r, dq/d(X,Y) = (q_d / w^2) 2 r, dq/dv_x = 2 q_v (v_x - v_target).
+__device__ __forceinline__ void add_direct(const DevParams& P, const float4* seg, const float* inv,
+                                           const State& x, int s, bool act_prev, bool act_next,
+                                           float w_run, float w_cbf, State& lam) {
+    const float2 r = seg_offset(seg, inv, s, x.X, x.Y);
+    float ch = 0.0f;
+    if (act_prev) ch -= w_cbf * P.C_cbf;
+    if (act_next) ch += w_cbf * P.C_cbf * P.one_m_alpha;
+    // dJ/d(e_y^2) = w_run q_d / w^2 - ch  (since h = w^2 - e_y^2)
+    const float cd2 = 2.0f * (w_run * P.qd_w2 - ch);
+    lam.X += cd2 * r.x;
+    lam.Y += cd2 * r.y;
+    lam.vx += w_run * 2.0f * P.q_v * (x.vx - P.v_target);
+}
+
+// Forward rollout of u_t = clamp(Vw_t - step G_t) for N steps from x0 (segment s0).
+// Returns J in float64 and, when STORE, fills the tape (every state when
+// ck <= 0, else every ck-th).  dec_out (optional) = sum_t G_t . (Vw_t - u'_t)
+// where u'_t = clip(Vw_t - step G_t) (the Armijo decrease term).  The terms are
+// summed in float32 over blocks of 16 steps and the block sums in float64
+// (FP64 arithmetic is slow on this part; one FP64 add per 16 steps).
+template <bool STORE, bool TRIAL>
+__device__ double forward_cost(const DevParams& P, const float4* seg, const float* inv,
+                               const State& x0, int s0, int N, const float2* Vw, const float2* G,
+                               float step, int ms, int seq, float w_run, float w_cbf, int ck,
+                               const Tape& tape, double* dec_out) {
+    State x = x0;
+    int s = s0;
+    float d2 = seg_d2(seg, inv, s, x.X, x.Y);
+    float h_prev = P.w2 - d2, h_pp = h_prev;
+    double J = (double)(w_run * run_cost(P, x.vx, d2));
+    double dec = 0.0;
+    float Jf = 0.0f, decf = 0.0f;
+    const float wc = w_cbf * P.C_cbf;
+    const bool full = ck <= 0;
+    for (int t = 0; t < N; ++t) {
+        if (STORE) {
+            if (full) tape.put(t, x, s, h_prev, h_pp);
+            else if (t % ck == 0) tape.put(t / ck, x, s, h_prev, h_pp);
+        }
+        float2 v = Vw[(size_t)t * ms + seq];
+        float2 u;
+        if (TRIAL) {
+            const float2 g = G[(size_t)t * ms + seq];
+            u = clamp2(P, make_float2(fmaf(-step, g.x, v.x), fmaf(-step, g.y, v.y)));
+            decf = fmaf(g.x, v.x - u.x, fmaf(g.y, v.y - u.y, decf));
+        } else {
+            u = clamp2(P, v);
+        }
+        model_step(P, x, u.x, u.y);
+        s = track_follow(seg, inv, P.n_track, s, x.X, x.Y, d2);
+        const float h = P.w2 - d2;
+        if (w_run != 0.0f) Jf = fmaf(w_run, run_cost(P, x.vx, d2), Jf);
+        const float a = cbf_arg(P, h_prev, h);
+        if (a > 0.0f) Jf = fmaf(wc, a, Jf);
+        h_pp = h_prev;
+        h_prev = h;
+        if ((t & 15) == 15) {
+            J += (double)Jf;
+            dec += (double)decf;
+            Jf = 0.0f;
+            decf = 0.0f;
+        }
+    }
+    J += (double)Jf;
+    dec += (double)decf;
+    if (STORE && full) tape.put(N, x, s, h_prev, h_pp);
+    if (dec_out) *dec_out = dec;
+    return J;
+}
+
+// Cost and gradient of one sequence (forward with tape + backward adjoint).
+// Writes G_t = dJ/dv_t for t < N (0 for N <= t < T).
+__device__ double seq_cost_grad(const DevParams& P, const float4* seg, const float* inv,
+                                const State& x0, int s0, int N, int T, const float2* Vw, float2* G,
+                                int ms, int seq, float w_run, float w_cbf, int ck,
+                                const Tape& tape) {
+    const double J = forward_cost<true, false>(P, seg, inv, x0, s0, N, Vw, nullptr, 0.0f, ms, seq,
+                                               w_run, w_cbf, ck, tape, nullptr);
+    for (int t = N; t < T; ++t) G[(size_t)t * ms + seq] = make_float2(0.0f, 0.0f);
+    if (N == 0) return J;
+    const bool full = ck <= 0;
+    const int nck = full ? 1 : (N + ck - 1) / ck;
+    const int rb = full ? 0 : nck;  // first slot of the recomputed segment
+    State lam = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int c = nck - 1; c >= 0; --c) {
+        const int t0 = full ? 0 : c * ck;
+        const int t1 = full ? N : min(t0 + ck, N);
+        if (!full) {
+            // recompute states t0..t1 from checkpoint c
+            State x;
+            int s;
+            float h, hp;
+            tape.get(c, x, s, h, hp);
+            tape.put(rb, x, s, h, hp);
+            for (int i = 1; i <= t1 - t0; ++i) {
+                const float2 u = clamp2(P, Vw[(size_t)(t0 + i - 1) * ms + seq]);
+                model_step(P, x, u.x, u.y);
+                float d2;
+                s = track_follow(seg, inv, P.n_track, s, x.X, x.Y, d2);
+                hp = h;
+                h = P.w2 - d2;
+                tape.put(rb + i, x, s, h, hp);
+            }
+        }
+        if (c == nck - 1) {
+            // lambda_N = direct term at x_N (only the pair (N-1, N))
+            State x;
+            int s;
+            float h, hp;
+            tape.get(rb + (t1 - t0), x, s, h, hp);
+            add_direct(P, seg, inv, x, s, cbf_arg(P, hp, h) > 0.0f, false, w_run, w_cbf, lam);
+        }
+        for (int t = t1 - 1; t >= t0; --t) {
+            const int i = rb + (t - t0);
+            State x;
+            int s;
+            float h, hp;
+            tape.get(i, x, s, h, hp);
+            const float h_next = tape.at(i + 1, 9);
+            const float2 v = Vw[(size_t)t * ms + seq];
+            const float2 u = clamp2(P, v);
+            float gd, ga;
+            model_step_adjoint(P, x, u.x, u.y, lam, &gd, &ga);
+            const bool in0 = v.x >= P.umin0 && v.x <= P.umax0;
+            const bool in1 = v.y >= P.umin1 && v.y <= P.umax1;
+            G[(size_t)t * ms + seq] = make_float2(in0 ? gd : 0.0f, in1 ? ga : 0.0f);
+            if (t >= 1)
+                add_direct(P, seg, inv, x, s, cbf_arg(P, hp, h) > 0.0f,
+                           cbf_arg(P, h, h_next) > 0.0f, w_run, w_cbf, lam);
+        }
+    }
+    return J;
+}
+
+// Closed-loop step (Alg. 2 ExecuteCommand + warm start, Eq. 26), one thread:
+// x0 <- f(x0, clamp(v_exec)) + w_n, V <- shift(V).
+__device__ void closed_loop_step(const DevParams& P, const ApplyArgs& ap, float2 v_exec) {
+    const uint32_t nn = ap.n + (ap.iter_dev ? *ap.iter_dev : 0u);
+    State x = make_state(ap.x0);
+    model_step(P, x, clampf(v_exec.x, P.umin0, P.umax0), clampf(v_exec.y, P.umin1, P.umax1));
+    const uint4 r = philox10(make_uint4(0u, 0u, nn, ap.ctr3), P);
+    const float2 z = box_muller(r.x, r.y);
+    ap.x0[0] = x.vx;
+    ap.x0[1] = fmaf(P.dsig0, z.x, x.vy);
+    ap.x0[2] = fmaf(P.dsig1, z.y, x.r);
+    ap.x0[3] = x.X;
+    ap.x0[4] = x.Y;
+    ap.x0[5] = x.psi;
+    float2* V = reinterpret_cast<float2*>(ap.V);
+    for (int t = 0; t + 1 < P.T; ++t) V[t] = V[t + 1];
+    if (ap.iter_dev) *ap.iter_dev += 1u;
+}
+
+
+// Shared-memory scratch of repair_in_block.
+struct RepairSmem {
+    double P;
+    float red[32];
+    float step;
+    int ok;
+};
+
+// Safety shield of one sequence by one block of BLK threads (Alg. 1 with
+// Armijo backtracking, mode 1; fixed step, mode 0).  seg / inv: the staged
+// track; Vw [T]: the controls, repaired in place; G [T], tape_s [(T+2) NFIELD]:
+// shared-memory scratch.  The Armijo trial steps s, s/2, s/4, ... are
+// evaluated in parallel by the lanes of warp 0 (lane j: s 2^-j) and the
+// largest accepted step is taken: the same iterate as sequential backtracking.
+// The gradient comes from thread 0 (seq_cost_grad).  merit_row (optional):
+// n_iters + 1 merits; *iters_done: iterations run.  Returns the final merit.
+template <int BLK>
+__device__ double repair_in_block(const DevParams& P, const float4* seg, const float* inv,
+                                  const State& x0, int s0, float2* Vw, float2* G, float* tape_s,
+                                  int n_iters, int mode, float delta, int ck, double* merit_row,
+                                  int* iters_done, unsigned* status, RepairSmem& sm) {
+    const int T = P.T, N = P.N_r;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = BLK / 32;
+    const Tape tape{tape_s, 1, 0};
+    if (tid == 0)
+        sm.P = forward_cost<false, false>(P, seg, inv, x0, s0, N, Vw, nullptr, 0.0f, 1, 0, 0.0f,
+                                          1.0f, 0, tape, nullptr);
+    __syncthreads();
+    double P0 = sm.P;
+    int it = 0;
+    bool stalled = false;
+    for (; it < n_iters; ++it) {
+        if (tid == 0 && merit_row) merit_row[it] = P0;
+        if (P0 == 0.0) break;
+        if (tid == 0) seq_cost_grad(P, seg, inv, x0, s0, N, T, Vw, G, 1, 0, 0.0f, 1.0f, ck, tape);
+        __syncthreads();
+        if (mode == 0) {
+            for (int t = tid; t < N; t += BLK)
+                Vw[t] = clamp2(P, make_float2(fmaf(-delta, G[t].x, Vw[t].x),
+                                              fmaf(-delta, G[t].y, Vw[t].y)));
+            __syncthreads();
+            if (tid == 0)
+                sm.P = forward_cost<false, false>(P, seg, inv, x0, s0, N, Vw, nullptr, 0.0f, 1, 0,
+                                                  0.0f, 1.0f, 0, tape, nullptr);
+            __syncthreads();
+            P0 = sm.P;
+            continue;
+        }
+        // |g|_inf
+        float gm = 0.0f;
+        for (int t = tid; t < N; t += BLK) gm = fmaxf(gm, fmaxf(fabsf(G[t].x), fabsf(G[t].y)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+        if (lane == 0) sm.red[warp] = gm;
+        __syncthreads();
+        gm = sm.red[0];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) gm = fmaxf(gm, sm.red[w]);
+        if (!(gm > 0.0f)) { stalled = true; break; }
+        const float s_first = P.ls_s0 / gm;
+        if (warp == 0) {
+            // lane j tries s_first 2^-j (j = lane, lane + 32, ...); keep the smallest accepted j
+            int best = 0x7fffffff;
+            double best_P = 0.0;
+            for (int j = lane; j < P.ls_max; j += 32) {
+                const float sj = ldexpf(s_first, -j);
+                double dec;
+                const double Pt = forward_cost<false, true>(P, seg, inv, x0, s0, N, Vw, G, sj, 1,
+                                                            0, 0.0f, 1.0f, 0, tape, &dec);
+                if (Pt <= P0 - (double)P.ls_c * dec && j < best) { best = j; best_P = Pt; }
+            }
+            int bj = best;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) bj = min(bj, __shfl_xor_sync(0xffffffffu, bj, o));
+            if (best == bj && bj != 0x7fffffff) {   // the owning lane publishes
+                sm.P = best_P;
+                sm.step = ldexpf(s_first, -bj);
+            }
+            if (lane == 0) sm.ok = (bj != 0x7fffffff);
+        }
+        __syncthreads();
+        if (!sm.ok) { stalled = true; break; }
+        const float sa = sm.step;
+        for (int t = tid; t < N; t += BLK)
+            Vw[t] = clamp2(P, make_float2(fmaf(-sa, G[t].x, Vw[t].x), fmaf(-sa, G[t].y, Vw[t].y)));
+        __syncthreads();
+        P0 = sm.P;
+    }
+    if (tid == 0) {
+        if (merit_row)
+            for (int i = it; i <= n_iters; ++i) merit_row[i] = P0;
+        if (iters_done) *iters_done = it;
+        if (stalled) atomicOr(status, SMPPI_DEV_STALLED);
+        if (!isfinite(P0)) atomicOr(status, SMPPI_DEV_NUMERIC);
+    }
+    __syncthreads();
+    return P0;
+}
+
+// Nearest segment of (X, Y) over the whole track by one block (lowest index on
+// ties); every thread gets the result.
+template <int BLK>
+__device__ int block_nearest_segment(const float4* seg, const float* inv, int n, float X, float Y,
+                                     float* red_f, int* red_i, float* d2_out) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float bd = 3.0e38f;
+    int bi = 0x7fffffff;
+    for (int i = tid; i < n; i += BLK) {
+        const float d = seg_d2(seg, inv, i, X, Y);
+        if (d < bd) { bd = d; bi = i; }
+    }
+    warp_argmin(bd, bi);
+    if (lane == 0) { red_f[warp] = bd; red_i[warp] = bi; }
+    __syncthreads();
+    bd = red_f[0];
+    bi = red_i[0];
+    for (int w = 1; w < BLK / 32; ++w)
+        if (red_f[w] < bd || (red_f[w] == bd && red_i[w] < bi)) { bd = red_f[w]; bi = red_i[w]; }
+    __syncthreads();
+    if (d2_out) *d2_out = bd;
+    return bi;
+}
+
+}  // namespace
+}  // namespace smppi

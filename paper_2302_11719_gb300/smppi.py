@@ -51,6 +51,11 @@ class Params(C.Structure):
     ]
 
 
+class InstanceDesc(C.Structure):
+    _fields_ = [("K", C.c_int), ("T", C.c_int), ("N_r", C.c_int), ("n_track", C.c_int),
+                ("half_width", C.c_float), ("track_offset", C.c_int), ("V_offset", C.c_int)]
+
+
 _vp, _i, _u32, _f, _dp = C.c_void_p, C.c_int, C.c_uint32, C.c_float, C.c_void_p
 
 _SIGS = {
@@ -68,6 +73,14 @@ _SIGS = {
     "smppi_shield_loop": ([_vp, _vp, _vp, _vp, _u32, _u32, _i, _i], _i),
     "smppi_debug_noise": ([_vp, _u32, _u32, _i, _i, _vp, _vp], _i),
     "smppi_step_noalloc": ([C.POINTER(Params), _vp, _vp, _u32, _u32, _vp, _vp], _i),
+    "smppi_batch_create": ([C.POINTER(Params), _i, C.POINTER(InstanceDesc), _vp, _i, _vp,
+                            C.POINTER(_vp)], _i),
+    "smppi_batch_destroy": ([_vp], _i),
+    "smppi_batch_last_error": ([_vp], C.c_char_p),
+    "smppi_batch_step": ([_vp, _vp, _vp, _vp, _u32, _i], _i),
+    "smppi_batch_loop": ([_vp, _vp, _vp, _vp, _u32, _i, _i], _i),
+    "smppi_batch_sync_status": ([_vp, C.POINTER(_u32)], _i),
+    "smppi_batch_config": ([_vp, C.POINTER(_i), C.POINTER(_i)], _i),
     "smppi_timing": ([_vp, _i], _i),
     "smppi_timing_read": ([_vp, C.POINTER(C.c_double), C.POINTER(C.c_int), _i], _i),
 }
@@ -214,6 +227,83 @@ def smppi_step_noalloc(params: Params, x0, V, iter=0, instance=0, S_out=None, st
     """smppi_step without a handle and without allocating (fixed in-library scratch)."""
     _check(load_library().smppi_step_noalloc(C.byref(params), _ptr(x0), _ptr(V), iter, instance,
                                              _ptr(S_out), _stream(stream)))
+
+
+def _bcheck(status, b=None):
+    if status != OK:
+        msg = load_library().smppi_batch_last_error(b)
+        raise SmppiError(status, msg.decode() if msg else "")
+
+
+def smppi_batch_create(shared: Params, descs, tracks_xy, block_rollouts=0, stream=None) -> int:
+    n = len(descs)
+    arr = (InstanceDesc * n)(*descs)
+    b = C.c_void_p()
+    _bcheck(load_library().smppi_batch_create(C.byref(shared), n, arr, _ptr(tracks_xy),
+                                              int(block_rollouts), _stream(stream), C.byref(b)))
+    return b.value
+
+
+def smppi_batch_destroy(b):
+    _bcheck(load_library().smppi_batch_destroy(b))
+
+
+def smppi_batch_step(b, x0, V, V_safe, iter, n_repair=10):
+    _bcheck(load_library().smppi_batch_step(b, _ptr(x0), _ptr(V), _ptr(V_safe), iter, n_repair), b)
+
+
+def smppi_batch_loop(b, x0, V, V_safe, iter0, n_repair=10, n_updates=1):
+    _bcheck(load_library().smppi_batch_loop(b, _ptr(x0), _ptr(V), _ptr(V_safe), iter0, n_repair,
+                                            n_updates), b)
+
+
+def smppi_batch_sync_status(b) -> tuple[int, int]:
+    bits = C.c_uint32()
+    st = load_library().smppi_batch_sync_status(b, C.byref(bits))
+    return st, bits.value
+
+
+def smppi_batch_config(b) -> tuple[int, int]:
+    rb, grid = C.c_int(), C.c_int()
+    _bcheck(load_library().smppi_batch_config(b, C.byref(rb), C.byref(grid)), b)
+    return rb.value, grid.value
+
+
+class Batch:
+    """Owns a batch handle for an inputs.InstanceBatch (device copies of tracks,
+    x0, V, V_safe laid out back to back)."""
+
+    def __init__(self, ib, block_rollouts=0, device="cuda", stream=None):
+        self.device = torch.device(device)
+        B = len(ib.params)
+        self.B = B
+        self.T = [int(t) for t in ib.T]
+        self.V_off = np.concatenate([[0], np.cumsum(self.T)[:-1]]).astype(int)
+        n_tr = ib.tracks.shape[1]
+        self.tracks = torch.as_tensor(np.ascontiguousarray(ib.tracks.reshape(-1, 2), np.float32),
+                                      device=self.device)
+        descs = [InstanceDesc(int(ib.K[i]), self.T[i], self.T[i], n_tr, float(ib.w[i]),
+                              i * n_tr, int(self.V_off[i])) for i in range(B)]
+        self.shared = params_from_dict(ib.params[0], self.tracks)
+        self.b = smppi_batch_create(self.shared, descs, self.tracks, block_rollouts, stream)
+        self.x0 = torch.as_tensor(np.ascontiguousarray(ib.x0, np.float32), device=self.device)
+        self.V = torch.zeros((sum(self.T), 2), dtype=torch.float32, device=self.device)
+        self.V_safe = torch.zeros_like(self.V)
+
+    def split(self, t):
+        a = t.detach().cpu().numpy()
+        return [a[o:o + T] for o, T in zip(self.V_off, self.T)]
+
+    def close(self):
+        if self.b:
+            smppi_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def smppi_timing(h, enable: bool):
