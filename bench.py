@@ -330,12 +330,200 @@ def run_ours(args):
     return 0
 
 
+def _timed_steps(fn, steps, flush):
+    """Per-step CUDA-event times (ms) of fn(i), L2 flushed before each step."""
+    import torch
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.zero_()
+        e0[i].record()
+        fn(i)
+        e1[i].record()
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(e0, e1)]
+
+
+def run_batch(args):
+    """512 uneven Shield-MPPI problems: one persistent launch per closed-loop
+    update vs 512 separate per-problem updates on one stream."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_2302_11719_gb300 import inputs as I
+    from paper_2302_11719_gb300 import smppi as S
+    __graft_entry__.build()
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ib = I.uneven_instances(512, seed=0)
+    B, n_rep = len(ib.params), N_REPAIR
+    bt = S.Batch(ib, block_rollouts=0, device=dev)
+    it = 0
+    for _ in range(args.warmup):
+        S.smppi_batch_step(bt.b, bt.x0, bt.V, bt.V_safe, it, n_rep)
+        it += 1
+    S.smppi_batch_sync_status(bt.b)
+    rb, grid = S.smppi_batch_config(bt.b)
+
+    def batched(i):
+        S.smppi_batch_step(bt.b, bt.x0, bt.V, bt.V_safe, it + i, n_rep)
+    t_b = _timed_steps(batched, args.steps, flush)
+    it += args.steps
+    # graph replays of the whole closed loop (no flush between replays)
+    n_loop = args.loop_updates
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    S.smppi_batch_loop(bt.b, bt.x0, bt.V, bt.V_safe, it, n_rep, 1)
+    torch.cuda.synchronize()
+    a0.record()
+    S.smppi_batch_loop(bt.b, bt.x0, bt.V, bt.V_safe, it, n_rep, n_loop)
+    a1.record()
+    torch.cuda.synchronize()
+    t_loop = a0.elapsed_time(a1)
+    st_b = S.smppi_batch_sync_status(bt.b)
+    # the same problems as 512 separate per-problem updates (handle path)
+    ctls, states = [], []
+    for i in range(B):
+        c = S.Controller(ib.params[i], ib.tracks[i], device=dev)
+        ctls.append(c)
+        states.append((c.tensor(ib.x0[i]), c.tensor(np.zeros((c.T, 2), np.float32)),
+                       torch.empty((c.T, 2), device=dev)))
+
+    def plain(i):
+        for j in range(B):
+            x0, V, Vs = states[j]
+            S.smppi_shield_update(ctls[j].h, x0, V, Vs, i, j, n_rep)
+    for w in range(2):
+        plain(w)
+    torch.cuda.synchronize()
+    t_p = _timed_steps(lambda i: plain(100 + i), max(3, args.steps // 4), flush)
+    for c in ctls:
+        c.close()
+    rs_b = sum(int(k) * int(t) for k, t in zip(ib.K, ib.T))
+    line = {
+        "workload": "batched Shield-MPPI, 512 problems, K log-uniform [64, 16384], T in [20, 150], "
+                    "ellipses 10-40 m, w in [1.5, 3] m, %d repair iterations, closed loop" % n_rep,
+        "metric": "control updates/s", "unit": "updates/s",
+        "batched": {"value": B * args.steps / (sum(t_b) / 1e3), "ms_per_update_all": float(np.median(t_b)),
+                    "rollout_steps_per_s": rs_b * args.steps / (sum(t_b) / 1e3),
+                    "block_rollouts": rb, "grid": grid, "l2": "flushed between steps"},
+        "batched_graph_loop": {"value": B * n_loop / (t_loop / 1e3), "updates": n_loop,
+                               "ms_per_update_all": t_loop / n_loop, "l2": "not flushed",
+                               "status": st_b[0]},
+        "plain_per_problem": {"value": B * len(t_p) / (sum(t_p) / 1e3),
+                              "ms_per_update_all": float(np.median(t_p)),
+                              "launches_per_update": 2 * B + B, "l2": "flushed between steps"},
+        "speedup": (B * args.steps / (sum(t_b) / 1e3)) / (B * len(t_p) / (sum(t_p) / 1e3)),
+    }
+    print(json.dumps(line), flush=True)
+    bt.close()
+    return 0
+
+
+def run_sweep(args):
+    """One MPPI iteration (rollouts + update) for K x T on the single-problem workload."""
+    import torch
+
+    import __graft_entry__
+    from paper_2302_11719_gb300 import inputs as I
+    from paper_2302_11719_gb300 import smppi as S
+    __graft_entry__.build()
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    rows = []
+    for K in (4096, 16384, 65536, 262144):
+        for T in (50, 100, 200):
+            pr = I.throughput_problem(K, T)
+            ctl = S.Controller(pr.params, pr.track, device=dev)
+            x0, V0 = ctl.tensor(pr.x0), ctl.tensor(pr.V)
+            Vb = [V0.clone() for _ in range(args.steps + args.warmup)]
+            for i in range(args.warmup):
+                S.smppi_step(ctl.h, x0, Vb[i], i, 0)
+            S.smppi_timing(ctl.h, True)
+            t = _timed_steps(lambda i: S.smppi_step(ctl.h, x0, Vb[args.warmup + i], i, 0),
+                             args.steps, flush)
+            S.smppi_timing(ctl.h, False)
+            kt = S.smppi_timing_read(ctl.h)
+            roll_s = kt["rollout"][0] / kt["rollout"][1] / 1e3
+            upd_s = kt["update"][0] / kt["update"][1] / 1e3
+            step_s = sum(t) / len(t) / 1e3
+            ach = F_ALG * K * T / roll_s / 1e12
+            rows.append({"K": K, "T": T, "us_per_update": step_s * 1e6,
+                         "rollout_steps_per_s": K * T / step_s,
+                         "rollout_kernel_us": roll_s * 1e6, "update_kernel_us": upd_s * 1e6,
+                         "fp32_tflops": ach, "fp32_frac": ach / FP32_PEAK_TFLOPS})
+            ctl.close()
+    print(json.dumps({"workload": "MPPI iteration sweep (rollouts + softmin update)",
+                      "peak_tflops": FP32_PEAK_TFLOPS, "flops_per_rollout_step": F_ALG,
+                      "l2": "flushed between steps", "rows": rows}), flush=True)
+    return 0
+
+
+def run_grad(args):
+    """8192 near-boundary sequences, T = 100: adjoint gradient (checkpoint every
+    10 steps vs full tape) and 20 Armijo repair iterations."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_2302_11719_gb300 import inputs as I
+    from paper_2302_11719_gb300 import smppi as S
+    __graft_entry__.build()
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    sb = I.near_boundary_sequences(8192, 100, seed=0)
+    n = sb.x0.shape[0]
+    ctl = S.Controller(sb.params, sb.track, max_seq=n, checkpoint=10, device=dev)
+    x0, V = ctl.tensor(sb.x0), ctl.tensor(sb.V)
+    J = torch.empty(n, dtype=torch.float64, device=dev)
+    g = torch.empty_like(V)
+    out = {}
+    for name, ck in (("checkpoint_10", 10), ("full_tape", -1)):
+        for _ in range(args.warmup):
+            S.smppi_cost_grad(ctl.h, n, x0, V, 100, 0.0, 1.0, ck, J, g)
+        t = _timed_steps(lambda i: S.smppi_cost_grad(ctl.h, n, x0, V, 100, 0.0, 1.0, ck, J, g),
+                         args.steps, flush)
+        out[name] = {"us_per_call": 1e3 * sum(t) / len(t),
+                     "sequence_steps_per_s": n * 100 / (sum(t) / len(t) / 1e3)}
+    Vout = torch.empty_like(V)
+    its = torch.empty(n, dtype=torch.int32, device=dev)
+    mer = torch.empty((n, 21), dtype=torch.float64, device=dev)
+    for _ in range(2):
+        S.smppi_repair(ctl.h, n, x0, V, Vout, 20, 1, 0.0, mer, its)
+    t = _timed_steps(lambda i: S.smppi_repair(ctl.h, n, x0, V, Vout, 20, 1, 0.0, mer, its),
+                     max(3, args.steps // 4), flush)
+    ctl.sync_status()
+    iters = its.cpu().numpy()
+    m = mer.cpu().numpy()
+    out["repair_20"] = {"us_per_call": 1e3 * sum(t) / len(t),
+                        "mean_iterations_run": float(iters.mean()),
+                        "us_per_iteration_run": 1e3 * sum(t) / len(t) / max(1.0, iters.max()),
+                        "merit_before_mean": float(m[:, 0].mean()),
+                        "merit_after_mean": float(m[:, -1].mean()),
+                        "sequences_safe_after": int((m[:, -1] == 0).sum())}
+    ctl.close()
+    # a plain MPPI iteration of the same size (K = 8192 rollouts, T = 100)
+    pr = I.throughput_problem(8192, 100)
+    c2 = S.Controller(pr.params, pr.track, device=dev)
+    x0p, Vp = c2.tensor(pr.x0), c2.tensor(pr.V)
+    t = _timed_steps(lambda i: S.smppi_step(c2.h, x0p, Vp.clone(), i, 0), args.steps, flush)
+    out["plain_mppi_step_K8192_T100_us"] = 1e3 * sum(t) / len(t)
+    c2.close()
+    print(json.dumps({"workload": "adjoint gradient and repair, 8192 sequences, T=100",
+                      "results": out, "l2": "flushed between calls"}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="shield", choices=["shield", "batch", "sweep", "grad"])
+    ap.add_argument("--loop-updates", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -343,6 +531,12 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
+    if args.workload == "grad":
+        return run_grad(args)
     return run_ours(args)
 
 
