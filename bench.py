@@ -36,7 +36,7 @@ UNIT = "rollout-steps/s"
 K_ROLL, T_HOR, N_REPAIR = 65536, 100, 10
 # FP32 flops of one rollout step (FMA = 2), hand count of the forward model,
 # noise, track projection and cost; see the design notes.
-F_ALG = 310
+F_ALG = 280
 # FP32 peak: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (maximum SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
