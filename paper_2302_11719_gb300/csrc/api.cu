@@ -133,7 +133,7 @@ DevParams derive(const smppi_params& p) {
         d.rk1[i] = d.key1 + (uint32_t)i * 0xBB67AE85u;
     }
     d.tyre15 = (p.Ct == 1.5f) ? 1 : 0;
-    d.steer_small = (std::fabs(p.u_min[0]) <= 1.0f && std::fabs(p.u_max[0]) <= 1.0f) ? 1 : 0;
+    d.steer_small = (std::fabs(p.u_min[0]) <= 0.5f && std::fabs(p.u_max[0]) <= 0.5f) ? 1 : 0;
     return d;
 }
 

@@ -141,8 +141,14 @@ __global__ void __launch_bounds__(RB) batch_kernel(DevParams P0, BatchArgs a) {
             for (int p = 0; p < npair; ++p) {
                 const uint4 rn = philox10(make_uint4((uint32_t)k, (uint32_t)(p + 1), iter, ctr3), P);
                 const float2 na = box_muller(rn.x, rn.y), nb = box_muller(rn.z, rn.w);
-                rollout_step(P, seg, inv, Vs[2 * p], za, x, s, h_prev, acc);
-                if (2 * p + 1 < T) rollout_step(P, seg, inv, Vs[2 * p + 1], zb, x, s, h_prev, acc);
+                const float2 va = Vs[2 * p];
+                rollout_step(P, seg, inv, make_float4(va.x, va.y, P.gis0 * va.x, P.gis1 * va.y), za,
+                             x, s, h_prev, acc);
+                if (2 * p + 1 < T) {
+                    const float2 vb = Vs[2 * p + 1];
+                    rollout_step(P, seg, inv, make_float4(vb.x, vb.y, P.gis0 * vb.x, P.gis1 * vb.y),
+                                 zb, x, s, h_prev, acc);
+                }
                 za = na;
                 zb = nb;
             }

@@ -18,8 +18,8 @@
 //   heading -- (cos psi, sin psi) is carried with the state and rotated by the
 //              Euler increment dt r each step (exactly cos / sin of the Euler
 //              psi up to rounding), so no sin / cos of an unbounded angle;
-//   small sin / cos -- Taylor series to x^13 / x^14 for |x| <= 1 (remainder
-//              < 1e-12), the library otherwise.
+//   small sin / cos -- Taylor series to x^9 / x^10 for |x| <= 1/2 (remainder
+//              < 1.2e-11), the library otherwise.
 #pragma once
 
 #include <cstdint>
@@ -44,7 +44,7 @@ struct DevParams {
     int ls_max;
     int K, T, N_r, n_track;
     int tyre15;                  // 1 when Ct == 1.5 (half-angle tyre path)
-    int steer_small;             // 1 when |steer| <= 1 on the whole control box
+    int steer_small;             // 1 when |steer| <= 1/2 on the whole control box
     uint32_t key0, key1;
     uint32_t rk0[10], rk1[10];   // Philox round keys key + i * Weyl
 };
@@ -70,9 +70,11 @@ __device__ __forceinline__ State make_state(const float* x) {
 __device__ __forceinline__ uint4 philox10(uint4 c, const DevParams& P) {
 #pragma unroll
     for (int i = 0; i < 10; ++i) {
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ P.rk0[i], lo1, hi0 ^ c.w ^ P.rk1[i], lo0);
+        // one 32 x 32 -> 64-bit product gives both halves
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ P.rk0[i], (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ P.rk1[i], (uint32_t)p0);
     }
     return c;
 }
@@ -82,9 +84,10 @@ __device__ __forceinline__ float u01(uint32_t x) {
     return fmaf(__uint2float_rn(x >> 9), 0x1p-23f, 0x1p-24f);
 }
 
-// Box-Muller pair (library logf / sqrtf / sincospif).
+// Box-Muller pair (library logf and sincospif; r = sqrt(q) as q rsqrt(q), q > 0).
 __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b) {
-    const float r = sqrtf(-2.0f * logf(u01(a)));
+    const float q = -2.0f * logf(u01(a));
+    const float r = q * rsqrtf(q);
     float s, c;
     sincospif(2.0f * u01(b), &s, &c);
     return make_float2(r * c, r * s);
@@ -115,28 +118,25 @@ __device__ __forceinline__ float atan2_poly(float y, float x) {
     return copysignf(r, y);
 }
 
-// sin and cos of |x| <= 1 by Taylor series (remainder < 1e-12).
-__device__ __forceinline__ void sincos_small(float x, float* s, float* c) {
+// sin and cos of |x| <= 1/2 by Taylor series to x^9 / x^10 (remainders below
+// 0.5^11 / 11! = 1.2e-11 and 0.5^12 / 12! = 5.1e-13).
+__device__ __forceinline__ void sincos_half(float x, float* s, float* c) {
     const float x2 = x * x;
-    float ps = -1.6059043836821615e-10f;            // -1/13!
-    ps = fmaf(ps, x2, 2.5052108385441720e-08f);      //  1/11!
-    ps = fmaf(ps, x2, -2.7557319223985893e-06f);     // -1/9!
-    ps = fmaf(ps, x2, 1.9841269841269841e-04f);      //  1/7!
-    ps = fmaf(ps, x2, -8.3333333333333333e-03f);     // -1/5!
-    ps = fmaf(ps, x2, 1.6666666666666667e-01f);      //  1/3!
-    *s = fmaf(-ps * x2, x, x);
-    float pc = 1.1470745597729725e-11f;              //  1/14!
-    pc = fmaf(pc, x2, -2.0876756987868099e-09f);     // -1/12!
-    pc = fmaf(pc, x2, 2.7557319223985891e-07f);      //  1/10!
-    pc = fmaf(pc, x2, -2.4801587301587302e-05f);     // -1/8!
-    pc = fmaf(pc, x2, 1.3888888888888889e-03f);      //  1/6!
-    pc = fmaf(pc, x2, -4.1666666666666667e-02f);     // -1/4!
-    pc = fmaf(pc, x2, 0.5f);                         //  1/2!
-    *c = fmaf(-pc, x2, 1.0f);
+    float ps = 2.7557319223985893e-06f;              //  1/9!
+    ps = fmaf(ps, x2, -1.9841269841269841e-04f);     // -1/7!
+    ps = fmaf(ps, x2, 8.3333333333333333e-03f);      //  1/5!
+    ps = fmaf(ps, x2, -1.6666666666666667e-01f);     // -1/3!
+    *s = fmaf(ps * x2, x, x);
+    float pc = -2.7557319223985891e-07f;             // -1/10!
+    pc = fmaf(pc, x2, 2.4801587301587302e-05f);      //  1/8!
+    pc = fmaf(pc, x2, -1.3888888888888889e-03f);     // -1/6!
+    pc = fmaf(pc, x2, 4.1666666666666667e-02f);      //  1/4!
+    pc = fmaf(pc, x2, -0.5f);                        // -1/2!
+    *c = fmaf(pc, x2, 1.0f);
 }
 
 __device__ __forceinline__ void sincos_any(float x, float* s, float* c) {
-    if (fabsf(x) <= 1.0f) sincos_small(x, s, c);
+    if (fabsf(x) <= 0.5f) sincos_half(x, s, c);
     else sincosf(x, s, c);
 }
 
@@ -167,7 +167,7 @@ __device__ __forceinline__ void model_step(const DevParams& P, State& x, float d
     const float Fyf = P.Fzf * tyre_shape(P, P.B * (d - bf), nullptr);
     const float Fyr = P.Fzr * tyre_shape(P, -P.B * br, nullptr);
     float sd, cd;
-    if (P.steer_small) sincos_small(d, &sd, &cd);
+    if (P.steer_small) sincos_half(d, &sd, &cd);
     else sincosf(d, &sd, &cd);
     const float Fx = P.fx_gain * a;
     const float dvx = fmaf(Fx - Fyf * sd, P.m_inv, x.vy * x.r);
@@ -205,7 +205,7 @@ __device__ __forceinline__ void model_step_adjoint(const DevParams& P, const Sta
     const float Fyf = P.Fzf * tyre_shape(P, P.B * af, &dphf);
     tyre_shape(P, P.B * ar, &dphr);
     float sd, cd;
-    if (P.steer_small) sincos_small(d, &sd, &cd);
+    if (P.steer_small) sincos_half(d, &sd, &cd);
     else sincosf(d, &sd, &cd);
     const float cp = x.cp, sp = x.sp;
     const float dX = x.vx * cp - x.vy * sp;
@@ -304,6 +304,57 @@ __device__ __forceinline__ int track_follow(const float4* __restrict__ seg,
     return s;
 }
 
+// The same walk with its first steps evaluated speculatively: the distances
+// to segments s-1 .. s+3 are computed independently (no dependent chain of
+// loads and compares), the forward decisions for up to two segments are
+// taken from them, and only a longer walk falls back to the loop.  The
+// comparisons and their order are those of track_follow, so the result is
+// identical.
+__device__ __forceinline__ int track_follow_spec(const float4* __restrict__ seg,
+                                                 const float* __restrict__ inv, int n, int s,
+                                                 float X, float Y, float& d2) {
+    const int sm1 = (s == 0) ? n - 1 : s - 1;
+    const int sp1 = (s + 1 == n) ? 0 : s + 1;
+    const int sp2 = (sp1 + 1 == n) ? 0 : sp1 + 1;
+    const int sp3 = (sp2 + 1 == n) ? 0 : sp2 + 1;
+    const float dm1 = seg_d2(seg, inv, sm1, X, Y);
+    const float d0 = seg_d2(seg, inv, s, X, Y);
+    const float dp1 = seg_d2(seg, inv, sp1, X, Y);
+    const float dp2 = seg_d2(seg, inv, sp2, X, Y);
+    const float dp3 = seg_d2(seg, inv, sp3, X, Y);
+    if (dp1 < d0) {
+        if (!(dp2 < dp1)) { d2 = dp1; return sp1; }
+        if (!(dp3 < dp2)) { d2 = dp2; return sp2; }
+        // longer forward walk: continue from s+3
+        int c = sp3;
+        float d = dp3;
+        int nx = (c + 1 == n) ? 0 : c + 1;
+        float dn = seg_d2(seg, inv, nx, X, Y);
+        for (int it = 3; it < n && dn < d; ++it) {
+            c = nx;
+            d = dn;
+            nx = (c + 1 == n) ? 0 : c + 1;
+            dn = seg_d2(seg, inv, nx, X, Y);
+        }
+        d2 = d;
+        return c;
+    }
+    if (!(dm1 < d0)) { d2 = d0; return s; }
+    // backward walk from s-1
+    int c = sm1;
+    float d = dm1;
+    int pv = (c == 0) ? n - 1 : c - 1;
+    float dp = seg_d2(seg, inv, pv, X, Y);
+    for (int it = 1; it < n && dp < d; ++it) {
+        c = pv;
+        d = dp;
+        pv = (c == 0) ? n - 1 : c - 1;
+        dp = seg_d2(seg, inv, pv, X, Y);
+    }
+    d2 = d;
+    return c;
+}
+
 // Running cost q (Eq. 24-25) given e_y^2.
 __device__ __forceinline__ float run_cost(const DevParams& P, float vx, float d2) {
     const float ev = vx - P.v_target;
@@ -363,15 +414,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // One sampled rollout step (Alg. 2 inner loop): u = v + eps, control term
 // gamma v' Sigma^-1 u, x <- f(x, clamp(u)), project on the track, add q and the
 // DCBF penalty (Eq. 12, 17-20).
+// vg = (v, gamma Sigma^-1 v) of the step.
 __device__ __forceinline__ void rollout_step(const DevParams& P, const float4* seg,
-                                             const float* inv, float2 v, float2 z, State& x,
+                                             const float* inv, float4 vg, float2 z, State& x,
                                              int& s, float& h_prev, float& acc) {
-    const float u0 = fmaf(P.sig0, z.x, v.x), u1 = fmaf(P.sig1, z.y, v.y);
-    acc = fmaf(P.gis0 * v.x, u0, acc);
-    acc = fmaf(P.gis1 * v.y, u1, acc);
+    const float u0 = fmaf(P.sig0, z.x, vg.x), u1 = fmaf(P.sig1, z.y, vg.y);
+    acc = fmaf(vg.z, u0, acc);
+    acc = fmaf(vg.w, u1, acc);
     model_step(P, x, clampf(u0, P.umin0, P.umax0), clampf(u1, P.umin1, P.umax1));
     float d2;
-    s = track_follow(seg, inv, P.n_track, s, x.X, x.Y, d2);
+    s = track_follow_spec(seg, inv, P.n_track, s, x.X, x.Y, d2);
     const float h = P.w2 - d2;
     acc += run_cost(P, x.vx, d2) + P.C_cbf * fmaxf(cbf_arg(P, h_prev, h), 0.0f);
     h_prev = h;

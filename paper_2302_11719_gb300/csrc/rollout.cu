@@ -35,14 +35,17 @@ template <int BLK>
 __device__ __forceinline__ void stage_problem(const DevParams& P, const float4* __restrict__ segg,
                                               const float* __restrict__ invg,
                                               const float* __restrict__ Vg, float X0, float Y0,
-                                              float4* seg, float* inv, float2* Vs, int* s_seg0,
+                                              float4* seg, float* inv, float4* Vs, int* s_seg0,
                                               float* s_d20, float* red_f, int* red_i) {
     const int tid = threadIdx.x;
     for (int i = tid; i < P.n_track; i += BLK) {
         seg[i] = segg[i];
         inv[i] = invg[i];
     }
-    for (int t = tid; t < P.T; t += BLK) Vs[t] = reinterpret_cast<const float2*>(Vg)[t];
+    for (int t = tid; t < P.T; t += BLK) {
+        const float2 v = reinterpret_cast<const float2*>(Vg)[t];
+        Vs[t] = make_float4(v.x, v.y, P.gis0 * v.x, P.gis1 * v.y);   // (v, gamma Sigma^-1 v)
+    }
     __syncthreads();
     // global nearest segment of x0 (lowest index on ties)
     float bd = 3.0e38f;
@@ -86,7 +89,7 @@ __global__ void __launch_bounds__(BLK) mppi_rollout_kernel(
     const int T = P.T, n = P.n_track;
     float4* seg = reinterpret_cast<float4*>(smem_raw);
     float* inv = reinterpret_cast<float*>(seg + n);
-    float2* Vs = reinterpret_cast<float2*>(inv + n + (n & 1));
+    float4* Vs = reinterpret_cast<float4*>(inv + ((n + 3) & ~3));
     __shared__ float red_f[NW];
     __shared__ int red_i[NW];
     __shared__ int s_seg0;
@@ -342,8 +345,8 @@ __global__ void debug_noise_kernel(DevParams P, uint32_t iter, uint32_t ctr3, in
 // Host-side launchers
 // ----------------------------------------------------------------------------
 size_t rollout_smem_bytes(int n_track, int T) {
-    return (size_t)n_track * sizeof(float4) + (size_t)(n_track + (n_track & 1)) * sizeof(float) +
-           (size_t)T * sizeof(float2);
+    return (size_t)n_track * sizeof(float4) + (size_t)((n_track + 3) & ~3) * sizeof(float) +
+           (size_t)T * sizeof(float4);
 }
 
 int update_grid(int K) {

@@ -86,7 +86,7 @@ __device__ double forward_cost(const DevParams& P, const float4* seg, const floa
             u = clamp2(P, v);
         }
         model_step(P, x, u.x, u.y);
-        s = track_follow(seg, inv, P.n_track, s, x.X, x.Y, d2);
+        s = track_follow_spec(seg, inv, P.n_track, s, x.X, x.Y, d2);
         const float h = P.w2 - d2;
         if (w_run != 0.0f) Jf = fmaf(w_run, run_cost(P, x.vx, d2), Jf);
         const float a = cbf_arg(P, h_prev, h);
@@ -135,7 +135,7 @@ __device__ double seq_cost_grad(const DevParams& P, const float4* seg, const flo
                 const float2 u = clamp2(P, Vw[(size_t)(t0 + i - 1) * ms + seq]);
                 model_step(P, x, u.x, u.y);
                 float d2;
-                s = track_follow(seg, inv, P.n_track, s, x.X, x.Y, d2);
+                s = track_follow_spec(seg, inv, P.n_track, s, x.X, x.Y, d2);
                 hp = h;
                 h = P.w2 - d2;
                 tape.put(rb + i, x, s, h, hp);
