@@ -63,14 +63,15 @@ struct BatchArgs {
 constexpr int BATCH_PPT = 8;      // costs per thread in one pass of the problem update
 constexpr int BATCH_MAXPS = 4;    // pair sets per thread (pairs <= 4 * RB)
 
-template <int RB>
+template <int RB, bool FAST>
 __global__ void __launch_bounds__(RB) batch_kernel(DevParams P0, BatchArgs a) {
     constexpr int NW = RB / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nmax = a.n_track_max, npad = (nmax + 3) & ~3, Tm = a.T_max;
     float4* seg = reinterpret_cast<float4*>(smem_raw);
     float* inv = reinterpret_cast<float*>(seg + nmax);
-    float2* Vs = reinterpret_cast<float2*>(inv + npad);     // nominal V, then V+
+    float4* Vs4 = reinterpret_cast<float4*>(inv + npad);   // (v, gamma Sigma^-1 v) per step
+    float2* Vs = reinterpret_cast<float2*>(Vs4 + Tm);      // nominal V, then V+
     float2* Vw = Vs + Tm;                                      // repaired controls
     float2* G = Vw + Tm;
     float* tape_s = reinterpret_cast<float*>(G + Tm);
@@ -116,7 +117,11 @@ __global__ void __launch_bounds__(RB) batch_kernel(DevParams P0, BatchArgs a) {
                 bulk_g2s(inv, a.inv + D.seg_off, b_inv, &bar);
             }
             const float2* Vg = reinterpret_cast<const float2*>(a.V) + D.V_off;
-            for (int t = tid; t < T; t += RB) Vs[t] = Vg[t];
+            for (int t = tid; t < T; t += RB) {
+                const float2 v = Vg[t];
+                Vs[t] = v;
+                Vs4[t] = make_float4(v.x, v.y, P.gis0 * v.x, P.gis1 * v.y);
+            }
             if (!mbar_wait_bounded(&bar, phase)) {
                 atomicOr(a.status, SMPPI_DEV_TIMEOUT);
                 mbar_wait_bounded(&bar, phase);
@@ -132,27 +137,8 @@ __global__ void __launch_bounds__(RB) batch_kernel(DevParams P0, BatchArgs a) {
         const bool active = k < D.K;
         float S = 3.0e38f;
         if (active) {
-            int s = s0;
-            float h_prev = P.w2 - d20;
-            float acc = run_cost(P, x.vx, d20) + P.C_cbf * fmaxf(cbf_arg(P, h_prev, h_prev), 0.0f);
-            uint4 r = philox10(make_uint4((uint32_t)k, 0u, iter, ctr3), P);
-            float2 za = box_muller(r.x, r.y), zb = box_muller(r.z, r.w);
-            const int npair = (T + 1) >> 1;
-            for (int p = 0; p < npair; ++p) {
-                const uint4 rn = philox10(make_uint4((uint32_t)k, (uint32_t)(p + 1), iter, ctr3), P);
-                const float2 na = box_muller(rn.x, rn.y), nb = box_muller(rn.z, rn.w);
-                const float2 va = Vs[2 * p];
-                rollout_step(P, seg, inv, make_float4(va.x, va.y, P.gis0 * va.x, P.gis1 * va.y), za,
-                             x, s, h_prev, acc);
-                if (2 * p + 1 < T) {
-                    const float2 vb = Vs[2 * p + 1];
-                    rollout_step(P, seg, inv, make_float4(vb.x, vb.y, P.gis0 * vb.x, P.gis1 * vb.y),
-                                 zb, x, s, h_prev, acc);
-                }
-                za = na;
-                zb = nb;
-            }
-            S = acc;
+            S = rollout_sample<FAST, false>(P, seg, inv, Vs4, x, s0, d20, (uint32_t)k, iter, ctr3,
+                                            nullptr);
             a.S[D.S_off + k] = S;
             if (!isfinite(S)) atomicOr(a.status, SMPPI_DEV_NUMERIC);
         }
@@ -283,7 +269,7 @@ __global__ void __launch_bounds__(RB) batch_kernel(DevParams P0, BatchArgs a) {
         // ---- safety shield on V+ (Alg. 1) ----
         State xr = make_state(a.x0 + 6 * i);
         if (a.n_repair > 0)
-            repair_in_block<RB>(P, seg, inv, xr, s0, Vw, G, tape_s, a.n_repair, 1, 0.0f, a.ck,
+            repair_in_block<RB, FAST>(P, seg, inv, xr, s0, Vw, G, tape_s, a.n_repair, 1, 0.0f, a.ck,
                                 nullptr, nullptr, a.status, rsm);
         float2* Vsafe = reinterpret_cast<float2*>(a.V_safe) + D.V_off;
         for (int t = tid; t < T; t += RB) Vsafe[t] = Vw[t];
@@ -383,14 +369,23 @@ smppi_status bfail(smppi_batch* b, smppi_status s, const std::string& m) {
 
 size_t batch_smem(int RB, int n_track_max, int T_max) {
     const int npad = (n_track_max + 3) & ~3;
-    return (size_t)n_track_max * 16 + (size_t)npad * 4 + (size_t)T_max * 8 * 3 +
+    return (size_t)n_track_max * 16 + (size_t)npad * 4 + (size_t)T_max * 16 + (size_t)T_max * 8 * 3 +
            (size_t)(T_max + 2) * NFIELD * 4 + (size_t)RB * BATCH_PPT * 8 + (size_t)T_max * 2 * 4;
 }
 
-const void* batch_kernel_ptr(int RB) {
-    if (RB == 64) return (const void*)batch_kernel<64>;
-    if (RB == 256) return (const void*)batch_kernel<256>;
-    return (const void*)batch_kernel<128>;
+template <bool FAST>
+const void* batch_kernel_ptr_t(int RB) {
+    if (RB == 64) return (const void*)batch_kernel<64, FAST>;
+    if (RB == 256) return (const void*)batch_kernel<256, FAST>;
+    return (const void*)batch_kernel<128, FAST>;
+}
+
+// The branch-free model step applies when C = 1.5 and the steering bound keeps
+// |delta| <= 0.5 (same selection as the single-problem rollout).
+bool batch_fast(const smppi_batch* b) { return b->dp.tyre15 && b->dp.steer_small; }
+
+const void* batch_kernel_ptr(const smppi_batch* b, int RB) {
+    return batch_fast(b) ? batch_kernel_ptr_t<true>(RB) : batch_kernel_ptr_t<false>(RB);
 }
 
 // Offsets, chunk counts and the work-item order (decreasing T, then problem,
@@ -436,10 +431,14 @@ smppi_status enqueue_batch(smppi_batch* b, cudaStream_t st, float* x0, float* V,
     a.status = b->status;
     const size_t smem = batch_smem(b->RB, b->n_track_max, b->T_max);
     BCU(b, cudaMemsetAsync(b->head, 0, sizeof(unsigned), st));
-    BCU(b, ensure_smem(batch_kernel_ptr(b->RB), smem));
-    if (b->RB == 64) batch_kernel<64><<<b->grid, 64, smem, st>>>(b->dp, a);
-    else if (b->RB == 256) batch_kernel<256><<<b->grid, 256, smem, st>>>(b->dp, a);
-    else batch_kernel<128><<<b->grid, 128, smem, st>>>(b->dp, a);
+    BCU(b, ensure_smem(batch_kernel_ptr(b, b->RB), smem));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(b->grid);
+    cfg.blockDim = dim3(b->RB);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    void* args[] = {(void*)&b->dp, (void*)&a};
+    BCU(b, cudaLaunchKernelExC(&cfg, batch_kernel_ptr(b, b->RB), args));
     BCU(b, cudaGetLastError());
     return SMPPI_OK;
 }
@@ -448,8 +447,8 @@ smppi_status enqueue_batch(smppi_batch* b, cudaStream_t st, float* x0, float* V,
 int max_bps(smppi_batch* b, int RB) {
     int nb = 0;
     const size_t smem = batch_smem(RB, b->n_track_max, b->T_max);
-    if (ensure_smem(batch_kernel_ptr(RB), smem) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel_ptr(RB), RB, smem) !=
+    if (ensure_smem(batch_kernel_ptr(b, RB), smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_kernel_ptr(b, RB), RB, smem) !=
         cudaSuccess)
         return 0;
     return nb;

@@ -140,6 +140,13 @@ __device__ __forceinline__ void sincos_any(float x, float* s, float* c) {
     else sincosf(x, s, c);
 }
 
+// sin(1.5 atan z) by the half-angle identities (no branch).
+__device__ __forceinline__ float tyre15(float z) {
+    const float c = rsqrtf(fmaf(z, z, 1.0f));        // cos t, t = atan z
+    const float u = fmaf(0.5f, c, 0.5f);             // cos^2(t/2)
+    return z * c * rsqrtf(u) * fmaf(0.5f, c, u);     // sin t cos(t/2) + cos t sin(t/2)
+}
+
 // Lateral tyre force shape sin(Ct atan(z)) and, if dz != nullptr, its
 // derivative Ct cos(Ct atan z) / (1 + z^2).
 __device__ __forceinline__ float tyre_shape(const DevParams& P, float z, float* dz) {
@@ -161,9 +168,39 @@ __device__ __forceinline__ float tyre_shape(const DevParams& P, float z, float* 
 // ---------------------------------------------------------------------------
 // One explicit Euler step of the single-track model (Eq. 1).
 // ---------------------------------------------------------------------------
+// FAST: the parameters satisfy Ct == 1.5 and |steer| <= 1/2 on the control
+// box (P.tyre15 && P.steer_small), so the step is one branch-free block (the
+// only branch left handles |dt r| > 1/2 after the block).
+template <bool FAST = false>
 __device__ __forceinline__ void model_step(const DevParams& P, State& x, float d, float a) {
     const float bf = atan2_poly(fmaf(P.lf, x.r, x.vy), x.vx);
     const float br = atan2_poly(fmaf(-P.lr, x.r, x.vy), x.vx);
+    if (FAST) {
+        const float Fyf = P.Fzf * tyre15(P.B * (d - bf));
+        const float Fyr = P.Fzr * tyre15(-P.B * br);
+        float sd, cd;
+        sincos_half(d, &sd, &cd);
+        const float Fx = P.fx_gain * a;
+        const float dvx = fmaf(Fx - Fyf * sd, P.m_inv, x.vy * x.r);
+        const float dvy = fmaf(Fyr + Fyf * cd, P.m_inv, -x.vx * x.r);
+        const float dr = (P.lf * Fyf * cd - P.lr * Fyr) * P.Iz_inv;
+        const float dX = x.vx * x.cp - x.vy * x.sp;
+        const float dY = x.vx * x.sp + x.vy * x.cp;
+        const float dpsi = P.dt * x.r;
+        float sa, ca;
+        sincos_half(dpsi, &sa, &ca);
+        const float cp0 = x.cp, sp0 = x.sp;
+        x.vx = fmaf(P.dt, dvx, x.vx);
+        x.vy = fmaf(P.dt, dvy, x.vy);
+        x.r = fmaf(P.dt, dr, x.r);
+        x.X = fmaf(P.dt, dX, x.X);
+        x.Y = fmaf(P.dt, dY, x.Y);
+        x.psi += dpsi;
+        if (fabsf(dpsi) > 0.5f) sincosf(dpsi, &sa, &ca);
+        x.cp = cp0 * ca - sp0 * sa;
+        x.sp = sp0 * ca + cp0 * sa;
+        return;
+    }
     const float Fyf = P.Fzf * tyre_shape(P, P.B * (d - bf), nullptr);
     const float Fyr = P.Fzr * tyre_shape(P, -P.B * br, nullptr);
     float sd, cd;
@@ -306,10 +343,9 @@ __device__ __forceinline__ int track_follow(const float4* __restrict__ seg,
 
 // The same walk with its first steps evaluated speculatively: the distances
 // to segments s-1 .. s+3 are computed independently (no dependent chain of
-// loads and compares), the forward decisions for up to two segments are
-// taken from them, and only a longer walk falls back to the loop.  The
-// comparisons and their order are those of track_follow, so the result is
-// identical.
+// loads and compares) and the outcome of the walk is selected from them when
+// it ends within s .. s+2; a longer forward walk or any backward walk reruns
+// track_follow from s.  The result is therefore identical to track_follow.
 __device__ __forceinline__ int track_follow_spec(const float4* __restrict__ seg,
                                                  const float* __restrict__ inv, int n, int s,
                                                  float X, float Y, float& d2) {
@@ -322,37 +358,12 @@ __device__ __forceinline__ int track_follow_spec(const float4* __restrict__ seg,
     const float dp1 = seg_d2(seg, inv, sp1, X, Y);
     const float dp2 = seg_d2(seg, inv, sp2, X, Y);
     const float dp3 = seg_d2(seg, inv, sp3, X, Y);
-    if (dp1 < d0) {
-        if (!(dp2 < dp1)) { d2 = dp1; return sp1; }
-        if (!(dp3 < dp2)) { d2 = dp2; return sp2; }
-        // longer forward walk: continue from s+3
-        int c = sp3;
-        float d = dp3;
-        int nx = (c + 1 == n) ? 0 : c + 1;
-        float dn = seg_d2(seg, inv, nx, X, Y);
-        for (int it = 3; it < n && dn < d; ++it) {
-            c = nx;
-            d = dn;
-            nx = (c + 1 == n) ? 0 : c + 1;
-            dn = seg_d2(seg, inv, nx, X, Y);
-        }
-        d2 = d;
-        return c;
-    }
-    if (!(dm1 < d0)) { d2 = d0; return s; }
-    // backward walk from s-1
-    int c = sm1;
-    float d = dm1;
-    int pv = (c == 0) ? n - 1 : c - 1;
-    float dp = seg_d2(seg, inv, pv, X, Y);
-    for (int it = 1; it < n && dp < d; ++it) {
-        c = pv;
-        d = dp;
-        pv = (c == 0) ? n - 1 : c - 1;
-        dp = seg_d2(seg, inv, pv, X, Y);
-    }
-    d2 = d;
-    return c;
+    const bool f1 = dp1 < d0, f2 = dp2 < dp1, f3 = dp3 < dp2, b1 = dm1 < d0;
+    int r = f1 ? (f2 ? sp2 : sp1) : s;
+    float dr = f1 ? (f2 ? dp2 : dp1) : d0;
+    if (f1 ? (f2 && f3) : b1) r = track_follow(seg, inv, n, s, X, Y, dr);
+    d2 = dr;
+    return r;
 }
 
 // Running cost q (Eq. 24-25) given e_y^2.
@@ -427,6 +438,91 @@ __device__ __forceinline__ void rollout_step(const DevParams& P, const float4* s
     const float h = P.w2 - d2;
     acc += run_cost(P, x.vx, d2) + P.C_cbf * fmaxf(cbf_arg(P, h_prev, h), 0.0f);
     h_prev = h;
+}
+
+// Cost of state x_t: walk to its segment, add q(x_t) and the DCBF penalty of
+// the pair (x_{t-1}, x_t) (Eq. 17, 24).
+__device__ __forceinline__ void track_cost(const DevParams& P, const float4* seg, const float* inv,
+                                           const State& x, int& s, float& h_prev, float& acc) {
+    float d2;
+    s = track_follow_spec(seg, inv, P.n_track, s, x.X, x.Y, d2);
+    const float h = P.w2 - d2;
+    acc += run_cost(P, x.vx, d2) + P.C_cbf * fmaxf(cbf_arg(P, h_prev, h), 0.0f);
+    h_prev = h;
+}
+
+// Perturbed control of one step: u = v + eps (returned clamped to the box) and
+// the control term gamma v' Sigma^-1 u added to acc (vg = (v, gamma Sigma^-1 v)).
+__device__ __forceinline__ float2 perturb(const DevParams& P, float4 vg, float2 z, float& acc) {
+    const float u0 = fmaf(P.sig0, z.x, vg.x), u1 = fmaf(P.sig1, z.y, vg.y);
+    acc = fmaf(vg.z, u0, acc);
+    acc = fmaf(vg.w, u1, acc);
+    return make_float2(clampf(u0, P.umin0, P.umax0), clampf(u1, P.umin1, P.umax1));
+}
+
+__device__ __forceinline__ void dump_row(float* tr, int t, const State& x) {
+    float* o = tr + (size_t)t * 6;
+    o[0] = x.vx; o[1] = x.vy; o[2] = x.r; o[3] = x.X; o[4] = x.Y; o[5] = x.psi;
+}
+
+// Trajectory cost S~ of sampled rollout k (Alg. 2 inner loop, Eq. 12, 17-20),
+// software-pipelined: the track projection and cost of x_t are issued
+// together with the dynamics x_t -> x_{t+1}, which do not depend on them, and
+// the noise of the next pair of steps is drawn one pair ahead.  x = x_0 with
+// segment s and squared offset d20; Vs[t] = (v_t, gamma Sigma^-1 v_t); traj
+// (DUMP only): this rollout's (T + 1) x 6 row.
+template <bool FAST, bool DUMP>
+__device__ __forceinline__ float rollout_sample(const DevParams& P, const float4* seg,
+                                                const float* inv, const float4* Vs, State x, int s,
+                                                float d20, uint32_t k, uint32_t iter,
+                                                uint32_t ctr3, float* traj) {
+    const int T = P.T, npair = (T + 1) >> 1;
+    float h_prev = P.w2 - d20;
+    float acc = run_cost(P, x.vx, d20) + P.C_cbf * fmaxf(cbf_arg(P, h_prev, h_prev), 0.0f);
+    if (DUMP) dump_row(traj, 0, x);
+    uint4 r = philox10(make_uint4(k, 0u, iter, ctr3), P);
+    float2 za = box_muller(r.x, r.y), zb = box_muller(r.z, r.w);
+    // pair 0 (the cost of x_0 is already in acc); afterwards the cost of x is pending
+    {
+        const uint4 rn = philox10(make_uint4(k, 1u, iter, ctr3), P);
+        const float2 na = box_muller(rn.x, rn.y), nb = box_muller(rn.z, rn.w);
+        const float2 ua = perturb(P, Vs[0], za, acc);
+        model_step<FAST>(P, x, ua.x, ua.y);
+        if (DUMP) dump_row(traj, 1, x);
+        if (T > 1) {
+            const float2 ub = perturb(P, Vs[1], zb, acc);
+            State xb = x;
+            model_step<FAST>(P, xb, ub.x, ub.y);
+            track_cost(P, seg, inv, x, s, h_prev, acc);
+            x = xb;
+            if (DUMP) dump_row(traj, 2, x);
+        }
+        za = na;
+        zb = nb;
+    }
+    for (int p = 1; p < npair; ++p) {
+        const uint4 rn = philox10(make_uint4(k, (uint32_t)(p + 1), iter, ctr3), P);
+        const float2 na = box_muller(rn.x, rn.y), nb = box_muller(rn.z, rn.w);
+        const float2 ua = perturb(P, Vs[2 * p], za, acc);
+        State xa = x;
+        model_step<FAST>(P, xa, ua.x, ua.y);
+        track_cost(P, seg, inv, x, s, h_prev, acc);
+        if (DUMP) dump_row(traj, 2 * p + 1, xa);
+        if (2 * p + 1 < T) {
+            const float2 ub = perturb(P, Vs[2 * p + 1], zb, acc);
+            State xb = xa;
+            model_step<FAST>(P, xb, ub.x, ub.y);
+            track_cost(P, seg, inv, xa, s, h_prev, acc);
+            x = xb;
+            if (DUMP) dump_row(traj, 2 * p + 2, x);
+        } else {
+            x = xa;
+        }
+        za = na;
+        zb = nb;
+    }
+    track_cost(P, seg, inv, x, s, h_prev, acc);   // x_T
+    return acc;
 }
 
 // Warp-level argmin of (d2, index) with lowest index on ties.

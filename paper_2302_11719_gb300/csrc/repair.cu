@@ -153,6 +153,7 @@ __global__ void __launch_bounds__(REP_BLK) repair_kernel(
 // checkpoint tape); see repair_in_block.
 constexpr int REPB_BLK = 64;
 
+template <bool FAST>
 __global__ void __launch_bounds__(REPB_BLK) repair_block_kernel(
     DevParams P, const float4* __restrict__ segg, const float* __restrict__ invg, int inv_pad,
     const float* __restrict__ x0g, const float* Vin, float* Vout, int n_iters, int mode,
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(REPB_BLK) repair_block_kernel(
         return;
     }
     const int s0 = block_nearest_segment<REPB_BLK>(seg, inv, n, x0.X, x0.Y, s_red, s_redi, nullptr);
-    repair_in_block<REPB_BLK>(P, seg, inv, x0, s0, Vw, G, tape_s, n_iters, mode, delta, ck,
+    repair_in_block<REPB_BLK, FAST>(P, seg, inv, x0, s0, Vw, G, tape_s, n_iters, mode, delta, ck,
                               merit_out ? merit_out + (size_t)q * (n_iters + 1) : nullptr,
                               iters_out ? iters_out + q : nullptr, status, sm);
     float2* vout = reinterpret_cast<float2*>(Vout) + (size_t)q * T;
@@ -241,11 +242,12 @@ cudaError_t launch_repair(const DevParams& P, const float4* seg, const float* in
         const int inv_pad = (P.n_track + 3) & ~3;
         const size_t smem = (size_t)P.n_track * 16 + (size_t)inv_pad * 4 + (size_t)P.T * 16 +
                             (size_t)(P.T + 2) * NFIELD * 4;
-        cudaError_t e = ensure_smem((const void*)repair_block_kernel, smem);
+        auto kern = (P.tyre15 && P.steer_small) ? repair_block_kernel<true>
+                                                 : repair_block_kernel<false>;
+        cudaError_t e = ensure_smem((const void*)kern, smem);
         if (e != cudaSuccess) return e;
-        repair_block_kernel<<<n_seq, REPB_BLK, smem, st>>>(P, seg, inv, inv_pad, x0, V_in, V_out,
-                                                           n_iters, mode, delta, ws.ck, merit_out,
-                                                           iters_out, ap, status);
+        kern<<<n_seq, REPB_BLK, smem, st>>>(P, seg, inv, inv_pad, x0, V_in, V_out, n_iters, mode,
+                                            delta, ws.ck, merit_out, iters_out, ap, status);
         return cudaGetLastError();
     }
     const size_t smem = track_smem(P.n_track);

@@ -67,16 +67,9 @@ __device__ __forceinline__ void stage_problem(const DevParams& P, const float4* 
     __syncthreads();
 }
 
-template <bool DUMP>
-__device__ __forceinline__ void dump_state(float* traj, int k, int T, int t, const State& x) {
-    if (DUMP) {
-        float* tr = traj + ((size_t)k * (T + 1) + t) * 6;
-        tr[0] = x.vx; tr[1] = x.vy; tr[2] = x.r; tr[3] = x.X; tr[4] = x.Y; tr[5] = x.psi;
-    }
-}
-
-// Launch 1: one thread per rollout.
-template <int BLK, bool DUMP>
+// Launch 1: one thread per rollout.  FAST: model parameters of the
+// branch-free model step (see model_step).
+template <int BLK, bool DUMP, bool FAST>
 __global__ void __launch_bounds__(BLK) mppi_rollout_kernel(
     DevParams P, const float* __restrict__ x0g, const float* __restrict__ Vg,
     const float4* __restrict__ segg, const float* __restrict__ invg, uint32_t iter,
@@ -104,28 +97,9 @@ __global__ void __launch_bounds__(BLK) mppi_rollout_kernel(
     if (blockIdx.x == 0 && tid == 0 && seg0_out) *seg0_out = s_seg0;
     float S = 3.0e38f;
     if (active) {
-        State x = make_state(x0g);
-        int s = s_seg0;
-        float h_prev = P.w2 - s_d20;
-        float acc = run_cost(P, x.vx, s_d20) + P.C_cbf * fmaxf(cbf_arg(P, h_prev, h_prev), 0.0f);
-        dump_state<DUMP>(traj, k, T, 0, x);
-        // noise of pair 0, then one pair ahead of the integration
-        uint4 r = philox10(make_uint4((uint32_t)k, 0u, iter, ctr3), P);
-        float2 za = box_muller(r.x, r.y), zb = box_muller(r.z, r.w);
-        const int npair = (T + 1) >> 1;
-        for (int p = 0; p < npair; ++p) {
-            const uint4 rn = philox10(make_uint4((uint32_t)k, (uint32_t)(p + 1), iter, ctr3), P);
-            const float2 na = box_muller(rn.x, rn.y), nb = box_muller(rn.z, rn.w);
-            rollout_step(P, seg, inv, Vs[2 * p], za, x, s, h_prev, acc);
-            dump_state<DUMP>(traj, k, T, 2 * p + 1, x);
-            if (2 * p + 1 < T) {
-                rollout_step(P, seg, inv, Vs[2 * p + 1], zb, x, s, h_prev, acc);
-                dump_state<DUMP>(traj, k, T, 2 * p + 2, x);
-            }
-            za = na;
-            zb = nb;
-        }
-        S = acc;
+        S = rollout_sample<FAST, DUMP>(P, seg, inv, Vs, make_state(x0g), s_seg0, s_d20,
+                                       (uint32_t)k, iter, ctr3,
+                                       DUMP ? traj + (size_t)k * (T + 1) * 6 : nullptr);
         S_out[k] = S;
         if (!isfinite(S)) atomicOr(status, SMPPI_DEV_NUMERIC);
     }
@@ -369,7 +343,11 @@ cudaError_t launch_rollout(const DevParams& P, bool dump, const float* x0, const
                            int* seg0_out, unsigned* status, cudaStream_t st) {
     const int nblk = (P.K + ROLL_BLK - 1) / ROLL_BLK;
     const size_t smem = rollout_smem_bytes(P.n_track, P.T);
-    auto kern = dump ? mppi_rollout_kernel<ROLL_BLK, true> : mppi_rollout_kernel<ROLL_BLK, false>;
+    const bool fast = P.tyre15 && P.steer_small;
+    auto kern = dump ? (fast ? mppi_rollout_kernel<ROLL_BLK, true, true>
+                             : mppi_rollout_kernel<ROLL_BLK, true, false>)
+                     : (fast ? mppi_rollout_kernel<ROLL_BLK, false, true>
+                             : mppi_rollout_kernel<ROLL_BLK, false, false>);
     cudaError_t e = ensure_smem((const void*)kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<nblk, ROLL_BLK, smem, st>>>(P, x0, V, seg, inv, iter, ctr3, iter_dev, S_out, traj,

@@ -57,7 +57,11 @@ __device__ __forceinline__ void add_direct(const DevParams& P, const float4* seg
 // where u'_t = clip(Vw_t - step G_t) (the Armijo decrease term).  The terms are
 // summed in float32 over blocks of 16 steps and the block sums in float64
 // (FP64 arithmetic is slow on this part; one FP64 add per 16 steps).
-template <bool STORE, bool TRIAL>
+//
+// The loop is software-pipelined like rollout_sample: in iteration t the
+// dynamics x_t -> x_{t+1} are issued together with the track projection, cost
+// and tape entry of x_t, which they do not depend on.
+template <bool STORE, bool TRIAL, bool FAST = false>
 __device__ double forward_cost(const DevParams& P, const float4* seg, const float* inv,
                                const State& x0, int s0, int N, const float2* Vw, const float2* G,
                                float step, int ms, int seq, float w_run, float w_cbf, int ck,
@@ -71,49 +75,62 @@ __device__ double forward_cost(const DevParams& P, const float4* seg, const floa
     float Jf = 0.0f, decf = 0.0f;
     const float wc = w_cbf * P.C_cbf;
     const bool full = ck <= 0;
-    for (int t = 0; t < N; ++t) {
-        if (STORE) {
-            if (full) tape.put(t, x, s, h_prev, h_pp);
-            else if (t % ck == 0) tape.put(t / ck, x, s, h_prev, h_pp);
-        }
-        float2 v = Vw[(size_t)t * ms + seq];
-        float2 u;
+    if (STORE && N > 0) tape.put(0, x, s, h_prev, h_pp);
+    auto control = [&](int t) {
+        const float2 v = Vw[(size_t)t * ms + seq];
         if (TRIAL) {
             const float2 g = G[(size_t)t * ms + seq];
-            u = clamp2(P, make_float2(fmaf(-step, g.x, v.x), fmaf(-step, g.y, v.y)));
+            const float2 u = clamp2(P, make_float2(fmaf(-step, g.x, v.x), fmaf(-step, g.y, v.y)));
             decf = fmaf(g.x, v.x - u.x, fmaf(g.y, v.y - u.y, decf));
-        } else {
-            u = clamp2(P, v);
+            return u;
         }
-        model_step(P, x, u.x, u.y);
-        s = track_follow_spec(seg, inv, P.n_track, s, x.X, x.Y, d2);
+        return clamp2(P, v);
+    };
+    // cost of state x_t (its predecessor's h is h_prev) and its tape entry
+    auto settle = [&](const State& xs, int t) {
+        s = track_follow_spec(seg, inv, P.n_track, s, xs.X, xs.Y, d2);
         const float h = P.w2 - d2;
-        if (w_run != 0.0f) Jf = fmaf(w_run, run_cost(P, x.vx, d2), Jf);
+        const float q = run_cost(P, xs.vx, d2);
+        Jf = (w_run != 0.0f) ? fmaf(w_run, q, Jf) : Jf;
         const float a = cbf_arg(P, h_prev, h);
-        if (a > 0.0f) Jf = fmaf(wc, a, Jf);
+        Jf = (a > 0.0f) ? fmaf(wc, a, Jf) : Jf;
         h_pp = h_prev;
         h_prev = h;
-        if ((t & 15) == 15) {
+        if (STORE && (full ? true : (t % ck == 0)) && (t < N || full))
+            tape.put(full ? t : t / ck, xs, s, h_prev, h_pp);
+        if ((t & 15) == 0) {
             J += (double)Jf;
             dec += (double)decf;
             Jf = 0.0f;
             decf = 0.0f;
         }
+    };
+    if (N > 0) {
+        const float2 u0 = control(0);
+        model_step<FAST>(P, x, u0.x, u0.y);
     }
+    for (int t = 1; t < N; ++t) {
+        const float2 u = control(t);
+        State xn = x;
+        model_step<FAST>(P, xn, u.x, u.y);
+        settle(x, t);
+        x = xn;
+    }
+    if (N > 0) settle(x, N);
     J += (double)Jf;
     dec += (double)decf;
-    if (STORE && full) tape.put(N, x, s, h_prev, h_pp);
     if (dec_out) *dec_out = dec;
     return J;
 }
 
 // Cost and gradient of one sequence (forward with tape + backward adjoint).
 // Writes G_t = dJ/dv_t for t < N (0 for N <= t < T).
+template <bool FAST = false>
 __device__ double seq_cost_grad(const DevParams& P, const float4* seg, const float* inv,
                                 const State& x0, int s0, int N, int T, const float2* Vw, float2* G,
                                 int ms, int seq, float w_run, float w_cbf, int ck,
                                 const Tape& tape) {
-    const double J = forward_cost<true, false>(P, seg, inv, x0, s0, N, Vw, nullptr, 0.0f, ms, seq,
+    const double J = forward_cost<true, false, FAST>(P, seg, inv, x0, s0, N, Vw, nullptr, 0.0f, ms, seq,
                                                w_run, w_cbf, ck, tape, nullptr);
     for (int t = N; t < T; ++t) G[(size_t)t * ms + seq] = make_float2(0.0f, 0.0f);
     if (N == 0) return J;
@@ -133,7 +150,7 @@ __device__ double seq_cost_grad(const DevParams& P, const float4* seg, const flo
             tape.put(rb, x, s, h, hp);
             for (int i = 1; i <= t1 - t0; ++i) {
                 const float2 u = clamp2(P, Vw[(size_t)(t0 + i - 1) * ms + seq]);
-                model_step(P, x, u.x, u.y);
+                model_step<FAST>(P, x, u.x, u.y);
                 float d2;
                 s = track_follow_spec(seg, inv, P.n_track, s, x.X, x.Y, d2);
                 hp = h;
@@ -207,7 +224,7 @@ struct RepairSmem {
 // largest accepted step is taken: the same iterate as sequential backtracking.
 // The gradient comes from thread 0 (seq_cost_grad).  merit_row (optional):
 // n_iters + 1 merits; *iters_done: iterations run.  Returns the final merit.
-template <int BLK>
+template <int BLK, bool FAST = false>
 __device__ double repair_in_block(const DevParams& P, const float4* seg, const float* inv,
                                   const State& x0, int s0, float2* Vw, float2* G, float* tape_s,
                                   int n_iters, int mode, float delta, int ck, double* merit_row,
@@ -217,7 +234,7 @@ __device__ double repair_in_block(const DevParams& P, const float4* seg, const f
     constexpr int NW = BLK / 32;
     const Tape tape{tape_s, 1, 0};
     if (tid == 0)
-        sm.P = forward_cost<false, false>(P, seg, inv, x0, s0, N, Vw, nullptr, 0.0f, 1, 0, 0.0f,
+        sm.P = forward_cost<false, false, FAST>(P, seg, inv, x0, s0, N, Vw, nullptr, 0.0f, 1, 0, 0.0f,
                                           1.0f, 0, tape, nullptr);
     __syncthreads();
     double P0 = sm.P;
@@ -226,7 +243,7 @@ __device__ double repair_in_block(const DevParams& P, const float4* seg, const f
     for (; it < n_iters; ++it) {
         if (tid == 0 && merit_row) merit_row[it] = P0;
         if (P0 == 0.0) break;
-        if (tid == 0) seq_cost_grad(P, seg, inv, x0, s0, N, T, Vw, G, 1, 0, 0.0f, 1.0f, ck, tape);
+        if (tid == 0) seq_cost_grad<FAST>(P, seg, inv, x0, s0, N, T, Vw, G, 1, 0, 0.0f, 1.0f, ck, tape);
         __syncthreads();
         if (mode == 0) {
             for (int t = tid; t < N; t += BLK)
@@ -234,7 +251,7 @@ __device__ double repair_in_block(const DevParams& P, const float4* seg, const f
                                               fmaf(-delta, G[t].y, Vw[t].y)));
             __syncthreads();
             if (tid == 0)
-                sm.P = forward_cost<false, false>(P, seg, inv, x0, s0, N, Vw, nullptr, 0.0f, 1, 0,
+                sm.P = forward_cost<false, false, FAST>(P, seg, inv, x0, s0, N, Vw, nullptr, 0.0f, 1, 0,
                                                   0.0f, 1.0f, 0, tape, nullptr);
             __syncthreads();
             P0 = sm.P;
@@ -259,7 +276,7 @@ __device__ double repair_in_block(const DevParams& P, const float4* seg, const f
             for (int j = lane; j < P.ls_max; j += 32) {
                 const float sj = ldexpf(s_first, -j);
                 double dec;
-                const double Pt = forward_cost<false, true>(P, seg, inv, x0, s0, N, Vw, G, sj, 1,
+                const double Pt = forward_cost<false, true, FAST>(P, seg, inv, x0, s0, N, Vw, G, sj, 1,
                                                             0, 0.0f, 1.0f, 0, tape, &dec);
                 if (Pt <= P0 - (double)P.ls_c * dec && j < best) { best = j; best_P = Pt; }
             }
