@@ -345,6 +345,14 @@ def _timed_steps(fn, steps, flush):
     return [a.elapsed_time(b) for a, b in zip(e0, e1)]
 
 
+def _status_names(bits):
+    """Names of the device status bits: 'stalled' means that in some update of
+    some problem the repair line search accepted no step (the update then
+    applies the last accepted iterate); it is not an error."""
+    names = [n for b, n in ((1, "numeric"), (2, "timeout"), (4, "stalled")) if bits & b]
+    return names or ["ok"]
+
+
 def run_batch(args):
     """512 uneven Shield-MPPI problems: one persistent launch per closed-loop
     update vs 512 separate per-problem updates on one stream."""
@@ -411,7 +419,7 @@ def run_batch(args):
                     "block_rollouts": rb, "grid": grid, "l2": "flushed between steps"},
         "batched_graph_loop": {"value": B * n_loop / (t_loop / 1e3), "updates": n_loop,
                                "ms_per_update_all": t_loop / n_loop, "l2": "not flushed",
-                               "status": st_b[0]},
+                               "device_status_bits": _status_names(st_b[1])},
         "plain_per_problem": {"value": B * len(t_p) / (sum(t_p) / 1e3),
                               "ms_per_update_all": float(np.median(t_p)),
                               "launches_per_update": 2 * B + B, "l2": "flushed between steps"},

@@ -19,6 +19,7 @@ struct smppi_handle {
     cudaStream_t cap = nullptr;      // private stream for graph capture
     float4* seg = nullptr;
     float* inv = nullptr;
+    float4* rec = nullptr;           // segment-pair table of the packed rollout kernel
     float* S_ws = nullptr;           // [K] rollout costs
     float* blk_min = nullptr;        // [nblk] block minima of S
     float* part_acc = nullptr;       // [UPD_BLK][2T] update-kernel partials
@@ -140,7 +141,7 @@ DevParams derive(const smppi_params& p) {
 void free_all(smppi_handle* h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
-    void* ptrs[] = {h->seg, h->inv, h->S_ws, h->blk_min, h->part_acc, h->part_eta, h->part_has,
+    void* ptrs[] = {h->seg, h->inv, h->rec, h->S_ws, h->blk_min, h->part_acc, h->part_eta, h->part_has,
                     h->ticket,
                     h->status,
                     h->iter_dev,
@@ -191,11 +192,11 @@ smppi_status enqueue_step(smppi_handle* h, cudaStream_t st, const float* x0, flo
     const uint32_t ctr3 = (instance << 8) | 0u;
     float* S = S_out ? S_out : h->S_ws;
     int ev = tic(h, st);
-    CU(h, launch_rollout(h->dp, traj_out != nullptr, x0, V, h->seg, h->inv, iter, ctr3, iter_dev,
-                         S, traj_out, h->blk_min, h->rws.seg0, h->status, st));
+    CU(h, launch_rollout(h->dp, traj_out != nullptr, x0, V, h->seg, h->inv, h->rec, iter, ctr3,
+                         iter_dev, S, traj_out, h->blk_min, h->rws.seg0, h->status, st));
     toc(h, st, SMPPI_KERNEL_ROLLOUT, ev);
     ev = tic(h, st);
-    CU(h, launch_update(h->dp, S, h->blk_min, h->nblk, V, iter, ctr3, iter_dev, h->part_acc,
+    CU(h, launch_update(h->dp, S, h->blk_min, rollout_blocks(h->dp), V, iter, ctr3, iter_dev, h->part_acc,
                         h->part_eta, h->part_has, h->ticket, h->status, st));
     toc(h, st, SMPPI_KERNEL_UPDATE, ev);
     return SMPPI_OK;
@@ -292,6 +293,7 @@ smppi_status smppi_create(const smppi_params* p, void* cuda_stream, smppi_handle
     if (e == cudaSuccess) e = alloc(&(ptr), (bytes));
     ALLOC(h->seg, sizeof(float4) * p->n_track);
     ALLOC(h->inv, sizeof(float) * ((p->n_track + 3) & ~3));   // padded for 16-byte bulk copies
+    ALLOC(h->rec, rec_table_bytes(p->n_track));
     ALLOC(h->S_ws, sizeof(float) * p->K);
     ALLOC(h->blk_min, sizeof(float) * h->nblk);
     ALLOC(h->part_acc, sizeof(float) * 2 * T * (size_t)UPD_BLK);
@@ -313,6 +315,7 @@ smppi_status smppi_create(const smppi_params* p, void* cuda_stream, smppi_handle
     if (e == cudaSuccess) e = cudaMemsetAsync(h->iter_dev, 0, sizeof(uint32_t), h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->ticket, 0, sizeof(unsigned), h->st);
     if (e == cudaSuccess) e = launch_seg_table(p->track_xy, p->n_track, h->seg, h->inv, h->st);
+    if (e == cudaSuccess) e = launch_rec_table(p->track_xy, p->n_track, h->rec, h->st);
     if (e != cudaSuccess) {
         const bool oom = (e == cudaErrorMemoryAllocation);
         fail(nullptr, oom ? SMPPI_ERR_NOMEM : SMPPI_ERR_CUDA,

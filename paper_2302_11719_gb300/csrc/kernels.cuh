@@ -6,6 +6,7 @@
 namespace smppi {
 
 constexpr int ROLL_BLK = 128;   // rollouts per block of the single-problem kernel
+constexpr int ROLL2_BLK = 128;  // threads per block of the packed kernel (two rollouts each)
 constexpr int UPD_BLK = 256;    // threads per block of the update kernel (also its max grid)
 
 // Opt a kernel in to more than 48 KB of dynamic shared memory when needed.
@@ -14,13 +15,21 @@ inline cudaError_t ensure_smem(const void* kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Dynamic shared memory of the rollout launch (the larger of its two kernels).
 size_t rollout_smem_bytes(int n_track, int T);
-// Rollouts: S_out [K] and blk_min [ceil(K / ROLL_BLK)]; traj (optional dump);
-// seg0_out (optional): nearest segment of x0.
+// Block minima the rollout launch writes (<= ceil(K / ROLL_BLK)).
+int rollout_blocks(const DevParams& P);
+// Rollouts: S_out [K] and blk_min [rollout_blocks(P)]; traj (optional dump);
+// seg0_out (optional): nearest segment of x0.  rec: segment-pair table of
+// launch_rec_table (read when the packed kernel runs: C = 1.5, |steer| <= 1/2).
 cudaError_t launch_rollout(const DevParams& P, bool dump, const float* x0, const float* V,
-                           const float4* seg, const float* inv, uint32_t iter, uint32_t ctr3,
-                           const uint32_t* iter_dev, float* S_out, float* traj, float* blk_min,
-                           int* seg0_out, unsigned* status, cudaStream_t st);
+                           const float4* seg, const float* inv, const float4* rec, uint32_t iter,
+                           uint32_t ctr3, const uint32_t* iter_dev, float* S_out, float* traj,
+                           float* blk_min, int* seg0_out, unsigned* status, cudaStream_t st);
+// Segment-pair table of a closed polyline (layout in rollout2.cuh): n + 5
+// records of three float4.
+__host__ __device__ inline size_t rec_table_bytes(int n) { return (size_t)(n + 5) * 3 * sizeof(float4); }
+cudaError_t launch_rec_table(const float* track_xy, int n, float4* rec, cudaStream_t st);
 // Grid of the update kernel for K rollouts (<= UPD_BLK blocks).
 int update_grid(int K);
 // Softmin update V <- clamp(V + sum omega eps / sum omega) from S [K].  blk_min

@@ -6,7 +6,9 @@
 //   memory holds the centreline segment table and the nominal sequence V.  Each
 //   thread steps its rollout in registers; the noise of the next pair of steps
 //   is drawn from Philox while the current pair is integrated (never stored).
-//   Writes S_k and the block minimum of S.
+//   Writes S_k and the block minimum of S.  For C = 1.5 and |steer| <= 1/2 the
+//   packed kernel runs instead: one thread steps two rollouts (k, k + BLK of
+//   its block) with FFMA2 / FADD2 / FMUL2 and reads the segment-pair table.
 // Launch 2 (update): G <= #SMs blocks of UPD_BLK threads.  Every block takes
 //   m = min_k S_k from the block minima, computes omega_k = exp(-(S_k - m)/lambda)
 //   for its contiguous slice of k (all of them enter eta), and regenerates the
@@ -17,6 +19,7 @@
 //   finish (device-scope ticket) sums the non-empty block partials in float64
 //   and writes V+ = clamp(V + A / eta).
 #include "kernels.cuh"
+#include "rollout2.cuh"
 
 namespace smppi {
 
@@ -112,6 +115,117 @@ __global__ void __launch_bounds__(BLK) mppi_rollout_kernel(
         for (int w = 1; w < NW; ++w) mb = fminf(mb, red_f[w]);
         blk_min[blockIdx.x] = mb;
     }
+}
+
+// Launch 1, packed form: thread t of block b steps rollouts 2 b BLK + t and
+// 2 b BLK + BLK + t together (rollout2.cuh).  The segment-pair table arrives
+// by one bulk copy; V is laid out as broadcast pairs.
+template <bool DUMP>
+__global__ void __launch_bounds__(ROLL2_BLK, 2) mppi_rollout2_kernel(
+    DevParams P, const float* __restrict__ x0g, const float* __restrict__ Vg,
+    const float4* __restrict__ recg, uint32_t iter, uint32_t ctr3,
+    const uint32_t* __restrict__ iter_dev, float* __restrict__ S_out, float* __restrict__ traj,
+    float* __restrict__ blk_min, int* __restrict__ seg0_out, unsigned* __restrict__ status) {
+    constexpr int BLK = ROLL2_BLK, NW = BLK / 32;
+    if (iter_dev) iter += *iter_dev;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int T = P.T, n = P.n_track;
+    float4* rec = reinterpret_cast<float4*>(smem_raw);
+    float4* Vp = rec + 3 * (n + 5);
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ float red_f[NW];
+    __shared__ int red_i[NW];
+    __shared__ int s_seg0, s_fail;
+    __shared__ float s_d20;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    if (tid == 0) {
+        s_fail = 0;
+        mbar_init(&bar, 1);
+        const uint32_t bytes = (uint32_t)rec_table_bytes(n);
+        mbar_expect_tx(&bar, bytes);
+        bulk_g2s(rec, recg, bytes, &bar);
+    }
+    for (int t = tid; t < T; t += BLK) {
+        const float2 v = reinterpret_cast<const float2*>(Vg)[t];
+        const float g0 = P.gis0 * v.x, g1 = P.gis1 * v.y;
+        Vp[2 * t] = make_float4(v.x, v.x, v.y, v.y);
+        Vp[2 * t + 1] = make_float4(g0, g0, g1, g1);
+    }
+    __syncthreads();
+    if (!mbar_wait_bounded(&bar, 0u)) s_fail = 1;
+    __syncthreads();
+    if (s_fail) {
+        if (tid == 0) {
+            atomicOr(status, SMPPI_DEV_TIMEOUT);
+            mbar_wait_bounded(&bar, 0u);   // let the copy in flight land before the block exits
+        }
+        return;
+    }
+    // global nearest segment of x0 (lowest index on ties)
+    const float X0 = x0g[3], Y0 = x0g[4];
+    float bd = 3.0e38f;
+    int bi = 0x7fffffff;
+    for (int i = tid; i < n; i += BLK) {
+        const float d = x2::rec_d2_seg(rec, i, X0, Y0);
+        if (d < bd) { bd = d; bi = i; }
+    }
+    warp_argmin(bd, bi);
+    if (lane == 0) { red_f[warp] = bd; red_i[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+        for (int w = 1; w < NW; ++w)
+            if (red_f[w] < bd || (red_f[w] == bd && red_i[w] < bi)) { bd = red_f[w]; bi = red_i[w]; }
+        s_seg0 = bi;
+        s_d20 = bd;
+        if (blockIdx.x == 0 && seg0_out) *seg0_out = bi;
+    }
+    __syncthreads();
+
+    const int ka = blockIdx.x * 2 * BLK + tid, kb = ka + BLK;
+    const bool act_a = ka < P.K, act_b = kb < P.K;
+    float* ta = (DUMP && act_a) ? traj + (size_t)ka * (T + 1) * 6 : nullptr;
+    float* tb = (DUMP && act_b) ? traj + (size_t)kb * (T + 1) * 6 : nullptr;
+    const float2 S = x2::rollout2<DUMP>(P, rec, Vp, make_state(x0g), s_seg0, s_d20,
+                                        (uint32_t)ka, (uint32_t)kb, iter, ctr3, ta, tb);
+    if (act_a) {
+        S_out[ka] = S.x;
+        if (!isfinite(S.x)) atomicOr(status, SMPPI_DEV_NUMERIC);
+    }
+    if (act_b) {
+        S_out[kb] = S.y;
+        if (!isfinite(S.y)) atomicOr(status, SMPPI_DEV_NUMERIC);
+    }
+    const float m = warp_min(fminf(act_a ? S.x : 3.0e38f, act_b ? S.y : 3.0e38f));
+    if (lane == 0) red_f[warp] = m;
+    __syncthreads();
+    if (tid == 0) {
+        float mb = red_f[0];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) mb = fminf(mb, red_f[w]);
+        blk_min[blockIdx.x] = mb;
+    }
+}
+
+// Segment-pair records j = 0 .. n + 4 (segments j - 1 and j, mod n).
+__global__ void rec_table_kernel(const float* __restrict__ xy, int n, float4* __restrict__ rec) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n + 5) return;
+    float ax[2], ay[2], dx[2], dy[2], gx[2], gy[2];
+    for (int h = 0; h < 2; ++h) {
+        const int i = (j - 1 + h + n) % n, i1 = (i + 1 == n) ? 0 : i + 1;
+        ax[h] = xy[2 * i];
+        ay[h] = xy[2 * i + 1];
+        dx[h] = xy[2 * i1] - ax[h];
+        dy[h] = xy[2 * i1 + 1] - ay[h];
+        const float l2 = fmaf(dx[h], dx[h], dy[h] * dy[h]);
+        const float inv = l2 > 0.0f ? 1.0f / l2 : 0.0f;
+        gx[h] = dx[h] * inv;
+        gy[h] = dy[h] * inv;
+    }
+    rec[3 * j] = make_float4(-ax[0], -ax[1], -ay[0], -ay[1]);
+    rec[3 * j + 1] = make_float4(-dx[0], -dx[1], -dy[0], -dy[1]);
+    rec[3 * j + 2] = make_float4(gx[0], gx[1], gy[0], gy[1]);
 }
 
 // Launch 2: weights, weighted noise sum of the rollouts whose weight exceeds
@@ -319,8 +433,22 @@ __global__ void debug_noise_kernel(DevParams P, uint32_t iter, uint32_t ctr3, in
 // Host-side launchers
 // ----------------------------------------------------------------------------
 size_t rollout_smem_bytes(int n_track, int T) {
-    return (size_t)n_track * sizeof(float4) + (size_t)((n_track + 3) & ~3) * sizeof(float) +
-           (size_t)T * sizeof(float4);
+    const size_t one = (size_t)n_track * sizeof(float4) +
+                       (size_t)((n_track + 3) & ~3) * sizeof(float) + (size_t)T * sizeof(float4);
+    const size_t two = rec_table_bytes(n_track) + (size_t)T * 2 * sizeof(float4);
+    return one > two ? one : two;
+}
+
+static bool packed_rollout(const DevParams& P) { return P.tyre15 && P.steer_small; }
+
+int rollout_blocks(const DevParams& P) {
+    return packed_rollout(P) ? (P.K + 2 * ROLL2_BLK - 1) / (2 * ROLL2_BLK)
+                             : (P.K + ROLL_BLK - 1) / ROLL_BLK;
+}
+
+cudaError_t launch_rec_table(const float* track_xy, int n, float4* rec, cudaStream_t st) {
+    rec_table_kernel<<<(n + 5 + 127) / 128, 128, 0, st>>>(track_xy, n, rec);
+    return cudaGetLastError();
 }
 
 int update_grid(int K) {
@@ -338,16 +466,22 @@ int update_grid(int K) {
 }
 
 cudaError_t launch_rollout(const DevParams& P, bool dump, const float* x0, const float* V,
-                           const float4* seg, const float* inv, uint32_t iter, uint32_t ctr3,
-                           const uint32_t* iter_dev, float* S_out, float* traj, float* blk_min,
-                           int* seg0_out, unsigned* status, cudaStream_t st) {
+                           const float4* seg, const float* inv, const float4* rec, uint32_t iter,
+                           uint32_t ctr3, const uint32_t* iter_dev, float* S_out, float* traj,
+                           float* blk_min, int* seg0_out, unsigned* status, cudaStream_t st) {
+    if (packed_rollout(P)) {
+        const size_t smem = rec_table_bytes(P.n_track) + (size_t)P.T * 2 * sizeof(float4);
+        auto kern = dump ? mppi_rollout2_kernel<true> : mppi_rollout2_kernel<false>;
+        cudaError_t e = ensure_smem((const void*)kern, smem);
+        if (e != cudaSuccess) return e;
+        kern<<<rollout_blocks(P), ROLL2_BLK, smem, st>>>(P, x0, V, rec, iter, ctr3, iter_dev, S_out,
+                                                         traj, blk_min, seg0_out, status);
+        return cudaGetLastError();
+    }
     const int nblk = (P.K + ROLL_BLK - 1) / ROLL_BLK;
     const size_t smem = rollout_smem_bytes(P.n_track, P.T);
-    const bool fast = P.tyre15 && P.steer_small;
-    auto kern = dump ? (fast ? mppi_rollout_kernel<ROLL_BLK, true, true>
-                             : mppi_rollout_kernel<ROLL_BLK, true, false>)
-                     : (fast ? mppi_rollout_kernel<ROLL_BLK, false, true>
-                             : mppi_rollout_kernel<ROLL_BLK, false, false>);
+    auto kern = dump ? mppi_rollout_kernel<ROLL_BLK, true, false>
+                     : mppi_rollout_kernel<ROLL_BLK, false, false>;
     cudaError_t e = ensure_smem((const void*)kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<nblk, ROLL_BLK, smem, st>>>(P, x0, V, seg, inv, iter, ctr3, iter_dev, S_out, traj,

@@ -84,13 +84,55 @@ def test_update_from_given_costs(S, orc):
         ctl.close()
 
 
-@pytest.mark.parametrize("K,T", [(1, 1), (1, 50), (129, 7), (1000, 51), (300, 1), (77, 100)])
+@pytest.mark.parametrize("K,T", [(1, 1), (1, 50), (129, 7), (1000, 51), (300, 1), (77, 100),
+                                 (64, 2), (257, 3), (513, 4)])
 def test_ragged_sizes(S, orc, K, T):
     pr = I.single_problem(K=K, T=T)
     V = (0.2 * np.random.default_rng(K + T).uniform(-1, 1, (T, 2))).astype(np.float32)
     Sg, Vg, _ = run_step(S, pr, it=3, inst=2, V=V)
     m, So, Vp, om, eps = oracle_step(orc, pr, 3, 2, V=V)
     assert rel_err(Sg, So) <= S_REL
+    check_update(pr, So, Vp, om, eps, Vg, V=V)
+
+
+def _path_case(name):
+    """Problems that drive each branch of the rollout kernels (see the test below)."""
+    if name == "dense_track":
+        # 2048 points on a 10 x 6 m ellipse (2.5 cm segments) at 8 m/s: the nearest
+        # segment moves ~6 segments per step, beyond the packed kernel's window
+        a, b = 10.0, 6.0
+        p = I.make_params(K=300, T=30, half_width=1.0)
+        return I.Problem(params=p, track=I.ellipse_track(a, b, 2048),
+                         x0=I.centreline_start(a, b, 8.0), V=np.zeros((30, 2), np.float32))
+    if name == "yaw_rate":
+        # r = 30 rad/s: |dt r| = 0.6 > 1/2, the library sin / cos of the heading step
+        pr = I.single_problem(K=200, T=20)
+        pr.x0[2] = 30.0
+        return pr
+    if name == "reverse":
+        # v_x < 0: the vehicle backs along the track, every walk goes backward
+        pr = I.single_problem(K=200, T=40, vx=-3.0)
+        return pr
+    if name == "tyre_c13":
+        return I.single_problem(K=256, T=50, Ct=1.3)          # scalar kernel, library atan / sin
+    if name == "wide_steer":
+        return I.single_problem(K=256, T=50, u_min=(-0.7, -1.0), u_max=(0.7, 1.0))
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name", ["dense_track", "yaw_rate", "reverse", "tyre_c13", "wide_steer"])
+def test_kernel_paths(S, orc, name):
+    # the packed kernel (C = 1.5, |steer| <= 1/2) replays a two-step iteration whose
+    # track walk left its window or whose heading step exceeded 1/2; other
+    # parameters run the one-rollout-per-thread kernel
+    pr = _path_case(name)
+    V = (0.1 * np.random.default_rng(11).uniform(-1, 1, (pr.T, 2))).astype(np.float32)
+    Sg, Vg, tr = run_step(S, pr, it=2, inst=1, V=V, traj=True)
+    m, So, Vp, om, eps = oracle_step(orc, pr, 2, 1, V=V)
+    assert rel_err(Sg, So) <= S_REL
+    for k in range(0, pr.K, 7):
+        _, to, _ = orc.rollout(m, pr.x0, V, k=k, it=2, instance=1)
+        assert rel_err(tr[k], to) <= X_REL, k
     check_update(pr, So, Vp, om, eps, Vg, V=V)
 
 
