@@ -47,7 +47,7 @@ ROLLOUT_TRAFFIC = {"sources_sha": None, "bytes_per_launch": None}
 
 def kernel_sha() -> str:
     h = hashlib.sha256()
-    for f in ("rollout.cu", "device.cuh", "kernels.cuh"):
+    for f in ("rollout.cu", "rollout2.cuh", "device.cuh", "kernels.cuh"):
         with open(os.path.join(ROOT, "paper_2302_11719_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
