@@ -123,6 +123,64 @@ __device__ double forward_cost(const DevParams& P, const float4* seg, const floa
     return J;
 }
 
+// Merit of Vw (forward_cost with w_run = 0, w_cbf = 1, no tape) by two threads
+// of the block in different warps: thread 0 integrates the model and publishes
+// each state's (X, Y) to buf [2 N] with a progress counter; thread 32 follows
+// with the track walk and the DCBF terms.  The arithmetic and the summation
+// order are those of forward_cost (the same merit), but the model recurrence
+// no longer waits on the track walk.  Called by every thread of the block
+// (BLK >= 64); the result lands in *out after the caller's __syncthreads.
+// The follower's wait is bounded: past the limit it sets SMPPI_DEV_TIMEOUT
+// and stops.
+template <bool FAST>
+__device__ void merit_split(const DevParams& P, const float4* seg, const float* inv,
+                            const State& x0, int s0, int N, const float2* Vw, float* buf,
+                            volatile int* prog, double* out, unsigned* status) {
+    const int tid = threadIdx.x;
+    if (tid == 0) *prog = 0;
+    __syncthreads();
+    if (tid == 0) {
+        State x = x0;
+        for (int t = 0; t < N; ++t) {
+            const float2 u = clamp2(P, Vw[t]);
+            model_step<FAST>(P, x, u.x, u.y);
+            reinterpret_cast<float2*>(buf)[t] = make_float2(x.X, x.Y);   // state t + 1
+            __threadfence_block();
+            *prog = t + 1;
+        }
+    } else if (tid == 32) {
+        int s = s0;
+        float d2 = seg_d2(seg, inv, s, x0.X, x0.Y);
+        float h_prev = P.w2 - d2;
+        double J = (double)(0.0f * run_cost(P, x0.vx, d2));
+        float Jf = 0.0f;
+        const float wc = P.C_cbf;
+        for (int t = 1; t <= N; ++t) {
+            int tries = 0;
+            while (*prog < t) {
+                if (++tries > (1 << 24)) {
+                    atomicOr(status, SMPPI_DEV_TIMEOUT);
+                    *out = 0.0;
+                    return;
+                }
+            }
+            __threadfence_block();
+            const float2 xy = reinterpret_cast<const float2*>(buf)[t - 1];
+            s = track_follow_spec(seg, inv, P.n_track, s, xy.x, xy.y, d2);
+            const float h = P.w2 - d2;
+            const float a = cbf_arg(P, h_prev, h);
+            Jf = (a > 0.0f) ? fmaf(wc, a, Jf) : Jf;
+            h_prev = h;
+            if ((t & 15) == 0) {
+                J += (double)Jf;
+                Jf = 0.0f;
+            }
+        }
+        J += (double)Jf;
+        *out = J;
+    }
+}
+
 // Cost and gradient of one sequence (forward with tape + backward adjoint).
 // Writes G_t = dJ/dv_t for t < N (0 for N <= t < T).
 template <bool FAST = false>
@@ -211,6 +269,7 @@ __device__ void closed_loop_step(const DevParams& P, const ApplyArgs& ap, float2
 // Shared-memory scratch of repair_in_block.
 struct RepairSmem {
     double P;
+    int prog;          // progress counter of merit_split
     float red[32];
     float step;
     int ok;
@@ -233,9 +292,7 @@ __device__ double repair_in_block(const DevParams& P, const float4* seg, const f
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = BLK / 32;
     const Tape tape{tape_s, 1, 0};
-    if (tid == 0)
-        sm.P = forward_cost<false, false, FAST>(P, seg, inv, x0, s0, N, Vw, nullptr, 0.0f, 1, 0, 0.0f,
-                                          1.0f, 0, tape, nullptr);
+    merit_split<FAST>(P, seg, inv, x0, s0, N, Vw, tape_s, &sm.prog, &sm.P, status);
     __syncthreads();
     double P0 = sm.P;
     int it = 0;
@@ -250,9 +307,7 @@ __device__ double repair_in_block(const DevParams& P, const float4* seg, const f
                 Vw[t] = clamp2(P, make_float2(fmaf(-delta, G[t].x, Vw[t].x),
                                               fmaf(-delta, G[t].y, Vw[t].y)));
             __syncthreads();
-            if (tid == 0)
-                sm.P = forward_cost<false, false, FAST>(P, seg, inv, x0, s0, N, Vw, nullptr, 0.0f, 1, 0,
-                                                  0.0f, 1.0f, 0, tape, nullptr);
+            merit_split<FAST>(P, seg, inv, x0, s0, N, Vw, tape_s, &sm.prog, &sm.P, status);
             __syncthreads();
             P0 = sm.P;
             continue;
