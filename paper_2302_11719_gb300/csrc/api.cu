@@ -17,9 +17,7 @@ struct smppi_handle {
     DevParams dp;
     cudaStream_t st = nullptr;
     cudaStream_t cap = nullptr;      // private stream for graph capture
-    float4* seg = nullptr;
-    float* inv = nullptr;
-    float4* rec = nullptr;           // segment-pair table of the packed rollout kernel
+    float4* rec = nullptr;           // segment-pair table of the centreline (device.cuh)
     float* S_ws = nullptr;           // [K] rollout costs
     float* blk_min = nullptr;        // [nblk] block minima of S
     float* part_acc = nullptr;       // [UPD_BLK][2T] update-kernel partials
@@ -141,7 +139,7 @@ DevParams derive(const smppi_params& p) {
 void free_all(smppi_handle* h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
-    void* ptrs[] = {h->seg, h->inv, h->rec, h->S_ws, h->blk_min, h->part_acc, h->part_eta, h->part_has,
+    void* ptrs[] = {h->rec, h->S_ws, h->blk_min, h->part_acc, h->part_eta, h->part_has,
                     h->ticket,
                     h->status,
                     h->iter_dev,
@@ -192,7 +190,7 @@ smppi_status enqueue_step(smppi_handle* h, cudaStream_t st, const float* x0, flo
     const uint32_t ctr3 = (instance << 8) | 0u;
     float* S = S_out ? S_out : h->S_ws;
     int ev = tic(h, st);
-    CU(h, launch_rollout(h->dp, traj_out != nullptr, x0, V, h->seg, h->inv, h->rec, iter, ctr3,
+    CU(h, launch_rollout(h->dp, traj_out != nullptr, x0, V, h->rec, iter, ctr3,
                          iter_dev, S, traj_out, h->blk_min, h->rws.seg0, h->status, st));
     toc(h, st, SMPPI_KERNEL_ROLLOUT, ev);
     ev = tic(h, st);
@@ -211,11 +209,11 @@ smppi_status enqueue_repair(smppi_handle* h, cudaStream_t st, int n_seq, const f
     int ev;
     if (!seg0_known) {
         ev = tic(h, st);
-        CU(h, launch_seg0(h->dp, h->seg, h->inv, n_seq, x0, h->rws.seg0, st));
+        CU(h, launch_seg0(h->dp, h->rec, n_seq, x0, h->rws.seg0, st));
         toc(h, st, SMPPI_KERNEL_SEG0, ev);
     }
     ev = tic(h, st);
-    CU(h, launch_repair(h->dp, h->seg, h->inv, h->rws, n_seq, x0, V_in, V_out, n_iters, mode,
+    CU(h, launch_repair(h->dp, h->rec, h->rws, n_seq, x0, V_in, V_out, n_iters, mode,
                         delta, merit_out, iters_out, ap, h->status, st));
     toc(h, st, SMPPI_KERNEL_REPAIR, ev);
     return SMPPI_OK;
@@ -291,8 +289,6 @@ smppi_status smppi_create(const smppi_params* p, void* cuda_stream, smppi_handle
     cudaError_t e = cudaSuccess;
 #define ALLOC(ptr, bytes)                                                   \
     if (e == cudaSuccess) e = alloc(&(ptr), (bytes));
-    ALLOC(h->seg, sizeof(float4) * p->n_track);
-    ALLOC(h->inv, sizeof(float) * ((p->n_track + 3) & ~3));   // padded for 16-byte bulk copies
     ALLOC(h->rec, rec_table_bytes(p->n_track));
     ALLOC(h->S_ws, sizeof(float) * p->K);
     ALLOC(h->blk_min, sizeof(float) * h->nblk);
@@ -314,7 +310,6 @@ smppi_status smppi_create(const smppi_params* p, void* cuda_stream, smppi_handle
     if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->iter_dev, 0, sizeof(uint32_t), h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->ticket, 0, sizeof(unsigned), h->st);
-    if (e == cudaSuccess) e = launch_seg_table(p->track_xy, p->n_track, h->seg, h->inv, h->st);
     if (e == cudaSuccess) e = launch_rec_table(p->track_xy, p->n_track, h->rec, h->st);
     if (e != cudaSuccess) {
         const bool oom = (e == cudaErrorMemoryAllocation);
@@ -384,10 +379,10 @@ smppi_status smppi_cost_grad(smppi_handle* h, int n_seq, const float* x0, const 
     if (checkpoint > h->p.T) return fail(h, SMPPI_ERR_ARG, "checkpoint must be <= T");
     const int ck = checkpoint == 0 ? h->p.checkpoint : (checkpoint < 0 ? 0 : checkpoint);
     int ev = tic(h, h->st);
-    CU(h, launch_seg0(h->dp, h->seg, h->inv, n_seq, x0, h->rws.seg0, h->st));
+    CU(h, launch_seg0(h->dp, h->rec, n_seq, x0, h->rws.seg0, h->st));
     toc(h, h->st, SMPPI_KERNEL_SEG0, ev);
     ev = tic(h, h->st);
-    CU(h, launch_cost_grad(h->dp, h->seg, h->inv, h->rws, n_seq, x0, V, N, w_run, w_cbf, ck, J_out,
+    CU(h, launch_cost_grad(h->dp, h->rec, h->rws, n_seq, x0, V, N, w_run, w_cbf, ck, J_out,
                            grad_out, h->status, h->st));
     toc(h, h->st, SMPPI_KERNEL_COST_GRAD, ev);
     return SMPPI_OK;

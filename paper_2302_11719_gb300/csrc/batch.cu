@@ -2,11 +2,12 @@
 // track and state, one closed-loop update of all of them in ONE persistent
 // launch over a device work queue (Alg. 2 body per problem).
 //
-// Work items are (problem i, chunk c) pairs of RB rollouts, ordered by
+// Work items are (problem i, chunk c) pairs of 2 RB rollouts (two per thread,
+// packed FP32 pairs, when C = 1.5 and |steer| <= 1/2; else RB), ordered by
 // decreasing horizon T_i so that the problems with the longest repairs finish
 // their rollouts first.  A grid of #SMs x (blocks per SM) blocks pops items
-// from an atomic head.  A block stages the problem's centreline table (bulk
-// copy) and nominal controls, finds the nearest segment of x0, runs its RB
+// from an atomic head.  A block stages the problem's segment-pair table (bulk
+// copy) and nominal controls, finds the nearest segment of x0, runs the item's
 // rollouts (the same per-rollout code as the single-problem kernel), writes
 // the costs and the chunk minimum, and takes a ticket on the problem's
 // completion counter.  The block that completes the last chunk of problem i
@@ -24,6 +25,7 @@
 #include <string>
 #include <vector>
 
+#include "rollout2.cuh"
 #include "shield.cuh"
 
 using namespace smppi;
@@ -32,7 +34,7 @@ namespace smppi {
 
 struct BatchInst {
     int K, T, N_r, n_track;
-    int seg_off;       // first entry of this problem's segment table
+    int rec_off;       // first float4 of this problem's segment-pair table
     int V_off;         // first control of this problem in V / V_safe
     int S_off;         // first cost of this problem in S
     int chunk_off;     // first chunk of this problem in chunk_min
@@ -44,8 +46,7 @@ struct BatchArgs {
     const BatchInst* inst;
     const int2* items;
     int n_items;
-    const float4* seg;
-    const float* inv;
+    const float4* rec;     // segment-pair tables, per-problem offsets
     float* S;
     float* chunk_min;
     unsigned* done;        // [B] completion counters (0 on entry, left 0)
@@ -63,15 +64,17 @@ struct BatchArgs {
 constexpr int BATCH_PPT = 8;      // costs per thread in one pass of the problem update
 constexpr int BATCH_MAXPS = 4;    // pair sets per thread (pairs <= 4 * RB)
 
+// FAST (C = 1.5, |steer| <= 1/2): a work item is 2 RB rollouts, two per
+// thread on the packed path (rollout2.cuh); otherwise RB, one per thread.
 template <int RB, bool FAST>
 __global__ void __launch_bounds__(RB) batch_kernel(DevParams P0, BatchArgs a) {
     constexpr int NW = RB / 32;
+    constexpr int CHUNK = FAST ? 2 * RB : RB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nmax = a.n_track_max, npad = (nmax + 3) & ~3, Tm = a.T_max;
-    float4* seg = reinterpret_cast<float4*>(smem_raw);
-    float* inv = reinterpret_cast<float*>(seg + nmax);
-    float4* Vs4 = reinterpret_cast<float4*>(inv + npad);   // (v, gamma Sigma^-1 v) per step
-    float2* Vs = reinterpret_cast<float2*>(Vs4 + Tm);      // nominal V, then V+
+    const int nmax = a.n_track_max, Tm = a.T_max;
+    float4* rec = reinterpret_cast<float4*>(smem_raw);
+    float4* Vs4 = rec + 3 * (nmax + 5);                     // V rows of the rollouts (2 Tm float4)
+    float2* Vs = reinterpret_cast<float2*>(Vs4 + 2 * Tm);   // nominal V, then V+
     float2* Vw = Vs + Tm;                                      // repaired controls
     float2* G = Vw + Tm;
     float* tape_s = reinterpret_cast<float*>(G + Tm);
@@ -111,16 +114,21 @@ __global__ void __launch_bounds__(RB) batch_kernel(DevParams P0, BatchArgs a) {
         if (staged != i) {
             // stage the problem's track (bulk copy), its nominal controls, nearest segment
             if (tid == 0) {
-                const uint32_t b_seg = (uint32_t)n * 16u, b_inv = (uint32_t)((n + 3) & ~3) * 4u;
-                mbar_expect_tx(&bar, b_seg + b_inv);
-                bulk_g2s(seg, a.seg + D.seg_off, b_seg, &bar);
-                bulk_g2s(inv, a.inv + D.seg_off, b_inv, &bar);
+                const uint32_t bytes = (uint32_t)rec_table_bytes(n);
+                mbar_expect_tx(&bar, bytes);
+                bulk_g2s(rec, a.rec + D.rec_off, bytes, &bar);
             }
             const float2* Vg = reinterpret_cast<const float2*>(a.V) + D.V_off;
             for (int t = tid; t < T; t += RB) {
                 const float2 v = Vg[t];
                 Vs[t] = v;
-                Vs4[t] = make_float4(v.x, v.y, P.gis0 * v.x, P.gis1 * v.y);
+                const float g0 = P.gis0 * v.x, g1 = P.gis1 * v.y;
+                if (FAST) {   // broadcast pairs of the packed rollouts
+                    Vs4[2 * t] = make_float4(v.x, v.x, v.y, v.y);
+                    Vs4[2 * t + 1] = make_float4(g0, g0, g1, g1);
+                } else {
+                    Vs4[t] = make_float4(v.x, v.y, g0, g1);
+                }
             }
             if (!mbar_wait_bounded(&bar, phase)) {
                 atomicOr(a.status, SMPPI_DEV_TIMEOUT);
@@ -128,21 +136,36 @@ __global__ void __launch_bounds__(RB) batch_kernel(DevParams P0, BatchArgs a) {
                 return;
             }
             phase ^= 1u;
-            s0 = block_nearest_segment<RB>(seg, inv, n, x.X, x.Y, red_f, red_i, &d20);
+            s0 = block_nearest_segment<RB>(rec, n, x.X, x.Y, red_f, red_i, &d20);
             staged = i;
         }
 
-        // RB rollouts of problem i (the single-problem rollout code)
-        const int k = c * RB + tid;
-        const bool active = k < D.K;
-        float S = 3.0e38f;
-        if (active) {
-            S = rollout_sample<FAST, false>(P, seg, inv, Vs4, x, s0, d20, (uint32_t)k, iter, ctr3,
-                                            nullptr);
-            a.S[D.S_off + k] = S;
-            if (!isfinite(S)) atomicOr(a.status, SMPPI_DEV_NUMERIC);
+        // CHUNK rollouts of problem i (the single-problem rollout code)
+        float m = 3.0e38f;
+        if (FAST) {
+            const int ka = c * CHUNK + tid, kb = ka + RB;
+            if (ka < D.K) {
+                const float2 S2 = x2::rollout2<false>(P, rec, Vs4, x, s0, d20, (uint32_t)ka,
+                                                      (uint32_t)kb, iter, ctr3, nullptr, nullptr);
+                a.S[D.S_off + ka] = S2.x;
+                if (!isfinite(S2.x)) atomicOr(a.status, SMPPI_DEV_NUMERIC);
+                m = S2.x;
+                if (kb < D.K) {
+                    a.S[D.S_off + kb] = S2.y;
+                    if (!isfinite(S2.y)) atomicOr(a.status, SMPPI_DEV_NUMERIC);
+                    m = fminf(m, S2.y);
+                }
+            }
+        } else {
+            const int k = c * CHUNK + tid;
+            if (k < D.K) {
+                const float S = rollout_sample<false, false>(P, rec, Vs4, x, s0, d20, (uint32_t)k,
+                                                             iter, ctr3, nullptr);
+                a.S[D.S_off + k] = S;
+                if (!isfinite(S)) atomicOr(a.status, SMPPI_DEV_NUMERIC);
+                m = S;
+            }
         }
-        float m = active ? S : 3.0e38f;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (lane == 0) red_f[warp] = m;
@@ -269,7 +292,7 @@ __global__ void __launch_bounds__(RB) batch_kernel(DevParams P0, BatchArgs a) {
         // ---- safety shield on V+ (Alg. 1) ----
         State xr = make_state(a.x0 + 6 * i);
         if (a.n_repair > 0)
-            repair_in_block<RB, FAST>(P, seg, inv, xr, s0, Vw, G, tape_s, a.n_repair, 1, 0.0f, a.ck,
+            repair_in_block<RB, FAST>(P, rec, xr, s0, Vw, G, tape_s, a.n_repair, 1, 0.0f, a.ck,
                                 nullptr, nullptr, a.status, rsm);
         float2* Vsafe = reinterpret_cast<float2*>(a.V_safe) + D.V_off;
         for (int t = tid; t < T; t += RB) Vsafe[t] = Vw[t];
@@ -298,19 +321,32 @@ __global__ void __launch_bounds__(RB) batch_kernel(DevParams P0, BatchArgs a) {
 // Advance the update counter of graph replays.
 __global__ void batch_iter_inc(uint32_t* iter_dev) { *iter_dev += 1u; }
 
-__global__ void batch_seg_tables(const float* __restrict__ xy, const BatchInst* __restrict__ inst,
-                                 const int* __restrict__ track_off, int B, float4* __restrict__ seg,
-                                 float* __restrict__ inv) {
+// Segment-pair tables of all problems (layout in device.cuh); block i builds
+// problem i's n_i + 5 records at rec + rec_off.
+__global__ void batch_rec_tables(const float* __restrict__ xy, const BatchInst* __restrict__ inst,
+                                 const int* __restrict__ track_off, int B, float4* __restrict__ rec) {
     const int i = blockIdx.x;
     if (i >= B) return;
     const BatchInst D = inst[i];
+    const int n = D.n_track;
     const float* p = xy + 2 * (size_t)track_off[i];
-    for (int j = threadIdx.x; j < D.n_track; j += blockDim.x) {
-        const int jn = (j + 1 == D.n_track) ? 0 : j + 1;
-        const float ax = p[2 * j], ay = p[2 * j + 1];
-        const float dx = p[2 * jn] - ax, dy = p[2 * jn + 1] - ay;
-        seg[D.seg_off + j] = make_float4(ax, ay, dx, dy);
-        inv[D.seg_off + j] = 1.0f / fmaf(dx, dx, dy * dy);
+    float4* r = rec + D.rec_off;
+    for (int j = threadIdx.x; j < n + 5; j += blockDim.x) {
+        float ax[2], ay[2], dx[2], dy[2], gx[2], gy[2];
+        for (int h = 0; h < 2; ++h) {
+            const int a0 = (j - 1 + h + n) % n, a1 = (a0 + 1 == n) ? 0 : a0 + 1;
+            ax[h] = p[2 * a0];
+            ay[h] = p[2 * a0 + 1];
+            dx[h] = p[2 * a1] - ax[h];
+            dy[h] = p[2 * a1 + 1] - ay[h];
+            const float l2 = fmaf(dx[h], dx[h], dy[h] * dy[h]);
+            const float iv = l2 > 0.0f ? 1.0f / l2 : 0.0f;
+            gx[h] = dx[h] * iv;
+            gy[h] = dy[h] * iv;
+        }
+        r[3 * j] = make_float4(-ax[0], -ax[1], -ay[0], -ay[1]);
+        r[3 * j + 1] = make_float4(-dx[0], -dx[1], -dy[0], -dy[1]);
+        r[3 * j + 2] = make_float4(gx[0], gx[1], gy[0], gy[1]);
     }
 }
 
@@ -329,8 +365,7 @@ struct smppi_batch {
     int* d_track_off = nullptr;
     int2* d_items = nullptr;
     int n_items = 0, max_items = 0;
-    float4* seg = nullptr;
-    float* inv = nullptr;
+    float4* rec = nullptr;                // segment-pair tables of all problems
     float* S = nullptr;
     float* chunk_min = nullptr;
     unsigned* done = nullptr;
@@ -368,8 +403,7 @@ smppi_status bfail(smppi_batch* b, smppi_status s, const std::string& m) {
     } while (0)
 
 size_t batch_smem(int RB, int n_track_max, int T_max) {
-    const int npad = (n_track_max + 3) & ~3;
-    return (size_t)n_track_max * 16 + (size_t)npad * 4 + (size_t)T_max * 16 + (size_t)T_max * 8 * 3 +
+    return rec_table_bytes(n_track_max) + (size_t)T_max * 32 + (size_t)T_max * 8 * 3 +
            (size_t)(T_max + 2) * NFIELD * 4 + (size_t)RB * BATCH_PPT * 8 + (size_t)T_max * 2 * 4;
 }
 
@@ -389,18 +423,19 @@ const void* batch_kernel_ptr(const smppi_batch* b, int RB) {
 }
 
 // Offsets, chunk counts and the work-item order (decreasing T, then problem,
-// then chunk) for RB rollouts per item.
+// then chunk) for items of RB threads (2 RB rollouts on the packed path).
 smppi_status layout(smppi_batch* b, int RB) {
     std::vector<int> order(b->B);
     for (int i = 0; i < b->B; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(),
                      [&](int x, int y) { return b->desc[x].T > b->desc[y].T; });
+    const int chunk = batch_fast(b) ? 2 * RB : RB;
     int S_off = 0, chunk_off = 0;
     std::vector<int2> items;
     for (int i = 0; i < b->B; ++i) {
         BatchInst& D = b->inst[i];
         D.S_off = S_off;
-        D.n_chunks = (D.K + RB - 1) / RB;
+        D.n_chunks = (D.K + chunk - 1) / chunk;
         D.chunk_off = chunk_off;
         S_off += D.K;
         chunk_off += D.n_chunks;
@@ -422,7 +457,7 @@ smppi_status enqueue_batch(smppi_batch* b, cudaStream_t st, float* x0, float* V,
                            uint32_t iter, int n_repair, uint32_t* iter_dev) {
     BatchArgs a;
     a.inst = b->d_inst; a.items = b->d_items; a.n_items = b->n_items;
-    a.seg = b->seg; a.inv = b->inv; a.S = b->S; a.chunk_min = b->chunk_min;
+    a.rec = b->rec; a.S = b->S; a.chunk_min = b->chunk_min;
     a.done = b->done; a.head = b->head;
     a.x0 = x0; a.V = V; a.V_safe = Vs;
     a.iter = iter; a.iter_dev = iter_dev;
@@ -510,7 +545,7 @@ smppi_status autotune(smppi_batch* b, const float* x0, const float* V, const flo
 
 void bfree(smppi_batch* b) {
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
-    void* ptrs[] = {b->d_inst, b->d_track_off, b->d_items, b->seg, b->inv, b->S, b->chunk_min,
+    void* ptrs[] = {b->d_inst, b->d_track_off, b->d_items, b->rec, b->S, b->chunk_min,
                     b->done, b->head, b->status, b->iter_dev, b->tune_x0, b->tune_V, b->tune_Vs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -542,7 +577,7 @@ smppi_status smppi_batch_create(const smppi_params* shared, int B, const smppi_i
     b->desc.assign(desc, desc + B);
     b->st = static_cast<cudaStream_t>(cuda_stream);
     b->inst.resize(B);
-    long long totK = 0, seg_tot = 0, chunks64 = 0;
+    long long totK = 0, rec_tot = 0, chunks64 = 0;
     std::vector<int> track_off(B);
     for (int i = 0; i < B; ++i) {
         const smppi_instance_desc& d = desc[i];
@@ -554,14 +589,14 @@ smppi_status smppi_batch_create(const smppi_params* shared, int B, const smppi_i
         }
         BatchInst& D = b->inst[i];
         D.K = d.K; D.T = d.T; D.N_r = d.N_r; D.n_track = d.n_track;
-        D.seg_off = (int)seg_tot;
+        D.rec_off = (int)rec_tot;
         D.V_off = d.V_offset;
         const double w2 = (double)d.half_width * d.half_width;
         D.w2 = (float)w2;
         D.qd_w2 = (float)(shared->q_d / w2);
         const double e_max = std::max(shared->sigma[0], shared->sigma[1]) * std::sqrt(48.0 * std::log(2.0));
         D.w_skip = e_max > 0.0 ? (float)(1e-8 / ((double)d.K * e_max)) : 3.0e38f;
-        seg_tot += (d.n_track + 3) & ~3;
+        rec_tot += 3LL * (d.n_track + 5);
         totK += d.K;
         chunks64 += (d.K + 63) / 64;
         track_off[i] = d.track_offset;
@@ -583,8 +618,7 @@ smppi_status smppi_batch_create(const smppi_params* shared, int B, const smppi_i
     BALLOC(b->d_inst, sizeof(BatchInst) * B);
     BALLOC(b->d_track_off, sizeof(int) * B);
     BALLOC(b->d_items, sizeof(int2) * b->max_items);
-    BALLOC(b->seg, sizeof(float4) * seg_tot);
-    BALLOC(b->inv, sizeof(float) * seg_tot);
+    BALLOC(b->rec, sizeof(float4) * rec_tot);
     BALLOC(b->S, sizeof(float) * totK);
     BALLOC(b->chunk_min, sizeof(float) * chunks64);
     BALLOC(b->done, sizeof(unsigned) * B);
@@ -610,7 +644,7 @@ smppi_status smppi_batch_create(const smppi_params* shared, int B, const smppi_i
     }
     s = layout(b, block_rollouts ? block_rollouts : 128);
     if (s == SMPPI_OK) {
-        batch_seg_tables<<<B, 128, 0, b->st>>>(tracks_xy, b->d_inst, b->d_track_off, B, b->seg, b->inv);
+        batch_rec_tables<<<B, 128, 0, b->st>>>(tracks_xy, b->d_inst, b->d_track_off, B, b->rec);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
         if (e != cudaSuccess) s = bfail(nullptr, SMPPI_ERR_CUDA, cudaGetErrorString(e));

@@ -291,78 +291,126 @@ __device__ __forceinline__ void model_step_adjoint(const DevParams& P, const Sta
 }
 
 // ---------------------------------------------------------------------------
-// Track: closed polyline, segment i = (A_i, D_i = A_{i+1} - A_i) plus 1/|D_i|^2.
+// Packed FP32 pairs (sm_100+: one FFMA2 / FADD2 / FMUL2 does the same IEEE
+// operation on both halves of a register pair).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float seg_d2(const float4* __restrict__ seg,
-                                        const float* __restrict__ inv, int i, float X, float Y) {
-    const float4 s = seg[i];
-    const float ex = X - s.x, ey = Y - s.y;
-    const float tau = __saturatef(fmaf(ex, s.z, ey * s.w) * inv[i]);
-    const float rx = fmaf(-tau, s.z, ex), ry = fmaf(-tau, s.w, ey);
+namespace x2 {
+
+using f2 = float2;
+
+__device__ __forceinline__ f2 bc(float v) { return make_float2(v, v); }
+__device__ __forceinline__ f2 add(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 mul(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 fma(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2 neg(f2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ f2 lo(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ f2 hi(float4 v) { return make_float2(v.z, v.w); }
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+}  // namespace x2
+
+// ---------------------------------------------------------------------------
+// Track: closed polyline P_0 .. P_{n-1}; segment i runs from A_i = P_i with
+// D_i = P_{i+1 mod n} - A_i.  Stored as a table of segment PAIRS built once
+// per track (launch_rec_table):
+//   record j (j = 0 .. n + 4) = segments (j - 1 mod n, j mod n) as
+//     float4 nA = (-A_x, -A_x', -A_y, -A_y'),
+//     float4 nD = (-D_x, -D_x', -D_y, -D_y'),
+//     float4 Dn = (D_x, D_x', D_y, D_y') / |D|^2   (0 for a zero-length segment)
+//   (primes: the second segment).  One record gives the squared distances to
+//   two consecutive segments with packed instructions; segment i is the first
+//   half of record i + 1.  The squared distance from (X, Y) to segment i is
+//   |e - tau D|^2 with e = (X, Y) - A, tau = clamp(e . Dn, 0, 1).
+// ---------------------------------------------------------------------------
+
+// Squared distances from (X, Y) to the two segments of record j.
+__device__ __forceinline__ float2 rec_d2(const float4* __restrict__ rec, int j, float2 XX,
+                                         float2 YY) {
+    using namespace x2;
+    const float4 nA = rec[3 * j], nD = rec[3 * j + 1], Dn = rec[3 * j + 2];
+    const f2 ex = add(XX, lo(nA)), ey = add(YY, hi(nA));
+    f2 t = fma(ex, lo(Dn), mul(ey, hi(Dn)));
+    t.x = __saturatef(t.x);
+    t.y = __saturatef(t.y);
+    const f2 rx = fma(t, lo(nD), ex), ry = fma(t, hi(nD), ey);
+    return fma(rx, rx, mul(ry, ry));
+}
+
+// The same arithmetic for segment i alone (first half of record i + 1).
+__device__ __forceinline__ float rec_d2_seg(const float4* __restrict__ rec, int i, float X,
+                                            float Y) {
+    const float4 nA = rec[3 * (i + 1)], nD = rec[3 * (i + 1) + 1], Dn = rec[3 * (i + 1) + 2];
+    const float ex = X + nA.x, ey = Y + nA.z;
+    const float t = __saturatef(fmaf(ex, Dn.x, ey * Dn.z));
+    const float rx = fmaf(t, nD.x, ex), ry = fmaf(t, nD.z, ey);
     return fmaf(rx, rx, ry * ry);
 }
 
-// Offset vector from the nearest point of segment i to (X, Y); d(e_y^2)/d(X,Y) = 2 r.
-__device__ __forceinline__ float2 seg_offset(const float4* __restrict__ seg,
-                                             const float* __restrict__ inv, int i, float X,
+// Offset from the nearest point of segment i to (X, Y): d(e_y^2)/d(X, Y) = 2 r.
+__device__ __forceinline__ float2 rec_offset(const float4* __restrict__ rec, int i, float X,
                                              float Y) {
-    const float4 s = seg[i];
-    const float ex = X - s.x, ey = Y - s.y;
-    const float tau = __saturatef(fmaf(ex, s.z, ey * s.w) * inv[i]);
-    return make_float2(fmaf(-tau, s.z, ex), fmaf(-tau, s.w, ey));
+    const float4 nA = rec[3 * (i + 1)], nD = rec[3 * (i + 1) + 1], Dn = rec[3 * (i + 1) + 2];
+    const float ex = X + nA.x, ey = Y + nA.z;
+    const float t = __saturatef(fmaf(ex, Dn.x, ey * Dn.z));
+    return make_float2(fmaf(t, nD.x, ex), fmaf(t, nD.z, ey));
 }
 
-// Continuous tracking of the nearest segment: walk forward while the next
-// segment is strictly closer, else backward while the previous one is.
-__device__ __forceinline__ int track_follow(const float4* __restrict__ seg,
-                                            const float* __restrict__ inv, int n, int s, float X,
-                                            float Y, float& d2) {
-    float d = seg_d2(seg, inv, s, X, Y);
+// Continuous tracking of the nearest segment (the walk that defines e_y along a
+// trajectory): from the previous segment s walk forward while the next segment
+// is strictly closer, else backward while the previous one is; one segment at
+// a time.
+static __device__ __noinline__ int walk_seq_rec(const float4* __restrict__ rec, int n, int s, float X,
+                                         float Y, float& d2) {
+    float d = rec_d2_seg(rec, s, X, Y);
     int nx = (s + 1 == n) ? 0 : s + 1;
-    float dn = seg_d2(seg, inv, nx, X, Y);
+    float dn = rec_d2_seg(rec, nx, X, Y);
     if (dn < d) {
         for (int it = 0; it < n && dn < d; ++it) {
             s = nx;
             d = dn;
             nx = (s + 1 == n) ? 0 : s + 1;
-            dn = seg_d2(seg, inv, nx, X, Y);
+            dn = rec_d2_seg(rec, nx, X, Y);
         }
     } else {
         int pv = (s == 0) ? n - 1 : s - 1;
-        float dp = seg_d2(seg, inv, pv, X, Y);
+        float dp = rec_d2_seg(rec, pv, X, Y);
         for (int it = 0; it < n && dp < d; ++it) {
             s = pv;
             d = dp;
             pv = (s == 0) ? n - 1 : s - 1;
-            dp = seg_d2(seg, inv, pv, X, Y);
+            dp = rec_d2_seg(rec, pv, X, Y);
         }
     }
     d2 = d;
     return s;
 }
 
-// The same walk with its first steps evaluated speculatively: the distances
-// to segments s-1 .. s+3 are computed independently (no dependent chain of
-// loads and compares) and the outcome of the walk is selected from them when
-// it ends within s .. s+2; a longer forward walk or any backward walk reruns
-// track_follow from s.  The result is therefore identical to track_follow.
-__device__ __forceinline__ int track_follow_spec(const float4* __restrict__ seg,
-                                                 const float* __restrict__ inv, int n, int s,
-                                                 float X, float Y, float& d2) {
-    const int sm1 = (s == 0) ? n - 1 : s - 1;
-    const int sp1 = (s + 1 == n) ? 0 : s + 1;
-    const int sp2 = (sp1 + 1 == n) ? 0 : sp1 + 1;
-    const int sp3 = (sp2 + 1 == n) ? 0 : sp2 + 1;
-    const float dm1 = seg_d2(seg, inv, sm1, X, Y);
-    const float d0 = seg_d2(seg, inv, s, X, Y);
-    const float dp1 = seg_d2(seg, inv, sp1, X, Y);
-    const float dp2 = seg_d2(seg, inv, sp2, X, Y);
-    const float dp3 = seg_d2(seg, inv, sp3, X, Y);
-    const bool f1 = dp1 < d0, f2 = dp2 < dp1, f3 = dp3 < dp2, b1 = dm1 < d0;
-    int r = f1 ? (f2 ? sp2 : sp1) : s;
-    float dr = f1 ? (f2 ? dp2 : dp1) : d0;
-    if (f1 ? (f2 && f3) : b1) r = track_follow(seg, inv, n, s, X, Y, dr);
-    d2 = dr;
+// The descent walk from s evaluated on the window s-1 .. s+4 (three records,
+// six packed distances): it ends within s .. s+3; a longer forward walk or
+// any backward step reruns walk_seq_rec (or, with SPEC, sets fb and returns a
+// segment in [0, n) that the caller discards).  Same result as walk_seq_rec.
+template <bool SPEC>
+__device__ __forceinline__ int walk_rec(const float4* __restrict__ rec, int n, int s, float X,
+                                        float Y, float& d2, bool& fb) {
+    const float2 XX = make_float2(X, X), YY = make_float2(Y, Y);
+    const float2 p0 = rec_d2(rec, s, XX, YY);       // d(s-1), d(s)
+    const float2 p1 = rec_d2(rec, s + 2, XX, YY);   // d(s+1), d(s+2)
+    const float2 p2 = rec_d2(rec, s + 4, XX, YY);   // d(s+3), d(s+4)
+    const bool f1 = p1.x < p0.y, f2_ = p1.y < p1.x, f3 = p2.x < p1.y, f4 = p2.y < p2.x;
+    const bool b1 = p0.x < p0.y;
+    const int adv = f1 ? (f2_ ? (f3 ? 3 : 2) : 1) : 0;
+    const float dd = f1 ? (f2_ ? (f3 ? p2.x : p1.y) : p1.x) : p0.y;
+    const bool out = f1 ? (f2_ && f3 && f4) : b1;
+    if (SPEC) fb |= out;
+    else if (out) return walk_seq_rec(rec, n, s, X, Y, d2);
+    int r = s + adv;
+    if (r >= n) r -= n;
+    d2 = dd;
     return r;
 }
 
@@ -426,15 +474,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 // gamma v' Sigma^-1 u, x <- f(x, clamp(u)), project on the track, add q and the
 // DCBF penalty (Eq. 12, 17-20).
 // vg = (v, gamma Sigma^-1 v) of the step.
-__device__ __forceinline__ void rollout_step(const DevParams& P, const float4* seg,
-                                             const float* inv, float4 vg, float2 z, State& x,
-                                             int& s, float& h_prev, float& acc) {
+__device__ __forceinline__ void rollout_step(const DevParams& P, const float4* rec, float4 vg,
+                                             float2 z, State& x, int& s, float& h_prev,
+                                             float& acc) {
     const float u0 = fmaf(P.sig0, z.x, vg.x), u1 = fmaf(P.sig1, z.y, vg.y);
     acc = fmaf(vg.z, u0, acc);
     acc = fmaf(vg.w, u1, acc);
     model_step(P, x, clampf(u0, P.umin0, P.umax0), clampf(u1, P.umin1, P.umax1));
     float d2;
-    s = track_follow_spec(seg, inv, P.n_track, s, x.X, x.Y, d2);
+    bool fb = false;
+    s = walk_rec<false>(rec, P.n_track, s, x.X, x.Y, d2, fb);
     const float h = P.w2 - d2;
     acc += run_cost(P, x.vx, d2) + P.C_cbf * fmaxf(cbf_arg(P, h_prev, h), 0.0f);
     h_prev = h;
@@ -442,10 +491,11 @@ __device__ __forceinline__ void rollout_step(const DevParams& P, const float4* s
 
 // Cost of state x_t: walk to its segment, add q(x_t) and the DCBF penalty of
 // the pair (x_{t-1}, x_t) (Eq. 17, 24).
-__device__ __forceinline__ void track_cost(const DevParams& P, const float4* seg, const float* inv,
-                                           const State& x, int& s, float& h_prev, float& acc) {
+__device__ __forceinline__ void track_cost(const DevParams& P, const float4* rec, const State& x,
+                                           int& s, float& h_prev, float& acc) {
     float d2;
-    s = track_follow_spec(seg, inv, P.n_track, s, x.X, x.Y, d2);
+    bool fb = false;
+    s = walk_rec<false>(rec, P.n_track, s, x.X, x.Y, d2, fb);
     const float h = P.w2 - d2;
     acc += run_cost(P, x.vx, d2) + P.C_cbf * fmaxf(cbf_arg(P, h_prev, h), 0.0f);
     h_prev = h;
@@ -472,8 +522,8 @@ __device__ __forceinline__ void dump_row(float* tr, int t, const State& x) {
 // segment s and squared offset d20; Vs[t] = (v_t, gamma Sigma^-1 v_t); traj
 // (DUMP only): this rollout's (T + 1) x 6 row.
 template <bool FAST, bool DUMP>
-__device__ __forceinline__ float rollout_sample(const DevParams& P, const float4* seg,
-                                                const float* inv, const float4* Vs, State x, int s,
+__device__ __forceinline__ float rollout_sample(const DevParams& P, const float4* rec,
+                                                const float4* Vs, State x, int s,
                                                 float d20, uint32_t k, uint32_t iter,
                                                 uint32_t ctr3, float* traj) {
     const int T = P.T, npair = (T + 1) >> 1;
@@ -493,7 +543,7 @@ __device__ __forceinline__ float rollout_sample(const DevParams& P, const float4
             const float2 ub = perturb(P, Vs[1], zb, acc);
             State xb = x;
             model_step<FAST>(P, xb, ub.x, ub.y);
-            track_cost(P, seg, inv, x, s, h_prev, acc);
+            track_cost(P, rec, x, s, h_prev, acc);
             x = xb;
             if (DUMP) dump_row(traj, 2, x);
         }
@@ -506,13 +556,13 @@ __device__ __forceinline__ float rollout_sample(const DevParams& P, const float4
         const float2 ua = perturb(P, Vs[2 * p], za, acc);
         State xa = x;
         model_step<FAST>(P, xa, ua.x, ua.y);
-        track_cost(P, seg, inv, x, s, h_prev, acc);
+        track_cost(P, rec, x, s, h_prev, acc);
         if (DUMP) dump_row(traj, 2 * p + 1, xa);
         if (2 * p + 1 < T) {
             const float2 ub = perturb(P, Vs[2 * p + 1], zb, acc);
             State xb = xa;
             model_step<FAST>(P, xb, ub.x, ub.y);
-            track_cost(P, seg, inv, xa, s, h_prev, acc);
+            track_cost(P, rec, xa, s, h_prev, acc);
             x = xb;
             if (DUMP) dump_row(traj, 2 * p + 2, x);
         } else {
@@ -521,7 +571,7 @@ __device__ __forceinline__ float rollout_sample(const DevParams& P, const float4
         za = na;
         zb = nb;
     }
-    track_cost(P, seg, inv, x, s, h_prev, acc);   // x_T
+    track_cost(P, rec, x, s, h_prev, acc);   // x_T
     return acc;
 }
 

@@ -21,12 +21,12 @@ size_t rollout_smem_bytes(int n_track, int T);
 int rollout_blocks(const DevParams& P);
 // Rollouts: S_out [K] and blk_min [rollout_blocks(P)]; traj (optional dump);
 // seg0_out (optional): nearest segment of x0.  rec: segment-pair table of
-// launch_rec_table (read when the packed kernel runs: C = 1.5, |steer| <= 1/2).
+// launch_rec_table.
 cudaError_t launch_rollout(const DevParams& P, bool dump, const float* x0, const float* V,
-                           const float4* seg, const float* inv, const float4* rec, uint32_t iter,
-                           uint32_t ctr3, const uint32_t* iter_dev, float* S_out, float* traj,
-                           float* blk_min, int* seg0_out, unsigned* status, cudaStream_t st);
-// Segment-pair table of a closed polyline (layout in rollout2.cuh): n + 5
+                           const float4* rec, uint32_t iter, uint32_t ctr3,
+                           const uint32_t* iter_dev, float* S_out, float* traj, float* blk_min,
+                           int* seg0_out, unsigned* status, cudaStream_t st);
+// Segment-pair table of a closed polyline (layout in device.cuh): n + 5
 // records of three float4.
 __host__ __device__ inline size_t rec_table_bytes(int n) { return (size_t)(n + 5) * 3 * sizeof(float4); }
 cudaError_t launch_rec_table(const float* track_xy, int n, float4* rec, cudaStream_t st);
@@ -43,9 +43,6 @@ cudaError_t launch_update(const DevParams& P, const float* S, const float* blk_m
 cudaError_t launch_debug_noise(const DevParams& P, uint32_t iter, uint32_t ctr3, int K, int T,
                                float* eps, uint32_t* raw, cudaStream_t st);
 
-// Segment table of a closed polyline: seg[i] = (A_i, A_{i+1} - A_i), inv[i] = 1/|D_i|^2.
-cudaError_t launch_seg_table(const float* track_xy, int n, float4* seg, float* inv,
-                             cudaStream_t st);
 
 // Repair / adjoint workspace (device), sized for max_seq sequences of horizon T.
 struct RepairWs {
@@ -69,13 +66,13 @@ struct ApplyArgs {
     uint32_t* iter_dev;        // graph replays: n += *iter_dev, then ++*iter_dev
 };
 
-cudaError_t launch_seg0(const DevParams& P, const float4* seg, const float* inv, int n_seq,
+cudaError_t launch_seg0(const DevParams& P, const float4* rec, int n_seq,
                         const float* x0, int* seg0, cudaStream_t st);
-cudaError_t launch_cost_grad(const DevParams& P, const float4* seg, const float* inv,
+cudaError_t launch_cost_grad(const DevParams& P, const float4* rec,
                              const RepairWs& ws, int n_seq, const float* x0, const float* V, int N,
                              float w_run, float w_cbf, int ck, double* J_out, float* grad_out,
                              unsigned* status, cudaStream_t st);
-cudaError_t launch_repair(const DevParams& P, const float4* seg, const float* inv,
+cudaError_t launch_repair(const DevParams& P, const float4* rec,
                           const RepairWs& ws, int n_seq, const float* x0, const float* V_in,
                           float* V_out, int n_iters, int mode, float delta, double* merit_out,
                           int* iters_out, const ApplyArgs& ap, unsigned* status, cudaStream_t st);

@@ -2,7 +2,7 @@
 // device memory (hard real-time control loops that forbid allocation after
 // start-up, or host runtimes that own every device allocation themselves).
 //
-// The iteration's scratch (segment tables, rollout costs, block minima, the
+// The iteration's scratch (segment-pair table, rollout costs, block minima, the
 // update kernel's partials and counters) lives in one file-scope __device__
 // array of fixed size, so the call allocates nothing.  Host code cannot use
 // the array's name as a device address: its device address is looked up once
@@ -24,9 +24,7 @@ constexpr int NA_MAX_K = 65536;
 constexpr int NA_MAX_BLK = (NA_MAX_K + ROLL_BLK - 1) / ROLL_BLK;
 
 constexpr size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
-constexpr size_t OFF_SEG = 0;
-constexpr size_t OFF_INV = OFF_SEG + align256(sizeof(float4) * SMPPI_MAX_TRACK);
-constexpr size_t OFF_REC = OFF_INV + align256(sizeof(float) * SMPPI_MAX_TRACK);
+constexpr size_t OFF_REC = 0;
 constexpr size_t OFF_S = OFF_REC + align256((size_t)(SMPPI_MAX_TRACK + 5) * 3 * sizeof(float4));
 constexpr size_t OFF_MIN = OFF_S + align256(sizeof(float) * NA_MAX_K);
 constexpr size_t OFF_ACC = OFF_MIN + align256(sizeof(float) * NA_MAX_BLK);
@@ -34,7 +32,7 @@ constexpr size_t OFF_ETA = OFF_ACC + align256(sizeof(float) * 2 * SMPPI_MAX_T * 
 constexpr size_t OFF_HAS = OFF_ETA + align256(sizeof(double) * UPD_BLK);
 constexpr size_t OFF_TICKET = OFF_HAS + align256(sizeof(int) * UPD_BLK);
 constexpr size_t OFF_STATUS = OFF_TICKET + 256;
-constexpr size_t SCRATCH_BYTES = OFF_STATUS + 256;   // about 1.5 MB per device
+constexpr size_t SCRATCH_BYTES = OFF_STATUS + 256;   // about 1.4 MB per device
 
 __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];
 
@@ -80,8 +78,6 @@ extern "C" smppi_status smppi_step_noalloc(const smppi_params* p, const float* x
     if (s != SMPPI_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     const DevParams dp = derive_params(*p);
-    float4* seg = reinterpret_cast<float4*>(base + OFF_SEG);
-    float* inv = reinterpret_cast<float*>(base + OFF_INV);
     float4* rec = reinterpret_cast<float4*>(base + OFF_REC);
     float* S = S_out ? S_out : reinterpret_cast<float*>(base + OFF_S);
     float* blk_min = reinterpret_cast<float*>(base + OFF_MIN);
@@ -93,10 +89,9 @@ extern "C" smppi_status smppi_step_noalloc(const smppi_params* p, const float* x
     const uint32_t ctr3 = instance << 8;
     // the update's ticket must start at zero (a launch that was cut short can leave it set)
     cudaError_t e = cudaMemsetAsync(base + OFF_TICKET, 0, 512, st);
-    if (e == cudaSuccess) e = launch_seg_table(p->track_xy, p->n_track, seg, inv, st);
     if (e == cudaSuccess) e = launch_rec_table(p->track_xy, p->n_track, rec, st);
     if (e == cudaSuccess)
-        e = launch_rollout(dp, false, x0, V, seg, inv, rec, iter, ctr3, nullptr, S, nullptr,
+        e = launch_rollout(dp, false, x0, V, rec, iter, ctr3, nullptr, S, nullptr,
                            blk_min, nullptr, status, st);
     if (e == cudaSuccess)
         e = launch_update(dp, S, blk_min, rollout_blocks(dp), V, iter, ctr3, nullptr,

@@ -13,28 +13,16 @@
 
 namespace smppi {
 
-__global__ void seg_table_kernel(const float* __restrict__ xy, int n, float4* __restrict__ seg,
-                                 float* __restrict__ inv) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int j = (i + 1 == n) ? 0 : i + 1;
-    const float ax = xy[2 * i], ay = xy[2 * i + 1];
-    const float dx = xy[2 * j] - ax, dy = xy[2 * j + 1] - ay;
-    seg[i] = make_float4(ax, ay, dx, dy);
-    inv[i] = 1.0f / fmaf(dx, dx, dy * dy);
-}
-
-// Global nearest segment of each x0 (one warp per sequence).
-__global__ void seg0_kernel(DevParams P, const float4* __restrict__ seg,
-                            const float* __restrict__ inv, int n_seq, const float* __restrict__ x0,
-                            int* __restrict__ seg0) {
+// Global nearest segment of each x0 (one warp per sequence; lowest index on ties).
+__global__ void seg0_kernel(DevParams P, const float4* __restrict__ rec, int n_seq,
+                            const float* __restrict__ x0, int* __restrict__ seg0) {
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (w >= n_seq) return;
     const float X = x0[6 * w + 3], Y = x0[6 * w + 4];
     float bd = 3.0e38f;
     int bi = 0x7fffffff;
     for (int i = lane; i < P.n_track; i += 32) {
-        const float d = seg_d2(seg, inv, i, X, Y);
+        const float d = rec_d2_seg(rec, i, X, Y);
         if (d < bd) { bd = d; bi = i; }
     }
     warp_argmin(bd, bi);
@@ -43,25 +31,21 @@ __global__ void seg0_kernel(DevParams P, const float4* __restrict__ seg,
 
 constexpr int REP_BLK = 64;
 
-__device__ __forceinline__ void stage_track(const DevParams& P, const float4* __restrict__ segg,
-                                            const float* __restrict__ invg, float4* seg,
-                                            float* inv) {
-    for (int i = threadIdx.x; i < P.n_track; i += blockDim.x) {
-        seg[i] = segg[i];
-        inv[i] = invg[i];
-    }
+__device__ __forceinline__ void stage_track(const DevParams& P, const float4* __restrict__ recg,
+                                            float4* rec) {
+    for (int i = threadIdx.x; i < 3 * (P.n_track + 5); i += blockDim.x) rec[i] = recg[i];
     __syncthreads();
 }
 
+template <bool FAST>
 __global__ void __launch_bounds__(REP_BLK) cost_grad_kernel(
-    DevParams P, const float4* __restrict__ segg, const float* __restrict__ invg, RepairWs ws,
+    DevParams P, const float4* __restrict__ recg, RepairWs ws,
     int n_seq, const float* __restrict__ x0g, const float* __restrict__ Vg, int N, float w_run,
     float w_cbf, int ck, double* __restrict__ J_out, float* __restrict__ grad_out,
     unsigned* __restrict__ status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float4* seg = reinterpret_cast<float4*>(smem_raw);
-    float* inv = reinterpret_cast<float*>(seg + P.n_track);
-    stage_track(P, segg, invg, seg, inv);
+    float4* rec = reinterpret_cast<float4*>(smem_raw);
+    stage_track(P, recg, rec);
     const int q = blockIdx.x * REP_BLK + threadIdx.x;
     if (q >= n_seq) return;
     const int T = P.T, ms = ws.max_seq;
@@ -69,23 +53,23 @@ __global__ void __launch_bounds__(REP_BLK) cost_grad_kernel(
     for (int t = 0; t < T; ++t) ws.Vw[(size_t)t * ms + q] = Vrow[t];
     const State x0 = make_state(x0g + 6 * q);
     const Tape tape{ws.tape, ms, q};
-    const double J = seq_cost_grad(P, seg, inv, x0, ws.seg0[q], N, T, ws.Vw, ws.G, ms, q, w_run,
-                                   w_cbf, ck, tape);
+    const double J = seq_cost_grad<FAST>(P, rec, x0, ws.seg0[q], N, T, ws.Vw, ws.G, ms, q, w_run,
+                                         w_cbf, ck, tape);
     if (J_out) J_out[q] = J;
     if (!isfinite(J)) atomicOr(status, SMPPI_DEV_NUMERIC);
     float2* grow = reinterpret_cast<float2*>(grad_out) + (size_t)q * T;
     for (int t = 0; t < T; ++t) grow[t] = ws.G[(size_t)t * ms + q];
 }
 
+template <bool FAST>
 __global__ void __launch_bounds__(REP_BLK) repair_kernel(
-    DevParams P, const float4* __restrict__ segg, const float* __restrict__ invg, RepairWs ws,
+    DevParams P, const float4* __restrict__ recg, RepairWs ws,
     int n_seq, const float* __restrict__ x0g, const float* Vin, float* Vout, int n_iters,
     int mode, float delta, double* __restrict__ merit_out, int* __restrict__ iters_out,
     ApplyArgs ap, unsigned* __restrict__ status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float4* seg = reinterpret_cast<float4*>(smem_raw);
-    float* inv = reinterpret_cast<float*>(seg + P.n_track);
-    stage_track(P, segg, invg, seg, inv);
+    float4* rec = reinterpret_cast<float4*>(smem_raw);
+    stage_track(P, recg, rec);
     const int q = blockIdx.x * REP_BLK + threadIdx.x;
     if (q >= n_seq) return;
     const int T = P.T, N = P.N_r, ms = ws.max_seq;
@@ -95,21 +79,21 @@ __global__ void __launch_bounds__(REP_BLK) repair_kernel(
     const State x0 = make_state(x0g + 6 * q);
     const int s0 = ws.seg0[q];
     const Tape tape{ws.tape, ms, q};
-    double P0 = forward_cost<false, false>(P, seg, inv, x0, s0, N, ws.Vw, nullptr, 0.0f, ms, q,
+    double P0 = forward_cost<false, false, FAST>(P, rec, x0, s0, N, ws.Vw, nullptr, 0.0f, ms, q,
                                            0.0f, 1.0f, 0, tape, nullptr);
     int it = 0;
     bool stalled = false;
     for (; it < n_iters; ++it) {
         if (merit_out) merit_out[(size_t)q * (n_iters + 1) + it] = P0;
         if (P0 == 0.0) break;
-        seq_cost_grad(P, seg, inv, x0, s0, N, T, ws.Vw, ws.G, ms, q, 0.0f, 1.0f, ws.ck, tape);
+        seq_cost_grad<FAST>(P, rec, x0, s0, N, T, ws.Vw, ws.G, ms, q, 0.0f, 1.0f, ws.ck, tape);
         if (mode == 0) {
             for (int t = 0; t < N; ++t) {
                 const size_t o = (size_t)t * ms + q;
                 const float2 v = ws.Vw[o], g = ws.G[o];
                 ws.Vw[o] = clamp2(P, make_float2(fmaf(-delta, g.x, v.x), fmaf(-delta, g.y, v.y)));
             }
-            P0 = forward_cost<false, false>(P, seg, inv, x0, s0, N, ws.Vw, nullptr, 0.0f, ms, q,
+            P0 = forward_cost<false, false, FAST>(P, rec, x0, s0, N, ws.Vw, nullptr, 0.0f, ms, q,
                                             0.0f, 1.0f, 0, tape, nullptr);
             continue;
         }
@@ -123,7 +107,7 @@ __global__ void __launch_bounds__(REP_BLK) repair_kernel(
         bool accepted = false;
         for (int j = 0; j < P.ls_max; ++j) {
             double dec;
-            const double Pt = forward_cost<false, true>(P, seg, inv, x0, s0, N, ws.Vw, ws.G, s, ms,
+            const double Pt = forward_cost<false, true, FAST>(P, rec, x0, s0, N, ws.Vw, ws.G, s, ms,
                                                         q, 0.0f, 1.0f, 0, tape, &dec);
             if (Pt <= P0 - (double)P.ls_c * dec) {
                 for (int t = 0; t < N; ++t) {
@@ -155,43 +139,46 @@ constexpr int REPB_BLK = 64;
 
 template <bool FAST>
 __global__ void __launch_bounds__(REPB_BLK) repair_block_kernel(
-    DevParams P, const float4* __restrict__ segg, const float* __restrict__ invg, int inv_pad,
-    const float* __restrict__ x0g, const float* Vin, float* Vout, int n_iters, int mode,
-    float delta, int ck, double* __restrict__ merit_out, int* __restrict__ iters_out, ApplyArgs ap,
-    unsigned* __restrict__ status) {
+    DevParams P, const float4* __restrict__ recg, const float* __restrict__ x0g, const float* Vin,
+    float* Vout, int n_iters, int mode, float delta, int ck, double* __restrict__ merit_out,
+    int* __restrict__ iters_out, ApplyArgs ap, unsigned* __restrict__ status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int T = P.T, n = P.n_track;
-    float4* seg = reinterpret_cast<float4*>(smem_raw);
-    float* inv = reinterpret_cast<float*>(seg + n);
-    float2* Vw = reinterpret_cast<float2*>(inv + inv_pad);
+    float4* rec = reinterpret_cast<float4*>(smem_raw);
+    float2* Vw = reinterpret_cast<float2*>(rec + 3 * (n + 5));
     float2* G = Vw + T;
     float* tape_s = reinterpret_cast<float*>(G + T);
     __shared__ __align__(8) uint64_t bar;
     __shared__ RepairSmem sm;
     __shared__ float s_red[REPB_BLK / 32];
     __shared__ int s_redi[REPB_BLK / 32];
+    __shared__ int s_fail;
     const int tid = threadIdx.x;
     const int q = blockIdx.x;
 
-    // stage the track (bulk copy) and this sequence's controls
-    if (tid == 0) mbar_init(&bar, 1);
-    __syncthreads();
+    // stage the track (bulk copy, bounded wait) and this sequence's controls
     if (tid == 0) {
-        const uint32_t b_seg = (uint32_t)n * 16u, b_inv = (uint32_t)inv_pad * 4u;
-        mbar_expect_tx(&bar, b_seg + b_inv);
-        bulk_g2s(seg, segg, b_seg, &bar);
-        bulk_g2s(inv, invg, b_inv, &bar);
+        s_fail = 0;
+        mbar_init(&bar, 1);
+        const uint32_t bytes = (uint32_t)rec_table_bytes(n);
+        mbar_expect_tx(&bar, bytes);
+        bulk_g2s(rec, recg, bytes, &bar);
     }
     const float2* vin = reinterpret_cast<const float2*>(Vin) + (size_t)q * T;
     for (int t = tid; t < T; t += REPB_BLK) Vw[t] = vin[t];
     const State x0 = make_state(x0g + 6 * q);
-    if (!mbar_wait_bounded(&bar, 0)) {
-        atomicOr(status, SMPPI_DEV_TIMEOUT);
-        mbar_wait_bounded(&bar, 0);   // give the copy in flight a second chance to land
+    __syncthreads();
+    if (!mbar_wait_bounded(&bar, 0)) s_fail = 1;
+    __syncthreads();
+    if (s_fail) {
+        if (tid == 0) {
+            atomicOr(status, SMPPI_DEV_TIMEOUT);
+            mbar_wait_bounded(&bar, 0);   // let the copy in flight land before the block exits
+        }
         return;
     }
-    const int s0 = block_nearest_segment<REPB_BLK>(seg, inv, n, x0.X, x0.Y, s_red, s_redi, nullptr);
-    repair_in_block<REPB_BLK, FAST>(P, seg, inv, x0, s0, Vw, G, tape_s, n_iters, mode, delta, ck,
+    const int s0 = block_nearest_segment<REPB_BLK>(rec, n, x0.X, x0.Y, s_red, s_redi, nullptr);
+    repair_in_block<REPB_BLK, FAST>(P, rec, x0, s0, Vw, G, tape_s, n_iters, mode, delta, ck,
                               merit_out ? merit_out + (size_t)q * (n_iters + 1) : nullptr,
                               iters_out ? iters_out + q : nullptr, status, sm);
     float2* vout = reinterpret_cast<float2*>(Vout) + (size_t)q * T;
@@ -206,56 +193,49 @@ __global__ void apply_kernel(DevParams P, ApplyArgs ap, const float* V_exec) {
 }
 
 // ----------------------------------------------------------------------------
-cudaError_t launch_seg_table(const float* xy, int n, float4* seg, float* inv, cudaStream_t st) {
-    seg_table_kernel<<<(n + 127) / 128, 128, 0, st>>>(xy, n, seg, inv);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_seg0(const DevParams& P, const float4* seg, const float* inv, int n_seq,
-                        const float* x0, int* seg0, cudaStream_t st) {
+cudaError_t launch_seg0(const DevParams& P, const float4* rec, int n_seq, const float* x0,
+                        int* seg0, cudaStream_t st) {
     const int warps_per_block = 4;
     seg0_kernel<<<(n_seq + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, st>>>(
-        P, seg, inv, n_seq, x0, seg0);
+        P, rec, n_seq, x0, seg0);
     return cudaGetLastError();
 }
 
-static size_t track_smem(int n) { return (size_t)n * (sizeof(float4) + sizeof(float)); }
+static bool fast_model(const DevParams& P) { return P.tyre15 && P.steer_small; }
 
-cudaError_t launch_cost_grad(const DevParams& P, const float4* seg, const float* inv,
-                             const RepairWs& ws, int n_seq, const float* x0, const float* V, int N,
-                             float w_run, float w_cbf, int ck, double* J_out, float* grad_out,
-                             unsigned* status, cudaStream_t st) {
-    const size_t smem = track_smem(P.n_track);
-    cudaError_t e = ensure_smem((const void*)cost_grad_kernel, smem);
+cudaError_t launch_cost_grad(const DevParams& P, const float4* rec, const RepairWs& ws, int n_seq,
+                             const float* x0, const float* V, int N, float w_run, float w_cbf,
+                             int ck, double* J_out, float* grad_out, unsigned* status,
+                             cudaStream_t st) {
+    const size_t smem = rec_table_bytes(P.n_track);
+    auto kern = fast_model(P) ? cost_grad_kernel<true> : cost_grad_kernel<false>;
+    cudaError_t e = ensure_smem((const void*)kern, smem);
     if (e != cudaSuccess) return e;
-    cost_grad_kernel<<<(n_seq + REP_BLK - 1) / REP_BLK, REP_BLK, smem, st>>>(
-        P, seg, inv, ws, n_seq, x0, V, N, w_run, w_cbf, ck, J_out, grad_out, status);
+    kern<<<(n_seq + REP_BLK - 1) / REP_BLK, REP_BLK, smem, st>>>(
+        P, rec, ws, n_seq, x0, V, N, w_run, w_cbf, ck, J_out, grad_out, status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_repair(const DevParams& P, const float4* seg, const float* inv,
-                          const RepairWs& ws, int n_seq, const float* x0, const float* V_in,
-                          float* V_out, int n_iters, int mode, float delta, double* merit_out,
-                          int* iters_out, const ApplyArgs& ap, unsigned* status,
-                          cudaStream_t st) {
+cudaError_t launch_repair(const DevParams& P, const float4* rec, const RepairWs& ws, int n_seq,
+                          const float* x0, const float* V_in, float* V_out, int n_iters, int mode,
+                          float delta, double* merit_out, int* iters_out, const ApplyArgs& ap,
+                          unsigned* status, cudaStream_t st) {
     if (n_seq <= REPAIR_BLOCK_MAX_SEQ) {
-        const int inv_pad = (P.n_track + 3) & ~3;
-        const size_t smem = (size_t)P.n_track * 16 + (size_t)inv_pad * 4 + (size_t)P.T * 16 +
+        const size_t smem = rec_table_bytes(P.n_track) + (size_t)P.T * 16 +
                             (size_t)(P.T + 2) * NFIELD * 4;
-        auto kern = (P.tyre15 && P.steer_small) ? repair_block_kernel<true>
-                                                 : repair_block_kernel<false>;
+        auto kern = fast_model(P) ? repair_block_kernel<true> : repair_block_kernel<false>;
         cudaError_t e = ensure_smem((const void*)kern, smem);
         if (e != cudaSuccess) return e;
-        kern<<<n_seq, REPB_BLK, smem, st>>>(P, seg, inv, inv_pad, x0, V_in, V_out, n_iters, mode,
-                                            delta, ws.ck, merit_out, iters_out, ap, status);
+        kern<<<n_seq, REPB_BLK, smem, st>>>(P, rec, x0, V_in, V_out, n_iters, mode, delta, ws.ck,
+                                            merit_out, iters_out, ap, status);
         return cudaGetLastError();
     }
-    const size_t smem = track_smem(P.n_track);
-    cudaError_t e = ensure_smem((const void*)repair_kernel, smem);
+    const size_t smem = rec_table_bytes(P.n_track);
+    auto kern = fast_model(P) ? repair_kernel<true> : repair_kernel<false>;
+    cudaError_t e = ensure_smem((const void*)kern, smem);
     if (e != cudaSuccess) return e;
-    repair_kernel<<<(n_seq + REP_BLK - 1) / REP_BLK, REP_BLK, smem, st>>>(
-        P, seg, inv, ws, n_seq, x0, V_in, V_out, n_iters, mode, delta, merit_out, iters_out, ap,
-        status);
+    kern<<<(n_seq + REP_BLK - 1) / REP_BLK, REP_BLK, smem, st>>>(
+        P, rec, ws, n_seq, x0, V_in, V_out, n_iters, mode, delta, merit_out, iters_out, ap, status);
     return cudaGetLastError();
 }
 

@@ -33,28 +33,41 @@ __device__ __forceinline__ float warp_min(float v) {
 
 }  // namespace
 
-// Stage the centreline segment table, V and the nearest segment of x0.
+// Stage the segment-pair table (one bulk copy, bounded wait), V and the
+// nearest segment of x0 (block argmin, lowest index on ties).  Returns false
+// (status set, copy drained) if the copy did not complete.
 template <int BLK>
-__device__ __forceinline__ void stage_problem(const DevParams& P, const float4* __restrict__ segg,
-                                              const float* __restrict__ invg,
+__device__ __forceinline__ bool stage_problem(const DevParams& P, const float4* __restrict__ recg,
                                               const float* __restrict__ Vg, float X0, float Y0,
-                                              float4* seg, float* inv, float4* Vs, int* s_seg0,
-                                              float* s_d20, float* red_f, int* red_i) {
-    const int tid = threadIdx.x;
-    for (int i = tid; i < P.n_track; i += BLK) {
-        seg[i] = segg[i];
-        inv[i] = invg[i];
+                                              float4* rec, float4* Vs, uint64_t* bar, int* s_flag,
+                                              int* s_seg0, float* s_d20, float* red_f,
+                                              int* red_i, unsigned* status) {
+    const int tid = threadIdx.x, n = P.n_track;
+    if (tid == 0) {
+        *s_flag = 0;
+        mbar_init(bar, 1);
+        const uint32_t bytes = (uint32_t)rec_table_bytes(n);
+        mbar_expect_tx(bar, bytes);
+        bulk_g2s(rec, recg, bytes, bar);
     }
     for (int t = tid; t < P.T; t += BLK) {
         const float2 v = reinterpret_cast<const float2*>(Vg)[t];
         Vs[t] = make_float4(v.x, v.y, P.gis0 * v.x, P.gis1 * v.y);   // (v, gamma Sigma^-1 v)
     }
     __syncthreads();
-    // global nearest segment of x0 (lowest index on ties)
+    if (!mbar_wait_bounded(bar, 0u)) *s_flag = 1;
+    __syncthreads();
+    if (*s_flag) {
+        if (tid == 0) {
+            atomicOr(status, SMPPI_DEV_TIMEOUT);
+            mbar_wait_bounded(bar, 0u);   // let the copy in flight land before the block exits
+        }
+        return false;
+    }
     float bd = 3.0e38f;
     int bi = 0x7fffffff;
-    for (int i = tid; i < P.n_track; i += BLK) {
-        const float d = seg_d2(seg, inv, i, X0, Y0);
+    for (int i = tid; i < n; i += BLK) {
+        const float d = rec_d2_seg(rec, i, X0, Y0);
         if (d < bd) { bd = d; bi = i; }
     }
     warp_argmin(bd, bi);
@@ -68,6 +81,7 @@ __device__ __forceinline__ void stage_problem(const DevParams& P, const float4* 
         *s_d20 = bd;
     }
     __syncthreads();
+    return true;
 }
 
 // Launch 1: one thread per rollout.  FAST: model parameters of the
@@ -75,32 +89,32 @@ __device__ __forceinline__ void stage_problem(const DevParams& P, const float4* 
 template <int BLK, bool DUMP, bool FAST>
 __global__ void __launch_bounds__(BLK) mppi_rollout_kernel(
     DevParams P, const float* __restrict__ x0g, const float* __restrict__ Vg,
-    const float4* __restrict__ segg, const float* __restrict__ invg, uint32_t iter,
-    uint32_t ctr3, const uint32_t* __restrict__ iter_dev, float* __restrict__ S_out,
-    float* __restrict__ traj, float* __restrict__ blk_min, int* __restrict__ seg0_out,
-    unsigned* __restrict__ status) {
+    const float4* __restrict__ recg, uint32_t iter, uint32_t ctr3,
+    const uint32_t* __restrict__ iter_dev, float* __restrict__ S_out, float* __restrict__ traj,
+    float* __restrict__ blk_min, int* __restrict__ seg0_out, unsigned* __restrict__ status) {
     constexpr int NW = BLK / 32;
     if (iter_dev) iter += *iter_dev;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int T = P.T, n = P.n_track;
-    float4* seg = reinterpret_cast<float4*>(smem_raw);
-    float* inv = reinterpret_cast<float*>(seg + n);
-    float4* Vs = reinterpret_cast<float4*>(inv + ((n + 3) & ~3));
+    const int T = P.T;
+    float4* rec = reinterpret_cast<float4*>(smem_raw);
+    float4* Vs = rec + 3 * (P.n_track + 5);
+    __shared__ __align__(8) uint64_t bar;
     __shared__ float red_f[NW];
     __shared__ int red_i[NW];
-    __shared__ int s_seg0;
+    __shared__ int s_seg0, s_flag;
     __shared__ float s_d20;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int k = blockIdx.x * BLK + tid;
     const bool active = k < P.K;
 
-    stage_problem<BLK>(P, segg, invg, Vg, x0g[3], x0g[4], seg, inv, Vs, &s_seg0, &s_d20, red_f,
-                       red_i);
+    if (!stage_problem<BLK>(P, recg, Vg, x0g[3], x0g[4], rec, Vs, &bar, &s_flag, &s_seg0, &s_d20,
+                            red_f, red_i, status))
+        return;
     if (blockIdx.x == 0 && tid == 0 && seg0_out) *seg0_out = s_seg0;
     float S = 3.0e38f;
     if (active) {
-        S = rollout_sample<FAST, DUMP>(P, seg, inv, Vs, make_state(x0g), s_seg0, s_d20,
+        S = rollout_sample<FAST, DUMP>(P, rec, Vs, make_state(x0g), s_seg0, s_d20,
                                        (uint32_t)k, iter, ctr3,
                                        DUMP ? traj + (size_t)k * (T + 1) * 6 : nullptr);
         S_out[k] = S;
@@ -167,7 +181,7 @@ __global__ void __launch_bounds__(ROLL2_BLK, 2) mppi_rollout2_kernel(
     float bd = 3.0e38f;
     int bi = 0x7fffffff;
     for (int i = tid; i < n; i += BLK) {
-        const float d = x2::rec_d2_seg(rec, i, X0, Y0);
+        const float d = rec_d2_seg(rec, i, X0, Y0);
         if (d < bd) { bd = d; bi = i; }
     }
     warp_argmin(bd, bi);
@@ -433,10 +447,8 @@ __global__ void debug_noise_kernel(DevParams P, uint32_t iter, uint32_t ctr3, in
 // Host-side launchers
 // ----------------------------------------------------------------------------
 size_t rollout_smem_bytes(int n_track, int T) {
-    const size_t one = (size_t)n_track * sizeof(float4) +
-                       (size_t)((n_track + 3) & ~3) * sizeof(float) + (size_t)T * sizeof(float4);
-    const size_t two = rec_table_bytes(n_track) + (size_t)T * 2 * sizeof(float4);
-    return one > two ? one : two;
+    // the packed kernel's V pairs take two float4 per step, the scalar kernel's one
+    return rec_table_bytes(n_track) + (size_t)T * 2 * sizeof(float4);
 }
 
 static bool packed_rollout(const DevParams& P) { return P.tyre15 && P.steer_small; }
@@ -466,9 +478,9 @@ int update_grid(int K) {
 }
 
 cudaError_t launch_rollout(const DevParams& P, bool dump, const float* x0, const float* V,
-                           const float4* seg, const float* inv, const float4* rec, uint32_t iter,
-                           uint32_t ctr3, const uint32_t* iter_dev, float* S_out, float* traj,
-                           float* blk_min, int* seg0_out, unsigned* status, cudaStream_t st) {
+                           const float4* rec, uint32_t iter, uint32_t ctr3,
+                           const uint32_t* iter_dev, float* S_out, float* traj, float* blk_min,
+                           int* seg0_out, unsigned* status, cudaStream_t st) {
     if (packed_rollout(P)) {
         const size_t smem = rec_table_bytes(P.n_track) + (size_t)P.T * 2 * sizeof(float4);
         auto kern = dump ? mppi_rollout2_kernel<true> : mppi_rollout2_kernel<false>;
@@ -479,13 +491,13 @@ cudaError_t launch_rollout(const DevParams& P, bool dump, const float* x0, const
         return cudaGetLastError();
     }
     const int nblk = (P.K + ROLL_BLK - 1) / ROLL_BLK;
-    const size_t smem = rollout_smem_bytes(P.n_track, P.T);
+    const size_t smem = rec_table_bytes(P.n_track) + (size_t)P.T * sizeof(float4);
     auto kern = dump ? mppi_rollout_kernel<ROLL_BLK, true, false>
                      : mppi_rollout_kernel<ROLL_BLK, false, false>;
     cudaError_t e = ensure_smem((const void*)kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<nblk, ROLL_BLK, smem, st>>>(P, x0, V, seg, inv, iter, ctr3, iter_dev, S_out, traj,
-                                       blk_min, seg0_out, status);
+    kern<<<nblk, ROLL_BLK, smem, st>>>(P, x0, V, rec, iter, ctr3, iter_dev, S_out, traj, blk_min,
+                                       seg0_out, status);
     return cudaGetLastError();
 }
 

@@ -26,20 +26,6 @@ namespace x2 {
 
 using f2 = float2;
 
-__device__ __forceinline__ f2 bc(float v) { return make_float2(v, v); }
-__device__ __forceinline__ f2 add(f2 a, f2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ f2 mul(f2 a, f2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ f2 fma(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ f2 neg(f2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ f2 lo(float4 v) { return make_float2(v.x, v.y); }
-__device__ __forceinline__ f2 hi(float4 v) { return make_float2(v.z, v.w); }
-
-__device__ __forceinline__ float rcp_approx(float x) {
-    float r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-    return r;
-}
-
 struct State2 {
     f2 vx, vy, r, X, Y, psi, cp, sp;   // psi is carried only when trajectories are dumped
 };
@@ -139,80 +125,6 @@ __device__ __forceinline__ void model_step2(const DevParams& P, State2& x, f2 d,
     const f2 cp0 = x.cp;
     x.cp = fma(x.cp, ca, mul(neg(x.sp), sa));
     x.sp = fma(x.sp, ca, mul(cp0, sa));
-}
-
-// Squared distances from (X, Y) to the two segments of record j.
-__device__ __forceinline__ f2 rec_d2(const float4* __restrict__ rec, int j, f2 XX, f2 YY) {
-    const float4 nA = rec[3 * j], nD = rec[3 * j + 1], Dn = rec[3 * j + 2];
-    const f2 ex = add(XX, lo(nA)), ey = add(YY, hi(nA));
-    f2 t = fma(ex, lo(Dn), mul(ey, hi(Dn)));
-    t.x = __saturatef(t.x);
-    t.y = __saturatef(t.y);
-    const f2 rx = fma(t, lo(nD), ex), ry = fma(t, hi(nD), ey);
-    return fma(rx, rx, mul(ry, ry));
-}
-
-// The same arithmetic for segment i alone (first half of record i + 1).
-__device__ __forceinline__ float rec_d2_seg(const float4* __restrict__ rec, int i, float X,
-                                            float Y) {
-    const float4 nA = rec[3 * (i + 1)], nD = rec[3 * (i + 1) + 1], Dn = rec[3 * (i + 1) + 2];
-    const float ex = X + nA.x, ey = Y + nA.z;
-    const float t = __saturatef(fmaf(ex, Dn.x, ey * Dn.z));
-    const float rx = fmaf(t, nD.x, ex), ry = fmaf(t, nD.z, ey);
-    return fmaf(rx, rx, ry * ry);
-}
-
-// Descent walk from segment s (the definition of track_follow) on the record
-// table: forward while the next segment is strictly closer, else backward
-// while the previous one is.
-__device__ __noinline__ int walk_seq_rec(const float4* __restrict__ rec, int n, int s, float X,
-                                         float Y, float& d2) {
-    float d = rec_d2_seg(rec, s, X, Y);
-    int nx = (s + 1 == n) ? 0 : s + 1;
-    float dn = rec_d2_seg(rec, nx, X, Y);
-    if (dn < d) {
-        for (int it = 0; it < n && dn < d; ++it) {
-            s = nx;
-            d = dn;
-            nx = (s + 1 == n) ? 0 : s + 1;
-            dn = rec_d2_seg(rec, nx, X, Y);
-        }
-    } else {
-        int pv = (s == 0) ? n - 1 : s - 1;
-        float dp = rec_d2_seg(rec, pv, X, Y);
-        for (int it = 0; it < n && dp < d; ++it) {
-            s = pv;
-            d = dp;
-            pv = (s == 0) ? n - 1 : s - 1;
-            dp = rec_d2_seg(rec, pv, X, Y);
-        }
-    }
-    d2 = d;
-    return s;
-}
-
-// The descent walk from s evaluated on the window s-1 .. s+4 (three records,
-// six packed distances): it ends within s .. s+3; a longer forward walk or
-// any backward step reruns walk_seq_rec (or, with SPEC, sets fb and returns a
-// segment in [0, n) that the caller discards).  Same result as walk_seq_rec.
-template <bool SPEC>
-__device__ __forceinline__ int walk_rec(const float4* __restrict__ rec, int n, int s, float X,
-                                        float Y, float& d2, bool& fb) {
-    const f2 XX = bc(X), YY = bc(Y);
-    const f2 p0 = rec_d2(rec, s, XX, YY);       // d(s-1), d(s)
-    const f2 p1 = rec_d2(rec, s + 2, XX, YY);   // d(s+1), d(s+2)
-    const f2 p2 = rec_d2(rec, s + 4, XX, YY);   // d(s+3), d(s+4)
-    const bool f1 = p1.x < p0.y, f2_ = p1.y < p1.x, f3 = p2.x < p1.y, f4 = p2.y < p2.x;
-    const bool b1 = p0.x < p0.y;
-    const int adv = f1 ? (f2_ ? (f3 ? 3 : 2) : 1) : 0;
-    const float dd = f1 ? (f2_ ? (f3 ? p2.x : p1.y) : p1.x) : p0.y;
-    const bool out = f1 ? (f2_ && f3 && f4) : b1;
-    if (SPEC) fb |= out;
-    else if (out) return walk_seq_rec(rec, n, s, X, Y, d2);
-    int r = s + adv;
-    if (r >= n) r -= n;
-    d2 = dd;
-    return r;
 }
 
 // Cost of the states x_t of both rollouts: walk to their segments, add q(x_t)

@@ -37,10 +37,10 @@ __device__ __forceinline__ float2 clamp2(const DevParams& P, float2 v) {
 // Direct derivative of the cost terms at x_t (segment s, h_{t-1}, h_t, h_{t+1}):
 //   w_run dq/dx_t + w_cbf C [act(t-1,t) (-dh_t/dx_t) + act(t,t+1) (1-alpha) dh_t/dx_t],
 // dh/d(X,Y) = -2 r, dq/d(X,Y) = (q_d / w^2) 2 r, dq/dv_x = 2 q_v (v_x - v_target).
-__device__ __forceinline__ void add_direct(const DevParams& P, const float4* seg, const float* inv,
+__device__ __forceinline__ void add_direct(const DevParams& P, const float4* rec,
                                            const State& x, int s, bool act_prev, bool act_next,
                                            float w_run, float w_cbf, State& lam) {
-    const float2 r = seg_offset(seg, inv, s, x.X, x.Y);
+    const float2 r = rec_offset(rec, s, x.X, x.Y);
     float ch = 0.0f;
     if (act_prev) ch -= w_cbf * P.C_cbf;
     if (act_next) ch += w_cbf * P.C_cbf * P.one_m_alpha;
@@ -62,13 +62,13 @@ __device__ __forceinline__ void add_direct(const DevParams& P, const float4* seg
 // dynamics x_t -> x_{t+1} are issued together with the track projection, cost
 // and tape entry of x_t, which they do not depend on.
 template <bool STORE, bool TRIAL, bool FAST = false>
-__device__ double forward_cost(const DevParams& P, const float4* seg, const float* inv,
+__device__ double forward_cost(const DevParams& P, const float4* rec,
                                const State& x0, int s0, int N, const float2* Vw, const float2* G,
                                float step, int ms, int seq, float w_run, float w_cbf, int ck,
                                const Tape& tape, double* dec_out) {
     State x = x0;
     int s = s0;
-    float d2 = seg_d2(seg, inv, s, x.X, x.Y);
+    float d2 = rec_d2_seg(rec, s, x.X, x.Y);
     float h_prev = P.w2 - d2, h_pp = h_prev;
     double J = (double)(w_run * run_cost(P, x.vx, d2));
     double dec = 0.0;
@@ -88,7 +88,8 @@ __device__ double forward_cost(const DevParams& P, const float4* seg, const floa
     };
     // cost of state x_t (its predecessor's h is h_prev) and its tape entry
     auto settle = [&](const State& xs, int t) {
-        s = track_follow_spec(seg, inv, P.n_track, s, xs.X, xs.Y, d2);
+        bool nofb = false;
+        s = walk_rec<false>(rec, P.n_track, s, xs.X, xs.Y, d2, nofb);
         const float h = P.w2 - d2;
         const float q = run_cost(P, xs.vx, d2);
         Jf = (w_run != 0.0f) ? fmaf(w_run, q, Jf) : Jf;
@@ -133,7 +134,7 @@ __device__ double forward_cost(const DevParams& P, const float4* seg, const floa
 // The follower's wait is bounded: past the limit it sets SMPPI_DEV_TIMEOUT
 // and stops.
 template <bool FAST>
-__device__ void merit_split(const DevParams& P, const float4* seg, const float* inv,
+__device__ void merit_split(const DevParams& P, const float4* rec,
                             const State& x0, int s0, int N, const float2* Vw, float* buf,
                             volatile int* prog, double* out, unsigned* status) {
     const int tid = threadIdx.x;
@@ -150,7 +151,7 @@ __device__ void merit_split(const DevParams& P, const float4* seg, const float* 
         }
     } else if (tid == 32) {
         int s = s0;
-        float d2 = seg_d2(seg, inv, s, x0.X, x0.Y);
+        float d2 = rec_d2_seg(rec, s, x0.X, x0.Y);
         float h_prev = P.w2 - d2;
         double J = (double)(0.0f * run_cost(P, x0.vx, d2));
         float Jf = 0.0f;
@@ -166,7 +167,8 @@ __device__ void merit_split(const DevParams& P, const float4* seg, const float* 
             }
             __threadfence_block();
             const float2 xy = reinterpret_cast<const float2*>(buf)[t - 1];
-            s = track_follow_spec(seg, inv, P.n_track, s, xy.x, xy.y, d2);
+            bool nofb = false;
+            s = walk_rec<false>(rec, P.n_track, s, xy.x, xy.y, d2, nofb);
             const float h = P.w2 - d2;
             const float a = cbf_arg(P, h_prev, h);
             Jf = (a > 0.0f) ? fmaf(wc, a, Jf) : Jf;
@@ -184,11 +186,11 @@ __device__ void merit_split(const DevParams& P, const float4* seg, const float* 
 // Cost and gradient of one sequence (forward with tape + backward adjoint).
 // Writes G_t = dJ/dv_t for t < N (0 for N <= t < T).
 template <bool FAST = false>
-__device__ double seq_cost_grad(const DevParams& P, const float4* seg, const float* inv,
+__device__ double seq_cost_grad(const DevParams& P, const float4* rec,
                                 const State& x0, int s0, int N, int T, const float2* Vw, float2* G,
                                 int ms, int seq, float w_run, float w_cbf, int ck,
                                 const Tape& tape) {
-    const double J = forward_cost<true, false, FAST>(P, seg, inv, x0, s0, N, Vw, nullptr, 0.0f, ms, seq,
+    const double J = forward_cost<true, false, FAST>(P, rec, x0, s0, N, Vw, nullptr, 0.0f, ms, seq,
                                                w_run, w_cbf, ck, tape, nullptr);
     for (int t = N; t < T; ++t) G[(size_t)t * ms + seq] = make_float2(0.0f, 0.0f);
     if (N == 0) return J;
@@ -210,7 +212,8 @@ __device__ double seq_cost_grad(const DevParams& P, const float4* seg, const flo
                 const float2 u = clamp2(P, Vw[(size_t)(t0 + i - 1) * ms + seq]);
                 model_step<FAST>(P, x, u.x, u.y);
                 float d2;
-                s = track_follow_spec(seg, inv, P.n_track, s, x.X, x.Y, d2);
+                bool nofb = false;
+                s = walk_rec<false>(rec, P.n_track, s, x.X, x.Y, d2, nofb);
                 hp = h;
                 h = P.w2 - d2;
                 tape.put(rb + i, x, s, h, hp);
@@ -222,7 +225,7 @@ __device__ double seq_cost_grad(const DevParams& P, const float4* seg, const flo
             int s;
             float h, hp;
             tape.get(rb + (t1 - t0), x, s, h, hp);
-            add_direct(P, seg, inv, x, s, cbf_arg(P, hp, h) > 0.0f, false, w_run, w_cbf, lam);
+            add_direct(P, rec, x, s, cbf_arg(P, hp, h) > 0.0f, false, w_run, w_cbf, lam);
         }
         for (int t = t1 - 1; t >= t0; --t) {
             const int i = rb + (t - t0);
@@ -239,7 +242,7 @@ __device__ double seq_cost_grad(const DevParams& P, const float4* seg, const flo
             const bool in1 = v.y >= P.umin1 && v.y <= P.umax1;
             G[(size_t)t * ms + seq] = make_float2(in0 ? gd : 0.0f, in1 ? ga : 0.0f);
             if (t >= 1)
-                add_direct(P, seg, inv, x, s, cbf_arg(P, hp, h) > 0.0f,
+                add_direct(P, rec, x, s, cbf_arg(P, hp, h) > 0.0f,
                            cbf_arg(P, h, h_next) > 0.0f, w_run, w_cbf, lam);
         }
     }
@@ -276,7 +279,7 @@ struct RepairSmem {
 };
 
 // Safety shield of one sequence by one block of BLK threads (Alg. 1 with
-// Armijo backtracking, mode 1; fixed step, mode 0).  seg / inv: the staged
+// Armijo backtracking, mode 1; fixed step, mode 0).  rec: the staged
 // track; Vw [T]: the controls, repaired in place; G [T], tape_s [(T+2) NFIELD]:
 // shared-memory scratch.  The Armijo trial steps s, s/2, s/4, ... are
 // evaluated in parallel by the lanes of warp 0 (lane j: s 2^-j) and the
@@ -284,7 +287,7 @@ struct RepairSmem {
 // The gradient comes from thread 0 (seq_cost_grad).  merit_row (optional):
 // n_iters + 1 merits; *iters_done: iterations run.  Returns the final merit.
 template <int BLK, bool FAST = false>
-__device__ double repair_in_block(const DevParams& P, const float4* seg, const float* inv,
+__device__ double repair_in_block(const DevParams& P, const float4* rec,
                                   const State& x0, int s0, float2* Vw, float2* G, float* tape_s,
                                   int n_iters, int mode, float delta, int ck, double* merit_row,
                                   int* iters_done, unsigned* status, RepairSmem& sm) {
@@ -292,7 +295,7 @@ __device__ double repair_in_block(const DevParams& P, const float4* seg, const f
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = BLK / 32;
     const Tape tape{tape_s, 1, 0};
-    merit_split<FAST>(P, seg, inv, x0, s0, N, Vw, tape_s, &sm.prog, &sm.P, status);
+    merit_split<FAST>(P, rec, x0, s0, N, Vw, tape_s, &sm.prog, &sm.P, status);
     __syncthreads();
     double P0 = sm.P;
     int it = 0;
@@ -300,14 +303,14 @@ __device__ double repair_in_block(const DevParams& P, const float4* seg, const f
     for (; it < n_iters; ++it) {
         if (tid == 0 && merit_row) merit_row[it] = P0;
         if (P0 == 0.0) break;
-        if (tid == 0) seq_cost_grad<FAST>(P, seg, inv, x0, s0, N, T, Vw, G, 1, 0, 0.0f, 1.0f, ck, tape);
+        if (tid == 0) seq_cost_grad<FAST>(P, rec, x0, s0, N, T, Vw, G, 1, 0, 0.0f, 1.0f, ck, tape);
         __syncthreads();
         if (mode == 0) {
             for (int t = tid; t < N; t += BLK)
                 Vw[t] = clamp2(P, make_float2(fmaf(-delta, G[t].x, Vw[t].x),
                                               fmaf(-delta, G[t].y, Vw[t].y)));
             __syncthreads();
-            merit_split<FAST>(P, seg, inv, x0, s0, N, Vw, tape_s, &sm.prog, &sm.P, status);
+            merit_split<FAST>(P, rec, x0, s0, N, Vw, tape_s, &sm.prog, &sm.P, status);
             __syncthreads();
             P0 = sm.P;
             continue;
@@ -331,7 +334,7 @@ __device__ double repair_in_block(const DevParams& P, const float4* seg, const f
             for (int j = lane; j < P.ls_max; j += 32) {
                 const float sj = ldexpf(s_first, -j);
                 double dec;
-                const double Pt = forward_cost<false, true, FAST>(P, seg, inv, x0, s0, N, Vw, G, sj, 1,
+                const double Pt = forward_cost<false, true, FAST>(P, rec, x0, s0, N, Vw, G, sj, 1,
                                                             0, 0.0f, 1.0f, 0, tape, &dec);
                 if (Pt <= P0 - (double)P.ls_c * dec && j < best) { best = j; best_P = Pt; }
             }
@@ -366,13 +369,13 @@ __device__ double repair_in_block(const DevParams& P, const float4* seg, const f
 // Nearest segment of (X, Y) over the whole track by one block (lowest index on
 // ties); every thread gets the result.
 template <int BLK>
-__device__ int block_nearest_segment(const float4* seg, const float* inv, int n, float X, float Y,
+__device__ int block_nearest_segment(const float4* rec, int n, float X, float Y,
                                      float* red_f, int* red_i, float* d2_out) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float bd = 3.0e38f;
     int bi = 0x7fffffff;
     for (int i = tid; i < n; i += BLK) {
-        const float d = seg_d2(seg, inv, i, X, Y);
+        const float d = rec_d2_seg(rec, i, X, Y);
         if (d < bd) { bd = d; bi = i; }
     }
     warp_argmin(bd, bi);
