@@ -292,7 +292,8 @@ smppi_status smppi_step_noalloc(const smppi_params* p, const float* x0, float* V
 #define SMPPI_KERNEL_REPAIR 3     /* safety shield iterations */
 #define SMPPI_KERNEL_APPLY 4      /* closed-loop step */
 #define SMPPI_KERNEL_COST_GRAD 5  /* cost + adjoint gradient */
-#define SMPPI_KERNEL_KINDS 6
+#define SMPPI_KERNEL_UPDATE_SHIELD 6  /* update -> V+, then (last block) shield and closed-loop step */
+#define SMPPI_KERNEL_KINDS 7
 smppi_status smppi_timing(smppi_handle* h, int enable);
 smppi_status smppi_timing_read(smppi_handle* h, double* ms_out, int* count_out, int n_kinds);
 

@@ -184,16 +184,24 @@ smppi_status check_seq_call(smppi_handle* h, int n_seq) {
     return SMPPI_OK;
 }
 
+smppi_status enqueue_rollout(smppi_handle* h, cudaStream_t st, const float* x0, const float* V,
+                             uint32_t iter, uint32_t instance, float* S, float* traj_out,
+                             uint32_t* iter_dev) {
+    const int ev = tic(h, st);
+    CU(h, launch_rollout(h->dp, traj_out != nullptr, x0, V, h->rec, iter, instance << 8,
+                         iter_dev, S, traj_out, h->blk_min, h->rws.seg0, h->status, st));
+    toc(h, st, SMPPI_KERNEL_ROLLOUT, ev);
+    return SMPPI_OK;
+}
+
 smppi_status enqueue_step(smppi_handle* h, cudaStream_t st, const float* x0, float* V,
                           uint32_t iter, uint32_t instance, float* S_out, float* traj_out,
                           uint32_t* iter_dev) {
     const uint32_t ctr3 = (instance << 8) | 0u;
     float* S = S_out ? S_out : h->S_ws;
+    smppi_status s = enqueue_rollout(h, st, x0, V, iter, instance, S, traj_out, iter_dev);
+    if (s != SMPPI_OK) return s;
     int ev = tic(h, st);
-    CU(h, launch_rollout(h->dp, traj_out != nullptr, x0, V, h->rec, iter, ctr3,
-                         iter_dev, S, traj_out, h->blk_min, h->rws.seg0, h->status, st));
-    toc(h, st, SMPPI_KERNEL_ROLLOUT, ev);
-    ev = tic(h, st);
     CU(h, launch_update(h->dp, S, h->blk_min, rollout_blocks(h->dp), V, iter, ctr3, iter_dev, h->part_acc,
                         h->part_eta, h->part_has, h->ticket, h->status, st));
     toc(h, st, SMPPI_KERNEL_UPDATE, ev);
@@ -219,14 +227,25 @@ smppi_status enqueue_repair(smppi_handle* h, cudaStream_t st, int n_seq, const f
     return SMPPI_OK;
 }
 
+// One Shield-MPPI control update: the rollout launch, then the update launch
+// whose last block also repairs V+ and takes the closed-loop step.
 smppi_status enqueue_shield(smppi_handle* h, cudaStream_t st, float* x0, float* V, float* Vs,
                             uint32_t iter, uint32_t instance, int n_repair, double* merit,
                             uint32_t* iter_dev) {
+    if (n_repair > 0) {
+        smppi_status s = enqueue_rollout(h, st, x0, V, iter, instance, h->S_ws, nullptr, iter_dev);
+        if (s != SMPPI_OK) return s;
+        const int ev = tic(h, st);
+        CU(h, launch_update_shield(h->dp, h->S_ws, h->blk_min, rollout_blocks(h->dp), V, iter,
+                                   instance << 8, iter_dev, h->part_acc, h->part_eta, h->part_has,
+                                   h->ticket, h->status, h->rec, h->rws.seg0, x0, Vs, n_repair,
+                                   h->rws.ck, merit, (instance << 8) | 1u, st));
+        toc(h, st, SMPPI_KERNEL_UPDATE_SHIELD, ev);
+        return SMPPI_OK;
+    }
     smppi_status s = enqueue_step(h, st, x0, V, iter, instance, nullptr, nullptr, iter_dev);
     if (s != SMPPI_OK) return s;
     const ApplyArgs ap{x0, V, iter, (instance << 8) | 1u, iter_dev};
-    if (n_repair > 0)
-        return enqueue_repair(h, st, 1, x0, V, Vs, n_repair, 1, 0.0f, merit, nullptr, true, ap);
     CU(h, cudaMemcpyAsync(Vs, V, sizeof(float) * 2 * h->p.T, cudaMemcpyDeviceToDevice, st));
     const int ev = tic(h, st);
     CU(h, launch_apply(h->dp, ap, Vs, st));

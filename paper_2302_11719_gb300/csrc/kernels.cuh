@@ -36,10 +36,21 @@ int update_grid(int K);
 // (n_min values) may be NULL.  part_acc [grid][2T], part_eta [grid]; ticket:
 // a device counter that is 0 on entry and left 0.
 cudaError_t launch_update(const DevParams& P, const float* S, const float* blk_min, int n_min,
-                          float* V, uint32_t iter, uint32_t ctr3, const uint32_t* iter_dev,
+                          float* V, uint32_t iter, uint32_t ctr3, uint32_t* iter_dev,
                           float* part_acc, double* part_eta, int* part_has, unsigned* ticket,
-                          unsigned* status,
-                          cudaStream_t st);
+                          unsigned* status, cudaStream_t st);
+// The same update followed, in its last block, by the safety shield on V+
+// (n_repair Armijo iterations; V_safe out; merits optional) and the
+// closed-loop step on x0 (disturbance counter word ctr3_dist); V ends as
+// shift(V+).  seg0: nearest segment of x0 from the rollout launch.  iter_dev
+// (graph replays) is advanced by one.
+cudaError_t launch_update_shield(const DevParams& P, const float* S, const float* blk_min,
+                                 int n_min, float* V, uint32_t iter, uint32_t ctr3,
+                                 uint32_t* iter_dev, float* part_acc, double* part_eta,
+                                 int* part_has, unsigned* ticket, unsigned* status,
+                                 const float4* rec, const int* seg0, float* x0, float* V_safe,
+                                 int n_repair, int ck, double* merit_out, uint32_t ctr3_dist,
+                                 cudaStream_t st);
 cudaError_t launch_debug_noise(const DevParams& P, uint32_t iter, uint32_t ctr3, int K, int T,
                                float* eps, uint32_t* raw, cudaStream_t st);
 

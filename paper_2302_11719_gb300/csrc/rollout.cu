@@ -18,8 +18,8 @@
 //   these problems that leaves a small fraction of K.  The last block to
 //   finish (device-scope ticket) sums the non-empty block partials in float64
 //   and writes V+ = clamp(V + A / eta).
-#include "kernels.cuh"
 #include "rollout2.cuh"
+#include "shield.cuh"
 
 namespace smppi {
 
@@ -248,14 +248,41 @@ __global__ void rec_table_kernel(const float* __restrict__ xy, int n, float4* __
 constexpr int UPD_PER_T = 8;                  // slice values per thread in one pass
 constexpr int UPD_LIST = UPD_PER_T * UPD_BLK;  // list of taken rollouts of one pass
 
+//
+// SHIELD: the last block then also runs the safety shield on V+ (Alg. 1,
+// repair_in_block; V_safe out) and the closed-loop step (x0 <- f(x0, v_0^safe)
+// + w, V <- shift(V+), Eq. 26), so that one control update is two launches.
+// Every block bulk-copies the segment-pair table into its shared memory at
+// entry (overlapping the weight pass); the non-last blocks wait for their copy
+// before they exit.
+struct ShieldTail {
+    const float4* rec;      // segment-pair table (global)
+    const int* seg0;        // nearest segment of x0 (written by the rollout launch)
+    float* x0;              // in/out state
+    float* V_safe;          // out: repaired controls
+    int n_repair, ck;
+    double* merit_out;      // optional: n_repair + 1 merits
+    uint32_t ctr3_dist;     // counter word of the disturbance
+};
+
+template <bool SHIELD, bool FAST>
 __global__ void __launch_bounds__(UPD_BLK) mppi_update_kernel(
     DevParams P, const float* __restrict__ S, const float* __restrict__ blk_min, int n_min,
-    float* V, uint32_t iter, uint32_t ctr3, const uint32_t* __restrict__ iter_dev,
+    float* V, uint32_t iter, uint32_t ctr3, uint32_t* __restrict__ iter_dev,
     float* __restrict__ part_acc, double* __restrict__ part_eta, int* __restrict__ part_has,
-    unsigned* __restrict__ ticket, unsigned* __restrict__ status) {
+    unsigned* __restrict__ ticket, unsigned* __restrict__ status, ShieldTail sh) {
     constexpr int NW = UPD_BLK / 32;
     constexpr int PER_T = UPD_PER_T;
-    if (iter_dev) iter += *iter_dev;
+    const uint32_t n_upd = iter_dev ? *iter_dev : 0u;
+    iter += n_upd;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    if (SHIELD && threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        const uint32_t bytes = (uint32_t)rec_table_bytes(P.n_track);
+        mbar_expect_tx(&bar, bytes);
+        bulk_g2s(reinterpret_cast<float4*>(smem_raw), sh.rec, bytes, &bar);
+    }
     __shared__ float red_f[NW];
     __shared__ int l_k[UPD_LIST];
     __shared__ float l_w[UPD_LIST];
@@ -373,7 +400,10 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_update_kernel(
     __syncthreads();
     if (tid == 0) s_last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
     __syncthreads();
-    if (!s_last) return;
+    if (!s_last) {
+        if (SHIELD && tid == 0) mbar_wait_bounded(&bar, 0u);   // the copy lands before exit
+        return;
+    }
     __threadfence();
     const int G = gridDim.x;            // <= UPD_BLK
     const int hb = (tid < G) ? __ldcg(&part_has[tid]) : 0;
@@ -412,8 +442,56 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_update_kernel(
         const float v = (float)fma(A, inv_eta, (double)V[j]);
         if (!isfinite(v)) atomicOr(status, SMPPI_DEV_NUMERIC);
         V[j] = clampf(v, lo, hi);
+        if (SHIELD) acc_s[j] = V[j];    // V+ (the merge no longer needs acc_s)
     }
     if (tid == 0) *ticket = 0u;
+    if (!SHIELD) return;
+
+    // ---- safety shield on V+ (Alg. 1) and closed-loop step (Eq. 26) ----
+    __shared__ int s_fail;
+    __shared__ RepairSmem rsm;
+    float4* rec = reinterpret_cast<float4*>(smem_raw);
+    float2* Vw = reinterpret_cast<float2*>(rec + 3 * (P.n_track + 5));
+    float2* G2 = Vw + T;
+    float* tape_s = reinterpret_cast<float*>(G2 + T);
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    if (!mbar_wait_bounded(&bar, 0u)) s_fail = 1;
+    __syncthreads();
+    if (s_fail) {
+        if (tid == 0) {
+            atomicOr(status, SMPPI_DEV_TIMEOUT);
+            mbar_wait_bounded(&bar, 0u);
+        }
+        return;
+    }
+    const float2* Vplus = reinterpret_cast<const float2*>(acc_s);
+    for (int t = tid; t < T; t += UPD_BLK) Vw[t] = Vplus[t];
+    __syncthreads();
+    const State x0 = make_state(sh.x0);
+    if (sh.n_repair > 0)
+        repair_in_block<UPD_BLK, FAST>(P, rec, x0, sh.seg0[0], Vw, G2, tape_s, sh.n_repair, 1,
+                                       0.0f, sh.ck, sh.merit_out, nullptr, status, rsm);
+    float2* Vs_out = reinterpret_cast<float2*>(sh.V_safe);
+    float2* V2 = reinterpret_cast<float2*>(V);
+    for (int t = tid; t < T; t += UPD_BLK) {
+        Vs_out[t] = Vw[t];
+        V2[t] = Vplus[t + 1 < T ? t + 1 : T - 1];   // warm start: shift(V+)
+    }
+    if (tid == 0) {   // x0 <- f(x0, clamp(v_0^safe)) + w_n
+        State x = x0;
+        const float2 v0 = Vw[0];
+        model_step(P, x, clampf(v0.x, P.umin0, P.umax0), clampf(v0.y, P.umin1, P.umax1));
+        const uint4 r = philox10(make_uint4(0u, 0u, iter, sh.ctr3_dist), P);
+        const float2 z = box_muller(r.x, r.y);
+        sh.x0[0] = x.vx;
+        sh.x0[1] = fmaf(P.dsig0, z.x, x.vy);
+        sh.x0[2] = fmaf(P.dsig1, z.y, x.r);
+        sh.x0[3] = x.X;
+        sh.x0[4] = x.Y;
+        sh.x0[5] = x.psi;
+        if (iter_dev) *iter_dev = n_upd + 1u;
+    }
 }
 
 // Control noise exactly as the rollout kernels draw it (test access).
@@ -502,12 +580,32 @@ cudaError_t launch_rollout(const DevParams& P, bool dump, const float* x0, const
 }
 
 cudaError_t launch_update(const DevParams& P, const float* S, const float* blk_min, int n_min,
-                          float* V, uint32_t iter, uint32_t ctr3, const uint32_t* iter_dev,
+                          float* V, uint32_t iter, uint32_t ctr3, uint32_t* iter_dev,
                           float* part_acc, double* part_eta, int* part_has, unsigned* ticket,
                           unsigned* status, cudaStream_t st) {
-    mppi_update_kernel<<<update_grid(P.K), UPD_BLK, 0, st>>>(P, S, blk_min, n_min, V, iter, ctr3,
-                                                             iter_dev, part_acc, part_eta,
-                                                             part_has, ticket, status);
+    mppi_update_kernel<false, false><<<update_grid(P.K), UPD_BLK, 0, st>>>(
+        P, S, blk_min, n_min, V, iter, ctr3, iter_dev, part_acc, part_eta, part_has, ticket,
+        status, ShieldTail{});
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update_shield(const DevParams& P, const float* S, const float* blk_min,
+                                 int n_min, float* V, uint32_t iter, uint32_t ctr3,
+                                 uint32_t* iter_dev, float* part_acc, double* part_eta,
+                                 int* part_has, unsigned* ticket, unsigned* status,
+                                 const float4* rec, const int* seg0, float* x0, float* V_safe,
+                                 int n_repair, int ck, double* merit_out, uint32_t ctr3_dist,
+                                 cudaStream_t st) {
+    const size_t smem = rec_table_bytes(P.n_track) + (size_t)P.T * 16 +
+                        (size_t)(P.T + 2) * NFIELD * 4;
+    const ShieldTail sh{rec, seg0, x0, V_safe, n_repair, ck, merit_out, ctr3_dist};
+    auto kern = (P.tyre15 && P.steer_small) ? mppi_update_kernel<true, true>
+                                             : mppi_update_kernel<true, false>;
+    cudaError_t e = ensure_smem((const void*)kern, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<update_grid(P.K), UPD_BLK, smem, st>>>(P, S, blk_min, n_min, V, iter, ctr3, iter_dev,
+                                                  part_acc, part_eta, part_has, ticket, status,
+                                                  sh);
     return cudaGetLastError();
 }
 

@@ -85,7 +85,7 @@ _SIGS = {
     "smppi_timing_read": ([_vp, C.POINTER(C.c_double), C.POINTER(C.c_int), _i], _i),
 }
 
-KERNEL_KINDS = ("rollout", "update", "seg0", "repair", "apply", "cost_grad")
+KERNEL_KINDS = ("rollout", "update", "seg0", "repair", "apply", "cost_grad", "update_shield")
 
 _lib = None
 

@@ -20,7 +20,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from paper_2302_11719_gb300 import inputs as I  # noqa: E402
-from tests.gpu_helpers import G_REL, S_REL, V_REP, X_REL, rel_err  # noqa: E402
+from tests.gpu_helpers import G_REL, S_REL, V_REP, X_REL, rel_err, update_bound  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -213,4 +213,37 @@ def test_shield_update_device_host_graph_agree(S):
     ctl.sync_status()
     assert np.array_equal(x0.cpu().numpy(), ref[0])
     assert np.array_equal(V.cpu().numpy(), ref[1]) and np.array_equal(Vs.cpu().numpy(), ref[2])
+    ctl.close()
+
+
+@pytest.mark.parametrize("offset,heading", [(1.7, 0.25), (-1.6, -0.3), (0.0, 0.0)])
+def test_shield_update_vs_oracle(S, orc, offset, heading):
+    # one whole Shield-MPPI update (rollouts, softmin, repair of V+ in the update's
+    # last block, closed-loop step) from a state near the boundary and heading out
+    # of the track, against the oracle's mppi_step -> repair -> apply -> shift
+    pr = I.single_problem(K=512, T=50)
+    x0 = pr.x0.copy()
+    x0[3] += offset                       # the start (a, 0) has outward normal +X
+    x0[5] -= heading                      # heading pi/2 - heading: toward +X for heading > 0
+    x0[0] = 6.0
+    V = np.tile(np.array([[0.0, 0.3]], np.float32), (pr.T, 1))
+    it, inst = 3, 2
+    ctl = S.Controller(pr.params, pr.track)
+    xg, Vg, Vsg = ctl.tensor(x0), ctl.tensor(V), torch.empty((pr.T, 2), device="cuda")
+    S.smppi_shield_update(ctl.h, xg, Vg, Vsg, it, inst, 10)
+    st, bits = ctl.sync_status()
+    assert st in (S.OK, S.ERR_STALLED), (st, bits)
+    m = orc.Model(pr.params, pr.track)
+    So, Vp = orc.mppi_step(m, x0, V, it, inst, nthreads=8)
+    Vsafe, mer, ost, its = orc.repair(m, x0, Vp.astype(np.float32), 10)
+    x1 = orc.apply(m, x0, Vsafe[0], it, inst)
+    print("offset %.1f: oracle repair iterations %d, merit %.4g -> %.4g"
+          % (offset, its, mer[0], mer[its]))
+    _, om = orc.update(m, So, V, it, inst)
+    eps = orc.noise_block(m, it, inst, range(m.K))
+    tol = update_bound(So, eps, om, Vp, V, pr.params["lam"])
+    tol_sh = np.concatenate([tol[1:], tol[-1:]])
+    assert np.all(np.abs(Vg.cpu().numpy() - orc.shift(m, Vp)) <= tol_sh)
+    assert np.max(np.abs(Vsg.cpu().numpy() - Vsafe)) <= V_REP
+    assert rel_err(xg.cpu().numpy(), x1) <= X_REL
     ctl.close()
