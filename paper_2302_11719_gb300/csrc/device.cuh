@@ -169,38 +169,59 @@ __device__ __forceinline__ float tyre_shape(const DevParams& P, float z, float* 
 // One explicit Euler step of the single-track model (Eq. 1).
 // ---------------------------------------------------------------------------
 // FAST: the parameters satisfy Ct == 1.5 and |steer| <= 1/2 on the control
-// box (P.tyre15 && P.steer_small), so the step is one branch-free block (the
-// only branch left handles |dt r| > 1/2 after the block).
+// box (P.tyre15 && P.steer_small).  The FAST step is split into its velocity
+// part (v_x, v_y, r: the tyre forces) and its pose part (X, Y, psi: driven by
+// the velocities of the same step) so that the repair's merit pass can run the
+// two recurrences on different threads; explicit fmaf fixes the rounding.
+//
+// Velocity part: (v_x, v_y, r) <- Euler update at steer d (sd, cd = sin, cos d)
+// with rear force Fx.
+__device__ __forceinline__ void vel_step_fast(const DevParams& P, float& vx, float& vy, float& r,
+                                              float d, float sd, float cd, float Fx) {
+    const float bf = atan2_poly(fmaf(P.lf, r, vy), vx);
+    const float br = atan2_poly(fmaf(-P.lr, r, vy), vx);
+    const float Fyf = P.Fzf * tyre15(P.B * (d - bf));
+    const float Fyr = P.Fzr * tyre15(-P.B * br);
+    const float dvx = fmaf(fmaf(-Fyf, sd, Fx), P.m_inv, vy * r);
+    const float dvy = fmaf(fmaf(Fyf, cd, Fyr), P.m_inv, -(vx * r));
+    const float dr = fmaf(P.lf * Fyf, cd, -(P.lr * Fyr)) * P.Iz_inv;
+    vx = fmaf(P.dt, dvx, vx);
+    vy = fmaf(P.dt, dvy, vy);
+    r = fmaf(P.dt, dr, r);
+}
+
+// Pose part, from the velocities (vx, vy, r) of the same step: (X, Y) by Euler,
+// psi += dt r and (cos psi, sin psi) rotated by dt r (library sin / cos when
+// |dt r| > 1/2).
+__device__ __forceinline__ void pose_step_fast(const DevParams& P, float vx, float vy, float r,
+                                               float& X, float& Y, float& psi, float& cp,
+                                               float& sp) {
+    const float dX = fmaf(vx, cp, -(vy * sp));
+    const float dY = fmaf(vx, sp, vy * cp);
+    const float dpsi = P.dt * r;
+    float sa, ca;
+    sincos_half(dpsi, &sa, &ca);
+    X = fmaf(P.dt, dX, X);
+    Y = fmaf(P.dt, dY, Y);
+    psi += dpsi;
+    if (fabsf(dpsi) > 0.5f) sincosf(dpsi, &sa, &ca);
+    const float cp0 = cp;
+    cp = fmaf(cp, ca, -(sp * sa));
+    sp = fmaf(sp, ca, cp0 * sa);
+}
+
 template <bool FAST = false>
 __device__ __forceinline__ void model_step(const DevParams& P, State& x, float d, float a) {
-    const float bf = atan2_poly(fmaf(P.lf, x.r, x.vy), x.vx);
-    const float br = atan2_poly(fmaf(-P.lr, x.r, x.vy), x.vx);
     if (FAST) {
-        const float Fyf = P.Fzf * tyre15(P.B * (d - bf));
-        const float Fyr = P.Fzr * tyre15(-P.B * br);
         float sd, cd;
         sincos_half(d, &sd, &cd);
-        const float Fx = P.fx_gain * a;
-        const float dvx = fmaf(Fx - Fyf * sd, P.m_inv, x.vy * x.r);
-        const float dvy = fmaf(Fyr + Fyf * cd, P.m_inv, -x.vx * x.r);
-        const float dr = (P.lf * Fyf * cd - P.lr * Fyr) * P.Iz_inv;
-        const float dX = x.vx * x.cp - x.vy * x.sp;
-        const float dY = x.vx * x.sp + x.vy * x.cp;
-        const float dpsi = P.dt * x.r;
-        float sa, ca;
-        sincos_half(dpsi, &sa, &ca);
-        const float cp0 = x.cp, sp0 = x.sp;
-        x.vx = fmaf(P.dt, dvx, x.vx);
-        x.vy = fmaf(P.dt, dvy, x.vy);
-        x.r = fmaf(P.dt, dr, x.r);
-        x.X = fmaf(P.dt, dX, x.X);
-        x.Y = fmaf(P.dt, dY, x.Y);
-        x.psi += dpsi;
-        if (fabsf(dpsi) > 0.5f) sincosf(dpsi, &sa, &ca);
-        x.cp = cp0 * ca - sp0 * sa;
-        x.sp = sp0 * ca + cp0 * sa;
+        const float vx = x.vx, vy = x.vy, r = x.r;
+        vel_step_fast(P, x.vx, x.vy, x.r, d, sd, cd, P.fx_gain * a);
+        pose_step_fast(P, vx, vy, r, x.X, x.Y, x.psi, x.cp, x.sp);
         return;
     }
+    const float bf = atan2_poly(fmaf(P.lf, x.r, x.vy), x.vx);
+    const float br = atan2_poly(fmaf(-P.lr, x.r, x.vy), x.vx);
     const float Fyf = P.Fzf * tyre_shape(P, P.B * (d - bf), nullptr);
     const float Fyr = P.Fzr * tyre_shape(P, -P.B * br, nullptr);
     float sd, cd;

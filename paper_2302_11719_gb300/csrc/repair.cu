@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(REP_BLK) repair_kernel(
 // Safety shield for few sequences: one block per sequence, everything in
 // shared memory (track table staged by a bulk copy, controls, gradient,
 // checkpoint tape); see repair_in_block.
-constexpr int REPB_BLK = 64;
+constexpr int REPB_BLK = 128;
 
 template <bool FAST>
 __global__ void __launch_bounds__(REPB_BLK) repair_block_kernel(

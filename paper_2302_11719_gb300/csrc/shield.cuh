@@ -183,6 +183,93 @@ __device__ void merit_split(const DevParams& P, const float4* rec,
     }
 }
 
+// The same merit for the FAST model by three threads in three warps: thread 0
+// runs the velocity recurrence (tyre forces; steer sin / cos and rear force of
+// every step precomputed by the whole block), thread 32 the pose recurrence
+// from the published velocities, thread 64 the track walk and the DCBF terms
+// from the published positions.  buf holds 40 N + 8 bytes; prog two counters.
+// Same arithmetic and summation order as forward_cost.  BLK >= 96.
+__device__ void merit_split3(const DevParams& P, const float4* rec, const State& x0, int s0,
+                             int N, const float2* Vw, float* buf, volatile int* prog, double* out,
+                             unsigned* status) {
+    const int tid = threadIdx.x;
+    // buf is only 8-byte aligned in some callers: round up to 16 bytes for the
+    // float4 rows (the tape scratch has 44 (T + 2) >= 40 N + 8 bytes)
+    float4* ctl = reinterpret_cast<float4*>((reinterpret_cast<uintptr_t>(buf) + 15) &
+                                            ~uintptr_t(15));  // (d, sin d, cos d, Fx) of step t
+    float4* vel = ctl + N;                                    // (v_x, v_y, r) of x_t
+    float2* pos = reinterpret_cast<float2*>(vel + N);         // (X, Y) of x_{t+1}
+    if (tid == 0) {
+        prog[0] = 0;
+        prog[1] = 0;
+    }
+    for (int t = tid; t < N; t += blockDim.x) {
+        const float2 u = clamp2(P, Vw[t]);
+        float sd, cd;
+        sincos_half(u.x, &sd, &cd);
+        ctl[t] = make_float4(u.x, sd, cd, P.fx_gain * u.y);
+    }
+    __syncthreads();
+    constexpr int LIMIT = 1 << 24;
+    if (tid == 0) {
+        float vx = x0.vx, vy = x0.vy, r = x0.r;
+        for (int t = 0; t < N; ++t) {
+            vel[t] = make_float4(vx, vy, r, 0.0f);
+            __threadfence_block();
+            prog[0] = t + 1;
+            const float4 c = ctl[t];
+            vel_step_fast(P, vx, vy, r, c.x, c.y, c.z, c.w);
+        }
+    } else if (tid == 32) {
+        float X = x0.X, Y = x0.Y, psi = x0.psi, cp = x0.cp, sp = x0.sp;
+        for (int t = 0; t < N; ++t) {
+            int tries = 0;
+            while (prog[0] <= t) {
+                if (++tries > LIMIT) {
+                    atomicOr(status, SMPPI_DEV_TIMEOUT);
+                    return;
+                }
+            }
+            __threadfence_block();
+            const float4 v = vel[t];
+            pose_step_fast(P, v.x, v.y, v.z, X, Y, psi, cp, sp);
+            pos[t] = make_float2(X, Y);
+            __threadfence_block();
+            prog[1] = t + 1;
+        }
+    } else if (tid == 64) {
+        int s = s0;
+        float d2 = rec_d2_seg(rec, s, x0.X, x0.Y);
+        float h_prev = P.w2 - d2;
+        double J = (double)(0.0f * run_cost(P, x0.vx, d2));
+        float Jf = 0.0f;
+        for (int t = 1; t <= N; ++t) {
+            int tries = 0;
+            while (prog[1] < t) {
+                if (++tries > LIMIT) {
+                    atomicOr(status, SMPPI_DEV_TIMEOUT);
+                    *out = 0.0;
+                    return;
+                }
+            }
+            __threadfence_block();
+            const float2 xy = pos[t - 1];
+            bool nofb = false;
+            s = walk_rec<false>(rec, P.n_track, s, xy.x, xy.y, d2, nofb);
+            const float h = P.w2 - d2;
+            const float a = cbf_arg(P, h_prev, h);
+            Jf = (a > 0.0f) ? fmaf(P.C_cbf, a, Jf) : Jf;
+            h_prev = h;
+            if ((t & 15) == 0) {
+                J += (double)Jf;
+                Jf = 0.0f;
+            }
+        }
+        J += (double)Jf;
+        *out = J;
+    }
+}
+
 // Cost and gradient of one sequence (forward with tape + backward adjoint).
 // Writes G_t = dJ/dv_t for t < N (0 for N <= t < T).
 template <bool FAST = false>
@@ -272,7 +359,7 @@ __device__ void closed_loop_step(const DevParams& P, const ApplyArgs& ap, float2
 // Shared-memory scratch of repair_in_block.
 struct RepairSmem {
     double P;
-    int prog;          // progress counter of merit_split
+    int prog[2];       // progress counters of merit_split / merit_split3
     float red[32];
     float step;
     int ok;
@@ -295,8 +382,14 @@ __device__ double repair_in_block(const DevParams& P, const float4* rec,
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = BLK / 32;
     const Tape tape{tape_s, 1, 0};
-    merit_split<FAST>(P, rec, x0, s0, N, Vw, tape_s, &sm.prog, &sm.P, status);
-    __syncthreads();
+    auto merit = [&]() {
+        if (FAST && BLK >= 96)
+            merit_split3(P, rec, x0, s0, N, Vw, tape_s, sm.prog, &sm.P, status);
+        else
+            merit_split<FAST>(P, rec, x0, s0, N, Vw, tape_s, sm.prog, &sm.P, status);
+        __syncthreads();
+    };
+    merit();
     double P0 = sm.P;
     int it = 0;
     bool stalled = false;
@@ -310,8 +403,7 @@ __device__ double repair_in_block(const DevParams& P, const float4* rec,
                 Vw[t] = clamp2(P, make_float2(fmaf(-delta, G[t].x, Vw[t].x),
                                               fmaf(-delta, G[t].y, Vw[t].y)));
             __syncthreads();
-            merit_split<FAST>(P, rec, x0, s0, N, Vw, tape_s, &sm.prog, &sm.P, status);
-            __syncthreads();
+            merit();
             P0 = sm.P;
             continue;
         }
