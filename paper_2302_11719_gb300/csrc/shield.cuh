@@ -124,20 +124,116 @@ __device__ double forward_cost(const DevParams& P, const float4* rec,
     return J;
 }
 
-// Merit of Vw (forward_cost with w_run = 0, w_cbf = 1, no tape) by two threads
-// of the block in different warps: thread 0 integrates the model and publishes
-// each state's (X, Y) to buf [2 N] with a progress counter; thread 32 follows
-// with the track walk and the DCBF terms.  The arithmetic and the summation
-// order are those of forward_cost (the same merit), but the model recurrence
-// no longer waits on the track walk.  Called by every thread of the block
-// (BLK >= 64); the result lands in *out after the caller's __syncthreads.
-// The follower's wait is bounded: past the limit it sets SMPPI_DEV_TIMEOUT
-// and stops.
+// ---------------------------------------------------------------------------
+// Merit of Vw (forward_cost with w_run = 0, w_cbf = 1, no tape: the DCBF
+// violation sum of Eq. 22) split across warps of the block so that the
+// serial chains run side by side: the model recurrence on one thread and the
+// track walk with the DCBF terms on a whole warp that follows the published
+// positions.  Arithmetic and summation order are those of forward_cost.
+// Progress is published every MERIT_PUB steps; every wait is bounded (past
+// the limit: SMPPI_DEV_TIMEOUT and the merit is reported as 0).
+// ---------------------------------------------------------------------------
+constexpr int MERIT_PUB = 4;
+constexpr int MERIT_WAIT_LIMIT = 1 << 24;
+
+// The follower warp: positions pos[t - 1] = (X, Y) of x_t, t = 1..N, ready when
+// *prog >= t (published in chunks of MERIT_PUB).  For a chunk, lane l
+// evaluates segment s - 1 + l of the window around the segment s where the
+// chunk starts, for every position of the chunk at once; the descent walks of
+// c15 are then read off ballots of "the next segment is strictly closer"
+// position after position: the walk from window lane L moves forward to the
+// first lane above L whose successor is not closer, and stays at L when L + 1
+// is not closer and L - 1 is not closer either.  A backward step or a walk
+// that reaches the window's last lane is finished one segment at a time by
+// lane 0 (walk_seq_rec), for that position and the rest of the chunk.
+// Returns J on every lane.
+__device__ __forceinline__ double merit_follow_warp(const DevParams& P, const float4* rec,
+                                                    const State& x0, int s0, int N,
+                                                    const float2* pos, volatile int* prog,
+                                                    unsigned* status) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, n = P.n_track;
+    int s = s0;
+    float d2 = rec_d2_seg(rec, s, x0.X, x0.Y);
+    float h_prev = P.w2 - d2;
+    double J = (double)(0.0f * run_cost(P, x0.vx, d2));
+    float Jf = 0.0f;
+    for (int t0 = 1; t0 <= N; t0 += MERIT_PUB) {
+        const int t1 = min(N, t0 + MERIT_PUB - 1), nq = t1 - t0 + 1;
+        int tries = 0;
+        while (*prog < t1 && tries <= MERIT_WAIT_LIMIT) ++tries;
+        if (__any_sync(FULL, tries > MERIT_WAIT_LIMIT)) {
+            if (lane == 0) atomicOr(status, SMPPI_DEV_TIMEOUT);
+            return 0.0;
+        }
+        __threadfence_block();
+        int j = s - 1 + lane;
+        if (j < 0) j += n;
+        while (j >= n) j -= n;
+        float2 xy[MERIT_PUB];
+        float dq[MERIT_PUB];
+        unsigned fw[MERIT_PUB], bw[MERIT_PUB];
+#pragma unroll
+        for (int q = 0; q < MERIT_PUB; ++q) {
+            xy[q] = pos[t0 - 1 + min(q, nq - 1)];
+            dq[q] = rec_d2_seg(rec, j, xy[q].x, xy[q].y);
+            const float dn = __shfl_down_sync(FULL, dq[q], 1);
+            fw[q] = __ballot_sync(FULL, lane < 31 && dn < dq[q]);   // bit l: d(l+1) < d(l)
+            bw[q] = __ballot_sync(FULL, lane < 31 && dq[q] < dn);   // bit l: d(l) < d(l+1)
+        }
+        int L = 1, scur = s;
+        bool seq = false;
+#pragma unroll
+        for (int q = 0; q < MERIT_PUB; ++q) {
+            if (q < nq) {
+                float dd = 0.0f;
+                if (!seq) {
+                    if ((fw[q] >> L) & 1u) {
+                        const int L2 = __ffs(~fw[q] & ~((2u << L) - 1u)) - 1;
+                        if (L2 >= 31) seq = true;
+                        else L = L2;
+                    } else if ((bw[q] >> (L - 1)) & 1u) {
+                        seq = true;
+                    }
+                    dd = __shfl_sync(FULL, dq[q], L);
+                    if (!seq) {
+                        scur = s - 1 + L;
+                        if (scur < 0) scur += n;
+                        while (scur >= n) scur -= n;
+                    }
+                }
+                if (seq) {
+                    int sr = 0;
+                    float dr = 0.0f;
+                    if (lane == 0) sr = walk_seq_rec(rec, n, scur, xy[q].x, xy[q].y, dr);
+                    scur = __shfl_sync(FULL, sr, 0);
+                    dd = __shfl_sync(FULL, dr, 0);
+                }
+                const float h = P.w2 - dd;
+                const float a = cbf_arg(P, h_prev, h);
+                Jf = (a > 0.0f) ? fmaf(P.C_cbf, a, Jf) : Jf;
+                h_prev = h;
+                if (((t0 + q) & 15) == 0) {
+                    J += (double)Jf;
+                    Jf = 0.0f;
+                }
+            }
+        }
+        s = scur;
+    }
+    J += (double)Jf;
+    return J;
+}
+
+// Two warps: thread 0 integrates the model (any parameters); warp 1 follows.
+// BLK >= 64; buf holds 8 N bytes.
 template <bool FAST>
-__device__ void merit_split(const DevParams& P, const float4* rec,
-                            const State& x0, int s0, int N, const float2* Vw, float* buf,
-                            volatile int* prog, double* out, unsigned* status) {
+__device__ __forceinline__ void merit_split(const DevParams& P, const float4* rec,
+                                            const State& x0, int s0, int N, const float2* Vw,
+                                            float* buf, volatile int* prog, double* out,
+                                            unsigned* status) {
     const int tid = threadIdx.x;
+    float2* pos = reinterpret_cast<float2*>(buf);            // (X, Y) of x_{t+1}
     if (tid == 0) *prog = 0;
     __syncthreads();
     if (tid == 0) {
@@ -145,53 +241,27 @@ __device__ void merit_split(const DevParams& P, const float4* rec,
         for (int t = 0; t < N; ++t) {
             const float2 u = clamp2(P, Vw[t]);
             model_step<FAST>(P, x, u.x, u.y);
-            reinterpret_cast<float2*>(buf)[t] = make_float2(x.X, x.Y);   // state t + 1
-            __threadfence_block();
-            *prog = t + 1;
-        }
-    } else if (tid == 32) {
-        int s = s0;
-        float d2 = rec_d2_seg(rec, s, x0.X, x0.Y);
-        float h_prev = P.w2 - d2;
-        double J = (double)(0.0f * run_cost(P, x0.vx, d2));
-        float Jf = 0.0f;
-        const float wc = P.C_cbf;
-        for (int t = 1; t <= N; ++t) {
-            int tries = 0;
-            while (*prog < t) {
-                if (++tries > (1 << 24)) {
-                    atomicOr(status, SMPPI_DEV_TIMEOUT);
-                    *out = 0.0;
-                    return;
-                }
-            }
-            __threadfence_block();
-            const float2 xy = reinterpret_cast<const float2*>(buf)[t - 1];
-            bool nofb = false;
-            s = walk_rec<false>(rec, P.n_track, s, xy.x, xy.y, d2, nofb);
-            const float h = P.w2 - d2;
-            const float a = cbf_arg(P, h_prev, h);
-            Jf = (a > 0.0f) ? fmaf(wc, a, Jf) : Jf;
-            h_prev = h;
-            if ((t & 15) == 0) {
-                J += (double)Jf;
-                Jf = 0.0f;
+            pos[t] = make_float2(x.X, x.Y);
+            if ((t + 1) % MERIT_PUB == 0 || t + 1 == N) {
+                __threadfence_block();
+                *prog = t + 1;
             }
         }
-        J += (double)Jf;
-        *out = J;
+    } else if ((tid >> 5) == 1) {
+        const double J = merit_follow_warp(P, rec, x0, s0, N, pos, prog, status);
+        if (tid == 32) *out = J;
     }
 }
 
-// The same merit for the FAST model by three threads in three warps: thread 0
-// runs the velocity recurrence (tyre forces; steer sin / cos and rear force of
-// every step precomputed by the whole block), thread 32 the pose recurrence
-// from the published velocities, thread 64 the track walk and the DCBF terms
-// from the published positions.  buf holds 40 N + 8 bytes; prog two counters.
-// Same arithmetic and summation order as forward_cost.  BLK >= 96.
-__device__ void merit_split3(const DevParams& P, const float4* rec, const State& x0, int s0,
-                             int N, const float2* Vw, float* buf, volatile int* prog, double* out,
-                             unsigned* status) {
+// Three warps for the C = 1.5 model: thread 0 runs the velocity recurrence
+// (tyre forces; the steer's sin / cos and the rear force of every step are
+// precomputed by the whole block), thread 32 the pose recurrence from the
+// published velocities, warp 2 the track walk from the published positions.
+// BLK >= 96; buf holds 40 N + 8 bytes; prog two counters.
+__device__ __forceinline__ void merit_split3(const DevParams& P, const float4* rec,
+                                             const State& x0, int s0, int N, const float2* Vw,
+                                             float* buf, volatile int* prog, double* out,
+                                             unsigned* status) {
     const int tid = threadIdx.x;
     // buf is only 8-byte aligned in some callers: round up to 16 bytes for the
     // float4 rows (the tape scratch has 44 (T + 2) >= 40 N + 8 bytes)
@@ -210,13 +280,14 @@ __device__ void merit_split3(const DevParams& P, const float4* rec, const State&
         ctl[t] = make_float4(u.x, sd, cd, P.fx_gain * u.y);
     }
     __syncthreads();
-    constexpr int LIMIT = 1 << 24;
     if (tid == 0) {
         float vx = x0.vx, vy = x0.vy, r = x0.r;
         for (int t = 0; t < N; ++t) {
             vel[t] = make_float4(vx, vy, r, 0.0f);
-            __threadfence_block();
-            prog[0] = t + 1;
+            if ((t + 1) % MERIT_PUB == 0 || t + 1 == N) {
+                __threadfence_block();
+                prog[0] = t + 1;
+            }
             const float4 c = ctl[t];
             vel_step_fast(P, vx, vy, r, c.x, c.y, c.z, c.w);
         }
@@ -225,7 +296,7 @@ __device__ void merit_split3(const DevParams& P, const float4* rec, const State&
         for (int t = 0; t < N; ++t) {
             int tries = 0;
             while (prog[0] <= t) {
-                if (++tries > LIMIT) {
+                if (++tries > MERIT_WAIT_LIMIT) {
                     atomicOr(status, SMPPI_DEV_TIMEOUT);
                     return;
                 }
@@ -234,39 +305,14 @@ __device__ void merit_split3(const DevParams& P, const float4* rec, const State&
             const float4 v = vel[t];
             pose_step_fast(P, v.x, v.y, v.z, X, Y, psi, cp, sp);
             pos[t] = make_float2(X, Y);
-            __threadfence_block();
-            prog[1] = t + 1;
-        }
-    } else if (tid == 64) {
-        int s = s0;
-        float d2 = rec_d2_seg(rec, s, x0.X, x0.Y);
-        float h_prev = P.w2 - d2;
-        double J = (double)(0.0f * run_cost(P, x0.vx, d2));
-        float Jf = 0.0f;
-        for (int t = 1; t <= N; ++t) {
-            int tries = 0;
-            while (prog[1] < t) {
-                if (++tries > LIMIT) {
-                    atomicOr(status, SMPPI_DEV_TIMEOUT);
-                    *out = 0.0;
-                    return;
-                }
-            }
-            __threadfence_block();
-            const float2 xy = pos[t - 1];
-            bool nofb = false;
-            s = walk_rec<false>(rec, P.n_track, s, xy.x, xy.y, d2, nofb);
-            const float h = P.w2 - d2;
-            const float a = cbf_arg(P, h_prev, h);
-            Jf = (a > 0.0f) ? fmaf(P.C_cbf, a, Jf) : Jf;
-            h_prev = h;
-            if ((t & 15) == 0) {
-                J += (double)Jf;
-                Jf = 0.0f;
+            if ((t + 1) % MERIT_PUB == 0 || t + 1 == N) {
+                __threadfence_block();
+                prog[1] = t + 1;
             }
         }
-        J += (double)Jf;
-        *out = J;
+    } else if ((tid >> 5) == 2) {
+        const double J = merit_follow_warp(P, rec, x0, s0, N, pos, prog + 1, status);
+        if (tid == 64) *out = J;
     }
 }
 
