@@ -449,6 +449,19 @@ __device__ __forceinline__ float cbf_arg(const DevParams& P, float h_prev, float
 }
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialization attribute may start while its predecessor in the
+// stream is still running; griddep_wait() blocks until the predecessor has
+// completed and its memory is visible (a no-op without such a predecessor), so
+// every read of data another launch produced comes after it.
+// griddep_launch_dependents() lets the next such launch start early.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" :::);
+}
+
+// ---------------------------------------------------------------------------
 // Bulk (TMA, non-tensor) global -> shared copies completed on an mbarrier.
 // Addresses 16-byte aligned, sizes multiples of 16 bytes.  The wait is
 // bounded: after the limit it reports failure (the caller sets a status bit).

@@ -38,11 +38,14 @@ __device__ __forceinline__ float warp_min(float v) {
 // (status set, copy drained) if the copy did not complete.
 template <int BLK>
 __device__ __forceinline__ bool stage_problem(const DevParams& P, const float4* __restrict__ recg,
-                                              const float* __restrict__ Vg, float X0, float Y0,
+                                              const float* __restrict__ Vg,
+                                              const float* __restrict__ x0g,
                                               float4* rec, float4* Vs, uint64_t* bar, int* s_flag,
                                               int* s_seg0, float* s_d20, float* red_f,
                                               int* red_i, unsigned* status) {
     const int tid = threadIdx.x, n = P.n_track;
+    griddep_launch_dependents();
+    griddep_wait();
     if (tid == 0) {
         *s_flag = 0;
         mbar_init(bar, 1);
@@ -64,6 +67,7 @@ __device__ __forceinline__ bool stage_problem(const DevParams& P, const float4* 
         }
         return false;
     }
+    const float X0 = x0g[3], Y0 = x0g[4];
     float bd = 3.0e38f;
     int bi = 0x7fffffff;
     for (int i = tid; i < n; i += BLK) {
@@ -93,7 +97,6 @@ __global__ void __launch_bounds__(BLK) mppi_rollout_kernel(
     const uint32_t* __restrict__ iter_dev, float* __restrict__ S_out, float* __restrict__ traj,
     float* __restrict__ blk_min, int* __restrict__ seg0_out, unsigned* __restrict__ status) {
     constexpr int NW = BLK / 32;
-    if (iter_dev) iter += *iter_dev;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int T = P.T;
     float4* rec = reinterpret_cast<float4*>(smem_raw);
@@ -108,9 +111,10 @@ __global__ void __launch_bounds__(BLK) mppi_rollout_kernel(
     const int k = blockIdx.x * BLK + tid;
     const bool active = k < P.K;
 
-    if (!stage_problem<BLK>(P, recg, Vg, x0g[3], x0g[4], rec, Vs, &bar, &s_flag, &s_seg0, &s_d20,
+    if (!stage_problem<BLK>(P, recg, Vg, x0g, rec, Vs, &bar, &s_flag, &s_seg0, &s_d20,
                             red_f, red_i, status))
         return;
+    if (iter_dev) iter += *iter_dev;
     if (blockIdx.x == 0 && tid == 0 && seg0_out) *seg0_out = s_seg0;
     float S = 3.0e38f;
     if (active) {
@@ -141,6 +145,8 @@ __global__ void __launch_bounds__(ROLL2_BLK, 2) mppi_rollout2_kernel(
     const uint32_t* __restrict__ iter_dev, float* __restrict__ S_out, float* __restrict__ traj,
     float* __restrict__ blk_min, int* __restrict__ seg0_out, unsigned* __restrict__ status) {
     constexpr int BLK = ROLL2_BLK, NW = BLK / 32;
+    griddep_launch_dependents();
+    griddep_wait();
     if (iter_dev) iter += *iter_dev;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int T = P.T, n = P.n_track;
@@ -273,6 +279,8 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_update_kernel(
     unsigned* __restrict__ ticket, unsigned* __restrict__ status, ShieldTail sh) {
     constexpr int NW = UPD_BLK / 32;
     constexpr int PER_T = UPD_PER_T;
+    griddep_launch_dependents();
+    griddep_wait();
     const uint32_t n_upd = iter_dev ? *iter_dev : 0u;
     iter += n_upd;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -524,6 +532,22 @@ __global__ void debug_noise_kernel(DevParams P, uint32_t iter, uint32_t ctr3, in
 // ----------------------------------------------------------------------------
 // Host-side launchers
 // ----------------------------------------------------------------------------
+// Launch with programmatic stream serialization (see griddep_wait).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kern)(KArgs...), int grid, int block, size_t smem,
+                              cudaStream_t st, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 size_t rollout_smem_bytes(int n_track, int T) {
     // the packed kernel's V pairs take two float4 per step, the scalar kernel's one
     return rec_table_bytes(n_track) + (size_t)T * 2 * sizeof(float4);
@@ -564,9 +588,8 @@ cudaError_t launch_rollout(const DevParams& P, bool dump, const float* x0, const
         auto kern = dump ? mppi_rollout2_kernel<true> : mppi_rollout2_kernel<false>;
         cudaError_t e = ensure_smem((const void*)kern, smem);
         if (e != cudaSuccess) return e;
-        kern<<<rollout_blocks(P), ROLL2_BLK, smem, st>>>(P, x0, V, rec, iter, ctr3, iter_dev, S_out,
-                                                         traj, blk_min, seg0_out, status);
-        return cudaGetLastError();
+        return launch_pdl(kern, rollout_blocks(P), ROLL2_BLK, smem, st, P, x0, V, rec, iter, ctr3,
+                          iter_dev, S_out, traj, blk_min, seg0_out, status);
     }
     const int nblk = (P.K + ROLL_BLK - 1) / ROLL_BLK;
     const size_t smem = rec_table_bytes(P.n_track) + (size_t)P.T * sizeof(float4);
@@ -574,19 +597,17 @@ cudaError_t launch_rollout(const DevParams& P, bool dump, const float* x0, const
                      : mppi_rollout_kernel<ROLL_BLK, false, false>;
     cudaError_t e = ensure_smem((const void*)kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<nblk, ROLL_BLK, smem, st>>>(P, x0, V, rec, iter, ctr3, iter_dev, S_out, traj, blk_min,
-                                       seg0_out, status);
-    return cudaGetLastError();
+    return launch_pdl(kern, nblk, ROLL_BLK, smem, st, P, x0, V, rec, iter, ctr3, iter_dev, S_out,
+                      traj, blk_min, seg0_out, status);
 }
 
 cudaError_t launch_update(const DevParams& P, const float* S, const float* blk_min, int n_min,
                           float* V, uint32_t iter, uint32_t ctr3, uint32_t* iter_dev,
                           float* part_acc, double* part_eta, int* part_has, unsigned* ticket,
                           unsigned* status, cudaStream_t st) {
-    mppi_update_kernel<false, false><<<update_grid(P.K), UPD_BLK, 0, st>>>(
-        P, S, blk_min, n_min, V, iter, ctr3, iter_dev, part_acc, part_eta, part_has, ticket,
-        status, ShieldTail{});
-    return cudaGetLastError();
+    return launch_pdl(mppi_update_kernel<false, false>, update_grid(P.K), UPD_BLK, 0, st, P, S,
+                      blk_min, n_min, V, iter, ctr3, iter_dev, part_acc, part_eta, part_has, ticket,
+                      status, ShieldTail{});
 }
 
 cudaError_t launch_update_shield(const DevParams& P, const float* S, const float* blk_min,
@@ -603,10 +624,8 @@ cudaError_t launch_update_shield(const DevParams& P, const float* S, const float
                                              : mppi_update_kernel<true, false>;
     cudaError_t e = ensure_smem((const void*)kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<update_grid(P.K), UPD_BLK, smem, st>>>(P, S, blk_min, n_min, V, iter, ctr3, iter_dev,
-                                                  part_acc, part_eta, part_has, ticket, status,
-                                                  sh);
-    return cudaGetLastError();
+    return launch_pdl(kern, update_grid(P.K), UPD_BLK, smem, st, P, S, blk_min, n_min, V, iter,
+                      ctr3, iter_dev, part_acc, part_eta, part_has, ticket, status, sh);
 }
 
 cudaError_t launch_debug_noise(const DevParams& P, uint32_t iter, uint32_t ctr3, int K, int T,
