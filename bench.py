@@ -42,7 +42,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 # DRAM traffic per rollout launch from the ncu capture in profiles/, valid only
 # for the kernel source it was taken on (hash of the files that define it).
-ROLLOUT_TRAFFIC = {"sources_sha": "715d5d3c277f81c7", "bytes_per_launch": 121856}
+ROLLOUT_TRAFFIC = {"sources_sha": "bfd86c16433f59cb", "bytes_per_launch": 122368}
 
 
 def kernel_sha() -> str:
@@ -143,6 +143,29 @@ def oracle_updates(K, T, n_repair, budget_s, nthreads, max_updates=None):
                                                    time.perf_counter() - t0 > budget_s):
             break
     return n, times
+
+
+def oracle_problem_updates(pr, n_repair, n_updates, nthreads):
+    """Time closed-loop updates of the FP64 oracle on the host for problem pr
+    (the CPU-baseline leg of the small configurations)."""
+    import numpy as np
+
+    import oracle as O
+    O.build()
+    m = O.Model(pr.params, pr.track)
+    x0 = pr.x0.astype(np.float64)
+    V = pr.V.astype(np.float64)
+    times = []
+    for n in range(n_updates):
+        a = time.perf_counter()
+        _, Vp = O.mppi_step(m, x0, V, n, 0, nthreads=nthreads)
+        Vs = Vp
+        if n_repair > 0:
+            Vs, _, _, _ = O.repair(m, x0, Vp, n_repair)
+        x0 = O.apply(m, x0, Vs[0], n)
+        V = O.shift(m, Vp)
+        times.append(time.perf_counter() - a)
+    return times
 
 
 def cpu_threads() -> int:
@@ -433,7 +456,7 @@ def run_batch(args):
                                "device_status_bits": _status_names(st_b[1])},
         "plain_per_problem": {"value": B * len(t_p) / (sum(t_p) / 1e3),
                               "ms_per_update_all": float(np.median(t_p)),
-                              "launches_per_update": 2 * B + B, "l2": "flushed between steps"},
+                              "launches_per_update": 2 * B, "l2": "flushed between steps"},
         "speedup": (B * args.steps / (sum(t_b) / 1e3)) / (B * len(t_p) / (sum(t_p) / 1e3)),
     }
     print(json.dumps(line), flush=True)
@@ -457,12 +480,16 @@ def run_sweep(args):
             pr = I.throughput_problem(K, T)
             ctl = S.Controller(pr.params, pr.track, device=dev)
             x0, V0 = ctl.tensor(pr.x0), ctl.tensor(pr.V)
-            Vb = [V0.clone() for _ in range(args.steps + args.warmup)]
+            n_b = args.warmup + 2 * args.steps
+            Vb = [V0.clone() for _ in range(n_b)]
             for i in range(args.warmup):
                 S.smppi_step(ctl.h, x0, Vb[i], i, 0)
-            S.smppi_timing(ctl.h, True)
             t = _timed_steps(lambda i: S.smppi_step(ctl.h, x0, Vb[args.warmup + i], i, 0),
                              args.steps, flush)
+            # per-kernel durations from a second pass with events around the launches
+            S.smppi_timing(ctl.h, True)
+            _timed_steps(lambda i: S.smppi_step(ctl.h, x0, Vb[args.warmup + args.steps + i], i, 0),
+                         args.steps, flush)
             S.smppi_timing(ctl.h, False)
             kt = S.smppi_timing_read(ctl.h)
             roll_s = kt["rollout"][0] / kt["rollout"][1] / 1e3
@@ -477,6 +504,53 @@ def run_sweep(args):
     print(json.dumps({"workload": "MPPI iteration sweep (rollouts + softmin update)",
                       "peak_tflops": FP32_PEAK_TFLOPS, "flops_per_rollout_step": F_ALG,
                       "l2": "flushed between steps", "rows": rows}), flush=True)
+    return 0
+
+
+def run_small(args):
+    """The small configurations, GPU and FP64 oracle side by side: the K = 256,
+    T = 50 Shield-MPPI update (10 Armijo iterations; also the MPPI iteration
+    alone) and the K = 1024, T = 60 plain MPPI closed-loop step (no shield, no
+    CBF cost)."""
+    import torch
+
+    import __graft_entry__
+    from paper_2302_11719_gb300 import inputs as I
+    from paper_2302_11719_gb300 import smppi as S
+    __graft_entry__.build()
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    out = {}
+    for name, pr, n_rep in (("shield_update_K256_T50", I.single_step_small(), N_REPAIR),
+                            ("plain_step_K1024_T60", I.closed_loop_plain(), 0)):
+        ctl = S.Controller(pr.params, pr.track, device=dev)
+        x0, V = ctl.tensor(pr.x0), ctl.tensor(pr.V)
+        Vs = torch.empty_like(V)
+        it = [0]
+
+        def upd(i):
+            S.smppi_shield_update(ctl.h, x0, V, Vs, it[0], 0, n_rep)
+            it[0] += 1
+        for i in range(args.warmup):
+            upd(i)
+        t = _timed_steps(upd, args.steps, flush)
+        row = {"gpu_us_per_update": statistics.median(t) * 1e3}
+        if n_rep > 0:
+            Vb = [ctl.tensor(pr.V) for _ in range(args.steps)]
+            t2 = _timed_steps(lambda i: S.smppi_step(ctl.h, x0, Vb[i], i, 0), args.steps, flush)
+            row["gpu_us_mppi_iteration_only"] = statistics.median(t2) * 1e3
+        st, bits = ctl.sync_status()
+        row["device_status_bits"] = _status_names(bits)
+        ctl.close()
+        for nt, key in ((cpu_threads(), "oracle_us_per_update_all_cores"),
+                        (1, "oracle_us_per_update_1_core")):
+            times = oracle_problem_updates(pr, n_rep, 5, nt)
+            row[key] = statistics.median(times) * 1e6
+        row["cores"] = cpu_threads()
+        out[name] = row
+    print(json.dumps({"workload": "small configurations (median of the timed steps, L2 flushed "
+                                  "between steps; oracle: 5 closed-loop updates on the host)",
+                      "results": out}), flush=True)
     return 0
 
 
@@ -541,7 +615,8 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="shield", choices=["shield", "batch", "sweep", "grad"])
+    ap.add_argument("--workload", default="shield",
+                    choices=["shield", "batch", "sweep", "grad", "small"])
     ap.add_argument("--loop-updates", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -556,6 +631,8 @@ def main():
         return run_sweep(args)
     if args.workload == "grad":
         return run_grad(args)
+    if args.workload == "small":
+        return run_small(args)
     return run_ours(args)
 
 

@@ -151,6 +151,8 @@ def test_repair_small_problem(S, orc):
         starts.append(np.tile(np.array([[b, 0.5]], np.float32), (pr.T, 1)))
     x0s = np.tile(pr.x0, (len(starts), 1))
     flips, worst = repair_compare(S, orc, pr.params, pr.track, x0s, np.stack(starts), 10)
+    print("K=256 T=50 repair (5 starts, 10 Armijo iterations): %d flips, max |V_safe err| %.2e"
+          % (flips, worst))
     assert flips == 0 and worst <= V_REP, (flips, worst)
 
 
