@@ -554,6 +554,55 @@ def run_small(args):
     return 0
 
 
+def run_compare(args):
+    """Closed-loop controller comparison on synthetic tracks (the analogue of the
+    paper's Sec. VI closed-loop experiments, which need the AutoRally simulator):
+    plain MPPI (no DCBF cost, no shield), MPPI with the DCBF cost (Eq. 17-20) and
+    Shield-MPPI (DCBF cost + 10 Armijo repair iterations), each on the same 128
+    narrow-track problems with the same disturbances, for a grid of (K, T).
+    Rates come from the batch's safety monitor (executed steps that break the
+    DCBF condition / end outside the track)."""
+    import torch
+
+    import __graft_entry__
+    from paper_2302_11719_gb300 import inputs as I
+    from paper_2302_11719_gb300 import smppi as S
+    __graft_entry__.build()
+    dev = torch.device("cuda", 0)
+    B, steps = 128, args.loop_updates
+    ctrls = (("plain MPPI", 0.0, 0), ("MPPI + DCBF cost", 1000.0, 0),
+             ("Shield-MPPI", 1000.0, N_REPAIR))
+    rows = []
+    for K in (64, 256, 1024, 4096):
+        for T in (20, 40):
+            for name, c_cbf, n_rep in ctrls:
+                ib = I.uneven_instances(n_inst=B, seed=7, K_lo=K, K_hi=K, T_lo=T, T_hi=T,
+                                        w_lo=1.0, w_hi=1.5, C_cbf=c_cbf, **I.HARSH)
+                bt = S.Batch(ib, block_rollouts=0, device=dev)
+                S.smppi_batch_loop(bt.b, bt.x0, bt.V, bt.V_safe, 0, n_rep, 1)   # autotune
+                bt.x0.copy_(torch.as_tensor(ib.x0, device=dev))
+                bt.V.zero_()
+                S.smppi_batch_monitor(bt.b, B, reset=True)
+                a0 = torch.cuda.Event(enable_timing=True)
+                a1 = torch.cuda.Event(enable_timing=True)
+                a0.record()
+                S.smppi_batch_loop(bt.b, bt.x0, bt.V, bt.V_safe, 0, n_rep, steps)
+                a1.record()
+                torch.cuda.synchronize()
+                viol, out = S.smppi_batch_monitor(bt.b, B, reset=True)
+                rows.append({"K": K, "T": T, "controller": name,
+                             "violation_rate": float(viol.sum()) / (B * steps),
+                             "outside_rate": float(out.sum()) / (B * steps),
+                             "problems_ever_outside": int((out > 0).sum()),
+                             "ms_per_update_all": a0.elapsed_time(a1) / steps})
+                bt.close()
+    print(json.dumps({"workload": "closed-loop controller comparison, %d problems x %d updates, "
+                                  "narrow tracks (w in [1, 1.5] m), v_target 14 m/s, q_d 10, "
+                                  "disturbance std 0.6" % (B, steps),
+                      "rows": rows}), flush=True)
+    return 0
+
+
 def run_grad(args):
     """8192 near-boundary sequences, T = 100: adjoint gradient (checkpoint every
     10 steps vs full tape) and 20 Armijo repair iterations."""
@@ -616,7 +665,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="shield",
-                    choices=["shield", "batch", "sweep", "grad", "small"])
+                    choices=["shield", "batch", "sweep", "grad", "small", "compare"])
     ap.add_argument("--loop-updates", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -633,6 +682,8 @@ def main():
         return run_grad(args)
     if args.workload == "small":
         return run_small(args)
+    if args.workload == "compare":
+        return run_compare(args)
     return run_ours(args)
 
 

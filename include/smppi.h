@@ -261,6 +261,18 @@ smppi_status smppi_batch_sync_status(smppi_batch* b, uint32_t* bits_out);
 /* The launch shape in use (after autotuning): rollouts per item and grid size. */
 smppi_status smppi_batch_config(const smppi_batch* b, int* block_rollouts, int* grid);
 
+/* Safety monitor of the batch (not part of the paper's method; it measures
+ * the closed loop the paper evaluates in Sec. VI).  For every problem, the
+ * number of executed closed-loop steps x_n -> x_{n+1} since creation (or the
+ * last read with reset != 0) that violated the discrete CBF condition of
+ * Eq. 15 / 17, h(x_{n+1}) < (1 - alpha) h(x_n), and that ended outside the
+ * track, h(x_{n+1}) < 0, with h = w^2 - e_y^2 (Eq. 23) and e_y tracked from
+ * x_n's nearest segment (the same projection as the cost).  viol_out and
+ * outside_out (host, B each) may be NULL.  Synchronises the batch's stream.
+ * The autotuner's timing runs are not counted. */
+smppi_status smppi_batch_monitor(smppi_batch* b, uint32_t* viol_out, uint32_t* outside_out,
+                                 int reset);
+
 /*
  * smppi_step without any allocation, for callers that cannot allocate device
  * memory: control loops that forbid allocation once running, or runtimes that

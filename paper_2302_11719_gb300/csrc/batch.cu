@@ -59,6 +59,8 @@ struct BatchArgs {
     int n_repair, ck;
     int n_track_max, T_max;
     unsigned* status;
+    unsigned* viol;        // [B] executed steps violating the DCBF condition (monitor)
+    unsigned* outside;     // [B] executed steps ending outside the track (monitor)
 };
 
 constexpr int BATCH_PPT = 8;      // costs per thread in one pass of the problem update
@@ -311,6 +313,14 @@ __global__ void __launch_bounds__(RB) batch_kernel(DevParams P0, BatchArgs a) {
             xo[4] = xn.Y;
             xo[5] = xn.psi;
             a.done[i] = 0u;
+            // safety monitor of the executed step: h = w^2 - e_y^2 (Eq. 23) of x0 and of the
+            // new state (tracked from x0's segment), DCBF condition of Eq. 17
+            float d21;
+            bool nofb = false;
+            walk_rec<false>(rec, n, s0, xn.X, xn.Y, d21, nofb);
+            const float h0 = P.w2 - d20, h1 = P.w2 - d21;
+            if (h1 < P.one_m_alpha * h0) a.viol[i] += 1u;
+            if (h1 < 0.0f) a.outside[i] += 1u;
         }
         for (int t = tid; t < T; t += RB) Vg[t] = Vs[t + 1 < T ? t + 1 : T - 1];
         staged = -1;      // Vs now holds V+ of this problem
@@ -371,6 +381,8 @@ struct smppi_batch {
     unsigned* done = nullptr;
     unsigned* head = nullptr;
     unsigned* status = nullptr;
+    unsigned* viol = nullptr;             // [B] safety-monitor counters
+    unsigned* outside = nullptr;
     uint32_t* iter_dev = nullptr;
     float* tune_x0 = nullptr;             // scratch state for the autotuner
     float* tune_V = nullptr;
@@ -464,6 +476,8 @@ smppi_status enqueue_batch(smppi_batch* b, cudaStream_t st, float* x0, float* V,
     a.n_repair = n_repair; a.ck = b->ck;
     a.n_track_max = b->n_track_max; a.T_max = b->T_max;
     a.status = b->status;
+    a.viol = b->viol;
+    a.outside = b->outside;
     const size_t smem = batch_smem(b->RB, b->n_track_max, b->T_max);
     BCU(b, cudaMemsetAsync(b->head, 0, sizeof(unsigned), st));
     BCU(b, ensure_smem(batch_kernel_ptr(b, b->RB), smem));
@@ -540,13 +554,17 @@ smppi_status autotune(smppi_batch* b, const float* x0, const float* V, const flo
     b->grid = b->sms * pick.bps;
     b->tuned = true;
     BCU(b, cudaMemsetAsync(b->status, 0, sizeof(unsigned), b->st));
+    // the timing runs stepped scratch copies: they do not count for the monitor
+    BCU(b, cudaMemsetAsync(b->viol, 0, sizeof(unsigned) * b->B, b->st));
+    BCU(b, cudaMemsetAsync(b->outside, 0, sizeof(unsigned) * b->B, b->st));
     return SMPPI_OK;
 }
 
 void bfree(smppi_batch* b) {
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     void* ptrs[] = {b->d_inst, b->d_track_off, b->d_items, b->rec, b->S, b->chunk_min,
-                    b->done, b->head, b->status, b->iter_dev, b->tune_x0, b->tune_V, b->tune_Vs};
+                    b->done, b->head, b->status, b->viol, b->outside, b->iter_dev,
+                    b->tune_x0, b->tune_V, b->tune_Vs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (b->cap) cudaStreamDestroy(b->cap);
@@ -624,6 +642,8 @@ smppi_status smppi_batch_create(const smppi_params* shared, int B, const smppi_i
     BALLOC(b->done, sizeof(unsigned) * B);
     BALLOC(b->head, sizeof(unsigned));
     BALLOC(b->status, sizeof(unsigned));
+    BALLOC(b->viol, sizeof(unsigned) * B);
+    BALLOC(b->outside, sizeof(unsigned) * B);
     BALLOC(b->iter_dev, sizeof(uint32_t));
     BALLOC(b->tune_x0, sizeof(float) * 6 * B);
     BALLOC(b->tune_V, sizeof(float) * b->V_len);
@@ -632,6 +652,8 @@ smppi_status smppi_batch_create(const smppi_params* shared, int B, const smppi_i
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->done, 0, sizeof(unsigned) * B, b->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->status, 0, sizeof(unsigned), b->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->viol, 0, sizeof(unsigned) * B, b->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->outside, 0, sizeof(unsigned) * B, b->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->iter_dev, 0, sizeof(uint32_t), b->st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_track_off, track_off.data(), sizeof(int) * B, cudaMemcpyHostToDevice, b->st);
@@ -741,6 +763,22 @@ smppi_status smppi_batch_sync_status(smppi_batch* b, uint32_t* bits_out) {
     if (bits & SMPPI_DEV_NUMERIC) return bfail(b, SMPPI_ERR_NUMERIC, "NaN/Inf met on the device");
     if (bits & SMPPI_DEV_TIMEOUT) return bfail(b, SMPPI_ERR_TIMEOUT, "a device wait gave up");
     if (bits & SMPPI_DEV_STALLED) return bfail(b, SMPPI_ERR_STALLED, "repair line search stalled");
+    return SMPPI_OK;
+}
+
+smppi_status smppi_batch_monitor(smppi_batch* b, uint32_t* viol_out, uint32_t* outside_out,
+                                 int reset) {
+    if (!b) return bfail(nullptr, SMPPI_ERR_ARG, "batch is NULL");
+    BCU(b, cudaStreamSynchronize(b->st));
+    if (viol_out)
+        BCU(b, cudaMemcpy(viol_out, b->viol, sizeof(unsigned) * b->B, cudaMemcpyDeviceToHost));
+    if (outside_out)
+        BCU(b, cudaMemcpy(outside_out, b->outside, sizeof(unsigned) * b->B,
+                          cudaMemcpyDeviceToHost));
+    if (reset) {
+        BCU(b, cudaMemset(b->viol, 0, sizeof(unsigned) * b->B));
+        BCU(b, cudaMemset(b->outside, 0, sizeof(unsigned) * b->B));
+    }
     return SMPPI_OK;
 }
 

@@ -182,24 +182,32 @@ class InstanceBatch:
     w: np.ndarray
 
 
+# Closed-loop stress setting of the controller comparison: a high target speed,
+# weak centring and strong disturbances on narrow tracks (w in [1, 1.5] m), so
+# that the three controllers' CBF-violation rates differ.
+HARSH = dict(v_target=14.0, q_d=10.0, dist_sigma=(0.6, 0.6))
+
+
 def uneven_instances(n_inst: int = 512, seed: int = 0, K_lo: int = 64, K_hi: int = 16384,
-                     T_lo: int = 20, T_hi: int = 150) -> InstanceBatch:
+                     T_lo: int = 20, T_hi: int = 150, w_lo: float = 1.5, w_hi: float = 3.0,
+                     **over) -> InstanceBatch:
     """K log-uniform in [K_lo, K_hi], T uniform in {T_lo..T_hi}, a, b ~ U[10, 40] m,
-    w ~ U[1.5, 3] m, resampled until min(a,b)^2 / max(a,b) > 2 w (no cusp on the
-    inner boundary); x0 on the centreline at theta = 0 with v_x ~ U[4, 6] m/s."""
+    w ~ U[w_lo, w_hi] m (default [1.5, 3]), resampled until min(a,b)^2 / max(a,b) > 2 w
+    (no cusp on the inner boundary); x0 on the centreline at theta = 0 with
+    v_x ~ U[4, 6] m/s.  over: parameter overrides shared by all problems."""
     rng = np.random.default_rng([seed, 4])
     Ks = np.rint(np.exp(rng.uniform(math.log(K_lo), math.log(K_hi), n_inst))).astype(np.int64)
     Ts = rng.integers(T_lo, T_hi + 1, n_inst)
     a = np.empty(n_inst); b = np.empty(n_inst); w = np.empty(n_inst)
     for i in range(n_inst):
         while True:
-            ai, bi, wi = rng.uniform(10, 40), rng.uniform(10, 40), rng.uniform(1.5, 3.0)
+            ai, bi, wi = rng.uniform(10, 40), rng.uniform(10, 40), rng.uniform(w_lo, w_hi)
             if min(ai, bi) ** 2 / max(ai, bi) > 2 * wi:
                 break
         a[i], b[i], w[i] = ai, bi, wi
     vx = rng.uniform(4.0, 6.0, n_inst)
     tracks = np.stack([ellipse_track(a[i], b[i]) for i in range(n_inst)])
     x0 = np.stack([centreline_start(a[i], b[i], vx[i]) for i in range(n_inst)])
-    params = [make_params(K=int(Ks[i]), T=int(Ts[i]), half_width=float(w[i]), seed=seed)
+    params = [make_params(K=int(Ks[i]), T=int(Ts[i]), half_width=float(w[i]), seed=seed, **over)
               for i in range(n_inst)]
     return InstanceBatch(params=params, tracks=tracks, x0=x0, K=Ks, T=Ts, a=a, b=b, w=w)

@@ -81,6 +81,7 @@ _SIGS = {
     "smppi_batch_loop": ([_vp, _vp, _vp, _vp, _u32, _i, _i], _i),
     "smppi_batch_sync_status": ([_vp, C.POINTER(_u32)], _i),
     "smppi_batch_config": ([_vp, C.POINTER(_i), C.POINTER(_i)], _i),
+    "smppi_batch_monitor": ([_vp, _vp, _vp, _i], _i),
     "smppi_timing": ([_vp, _i], _i),
     "smppi_timing_read": ([_vp, C.POINTER(C.c_double), C.POINTER(C.c_int), _i], _i),
 }
@@ -267,6 +268,16 @@ def smppi_batch_config(b) -> tuple[int, int]:
     rb, grid = C.c_int(), C.c_int()
     _bcheck(load_library().smppi_batch_config(b, C.byref(rb), C.byref(grid)), b)
     return rb.value, grid.value
+
+
+def smppi_batch_monitor(b, B: int, reset: bool = False):
+    """(violations, outside) per problem: executed closed-loop steps that broke the
+    discrete CBF condition, and that ended outside the track (uint32 arrays)."""
+    viol = np.zeros(B, np.uint32)
+    out = np.zeros(B, np.uint32)
+    _bcheck(load_library().smppi_batch_monitor(b, viol.ctypes.data, out.ctypes.data,
+                                               int(bool(reset))), b)
+    return viol, out
 
 
 class Batch:

@@ -110,3 +110,58 @@ def test_batch_matches_single_problem_path(S, ib):
         assert rel_err(xg[i], x0.cpu().numpy()) <= 1e-5
         ctl.close()
     bt.close()
+
+
+@pytest.mark.parametrize("n_rep,c_cbf", [(0, 0.0), (10, 1000.0)])
+def test_batch_monitor_vs_oracle(S, orc, n_rep, c_cbf):
+    # safety monitor (executed steps that break the DCBF condition / leave the track)
+    # against the oracle's own closed loop, one step at a time: the oracle's state
+    # goes to the GPU (oracle -> GPU only), one batch update runs, and the monitor's
+    # counts for that step are compared with the condition evaluated on the
+    # oracle's executed step; decisions within 1e-3 of the threshold, and steps
+    # whose executed control differs (a line-search flip), are skipped
+    ib = I.uneven_instances(n_inst=6, seed=11, K_lo=64, K_hi=256, T_lo=20, T_hi=30,
+                            w_lo=1.0, w_hi=1.5, C_cbf=c_cbf, **I.HARSH)
+    bt = S.Batch(ib, block_rollouts=64)
+    B = bt.B
+    models = [orc.Model(ib.params[i], ib.tracks[i]) for i in range(B)]
+    xs = [ib.x0[i].astype(np.float64) for i in range(B)]
+    Vs = [np.zeros((bt.T[i], 2)) for i in range(B)]
+    a = 1.0 - float(np.float32(ib.params[0]["alpha"]))
+    checked = mism = viol_seen = flips = 0
+    for n in range(30):
+        _set_state(bt, xs, Vs)
+        S.smppi_batch_monitor(bt.b, B, reset=True)
+        S.smppi_batch_step(bt.b, bt.x0, bt.V, bt.V_safe, n, n_rep)
+        st, bits = S.smppi_batch_sync_status(bt.b)
+        assert st in (S.OK, S.ERR_STALLED), (st, bits)
+        viol, out = S.smppi_batch_monitor(bt.b, B, reset=True)
+        v0_gpu = [v[0] for v in bt.split(bt.V_safe)]
+        for i in range(B):
+            m = models[i]
+            x32, V32 = xs[i].astype(np.float32), Vs[i].astype(np.float32)
+            _, Vp = orc.mppi_step(m, x32, V32, n, i, nthreads=8)
+            v_exec = Vp[0]
+            if n_rep:
+                v_exec = orc.repair(m, x32, Vp.astype(np.float32), n_rep)[0][0]
+            x1 = orc.apply(m, x32, v_exec, n, i)
+            if np.max(np.abs(v0_gpu[i] - v_exec)) > 1e-4:
+                flips += 1          # a line-search decision differs: another executed step
+                xs[i], Vs[i] = x1, orc.shift(m, Vp)
+                continue
+            seg, d2 = orc.track_nearest(m, x32[3], x32[4])
+            h0 = orc.h(m, d2)
+            _, d21 = orc.track_follow(m, seg, x1[3], x1[4])
+            h1 = orc.h(m, d21)
+            if abs(h1 - a * h0) > 1e-3 * (abs(h0) + 1.0):
+                checked += 1
+                mism += int(viol[i]) != int(h1 < a * h0)
+                viol_seen += int(h1 < a * h0)
+            if abs(h1) > 1e-3:
+                checked += 1
+                mism += int(out[i]) != int(h1 < 0.0)
+            xs[i], Vs[i] = x1, orc.shift(m, Vp)
+    print("monitor (n_repair %d): %d decisions checked, %d mismatches, %d violations, %d flips"
+          % (n_rep, checked, mism, viol_seen, flips))
+    assert checked >= 300 and mism == 0 and flips <= 6
+    bt.close()
