@@ -158,13 +158,15 @@ __device__ __forceinline__ double merit_follow_warp(const DevParams& P, const fl
     float h_prev = P.w2 - d2;
     double J = (double)(0.0f * run_cost(P, x0.vx, d2));
     float Jf = 0.0f;
+    bool timed_out = false;
     for (int t0 = 1; t0 <= N; t0 += MERIT_PUB) {
         const int t1 = min(N, t0 + MERIT_PUB - 1), nq = t1 - t0 + 1;
         int tries = 0;
         while (*prog < t1 && tries <= MERIT_WAIT_LIMIT) ++tries;
-        if (__any_sync(FULL, tries > MERIT_WAIT_LIMIT)) {
+        if (__any_sync(FULL, tries > MERIT_WAIT_LIMIT)) {   // warp-uniform
             if (lane == 0) atomicOr(status, SMPPI_DEV_TIMEOUT);
-            return 0.0;
+            timed_out = true;
+            break;
         }
         __threadfence_block();
         int j = s - 1 + lane;
@@ -222,7 +224,7 @@ __device__ __forceinline__ double merit_follow_warp(const DevParams& P, const fl
         s = scur;
     }
     J += (double)Jf;
-    return J;
+    return timed_out ? 0.0 : J;
 }
 
 // Two warps: thread 0 integrates the model (any parameters); warp 1 follows.
@@ -231,10 +233,13 @@ template <bool FAST>
 __device__ __forceinline__ void merit_split(const DevParams& P, const float4* rec,
                                             const State& x0, int s0, int N, const float2* Vw,
                                             float* buf, volatile int* prog, double* out,
-                                            unsigned* status) {
+                                            volatile int* done, unsigned* status) {
     const int tid = threadIdx.x;
     float2* pos = reinterpret_cast<float2*>(buf);            // (X, Y) of x_{t+1}
-    if (tid == 0) *prog = 0;
+    if (tid == 0) {
+        *prog = 0;
+        *done = 0;
+    }
     __syncthreads();
     if (tid == 0) {
         State x = x0;
@@ -249,8 +254,13 @@ __device__ __forceinline__ void merit_split(const DevParams& P, const float4* re
         }
     } else if ((tid >> 5) == 1) {
         const double J = merit_follow_warp(P, rec, x0, s0, N, pos, prog, status);
-        if (tid == 32) *out = J;
+        if (tid == 32) {
+            *out = J;
+            __threadfence_block();
+            *done = 1;
+        }
     }
+    __syncwarp();
 }
 
 // Three warps for the C = 1.5 model: thread 0 runs the velocity recurrence
@@ -261,7 +271,7 @@ __device__ __forceinline__ void merit_split(const DevParams& P, const float4* re
 __device__ __forceinline__ void merit_split3(const DevParams& P, const float4* rec,
                                              const State& x0, int s0, int N, const float2* Vw,
                                              float* buf, volatile int* prog, double* out,
-                                             unsigned* status) {
+                                             volatile int* done, unsigned* status) {
     const int tid = threadIdx.x;
     // buf is only 8-byte aligned in some callers: round up to 16 bytes for the
     // float4 rows (the tape scratch has 44 (T + 2) >= 40 N + 8 bytes)
@@ -272,6 +282,7 @@ __device__ __forceinline__ void merit_split3(const DevParams& P, const float4* r
     if (tid == 0) {
         prog[0] = 0;
         prog[1] = 0;
+        *done = 0;
     }
     for (int t = tid; t < N; t += blockDim.x) {
         const float2 u = clamp2(P, Vw[t]);
@@ -295,11 +306,10 @@ __device__ __forceinline__ void merit_split3(const DevParams& P, const float4* r
         float X = x0.X, Y = x0.Y, psi = x0.psi, cp = x0.cp, sp = x0.sp;
         for (int t = 0; t < N; ++t) {
             int tries = 0;
-            while (prog[0] <= t) {
-                if (++tries > MERIT_WAIT_LIMIT) {
-                    atomicOr(status, SMPPI_DEV_TIMEOUT);
-                    return;
-                }
+            while (prog[0] <= t && tries <= MERIT_WAIT_LIMIT) ++tries;
+            if (tries > MERIT_WAIT_LIMIT) {
+                atomicOr(status, SMPPI_DEV_TIMEOUT);
+                break;
             }
             __threadfence_block();
             const float4 v = vel[t];
@@ -312,8 +322,13 @@ __device__ __forceinline__ void merit_split3(const DevParams& P, const float4* r
         }
     } else if ((tid >> 5) == 2) {
         const double J = merit_follow_warp(P, rec, x0, s0, N, pos, prog + 1, status);
-        if (tid == 64) *out = J;
+        if (tid == 64) {
+            *out = J;
+            __threadfence_block();
+            *done = 1;
+        }
     }
+    __syncwarp();
 }
 
 // Cost and gradient of one sequence (forward with tape + backward adjoint).
@@ -406,6 +421,7 @@ __device__ void closed_loop_step(const DevParams& P, const ApplyArgs& ap, float2
 struct RepairSmem {
     double P;
     int prog[2];       // progress counters of merit_split / merit_split3
+    int done;          // set by the merit follower once P is written
     float red[32];
     float step;
     int ok;
@@ -428,11 +444,19 @@ __device__ double repair_in_block(const DevParams& P, const float4* rec,
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = BLK / 32;
     const Tape tape{tape_s, 1, 0};
+    // every thread waits (bounded) for the follower's completion flag before it
+    // reads the merit, so that the branch on P below is taken by the whole block
     auto merit = [&]() {
         if (FAST && BLK >= 96)
-            merit_split3(P, rec, x0, s0, N, Vw, tape_s, sm.prog, &sm.P, status);
+            merit_split3(P, rec, x0, s0, N, Vw, tape_s, sm.prog, &sm.P, &sm.done, status);
         else
-            merit_split<FAST>(P, rec, x0, s0, N, Vw, tape_s, sm.prog, &sm.P, status);
+            merit_split<FAST>(P, rec, x0, s0, N, Vw, tape_s, sm.prog, &sm.P, &sm.done, status);
+        __syncthreads();
+        int tries = 0;
+        while (*reinterpret_cast<volatile int*>(&sm.done) == 0 && tries <= MERIT_WAIT_LIMIT)
+            ++tries;
+        if (tries > MERIT_WAIT_LIMIT && tid == 0) atomicOr(status, SMPPI_DEV_TIMEOUT);
+        __threadfence_block();
         __syncthreads();
     };
     merit();
