@@ -255,7 +255,10 @@ smppi_status smppi_batch_step(smppi_batch* b, float* x0, float* V, float* V_safe
 smppi_status smppi_batch_loop(smppi_batch* b, float* x0, float* V, float* V_safe,
                               uint32_t iter0, int n_repair, int n_updates);
 
-/* Synchronise the batch stream and read / clear its device status word. */
+/* Synchronise the batch stream and read / clear its device status word.
+ * After SMPPI_DEV_TIMEOUT (a block gave up on a bounded wait and left the
+ * launch) the problems' completion counters are cleared as well; the state
+ * of the problems that block held (x0, V, V_safe) is then undefined. */
 smppi_status smppi_batch_sync_status(smppi_batch* b, uint32_t* bits_out);
 
 /* The launch shape in use (after autotuning): rollouts per item and grid size. */

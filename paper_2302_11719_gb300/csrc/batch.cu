@@ -132,9 +132,14 @@ __global__ void __launch_bounds__(RB) batch_kernel(DevParams P0, BatchArgs a) {
                     Vs4[t] = make_float4(v.x, v.y, g0, g1);
                 }
             }
-            if (!mbar_wait_bounded(&bar, phase)) {
-                atomicOr(a.status, SMPPI_DEV_TIMEOUT);
-                mbar_wait_bounded(&bar, phase);
+            // a failed wait ends the whole block (block-uniform decision), after
+            // thread 0 has let the copy in flight land
+            const bool ok = mbar_wait_bounded(&bar, phase);
+            if (__syncthreads_or(!ok)) {
+                if (tid == 0) {
+                    atomicOr(a.status, SMPPI_DEV_TIMEOUT);
+                    mbar_wait_bounded(&bar, phase);
+                }
                 return;
             }
             phase ^= 1u;
@@ -759,6 +764,9 @@ smppi_status smppi_batch_sync_status(smppi_batch* b, uint32_t* bits_out) {
     BCU(b, cudaStreamSynchronize(b->st));
     BCU(b, cudaMemcpy(&bits, b->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
     BCU(b, cudaMemset(b->status, 0, sizeof(unsigned)));
+    // a block that gave up on a wait left its problems' completion counters
+    // behind: clear them so that the next launch starts from a clean queue
+    if (bits & SMPPI_DEV_TIMEOUT) BCU(b, cudaMemset(b->done, 0, sizeof(unsigned) * b->B));
     if (bits_out) *bits_out = bits;
     if (bits & SMPPI_DEV_NUMERIC) return bfail(b, SMPPI_ERR_NUMERIC, "NaN/Inf met on the device");
     if (bits & SMPPI_DEV_TIMEOUT) return bfail(b, SMPPI_ERR_TIMEOUT, "a device wait gave up");

@@ -497,10 +497,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 // Wait for phase `parity` of the barrier; false if it did not complete in time.
+// A try_wait may suspend the thread for a hardware-defined time before it
+// returns false, so the wait is bounded in time (MBAR_WAIT_NS of the global
+// timer) as well as in tries.
+constexpr uint64_t MBAR_WAIT_NS = 250000000ull;   // 0.25 s
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (int i = 0; i < (1 << 22); ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (int i = 0; i < (1 << 22); ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer_ns() - t0 > MBAR_WAIT_NS) return false;
+    }
     return false;
 }
 
