@@ -637,19 +637,25 @@ def run_grad(args):
     Vout = torch.empty_like(V)
     its = torch.empty(n, dtype=torch.int32, device=dev)
     mer = torch.empty((n, 21), dtype=torch.float64, device=dev)
-    for _ in range(2):
-        S.smppi_repair(ctl.h, n, x0, V, Vout, 20, 1, 0.0, mer, its)
-    t = _timed_steps(lambda i: S.smppi_repair(ctl.h, n, x0, V, Vout, 20, 1, 0.0, mer, its),
-                     max(3, args.steps // 4), flush)
-    ctl.sync_status()
-    iters = its.cpu().numpy()
-    m = mer.cpu().numpy()
-    out["repair_20"] = {"us_per_call": 1e3 * sum(t) / len(t),
-                        "mean_iterations_run": float(iters.mean()),
-                        "us_per_iteration_run": 1e3 * sum(t) / len(t) / max(1.0, iters.max()),
-                        "merit_before_mean": float(m[:, 0].mean()),
-                        "merit_after_mean": float(m[:, -1].mean()),
-                        "sequences_safe_after": int((m[:, -1] == 0).sum())}
+    # 20 repair iterations: projected gradient + Armijo (mode 1, one thread per
+    # sequence at this size) and BFGS (mode 2, one block per sequence)
+    for key, mode in (("repair_20", 1), ("bfgs_20", 2)):
+        for _ in range(2):
+            S.smppi_repair(ctl.h, n, x0, V, Vout, 20, mode, 0.0, mer, its)
+        t = _timed_steps(lambda i: S.smppi_repair(ctl.h, n, x0, V, Vout, 20, mode, 0.0, mer, its),
+                         max(3, args.steps // 4), flush)
+        st, bits = ctl.sync_status()
+        iters = its.cpu().numpy()
+        m = mer.cpu().numpy()
+        us = 1e3 * sum(t) / len(t)
+        out[key] = {"us_per_call": us,
+                    "mean_iterations_run": float(iters.mean()),
+                    "us_per_iteration_run": us / max(1.0, iters.max()),
+                    "merit_before_mean": float(m[:, 0].mean()),
+                    "merit_after_mean": float(m[:, -1].mean()),
+                    "merit_reduction_per_us": float((m[:, 0] - m[:, -1]).sum()) / us,
+                    "sequences_safe_after": int((m[:, -1] == 0).sum()),
+                    "device_status_bits": _status_names(bits)}
     ctl.close()
     # a plain MPPI iteration of the same size (K = 8192 rollouts, T = 100)
     pr = I.throughput_problem(8192, 100)

@@ -168,6 +168,19 @@ smppi_status smppi_cost_grad(smppi_handle* h, int n_seq, const float* x0, const 
  *   mode 1: projected gradient with Armijo backtracking: s = ls_s0 / |g|_inf,
  *           accept clip(V - s g) when P' <= P - ls_c g'(V - V'), else halve s
  *           (ls_max_halvings trials); stop early when P = 0 (already safe).
+ *   mode 2: BFGS (the solver Sec. IV-B names), box-projected: an inverse-
+ *           Hessian approximation H over the 2 N_r controls, unset at first
+ *           (direction = the mode-1 step -(ls_s0/|g|_inf) g); after each
+ *           accepted step s with gradient change y and s'y > 1e-5 |s||y|, H
+ *           (first (s'y/y'y) I) takes H <- (I - rho s y') H (I - rho y s')
+ *           + rho s s', rho = 1/(y's).  Coordinates at a bound whose gradient
+ *           pushes outward keep d_i = 0; the others take d = -H_FF g_F (H is
+ *           unset again when g'd >= 0).  Trials clip(V + a d), a = 1, 1/2, ...
+ *           (ls_max_halvings), accepted when g'(V - V') > 0 and
+ *           P' <= P - ls_c g'(V - V'); if none is and d came from H, the search
+ *           is repeated along the gradient step.  One block per sequence; the
+ *           first mode-2 call allocates the H workspace ((2 N_r)^2 floats per
+ *           resident block, at most 256 MB).
  *   x0 [n_seq x 6]; V_in, V_out [n_seq x T x 2] (may alias);
  *   merit_out [n_seq x (n_iters + 1)] optional (float64): P before each
  *   iteration and after the last, repeated after an early stop;

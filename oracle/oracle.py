@@ -94,6 +94,10 @@ def lib():
         L.orc_repair.argtypes = [_PP, _dp, _dp, C.c_int, C.c_int, C.c_double, _dp,
                                  C.POINTER(C.c_int)]
         L.orc_repair.restype = C.c_int
+        L.orc_bfgs_update.argtypes = [C.c_int, _dp, _dp, _dp]
+        L.orc_bfgs_quadratic.argtypes = [C.c_int, _dp, _dp, _dp, _dp, _dp, C.c_int, C.c_double,
+                                         C.c_double, C.c_int, _dp, C.POINTER(C.c_int)]
+        L.orc_bfgs_quadratic.restype = C.c_int
         L.orc_apply.argtypes = [_PP, _dp, _dp, C.c_uint32, C.c_uint32, _dp]
         L.orc_shift.argtypes = [_PP, _dp, _dp]
         L.orc_max_threads.restype = C.c_int
@@ -313,7 +317,8 @@ def cost_grad(m: Model, x0, V, N=None, w_run=0.0, w_cbf=1.0):
 
 
 def repair(m: Model, x0, V, n_iters, mode=1, delta=0.0):
-    """(V_safe (T, 2), merit (n_iters + 1,), status, iterations run)."""
+    """(V_safe (T, 2), merit (n_iters + 1,), status, iterations run).
+    mode 0: fixed step, 1: projected gradient + Armijo, 2: BFGS."""
     x0, xp = _d(x0, 6)
     Vs = np.array(V, dtype=np.float64).reshape(m.T, 2).copy()
     mer = np.zeros(n_iters + 1)
@@ -321,6 +326,31 @@ def repair(m: Model, x0, V, n_iters, mode=1, delta=0.0):
     st = lib().orc_repair(m.ptr, xp, Vs.ctypes.data_as(_dp), int(n_iters), int(mode),
                           float(delta), mer.ctypes.data_as(_dp), C.byref(it))
     return Vs, mer, st, it.value
+
+
+def bfgs_update(H, s, y):
+    """The inverse BFGS update (I - rho s y') H (I - rho y s') + rho s s' (a new array)."""
+    n = len(s)
+    Hn = np.array(H, dtype=np.float64).reshape(n, n).copy()
+    s = np.ascontiguousarray(s, np.float64); y = np.ascontiguousarray(y, np.float64)
+    lib().orc_bfgs_update(n, Hn.ctypes.data_as(_dp), s.ctypes.data_as(_dp), y.ctypes.data_as(_dp))
+    return Hn
+
+
+def bfgs_quadratic(A, b, lo, hi, z0, n_iters, s0=0.1, c=1e-4, ls_max=20):
+    """Box BFGS (the repair's mode-2 solver) on 1/2 z'Az - b'z:
+    (z, f before each iteration and after the last, status, iterations run)."""
+    n = len(b)
+    A = np.ascontiguousarray(A, np.float64); b = np.ascontiguousarray(b, np.float64)
+    lo = np.ascontiguousarray(lo, np.float64); hi = np.ascontiguousarray(hi, np.float64)
+    z = np.array(z0, dtype=np.float64).copy()
+    mer = np.zeros(n_iters + 1)
+    it = C.c_int()
+    st = lib().orc_bfgs_quadratic(n, A.ctypes.data_as(_dp), b.ctypes.data_as(_dp),
+                                  lo.ctypes.data_as(_dp), hi.ctypes.data_as(_dp),
+                                  z.ctypes.data_as(_dp), int(n_iters), float(s0), float(c),
+                                  int(ls_max), mer.ctypes.data_as(_dp), C.byref(it))
+    return z, mer, st, it.value
 
 
 def apply(m: Model, x0, v0, n, instance=0):

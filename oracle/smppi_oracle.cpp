@@ -31,6 +31,9 @@
 //       the update result and every repair iterate are projected on the box;
 //   c9  repair = projected gradient with Armijo backtracking (mode 1) or the
 //       fixed step of Alg. 1 (mode 0);
+//   c27 the BFGS repair (mode 2; the solver Sec. IV-B names for Eq. 22, run
+//       for a fixed number of iterations) is box-projected BFGS with Armijo
+//       backtracking on the projected path, see bfgs_box below;
 //   c12 max(0, .) has derivative 0 at a non-positive argument; clamp(v) has
 //       derivative 1 on the closed box and 0 strictly outside it;
 //   c15 e_y is the distance to the centreline polyline, tracked continuously
@@ -504,7 +507,7 @@ double orc_cost_grad(const OrcParams* p, const double x0[6], const double* V, in
     return J;
 }
 
-// Safety shield (Alg. 1, reading c9).  mode 0: n_iters fixed steps
+// Safety shield (Alg. 1, reading c9; mode 2 = BFGS, reading c27).  mode 0: n_iters fixed steps
 // V <- clip(V - delta grad P).  mode 1: projected gradient with Armijo
 // backtracking: s = ls_s0 / |g|_inf, V' = clip(V - s g), accept when
 // P(V') <= P(V) - ls_c g'(V - V'), else halve s (ls_max_halvings trials).
@@ -512,8 +515,12 @@ double orc_cost_grad(const OrcParams* p, const double x0[6], const double* V, in
 // safe).  merit_out gets P before each iteration and after the last one
 // (n_iters + 1 values, repeated after an early stop).  Returns 0 when the
 // loop ended normally, 5 when no trial step was accepted (stalled).
+int orc_repair_bfgs(const OrcParams* p, const double x0[6], double* V, int n_iters,
+                    double* merit_out, int* iters_done);
+
 int orc_repair(const OrcParams* p, const double x0[6], double* V, int n_iters, int mode,
                double delta, double* merit_out, int* iters_done) {
+    if (mode == 2) return orc_repair_bfgs(p, x0, V, n_iters, merit_out, iters_done);
     const int N = p->N_r, T = p->T;
     std::vector<double> g(2 * (size_t)T), Vt(2 * (size_t)T);
     int status = 0, it = 0;
@@ -553,6 +560,218 @@ int orc_repair(const OrcParams* p, const double x0[6], double* V, int n_iters, i
     for (int i = it; i <= n_iters; ++i) merit_out[i] = P;
     if (iters_done) *iters_done = it;
     return status;
+}
+
+// ---------------------------------------------------------------------------
+// BFGS (Sec. IV-B names it as the solver of Eq. 22, run for a fixed number of
+// iterations; the variant is reading c27).
+//
+// Inverse update of the n x n matrix H (row-major) from the step s and the
+// gradient change y, as defined:
+//   H <- (I - rho s y') H (I - rho y s') + rho s s',   rho = 1 / (y' s).
+// ---------------------------------------------------------------------------
+void orc_bfgs_update(int n, double* H, const double* s, const double* y) {
+    double ys = 0.0;
+    for (int i = 0; i < n; ++i) ys += y[i] * s[i];
+    const double rho = 1.0 / ys;
+    std::vector<double> A((size_t)n * n), AH((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i)                       // A = I - rho s y'
+        for (int j = 0; j < n; ++j) A[(size_t)i * n + j] = (i == j ? 1.0 : 0.0) - rho * s[i] * y[j];
+    for (int i = 0; i < n; ++i)                       // A H
+        for (int k = 0; k < n; ++k)
+            for (int j = 0; j < n; ++j) AH[(size_t)i * n + j] += A[(size_t)i * n + k] * H[(size_t)k * n + j];
+    for (int i = 0; i < n; ++i)                       // (A H) A' + rho s s'
+        for (int j = 0; j < n; ++j) {
+            double v = 0.0;
+            for (int k = 0; k < n; ++k) v += AH[(size_t)i * n + k] * A[(size_t)j * n + k];
+            H[(size_t)i * n + j] = v + rho * s[i] * s[j];
+        }
+}
+
+}  // extern "C"
+
+// Box-constrained BFGS with Armijo backtracking (reading c27), minimising f
+// over lo <= z <= hi from z for at most n_iters iterations:
+//   - H, the inverse-Hessian approximation, starts unset.  While it is unset
+//     the direction is the scaled gradient step of mode 1, d = -(s0/|g|_inf) g.
+//   - After an accepted step s = z' - z with y = g(z') - g(z): when
+//     s'y > 1e-5 |s| |y|, H is set to (s'y / y'y) I if it was unset and then
+//     takes the update of orc_bfgs_update; otherwise H is kept as it is.
+//   - Binding coordinates (at a bound with the gradient pushing outward:
+//     z_i = lo_i and g_i > 0, or z_i = hi_i and g_i < 0) keep d_i = 0.  With
+//     H set, the free coordinates take d_F = -H_FF g_F (H restricted to the
+//     free rows and columns); H is unset (and the gradient step taken) when
+//     g'd >= 0.
+//   - Line search: trials z(a) = clip(z + a d), a = 1, 1/2, 1/4, ...
+//     (ls_max trials); the first with dec = g'(z - z(a)) > 0 and
+//     f(z(a)) <= f(z) - c dec is accepted.  If none is and d came from H, H
+//     is unset and the search is repeated along the gradient step; if none is
+//     then, the iteration stops (stalled).
+//   - The loop stops early when f = 0 (for the repair: already safe).
+// merit_out gets f before each iteration and after the last one (n_iters + 1
+// values, repeated after an early stop).  Returns 0, or 5 when stalled.
+// F provides double value(const double* z) and void grad(const double* z, double* g).
+template <class F>
+static int bfgs_box(F& f, int n, const double* lo, const double* hi, double* z, int n_iters,
+                    double s0, double c, int ls_max, double* merit_out, int* iters_done) {
+    std::vector<double> g(n), gp(n), s(n), y(n), d(n), zt(n), H((size_t)n * n);
+    std::vector<char> fr(n);
+    bool H_set = false, have_step = false;
+    int status = 0, it = 0;
+    double fz = f.value(z);
+    double gmax = 0.0;
+    auto gradient_step = [&]() {
+        for (int i = 0; i < n; ++i) d[i] = fr[i] ? -(s0 / gmax) * g[i] : 0.0;
+    };
+    auto line_search = [&](double* f_new) {
+        double a = 1.0;
+        for (int j = 0; j < ls_max; ++j) {
+            double dec = 0.0;
+            for (int i = 0; i < n; ++i) {
+                zt[i] = std::fmin(std::fmax(z[i] + a * d[i], lo[i]), hi[i]);
+                dec += g[i] * (z[i] - zt[i]);
+            }
+            if (dec > 0.0) {
+                const double ft = f.value(zt.data());
+                if (ft <= fz - c * dec) {
+                    *f_new = ft;
+                    return true;
+                }
+            }
+            a *= 0.5;
+        }
+        return false;
+    };
+    for (; it < n_iters; ++it) {
+        merit_out[it] = fz;
+        if (fz == 0.0) break;
+        f.grad(z, g.data());
+        if (have_step) {
+            double sy = 0.0, yy = 0.0, ss = 0.0;
+            for (int i = 0; i < n; ++i) {
+                y[i] = g[i] - gp[i];
+                sy += s[i] * y[i];
+                yy += y[i] * y[i];
+                ss += s[i] * s[i];
+            }
+            if (sy > 1e-5 * std::sqrt(ss * yy)) {
+                if (!H_set) {
+                    for (size_t k = 0; k < H.size(); ++k) H[k] = 0.0;
+                    for (int i = 0; i < n; ++i) H[(size_t)i * n + i] = sy / yy;
+                    H_set = true;
+                }
+                orc_bfgs_update(n, H.data(), s.data(), y.data());
+            }
+        }
+        gmax = 0.0;
+        for (int i = 0; i < n; ++i) {
+            gmax = std::fmax(gmax, std::fabs(g[i]));
+            fr[i] = !((z[i] <= lo[i] && g[i] > 0.0) || (z[i] >= hi[i] && g[i] < 0.0));
+        }
+        if (gmax == 0.0) { status = 5; break; }
+        if (H_set) {
+            double gd = 0.0;
+            for (int i = 0; i < n; ++i) {
+                double v = 0.0;
+                if (fr[i])
+                    for (int j = 0; j < n; ++j)
+                        if (fr[j]) v += H[(size_t)i * n + j] * g[j];
+                d[i] = -v;
+                gd += g[i] * d[i];
+            }
+            if (!(gd < 0.0)) {
+                H_set = false;
+                gradient_step();
+            }
+        } else {
+            gradient_step();
+        }
+        double f_new = fz;
+        bool ok = line_search(&f_new);
+        if (!ok && H_set) {
+            H_set = false;
+            gradient_step();
+            ok = line_search(&f_new);
+        }
+        if (!ok) { status = 5; break; }
+        for (int i = 0; i < n; ++i) {
+            s[i] = zt[i] - z[i];
+            gp[i] = g[i];
+            z[i] = zt[i];
+        }
+        fz = f_new;
+        have_step = true;
+    }
+    for (int i = it; i <= n_iters; ++i) merit_out[i] = fz;
+    if (iters_done) *iters_done = it;
+    return status;
+}
+
+// The repair merit P as a function of the first 2 N_r controls (the rest of V
+// held fixed), with its gradient by dual numbers.
+struct RepairObjective {
+    const OrcParams* p;
+    const double* x0;
+    std::vector<double> V;
+    double value(const double* z) {
+        for (int i = 0; i < 2 * p->N_r; ++i) V[i] = z[i];
+        return orc_merit(p, x0, V.data());
+    }
+    void grad(const double* z, double* g) {
+        for (int i = 0; i < 2 * p->N_r; ++i) V[i] = z[i];
+        std::vector<double> gall(2 * (size_t)p->T);
+        orc_cost_grad(p, x0, V.data(), p->N_r, 0.0, 1.0, gall.data());
+        for (int i = 0; i < 2 * p->N_r; ++i) g[i] = gall[i];
+    }
+};
+
+// f(z) = 1/2 z'Az - b'z (A symmetric, row-major), for the checks of bfgs_box.
+struct QuadraticObjective {
+    int n;
+    const double* A;
+    const double* b;
+    double value(const double* z) {
+        double v = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double Az = 0.0;
+            for (int j = 0; j < n; ++j) Az += A[(size_t)i * n + j] * z[j];
+            v += 0.5 * z[i] * Az - b[i] * z[i];
+        }
+        return v;
+    }
+    void grad(const double* z, double* g) {
+        for (int i = 0; i < n; ++i) {
+            double Az = 0.0;
+            for (int j = 0; j < n; ++j) Az += A[(size_t)i * n + j] * z[j];
+            g[i] = Az - b[i];
+        }
+    }
+};
+
+extern "C" {
+
+// BFGS repair of V (mode 2 of orc_repair; reading c27).
+int orc_repair_bfgs(const OrcParams* p, const double x0[6], double* V, int n_iters,
+                    double* merit_out, int* iters_done) {
+    const int n = 2 * p->N_r;
+    RepairObjective f{p, x0, std::vector<double>(V, V + 2 * (size_t)p->T)};
+    std::vector<double> lo(n), hi(n), z(V, V + n);
+    for (int i = 0; i < n; ++i) {
+        lo[i] = p->u_min[i & 1];
+        hi[i] = p->u_max[i & 1];
+    }
+    const int st = bfgs_box(f, n, lo.data(), hi.data(), z.data(), n_iters, p->ls_s0, p->ls_c,
+                            p->ls_max_halvings, merit_out, iters_done);
+    for (int i = 0; i < n; ++i) V[i] = z[i];
+    return st;
+}
+
+// bfgs_box on the quadratic 1/2 z'Az - b'z (checks of the solver itself).
+int orc_bfgs_quadratic(int n, const double* A, const double* b, const double* lo,
+                       const double* hi, double* z, int n_iters, double s0, double c, int ls_max,
+                       double* merit_out, int* iters_done) {
+    QuadraticObjective f{n, A, b};
+    return bfgs_box(f, n, lo, hi, z, n_iters, s0, c, ls_max, merit_out, iters_done);
 }
 
 // Closed loop (Alg. 2, ExecuteCommand, on the disturbed system Eq. 26):

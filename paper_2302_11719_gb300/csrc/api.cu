@@ -33,6 +33,9 @@ struct smppi_handle {
     float* d_Vs = nullptr;
     double* d_merit = nullptr;
     int merit_cap = 0;
+    float* bfgs_H = nullptr;         // H slices of the BFGS repair (grown on first use)
+    size_t bfgs_H_bytes = 0;
+    int sms = 1;
     cudaGraphExec_t gexec = nullptr;
     std::string graph_key;
     std::string err;
@@ -144,7 +147,7 @@ void free_all(smppi_handle* h) {
                     h->status,
                     h->iter_dev,
                     h->rws.tape, h->rws.Vw, h->rws.G, h->rws.seg0, h->d_x0, h->d_V, h->d_Vs,
-                    h->d_merit};
+                    h->d_merit, h->bfgs_H};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (h->cap) cudaStreamDestroy(h->cap);
@@ -219,6 +222,29 @@ smppi_status enqueue_repair(smppi_handle* h, cudaStream_t st, int n_seq, const f
         ev = tic(h, st);
         CU(h, launch_seg0(h->dp, h->rec, n_seq, x0, h->rws.seg0, st));
         toc(h, st, SMPPI_KERNEL_SEG0, ev);
+    }
+    if (mode == 2) {
+        const int grid = bfgs_grid(h->dp, n_seq, h->sms);
+        if (grid < 1) return fail(h, SMPPI_ERR_CUDA, "BFGS repair: no launch shape fits");
+        const size_t need = bfgs_ws_bytes(h->dp, grid);
+        if (need > h->bfgs_H_bytes) {
+            if (h->bfgs_H) {
+                CU(h, cudaStreamSynchronize(st));
+                cudaFree(h->bfgs_H);
+                h->bfgs_H = nullptr;
+                h->bfgs_H_bytes = 0;
+            }
+            const cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&h->bfgs_H), need);
+            if (e != cudaSuccess)
+                return fail(h, e == cudaErrorMemoryAllocation ? SMPPI_ERR_NOMEM : SMPPI_ERR_CUDA,
+                            std::string("BFGS workspace: ") + cudaGetErrorString(e));
+            h->bfgs_H_bytes = need;
+        }
+        ev = tic(h, st);
+        CU(h, launch_repair_bfgs(h->dp, h->rec, n_seq, x0, V_in, V_out, n_iters, h->rws.ck,
+                                 h->bfgs_H, grid, merit_out, iters_out, ap, h->status, st));
+        toc(h, st, SMPPI_KERNEL_REPAIR, ev);
+        return SMPPI_OK;
     }
     ev = tic(h, st);
     CU(h, launch_repair(h->dp, h->rec, h->rws, n_seq, x0, V_in, V_out, n_iters, mode,
@@ -301,6 +327,12 @@ smppi_status smppi_create(const smppi_params* p, void* cuda_stream, smppi_handle
     h->st = static_cast<cudaStream_t>(cuda_stream);
     h->nblk = (p->K + ROLL_BLK - 1) / ROLL_BLK;
     const int T = p->T, ms = p->max_seq;
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev);
+        if (h->sms < 1) h->sms = 1;
+    }
     h->rws.max_seq = ms;
     h->rws.T = T;
     h->rws.ck = h->p.checkpoint;
@@ -442,7 +474,7 @@ smppi_status smppi_repair(smppi_handle* h, int n_seq, const float* x0, const flo
     if (s != SMPPI_OK) return s;
     if (!x0 || !V_in || !V_out) return fail(h, SMPPI_ERR_ARG, "x0, V_in, V_out must not be NULL");
     if (n_iters < 0 || n_iters > 100000) return fail(h, SMPPI_ERR_ARG, "n_iters must be in [0, 1e5]");
-    if (mode != 0 && mode != 1) return fail(h, SMPPI_ERR_ARG, "mode must be 0 or 1");
+    if (mode != 0 && mode != 1 && mode != 2) return fail(h, SMPPI_ERR_ARG, "mode must be 0, 1 or 2");
     if (mode == 0 && !(std::isfinite(delta) && delta >= 0)) return fail(h, SMPPI_ERR_ARG, "delta must be >= 0");
     const ApplyArgs none{nullptr, nullptr, 0u, 0u, nullptr};
     return enqueue_repair(h, h->st, n_seq, x0, V_in, V_out, n_iters, mode, delta, merit_out,

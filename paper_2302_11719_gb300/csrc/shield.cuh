@@ -54,7 +54,8 @@ __device__ __forceinline__ void add_direct(const DevParams& P, const float4* rec
 // Forward rollout of u_t = clamp(Vw_t - step G_t) for N steps from x0 (segment s0).
 // Returns J in float64 and, when STORE, fills the tape (every state when
 // ck <= 0, else every ck-th).  dec_out (optional) = sum_t G_t . (Vw_t - u'_t)
-// where u'_t = clip(Vw_t - step G_t) (the Armijo decrease term).  The terms are
+// where u'_t = clip(Vw_t - step Dn_t) (the Armijo decrease term), Dn = G when
+// no search direction is given (the gradient step).  The terms are
 // summed in float32 over blocks of 16 steps and the block sums in float64
 // (FP64 arithmetic is slow on this part; one FP64 add per 16 steps).
 //
@@ -65,7 +66,7 @@ template <bool STORE, bool TRIAL, bool FAST = false>
 __device__ double forward_cost(const DevParams& P, const float4* rec,
                                const State& x0, int s0, int N, const float2* Vw, const float2* G,
                                float step, int ms, int seq, float w_run, float w_cbf, int ck,
-                               const Tape& tape, double* dec_out) {
+                               const Tape& tape, double* dec_out, const float2* Dn = nullptr) {
     State x = x0;
     int s = s0;
     float d2 = rec_d2_seg(rec, s, x.X, x.Y);
@@ -80,7 +81,8 @@ __device__ double forward_cost(const DevParams& P, const float4* rec,
         const float2 v = Vw[(size_t)t * ms + seq];
         if (TRIAL) {
             const float2 g = G[(size_t)t * ms + seq];
-            const float2 u = clamp2(P, make_float2(fmaf(-step, g.x, v.x), fmaf(-step, g.y, v.y)));
+            const float2 dn = Dn ? Dn[(size_t)t * ms + seq] : g;
+            const float2 u = clamp2(P, make_float2(fmaf(-step, dn.x, v.x), fmaf(-step, dn.y, v.y)));
             decf = fmaf(g.x, v.x - u.x, fmaf(g.y, v.y - u.y, decf));
             return u;
         }

@@ -30,3 +30,39 @@ def update_bound(S, eps, omega_norm, Vplus, V, lam):
     tau = S_REL * (np.abs(S) + 1.0) / lam                     # (K,)
     B = np.einsum("k,k,ktj->tj", omega_norm, tau, np.abs(eps - dV[None]))
     return V_UPD + 2.0 * B
+
+
+def repair_compare(S, orc, params, track, x0s, Vs, n_iters, mode=1):
+    """GPU smppi_repair against the oracle's repair (same mode) on each start:
+    (flips, worst |V_safe - oracle| over the sequences without a flip).  A flip
+    is a sequence whose iteration count differs or whose controls differ by
+    more than V_REP: a line-search accept/reject decision that float32 and
+    float64 take differently.  Asserts monotone GPU merits and P(V) at the
+    start within S_REL."""
+    import pytest
+    import torch
+    n = x0s.shape[0]
+    ctl = S.Controller(params, track, max_seq=n)
+    Vout = torch.empty((n, ctl.T, 2), device="cuda")
+    mer = torch.empty((n, n_iters + 1), dtype=torch.float64, device="cuda")
+    its = torch.empty(n, dtype=torch.int32, device="cuda")
+    S.smppi_repair(ctl.h, n, ctl.tensor(x0s), ctl.tensor(Vs), Vout, n_iters, mode, 0.0, mer, its)
+    st, bits = ctl.sync_status()
+    assert st in (S.OK, S.ERR_STALLED), st
+    Vout, mer, its = Vout.cpu().numpy(), mer.cpu().numpy(), its.cpu().numpy()
+    m = orc.Model(params, track)
+    flips, worst = 0, 0.0
+    for i in range(n):
+        Vo, mo, so, io = orc.repair(m, x0s[i], Vs[i], n_iters, mode=mode)
+        assert np.all(np.diff(mer[i]) <= 1e-9 * (1 + mer[i][:-1]))     # monotone merit
+        assert mer[i][0] == pytest.approx(mo[0], rel=S_REL, abs=1e-2)
+        if io != its[i]:
+            flips += 1
+            continue
+        e = np.max(np.abs(Vout[i] - Vo))
+        if e > V_REP:
+            flips += 1       # same iteration count but a different accepted trial step
+            continue
+        worst = max(worst, e)
+    ctl.close()
+    return flips, worst

@@ -1,0 +1,90 @@
+"""GPU BFGS repair (smppi_repair mode 2: the solver Sec. IV-B names for
+Eq. 22, variant = reading c27) against the FP64 oracle's BFGS.
+
+  * the K = 256, T = 50 problem's repair starts (its V+ and sequences that
+    leave the track): repaired controls within V_REP of the oracle, no flip;
+  * near-boundary sequences (T = 100, more sequences than the persistent grid
+    has blocks, so blocks take several sequences and reuse their H slice):
+    controls within V_REP unless a line-search decision differs between
+    float32 and float64 (a flip, at most 1/8 of the sequences);
+  * one iteration from a gradient-step start equals the oracle's mode-1
+    iteration (the first BFGS step is the scaled gradient step);
+  * merits and iterations against the gradient repair are printed.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2302_11719_gb300 import inputs as I  # noqa: E402
+from tests.gpu_helpers import V_REP, repair_compare  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def S():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2302_11719_gb300 import smppi
+    return smppi
+
+
+def test_bfgs_small_problem(S, orc):
+    pr = I.single_step_small()
+    m = orc.Model(pr.params, pr.track)
+    _, Vp = orc.mppi_step(m, pr.x0, pr.V, nthreads=8)
+    starts = [Vp.astype(np.float32)]
+    for b in (0.0, -0.05, -0.1, 0.05):
+        starts.append(np.tile(np.array([[b, 0.5]], np.float32), (pr.T, 1)))
+    x0s = np.tile(pr.x0, (len(starts), 1))
+    flips, worst = repair_compare(S, orc, pr.params, pr.track, x0s, np.stack(starts), 10, mode=2)
+    print("K=256 T=50 BFGS repair (5 starts, 10 iterations): %d flips, max |V_safe err| %.2e"
+          % (flips, worst))
+    assert flips == 0 and worst <= V_REP, (flips, worst)
+
+
+def test_bfgs_one_iteration_is_gradient_step(S, orc):
+    sq = I.near_boundary_sequences(n_seq=32, T=60, seed=5)
+    m = orc.Model(sq.params, sq.track)
+    flips, worst = repair_compare(S, orc, sq.params, sq.track, sq.x0, sq.V, 1, mode=2)
+    assert flips <= 32 // 8 and worst <= V_REP, (flips, worst)
+    for q in range(8):   # the oracle's own identity, so the GPU is held to mode 1 as well
+        Va = orc.repair(m, sq.x0[q], sq.V[q], 1, mode=1)[0]
+        Vb = orc.repair(m, sq.x0[q], sq.V[q], 1, mode=2)[0]
+        assert np.array_equal(Va, Vb)
+
+
+def test_bfgs_near_boundary_batch(S, orc):
+    sq = I.near_boundary_sequences(n_seq=400, T=100, seed=2)
+    n = 400    # more than the resident blocks (two per SM): blocks loop over sequences
+    flips, worst = repair_compare(S, orc, sq.params, sq.track, sq.x0[:n], sq.V[:n], 10, mode=2)
+    print("near-boundary BFGS repair: %d flips of %d, worst |dV| %.2e" % (flips, n, worst))
+    assert worst <= V_REP
+    assert flips <= n // 8
+
+
+def test_bfgs_vs_gradient_repair(S):
+    sq = I.near_boundary_sequences(n_seq=1024, T=100, seed=3)
+    n = sq.x0.shape[0]
+    ctl = S.Controller(sq.params, sq.track, max_seq=n)
+    x0, V = ctl.tensor(sq.x0), ctl.tensor(sq.V)
+    out = {}
+    for mode in (1, 2):
+        Vout = torch.empty_like(V)
+        mer = torch.empty((n, 11), dtype=torch.float64, device="cuda")
+        its = torch.empty(n, dtype=torch.int32, device="cuda")
+        S.smppi_repair(ctl.h, n, x0, V, Vout, 10, mode, 0.0, mer, its)
+        st, _ = ctl.sync_status()
+        assert st in (S.OK, S.ERR_STALLED)
+        out[mode] = (mer.cpu().numpy(), its.cpu().numpy())
+    ctl.close()
+    for mode, (mer, its) in out.items():
+        print("mode %d: mean merit %.4g -> %.4g, safe after %d of %d, mean iterations %.2f"
+              % (mode, mer[:, 0].mean(), mer[:, -1].mean(), int((mer[:, -1] == 0).sum()), n,
+                 its.mean()))
+    m1, m2 = out[1][0], out[2][0]
+    # the start merit: three-warp merit pass (mode 1) and one thread's forward pass (mode 2)
+    print("start merit max rel difference %.2e"
+          % np.max(np.abs(m1[:, 0] - m2[:, 0]) / np.maximum(np.abs(m1[:, 0]), 1.0)))
+    assert np.allclose(m1[:, 0], m2[:, 0], rtol=1e-6, atol=1e-6)
+    assert np.all(m2[:, -1] <= m2[:, 0])

@@ -20,7 +20,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from paper_2302_11719_gb300 import inputs as I  # noqa: E402
-from tests.gpu_helpers import G_REL, S_REL, V_REP, X_REL, rel_err, update_bound  # noqa: E402
+from tests.gpu_helpers import (G_REL, S_REL, V_REP, X_REL, rel_err, repair_compare,  # noqa: E402
+                                update_bound)
 
 
 @pytest.fixture(scope="module")
@@ -110,34 +111,6 @@ def test_autograd_function(S, seqs):
     Jr, gr = gpu_cost_grad(S, ctl, seqs.x0[:n], seqs.V[:n], 100, 1.0, 1.0, 0)
     assert np.allclose(V.grad.cpu().numpy(), gr * w.cpu().numpy()[:, None, None], rtol=1e-6)
     ctl.close()
-
-
-def repair_compare(S, orc, params, track, x0s, Vs, n_iters):
-    n = x0s.shape[0]
-    ctl = S.Controller(params, track, max_seq=n)
-    Vout = torch.empty((n, ctl.T, 2), device="cuda")
-    mer = torch.empty((n, n_iters + 1), dtype=torch.float64, device="cuda")
-    its = torch.empty(n, dtype=torch.int32, device="cuda")
-    S.smppi_repair(ctl.h, n, ctl.tensor(x0s), ctl.tensor(Vs), Vout, n_iters, 1, 0.0, mer, its)
-    st, bits = ctl.sync_status()
-    assert st in (S.OK, S.ERR_STALLED), st
-    Vout, mer, its = Vout.cpu().numpy(), mer.cpu().numpy(), its.cpu().numpy()
-    m = orc.Model(params, track)
-    flips, worst = 0, 0.0
-    for i in range(n):
-        Vo, mo, so, io = orc.repair(m, x0s[i], Vs[i], n_iters)
-        assert np.all(np.diff(mer[i]) <= 1e-9 * (1 + mer[i][:-1]))     # monotone merit
-        assert mer[i][0] == pytest.approx(mo[0], rel=S_REL, abs=1e-2)
-        if io != its[i]:
-            flips += 1
-            continue
-        e = np.max(np.abs(Vout[i] - Vo))
-        if e > V_REP:
-            flips += 1       # same iteration count but a different accepted trial step
-            continue
-        worst = max(worst, e)
-    ctl.close()
-    return flips, worst
 
 
 def test_repair_small_problem(S, orc):
