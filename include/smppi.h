@@ -178,9 +178,10 @@ smppi_status smppi_cost_grad(smppi_handle* h, int n_seq, const float* x0, const 
  *           unset again when g'd >= 0).  Trials clip(V + a d), a = 1, 1/2, ...
  *           (ls_max_halvings), accepted when g'(V - V') > 0 and
  *           P' <= P - ls_c g'(V - V'); if none is and d came from H, the search
- *           is repeated along the gradient step.  One block per sequence; the
- *           first mode-2 call allocates the H workspace ((2 N_r)^2 floats per
- *           resident block, at most 256 MB).
+ *           is repeated along the gradient step.  One warp per sequence; a
+ *           mode-2 call that needs more workspace than the handle holds
+ *           allocates it (a work counter and (2 N_r)^2 floats per resident
+ *           warp, about 256 MB at most).
  *   x0 [n_seq x 6]; V_in, V_out [n_seq x T x 2] (may alias);
  *   merit_out [n_seq x (n_iters + 1)] optional (float64): P before each
  *   iteration and after the last, repeated after an early stop;

@@ -33,8 +33,8 @@ struct smppi_handle {
     float* d_Vs = nullptr;
     double* d_merit = nullptr;
     int merit_cap = 0;
-    float* bfgs_H = nullptr;         // H slices of the BFGS repair (grown on first use)
-    size_t bfgs_H_bytes = 0;
+    void* bfgs_ws = nullptr;         // BFGS repair workspace: counter + H slices (grown on use)
+    size_t bfgs_ws_bytes = 0;
     int sms = 1;
     cudaGraphExec_t gexec = nullptr;
     std::string graph_key;
@@ -147,7 +147,7 @@ void free_all(smppi_handle* h) {
                     h->status,
                     h->iter_dev,
                     h->rws.tape, h->rws.Vw, h->rws.G, h->rws.seg0, h->d_x0, h->d_V, h->d_Vs,
-                    h->d_merit, h->bfgs_H};
+                    h->d_merit, h->bfgs_ws};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (h->cap) cudaStreamDestroy(h->cap);
@@ -224,25 +224,26 @@ smppi_status enqueue_repair(smppi_handle* h, cudaStream_t st, int n_seq, const f
         toc(h, st, SMPPI_KERNEL_SEG0, ev);
     }
     if (mode == 2) {
-        const int grid = bfgs_grid(h->dp, n_seq, h->sms);
+        int wpb = 0;
+        const int grid = bfgs_grid(h->dp, n_seq, h->sms, &wpb);
         if (grid < 1) return fail(h, SMPPI_ERR_CUDA, "BFGS repair: no launch shape fits");
-        const size_t need = bfgs_ws_bytes(h->dp, grid);
-        if (need > h->bfgs_H_bytes) {
-            if (h->bfgs_H) {
+        const size_t need = bfgs_ws_bytes(h->dp, grid, wpb);
+        if (need > h->bfgs_ws_bytes) {
+            if (h->bfgs_ws) {
                 CU(h, cudaStreamSynchronize(st));
-                cudaFree(h->bfgs_H);
-                h->bfgs_H = nullptr;
-                h->bfgs_H_bytes = 0;
+                cudaFree(h->bfgs_ws);
+                h->bfgs_ws = nullptr;
+                h->bfgs_ws_bytes = 0;
             }
-            const cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&h->bfgs_H), need);
+            const cudaError_t e = cudaMalloc(&h->bfgs_ws, need);
             if (e != cudaSuccess)
                 return fail(h, e == cudaErrorMemoryAllocation ? SMPPI_ERR_NOMEM : SMPPI_ERR_CUDA,
                             std::string("BFGS workspace: ") + cudaGetErrorString(e));
-            h->bfgs_H_bytes = need;
+            h->bfgs_ws_bytes = need;
         }
         ev = tic(h, st);
         CU(h, launch_repair_bfgs(h->dp, h->rec, n_seq, x0, V_in, V_out, n_iters, h->rws.ck,
-                                 h->bfgs_H, grid, merit_out, iters_out, ap, h->status, st));
+                                 h->bfgs_ws, grid, wpb, merit_out, iters_out, ap, h->status, st));
         toc(h, st, SMPPI_KERNEL_REPAIR, ev);
         return SMPPI_OK;
     }

@@ -3,249 +3,246 @@
 // projected path, binding coordinates held, gradient-step restarts) is stated
 // with smppi_repair's mode 2 in smppi.h.
 //
-// One block per sequence on a persistent grid.  The n x n inverse-Hessian
-// approximation H (n = 2 N_r controls) of the sequence a block works on lives
-// in that block's slice of a global workspace, small enough to stay in L2;
-// the O(n^2) parts (H y, H_FF g_F, the rank-two update) are spread over the
-// block, one warp per row for the products so that the row reads coalesce.
-// Thread 0 computes the adjoint gradient (seq_cost_grad); the lanes of warp 0
-// evaluate the line-search trials a = 1, 1/2, ... in parallel and the largest
-// accepted a is taken, the same iterate as sequential backtracking.
+// One WARP per sequence: lane 0 computes the adjoint gradient (seq_cost_grad,
+// a serial chain), the lanes evaluate the line-search trials a = 1, 1/2, ...
+// in parallel (the largest accepted a is taken: the same iterate as
+// sequential backtracking), and the O(n^2) parts (H y, H_FF g_F, the rank-two
+// update, n = 2 N_r) are spread over the lanes.  A block holds a few warps
+// that share the staged track table; warps take sequences from an atomic
+// counter, so the sequences that need many iterations do not hold up a fixed
+// share of the others.
+//
+// H of the sequence a warp works on lives in that warp's slice of a global
+// workspace, small enough to stay in L2.  The update is evaluated in a form
+// that is symmetric in (i, j) operation by operation (no fused multiply-add),
+// so H stays exactly symmetric; products with H then read it by columns,
+// H[j][i] = H[i][j], so that the lanes' loads of one j coalesce.
 #include <algorithm>
 
 #include "shield.cuh"
 
 namespace smppi {
 
-constexpr int BFGS_BLK = 256;
-constexpr size_t BFGS_WS_MAX = size_t(256) << 20;   // bytes of H slices at most
+constexpr int BFGS_WPB_MAX = 4;                      // warps (sequences) per block
+constexpr size_t BFGS_WS_MAX = size_t(256) << 20;    // bytes of H slices at most
+constexpr int BFGS_ROWS = 8;                         // rows per lane per pass of a product
 
 namespace {
 
-constexpr int BNW = BFGS_BLK / 32;
+constexpr unsigned FULL = 0xffffffffu;
 
-struct BfgsSmem {
-    double P;               // merit of the iterate the block agrees on
-    double red[BNW][3];     // block sums
-    float redf[BNW];        // block maxima
-    float step;             // accepted trial step a
-    int ok;                 // a trial was accepted
-};
-
-// Sums of a, b, c over the block (the same value, in the same order, on every thread).
-__device__ __forceinline__ void block_sum3(double& a, double& b, double& c, BfgsSmem& sm) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-        c += __shfl_xor_sync(0xffffffffu, c, o);
-    }
-    if (lane == 0) {
-        sm.red[warp][0] = a;
-        sm.red[warp][1] = b;
-        sm.red[warp][2] = c;
-    }
-    __syncthreads();
-    a = b = c = 0.0;
-#pragma unroll
-    for (int w = 0; w < BNW; ++w) {
-        a += sm.red[w][0];
-        b += sm.red[w][1];
-        c += sm.red[w][2];
-    }
-    __syncthreads();
-}
-
-__device__ __forceinline__ float block_max(float v, BfgsSmem& sm) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (lane == 0) sm.redf[warp] = v;
-    __syncthreads();
-    v = sm.redf[0];
-#pragma unroll
-    for (int w = 1; w < BNW; ++w) v = fmaxf(v, sm.redf[w]);
-    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     return v;
 }
 
-// out_i = sum_{j} M_ij x_j over the rows i < n (row-major n x n), one warp per
-// row; with mask, only rows and columns whose flag is set (others give 0).
-__device__ __forceinline__ void block_matvec(const float* __restrict__ M, const float* x, int n,
-                                             const unsigned char* mask, float* out) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = warp; i < n; i += BNW) {
-        float a = 0.0f;
-        if (!mask || mask[i]) {
-            const float* row = M + (size_t)i * n;
-            for (int j = lane; j < n; j += 32)
-                if (!mask || mask[j]) a = fmaf(row[j], x[j], a);
+// out_i = sum_j H_ji x_j (= (H x)_i, H symmetric) for i < n, lanes over i;
+// with mask, only the flagged rows and columns (other rows give 0).
+__device__ __forceinline__ void warp_symv(const float* __restrict__ H, const float* x, int n,
+                                          const unsigned char* mask, float* out) {
+    const int lane = threadIdx.x & 31;
+    for (int i0 = lane; i0 < n; i0 += 32 * BFGS_ROWS) {
+        float acc[BFGS_ROWS];
+#pragma unroll
+        for (int r = 0; r < BFGS_ROWS; ++r) acc[r] = 0.0f;
+        for (int j = 0; j < n; ++j) {
+            if (mask && !mask[j]) continue;          // the same j on every lane
+            const float xj = x[j];
+            const float* col = H + (size_t)j * n;
+#pragma unroll
+            for (int r = 0; r < BFGS_ROWS; ++r) {
+                const int i = i0 + 32 * r;
+                if (i < n) acc[r] = fmaf(col[i], xj, acc[r]);
+            }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if (lane == 0) out[i] = a;
+        for (int r = 0; r < BFGS_ROWS; ++r) {
+            const int i = i0 + 32 * r;
+            if (i < n) out[i] = (mask && !mask[i]) ? 0.0f : acc[r];
+        }
     }
-    __syncthreads();
+    __syncwarp();
 }
 
 }  // namespace
 
+// Bytes of one warp's shared-memory region for horizon T (a multiple of 8, so
+// every warp's float2 arrays stay aligned): five float2 arrays of T, two float
+// arrays of 2T, 2T flag bytes and the tape, the last two padded to 16 bytes.
+__host__ __device__ inline size_t bfgs_warp_bytes(int T) {
+    const size_t t = (size_t)T;
+    return 5 * t * 8 + 2 * t * 8 + ((2 * t + 15) & ~size_t(15)) +
+           ((((t + 2) * NFIELD * 4) + 15) & ~size_t(15));
+}
+
 template <bool FAST>
-__global__ void __launch_bounds__(BFGS_BLK) repair_bfgs_kernel(
+__global__ void __launch_bounds__(32 * BFGS_WPB_MAX) repair_bfgs_kernel(
     DevParams P, const float4* __restrict__ recg, const float* __restrict__ x0g, const float* Vin,
     float* Vout, int n_seq, int n_iters, int ck, float* __restrict__ Hws,
-    double* __restrict__ merit_out, int* __restrict__ iters_out, ApplyArgs ap,
-    unsigned* __restrict__ status) {
+    unsigned* __restrict__ next, double* __restrict__ merit_out, int* __restrict__ iters_out,
+    ApplyArgs ap, unsigned* __restrict__ status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int T = P.T, N = P.N_r, nt = P.n_track, n = 2 * N;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     float4* rec = reinterpret_cast<float4*>(smem_raw);
-    float2* Vw = reinterpret_cast<float2*>(rec + 3 * (nt + 5));   // iterate z (first N)
-    float2* G = Vw + T;                                              // gradient at z
-    float2* Gp = G + T;                                              // gradient at the previous z
-    float2* Sv = Gp + T;                                             // last step s = z' - z
-    float2* Dn = Sv + T;                                             // negated direction
-    float* Yv = reinterpret_cast<float*>(Dn + T);                    // y = g - g_prev (n)
-    float* Hy = Yv + 2 * T;                                          // H y (n)
+    unsigned char* wbase = smem_raw + rec_table_bytes(nt) + (size_t)warp * bfgs_warp_bytes(T);
+    float2* Vw = reinterpret_cast<float2*>(wbase);   // iterate z (first N)
+    float2* G = Vw + T;                              // gradient at z
+    float2* Gp = G + T;                              // gradient at the previous z
+    float2* Sv = Gp + T;                             // last step s = z' - z
+    float2* Dn = Sv + T;                             // negated direction
+    float* Yv = reinterpret_cast<float*>(Dn + T);    // y = g - g_prev (n)
+    float* Hy = Yv + 2 * T;                          // H y (n)
     unsigned char* fr = reinterpret_cast<unsigned char*>(Hy + 2 * T);   // free coordinate flags
     float* tape_s = reinterpret_cast<float*>(fr + ((2 * T + 15) & ~15));
-    __shared__ BfgsSmem sm;
-    __shared__ float s_red[BNW];
-    __shared__ int s_redi[BNW];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const Tape tape{tape_s, 1, 0};
-    float* H = Hws + (size_t)blockIdx.x * n * n;
+    float* H = Hws + ((size_t)blockIdx.x * wpb + warp) * n * n;
     const float* zf = reinterpret_cast<const float*>(Vw);
     const float* gf = reinterpret_cast<const float*>(G);
     const float* gpf = reinterpret_cast<const float*>(Gp);
     const float* sf = reinterpret_cast<const float*>(Sv);
     float* dnf = reinterpret_cast<float*>(Dn);
 
-    for (int i = tid; i < 3 * (nt + 5); i += BFGS_BLK) rec[i] = recg[i];
+    for (int i = threadIdx.x; i < 3 * (nt + 5); i += blockDim.x) rec[i] = recg[i];
     __syncthreads();
 
-    for (int q = blockIdx.x; q < n_seq; q += gridDim.x) {
+    for (;;) {
+        int q = 0;
+        if (lane == 0) q = (int)atomicAdd(next, 1u);
+        q = __shfl_sync(FULL, q, 0);
+        if (q >= n_seq) break;
         const float2* vin = reinterpret_cast<const float2*>(Vin) + (size_t)q * T;
-        for (int t = tid; t < T; t += BFGS_BLK) Vw[t] = vin[t];
+        for (int t = lane; t < T; t += 32) Vw[t] = vin[t];
         const State x0 = make_state(x0g + 6 * q);
-        __syncthreads();
-        const int s0 = block_nearest_segment<BFGS_BLK>(rec, nt, x0.X, x0.Y, s_red, s_redi, nullptr);
+        // global nearest segment of x0 (lowest index on ties)
+        float bd = 3.0e38f;
+        int s0 = 0x7fffffff;
+        for (int i = lane; i < nt; i += 32) {
+            const float d = rec_d2_seg(rec, i, x0.X, x0.Y);
+            if (d < bd) { bd = d; s0 = i; }
+        }
+        warp_argmin(bd, s0);
+        __syncwarp();
         double* mrow = merit_out ? merit_out + (size_t)q * (n_iters + 1) : nullptr;
-        if (tid == 0)
-            sm.P = forward_cost<false, false, FAST>(P, rec, x0, s0, N, Vw, nullptr, 0.0f, 1, 0, 0.0f,
-                                                    1.0f, 0, tape, nullptr);
-        __syncthreads();
-        double P0 = sm.P;
+        double P0 = 0.0;
+        if (lane == 0)
+            P0 = forward_cost<false, false, FAST>(P, rec, x0, s0, N, Vw, nullptr, 0.0f, 1, 0, 0.0f,
+                                                  1.0f, 0, tape, nullptr);
+        P0 = __shfl_sync(FULL, P0, 0);
         bool H_set = false, have_step = false, stalled = false;
         int it = 0;
         for (; it < n_iters; ++it) {
-            if (tid == 0 && mrow) mrow[it] = P0;
+            if (lane == 0 && mrow) mrow[it] = P0;
             if (P0 == 0.0) break;
-            if (tid == 0) seq_cost_grad<FAST>(P, rec, x0, s0, N, T, Vw, G, 1, 0, 0.0f, 1.0f, ck, tape);
-            __syncthreads();
+            if (lane == 0) seq_cost_grad<FAST>(P, rec, x0, s0, N, T, Vw, G, 1, 0, 0.0f, 1.0f, ck, tape);
+            __syncwarp();
             // curvature pair of the last accepted step and the inverse update
             //   H <- (I - rho s y') H (I - rho y s') + rho s s'
             //      = H - rho (s (Hy)' + (Hy) s') + (rho^2 y'Hy + rho) s s'   (H symmetric)
             if (have_step) {
                 double sy = 0.0, yy = 0.0, ss = 0.0;
-                for (int i = tid; i < n; i += BFGS_BLK) {
+                for (int i = lane; i < n; i += 32) {
                     const float y = gf[i] - gpf[i];
                     Yv[i] = y;
                     sy += (double)sf[i] * y;
                     yy += (double)y * y;
                     ss += (double)sf[i] * sf[i];
                 }
-                block_sum3(sy, yy, ss, sm);
+                sy = warp_sum(sy);
+                yy = warp_sum(yy);
+                ss = warp_sum(ss);
+                __syncwarp();
                 if (sy > 1e-5 * sqrt(ss * yy)) {
                     if (!H_set) {
                         const float h0 = (float)(sy / yy);
-                        for (int k = tid; k < n * n; k += BFGS_BLK) H[k] = (k % (n + 1) == 0) ? h0 : 0.0f;
-                        __syncthreads();
+                        for (int k = lane; k < n * n; k += 32) H[k] = (k % (n + 1) == 0) ? h0 : 0.0f;
+                        __syncwarp();
                         H_set = true;
                     }
-                    block_matvec(H, Yv, n, nullptr, Hy);
-                    double yHy = 0.0, d1 = 0.0, d2 = 0.0;
-                    for (int i = tid; i < n; i += BFGS_BLK) yHy += (double)Yv[i] * Hy[i];
-                    block_sum3(yHy, d1, d2, sm);
+                    warp_symv(H, Yv, n, nullptr, Hy);
+                    double yHy = 0.0;
+                    for (int i = lane; i < n; i += 32) yHy += (double)Yv[i] * Hy[i];
+                    yHy = warp_sum(yHy);
                     const float rho = (float)(1.0 / sy);
                     const float cs = (float)(yHy / (sy * sy) + 1.0 / sy);
-                    for (int k = tid; k < n * n; k += BFGS_BLK) {
+                    for (int k = lane; k < n * n; k += 32) {
                         const int i = k / n, j = k - i * n;
                         const float si = sf[i], sj = sf[j];
-                        H[k] = fmaf(cs * si, sj, fmaf(-rho, fmaf(si, Hy[j], Hy[i] * sj), H[k]));
+                        const float cross = __fadd_rn(__fmul_rn(si, Hy[j]), __fmul_rn(sj, Hy[i]));
+                        const float delta = __fsub_rn(__fmul_rn(cs, __fmul_rn(si, sj)), __fmul_rn(rho, cross));
+                        H[k] = __fadd_rn(H[k], delta);
                     }
-                    __syncthreads();
+                    __syncwarp();
                 }
             }
             // |g|_inf and the binding coordinates (at a bound, gradient pushing outward)
             float gm = 0.0f;
-            for (int i = tid; i < n; i += BFGS_BLK) {
+            for (int i = lane; i < n; i += 32) {
                 const float g = gf[i], z = zf[i];
                 const float lo = (i & 1) ? P.umin1 : P.umin0, hi = (i & 1) ? P.umax1 : P.umax0;
                 fr[i] = !((z <= lo && g > 0.0f) || (z >= hi && g < 0.0f));
                 gm = fmaxf(gm, fabsf(g));
             }
-            gm = block_max(gm, sm);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) gm = fmaxf(gm, __shfl_xor_sync(FULL, gm, o));
+            __syncwarp();
             if (!(gm > 0.0f)) { stalled = true; break; }
             const float s_first = P.ls_s0 / gm;
             // direction (negated): Dn = H_FF g_F, or the scaled gradient step
             if (H_set) {
-                block_matvec(H, gf, n, fr, dnf);
-                double gHg = 0.0, d1 = 0.0, d2 = 0.0;
-                for (int i = tid; i < n; i += BFGS_BLK) gHg += (double)gf[i] * dnf[i];
-                block_sum3(gHg, d1, d2, sm);
+                warp_symv(H, gf, n, fr, dnf);
+                double gHg = 0.0;
+                for (int i = lane; i < n; i += 32) gHg += (double)gf[i] * dnf[i];
+                gHg = warp_sum(gHg);
                 if (!(gHg > 0.0)) H_set = false;      // g'd = -g'Dn >= 0: not a descent direction
             }
             if (!H_set) {
-                for (int i = tid; i < n; i += BFGS_BLK) dnf[i] = fr[i] ? s_first * gf[i] : 0.0f;
-                __syncthreads();
+                for (int i = lane; i < n; i += 32) dnf[i] = fr[i] ? s_first * gf[i] : 0.0f;
+                __syncwarp();
             }
-            // Armijo on the projected path (trials in parallel on warp 0); if the
+            // Armijo on the projected path (trials in parallel on the lanes); if the
             // direction came from H and nothing is accepted, once more along the
             // gradient step
+            int bj = 0x7fffffff;
+            double best_P = 0.0;
             for (int pass = 0; pass < 2; ++pass) {
-                if (warp == 0) {
-                    int best = 0x7fffffff;
-                    double best_P = 0.0;
-                    for (int j = lane; j < P.ls_max; j += 32) {
-                        const float a = ldexpf(1.0f, -j);
-                        double dec;
-                        const double Pt = forward_cost<false, true, FAST>(
-                            P, rec, x0, s0, N, Vw, G, a, 1, 0, 0.0f, 1.0f, 0, tape, &dec, Dn);
-                        if (dec > 0.0 && Pt <= P0 - (double)P.ls_c * dec && j < best) {
-                            best = j;
-                            best_P = Pt;
-                        }
+                int best = 0x7fffffff;
+                double bp = 0.0;
+                for (int j = lane; j < P.ls_max; j += 32) {
+                    const float a = ldexpf(1.0f, -j);
+                    double dec;
+                    const double Pt = forward_cost<false, true, FAST>(P, rec, x0, s0, N, Vw, G, a, 1, 0,
+                                                                      0.0f, 1.0f, 0, tape, &dec, Dn);
+                    if (dec > 0.0 && Pt <= P0 - (double)P.ls_c * dec && j < best) {
+                        best = j;
+                        bp = Pt;
                     }
-                    int bj = best;
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) bj = min(bj, __shfl_xor_sync(0xffffffffu, bj, o));
-                    if (best == bj && bj != 0x7fffffff) {
-                        sm.P = best_P;
-                        sm.step = ldexpf(1.0f, -bj);
-                    }
-                    if (lane == 0) sm.ok = (bj != 0x7fffffff);
                 }
-                __syncthreads();
-                if (sm.ok || !H_set) break;
+                bj = best;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) bj = min(bj, __shfl_xor_sync(FULL, bj, o));
+                // the lane that owns trial bj (j = lane + 32 m) holds its merit
+                best_P = __shfl_sync(FULL, bp, (bj == 0x7fffffff) ? 0 : (bj & 31));
+                if (bj != 0x7fffffff || !H_set) break;
                 H_set = false;
-                for (int i = tid; i < n; i += BFGS_BLK) dnf[i] = fr[i] ? s_first * gf[i] : 0.0f;
-                __syncthreads();
+                for (int i = lane; i < n; i += 32) dnf[i] = fr[i] ? s_first * gf[i] : 0.0f;
+                __syncwarp();
             }
-            if (!sm.ok) { stalled = true; break; }
-            const float a = sm.step;
-            for (int t = tid; t < N; t += BFGS_BLK) {
+            if (bj == 0x7fffffff) { stalled = true; break; }
+            const float a = ldexpf(1.0f, -bj);
+            for (int t = lane; t < N; t += 32) {
                 const float2 v = Vw[t], dn = Dn[t];
                 const float2 u = clamp2(P, make_float2(fmaf(-a, dn.x, v.x), fmaf(-a, dn.y, v.y)));
                 Sv[t] = make_float2(u.x - v.x, u.y - v.y);
                 Gp[t] = G[t];
                 Vw[t] = u;
             }
-            __syncthreads();
-            P0 = sm.P;
+            __syncwarp();
+            P0 = best_P;
             have_step = true;
         }
-        if (tid == 0) {
+        if (lane == 0) {
             if (mrow)
                 for (int i = it; i <= n_iters; ++i) mrow[i] = P0;
             if (iters_out) iters_out[q] = it;
@@ -253,50 +250,77 @@ __global__ void __launch_bounds__(BFGS_BLK) repair_bfgs_kernel(
             if (!isfinite(P0)) atomicOr(status, SMPPI_DEV_NUMERIC);
         }
         float2* vout = reinterpret_cast<float2*>(Vout) + (size_t)q * T;
-        for (int t = tid; t < T; t += BFGS_BLK) vout[t] = Vw[t];
-        if (q == 0 && tid == 0 && ap.x0) closed_loop_step(P, ap, Vw[0]);
-        __syncthreads();   // shared memory is reused by the next sequence
+        for (int t = lane; t < T; t += 32) vout[t] = Vw[t];
+        if (q == 0 && lane == 0 && ap.x0) closed_loop_step(P, ap, Vw[0]);
+        __syncwarp();   // the warp's shared memory is reused by its next sequence
     }
 }
 
-size_t bfgs_smem_bytes(const DevParams& P) {
-    const size_t T = (size_t)P.T;
-    return rec_table_bytes(P.n_track) + 5 * T * 8 + 2 * T * 8 + ((2 * T + 15) & ~size_t(15)) +
-           (T + 2) * NFIELD * 4;
+namespace {
+
+const void* bfgs_kernel(const DevParams& P) {
+    return (P.tyre15 && P.steer_small) ? (const void*)repair_bfgs_kernel<true>
+                                       : (const void*)repair_bfgs_kernel<false>;
 }
 
-// Blocks of the persistent grid: resident blocks, at most n_seq, and few
-// enough that their H slices fit in BFGS_WS_MAX.
-int bfgs_grid(const DevParams& P, int n_seq, int sms) {
-    const bool fast = P.tyre15 && P.steer_small;
-    const void* kern = fast ? (const void*)repair_bfgs_kernel<true> : (const void*)repair_bfgs_kernel<false>;
-    const size_t smem = bfgs_smem_bytes(P);
+// Warps per block: as many as fit next to the track table (at most BFGS_WPB_MAX).
+int bfgs_wpb(const DevParams& P) {
+    int dev = 0, max_optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t track = rec_table_bytes(P.n_track), per = bfgs_warp_bytes(P.T);
+    if ((size_t)max_optin < track + per) return 0;
+    return (int)std::min<size_t>(BFGS_WPB_MAX, ((size_t)max_optin - track) / per);
+}
+
+}  // namespace
+
+// Launch shape of the BFGS repair: blocks of `wpb` warps, as many blocks as
+// are resident, no more warps than sequences, and few enough warp slots that
+// their H slices fit in BFGS_WS_MAX.  Returns the block count (0: no fit).
+int bfgs_grid(const DevParams& P, int n_seq, int sms, int* wpb_out) {
+    const int wpb = bfgs_wpb(P);
+    if (wpb < 1) return 0;
+    const size_t smem = rec_table_bytes(P.n_track) + (size_t)wpb * bfgs_warp_bytes(P.T);
+    const void* kern = bfgs_kernel(P);
     if (ensure_smem(kern, smem) != cudaSuccess) return 0;
     int bps = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, BFGS_BLK, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, 32 * wpb, smem) != cudaSuccess)
         return 0;
     const size_t n = 2 * (size_t)P.N_r;
     const size_t per = std::max<size_t>(1, n * n * sizeof(float));
-    const int by_ws = (int)std::max<size_t>(1, BFGS_WS_MAX / per);
-    return std::max(1, std::min({n_seq, std::max(1, bps) * sms, by_ws}));
+    const int by_ws = (int)std::max<size_t>(1, BFGS_WS_MAX / per / wpb);
+    const int by_seq = (n_seq + wpb - 1) / wpb;
+    if (wpb_out) *wpb_out = wpb;
+    return std::max(1, std::min({by_seq, std::max(1, bps) * sms, by_ws}));
 }
 
-size_t bfgs_ws_bytes(const DevParams& P, int grid) {
+// Workspace: a 16-byte work counter, then one H slice per warp slot.
+size_t bfgs_ws_bytes(const DevParams& P, int grid, int wpb) {
     const size_t n = 2 * (size_t)P.N_r;
-    return std::max<size_t>(16, (size_t)grid * n * n * sizeof(float));
+    return 16 + (size_t)grid * wpb * n * n * sizeof(float);
 }
 
 cudaError_t launch_repair_bfgs(const DevParams& P, const float4* rec, int n_seq, const float* x0,
-                               const float* V_in, float* V_out, int n_iters, int ck, float* H_ws,
-                               int grid, double* merit_out, int* iters_out, const ApplyArgs& ap,
-                               unsigned* status, cudaStream_t st) {
-    const bool fast = P.tyre15 && P.steer_small;
-    auto kern = fast ? repair_bfgs_kernel<true> : repair_bfgs_kernel<false>;
-    const size_t smem = bfgs_smem_bytes(P);
-    cudaError_t e = ensure_smem((const void*)kern, smem);
+                               const float* V_in, float* V_out, int n_iters, int ck, void* ws,
+                               int grid, int wpb, double* merit_out, int* iters_out,
+                               const ApplyArgs& ap, unsigned* status, cudaStream_t st) {
+    const size_t smem = rec_table_bytes(P.n_track) + (size_t)wpb * bfgs_warp_bytes(P.T);
+    const void* kern = bfgs_kernel(P);
+    cudaError_t e = ensure_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid, BFGS_BLK, smem, st>>>(P, rec, x0, V_in, V_out, n_seq, n_iters, ck, H_ws, merit_out,
-                                        iters_out, ap, status);
+    unsigned* next = static_cast<unsigned*>(ws);
+    float* H = reinterpret_cast<float*>(static_cast<unsigned char*>(ws) + 16);
+    e = cudaMemsetAsync(next, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    if (P.tyre15 && P.steer_small)
+        repair_bfgs_kernel<true><<<grid, 32 * wpb, smem, st>>>(P, rec, x0, V_in, V_out, n_seq, n_iters,
+                                                                ck, H, next, merit_out, iters_out, ap,
+                                                                status);
+    else
+        repair_bfgs_kernel<false><<<grid, 32 * wpb, smem, st>>>(P, rec, x0, V_in, V_out, n_seq, n_iters,
+                                                                 ck, H, next, merit_out, iters_out, ap,
+                                                                 status);
     return cudaGetLastError();
 }
 

@@ -90,14 +90,15 @@ cudaError_t launch_repair(const DevParams& P, const float4* rec,
 cudaError_t launch_apply(const DevParams& P, const ApplyArgs& ap, const float* V_exec,
                          cudaStream_t st);
 
-// BFGS repair (bfgs.cu): persistent grid of bfgs_grid() blocks, each with an
-// H slice of (2 N_r)^2 floats in H_ws (bfgs_ws_bytes() in all).
-int bfgs_grid(const DevParams& P, int n_seq, int sms);
-size_t bfgs_ws_bytes(const DevParams& P, int grid);
+// BFGS repair (bfgs.cu): bfgs_grid() blocks of *wpb warps, one sequence per
+// warp at a time; the workspace (bfgs_ws_bytes()) holds a work counter and an
+// H slice of (2 N_r)^2 floats per warp slot.
+int bfgs_grid(const DevParams& P, int n_seq, int sms, int* wpb);
+size_t bfgs_ws_bytes(const DevParams& P, int grid, int wpb);
 cudaError_t launch_repair_bfgs(const DevParams& P, const float4* rec, int n_seq, const float* x0,
-                               const float* V_in, float* V_out, int n_iters, int ck, float* H_ws,
-                               int grid, double* merit_out, int* iters_out, const ApplyArgs& ap,
-                               unsigned* status, cudaStream_t st);
+                               const float* V_in, float* V_out, int n_iters, int ck, void* ws,
+                               int grid, int wpb, double* merit_out, int* iters_out,
+                               const ApplyArgs& ap, unsigned* status, cudaStream_t st);
 
 // Host helpers of the C ABI for entry points that have no handle: check a
 // parameter struct, derive the kernel constants, record the message that

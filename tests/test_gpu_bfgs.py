@@ -3,10 +3,12 @@ Eq. 22, variant = reading c27) against the FP64 oracle's BFGS.
 
   * the K = 256, T = 50 problem's repair starts (its V+ and sequences that
     leave the track): repaired controls within V_REP of the oracle, no flip;
-  * near-boundary sequences (T = 100, more sequences than the persistent grid
-    has blocks, so blocks take several sequences and reuse their H slice):
-    controls within V_REP unless a line-search decision differs between
-    float32 and float64 (a flip, at most 1/8 of the sequences);
+  * near-boundary sequences (T = 100): controls within V_REP unless a
+    line-search decision differs between float32 and float64 (a flip, at most
+    1/8 of the sequences);
+  * a batch larger than the resident warps (so warps take several sequences
+    and reuse their H slice) gives bit-identical results for the sequences it
+    shares with a small batch;
   * one iteration from a gradient-step start equals the oracle's mode-1
     iteration (the first BFGS step is the scaled gradient step);
   * merits and iterations against the gradient repair are printed.
@@ -56,11 +58,32 @@ def test_bfgs_one_iteration_is_gradient_step(S, orc):
 
 def test_bfgs_near_boundary_batch(S, orc):
     sq = I.near_boundary_sequences(n_seq=400, T=100, seed=2)
-    n = 400    # more than the resident blocks (two per SM): blocks loop over sequences
+    n = 400
     flips, worst = repair_compare(S, orc, sq.params, sq.track, sq.x0[:n], sq.V[:n], 10, mode=2)
     print("near-boundary BFGS repair: %d flips of %d, worst |dV| %.2e" % (flips, n, worst))
     assert worst <= V_REP
     assert flips <= n // 8
+
+
+def _bfgs_run(S, ctl, x0, V, n, n_iters):
+    Vout = torch.empty((n, ctl.T, 2), device="cuda")
+    mer = torch.empty((n, n_iters + 1), dtype=torch.float64, device="cuda")
+    its = torch.empty(n, dtype=torch.int32, device="cuda")
+    S.smppi_repair(ctl.h, n, x0[:n], V[:n], Vout, n_iters, 2, 0.0, mer, its)
+    st, _ = ctl.sync_status()
+    assert st in (S.OK, S.ERR_STALLED)
+    return Vout.cpu().numpy(), mer.cpu().numpy(), its.cpu().numpy()
+
+
+def test_bfgs_independent_of_batch(S):
+    sq = I.near_boundary_sequences(n_seq=2048, T=100, seed=4)
+    ctl = S.Controller(sq.params, sq.track, max_seq=2048)
+    x0, V = ctl.tensor(sq.x0), ctl.tensor(sq.V)
+    big = _bfgs_run(S, ctl, x0, V, 2048, 10)     # more sequences than resident warps
+    small = _bfgs_run(S, ctl, x0, V, 256, 10)
+    ctl.close()
+    for a, b in zip(big, small):
+        assert np.array_equal(a[:256], b)
 
 
 def test_bfgs_vs_gradient_repair(S):
