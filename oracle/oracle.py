@@ -46,6 +46,9 @@ class OrcParams(C.Structure):
         ("n_track", C.c_int),
         ("track_xy", C.POINTER(C.c_float)),
         ("seed", C.c_uint64),
+        ("state_kind", C.c_int),
+        ("kappa", C.POINTER(C.c_double)),
+        ("track_len", C.c_double),
     ]
 
 
@@ -99,6 +102,7 @@ def lib():
                                          C.c_double, C.c_int, _dp, C.POINTER(C.c_int)]
         L.orc_bfgs_quadratic.restype = C.c_int
         L.orc_apply.argtypes = [_PP, _dp, _dp, C.c_uint32, C.c_uint32, _dp]
+        L.orc_curvature_table.argtypes = [_PP, _dp, _dp]
         L.orc_shift.argtypes = [_PP, _dp, _dp]
         L.orc_max_threads.restype = C.c_int
         _lib = L
@@ -129,8 +133,16 @@ class Model:
         p.n_track = int(self.track.shape[0])
         p.track_xy = self.track.ctypes.data_as(C.POINTER(C.c_float))
         p.seed = int(params["seed"])
+        p.state_kind = int(params.get("state_kind", 0))
         self.p = p
         self.ptr = C.pointer(self.p)
+        self.kappa = None
+        if p.state_kind == 1:
+            self.kappa = np.zeros(p.n_track)
+            L = C.c_double()
+            lib().orc_curvature_table(self.ptr, self.kappa.ctypes.data_as(_dp), C.byref(L))
+            p.kappa = self.kappa.ctypes.data_as(_dp)
+            p.track_len = L.value
 
     @property
     def K(self):
@@ -146,6 +158,9 @@ class Model:
         m.track = self.track
         m.p = OrcParams.from_buffer_copy(self.p)
         m.p.track_xy = self.track.ctypes.data_as(C.POINTER(C.c_float))
+        m.kappa = self.kappa
+        if self.kappa is not None:
+            m.p.kappa = self.kappa.ctypes.data_as(_dp)
         for k, v in kw.items():
             if k in ("sigma", "u_min", "u_max", "dist_sigma"):
                 arr = getattr(m.p, k)
@@ -365,6 +380,14 @@ def shift(m: Model, Vplus):
     out = np.zeros((m.T, 2))
     lib().orc_shift(m.ptr, vp, out.ctypes.data_as(_dp))
     return out
+
+
+def curvature_table(m: Model):
+    """(kappa samples at the n uniform arc-length stations, track length L)."""
+    k = np.zeros(m.p.n_track)
+    L = C.c_double()
+    lib().orc_curvature_table(m.ptr, k.ctypes.data_as(_dp), C.byref(L))
+    return k, L.value
 
 
 def max_threads() -> int:

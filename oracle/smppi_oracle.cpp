@@ -39,6 +39,12 @@
 //   c15 e_y is the distance to the centreline polyline, tracked continuously
 //       from the previous step's segment (the curvilinear coordinate of the
 //       paper's model); the first segment is the global nearest one.
+//   c28 curvature of the centreline as a function of arc length: turning angle
+//       over mean segment length at each vertex, piecewise linear in s between
+//       vertices, sampled at n uniform stations and interpolated linearly;
+//   c29 curvilinear state (s, e_y, e_psi) of the paper's AutoRally model
+//       (Sec. VI-A): Frenet kinematics on that curvature, 1 - kappa e_y held
+//       at >= 0.1, h and q from e_y directly.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -70,6 +76,9 @@ struct OrcParams {
     int n_track;                       // centreline points
     const float* track_xy;             // n_track x 2, closed polyline (float32 values)
     uint64_t seed;
+    int state_kind;                    // 0: (X, Y, psi), e_y from the polyline; 1: (s, e_y, e_psi)
+    const double* kappa;               // state_kind 1: n_track curvature samples (reading c28)
+    double track_len;                  // state_kind 1: arc length L of the closed centreline
 };
 
 // ---------------------------------------------------------------------------
@@ -204,6 +213,55 @@ static inline double val(double a) { return a; }
 static inline double val(Dual a) { return a.v; }
 
 // ---------------------------------------------------------------------------
+// Curvature of the closed centreline as a function of arc length (reading
+// c28).  Vertex P_i between the segments d_{i-1} = P_i - P_{i-1} and
+// d_i = P_{i+1} - P_i (lengths l_{i-1}, l_i):
+//   kappa_i = atan2(d_{i-1} x d_i, d_{i-1} . d_i) / ((l_{i-1} + l_i) / 2),
+// positive where the centreline turns left.  kappa(s) is piecewise linear
+// between the vertex stations s_i = l_0 + ... + l_{i-1} (period L = total
+// length); its samples at the n uniform stations s = j L / n form the table
+// that the model interpolates linearly.
+// ---------------------------------------------------------------------------
+extern "C" void orc_curvature_table(const OrcParams* p, double* kappa_out, double* len_out) {
+    const int n = p->n_track;
+    std::vector<double> len(n), kv(n), st(n + 1, 0.0);
+    auto pt = [&](int i, int c) { return (double)p->track_xy[2 * (((i % n) + n) % n) + c]; };
+    for (int i = 0; i < n; ++i) {
+        len[i] = std::hypot(pt(i + 1, 0) - pt(i, 0), pt(i + 1, 1) - pt(i, 1));
+        st[i + 1] = st[i] + len[i];
+    }
+    for (int i = 0; i < n; ++i) {
+        const double ax = pt(i, 0) - pt(i - 1, 0), ay = pt(i, 1) - pt(i - 1, 1);
+        const double bx = pt(i + 1, 0) - pt(i, 0), by = pt(i + 1, 1) - pt(i, 1);
+        const double turn = std::atan2(ax * by - ay * bx, ax * bx + ay * by);
+        kv[i] = turn / (0.5 * (len[(i + n - 1) % n] + len[i]));
+    }
+    const double L = st[n];
+    int seg = 0;
+    for (int j = 0; j < n; ++j) {
+        const double sj = j * L / n;
+        while (seg + 1 < n && st[seg + 1] <= sj) ++seg;
+        const double f = (sj - st[seg]) / len[seg];
+        kappa_out[j] = (1.0 - f) * kv[seg] + f * kv[(seg + 1) % n];
+    }
+    *len_out = L;
+}
+
+// kappa(s): linear interpolation of the uniform samples, s taken modulo L.
+template <class R>
+static R kappa_at(const OrcParams* p, R s) {
+    const int M = p->n_track;
+    const double L = p->track_len;
+    const R sw = s - R(std::floor(val(s) / L) * L);
+    const R x = sw * R(M / L);
+    int i = (int)std::floor(val(x));
+    if (i < 0) i = 0;
+    if (i > M - 1) i = M - 1;
+    const R f = x - R((double)i);
+    return R(p->kappa[i]) + f * R(p->kappa[(i + 1) % M] - p->kappa[i]);
+}
+
+// ---------------------------------------------------------------------------
 // Vehicle model (Sec. VI-A uses a single-track model; its parameters are not
 // given, so the dynamic single-track model with Pacejka-type lateral tyre
 // forces below is the model this build fixes).  State x = (v_x, v_y, r, X, Y,
@@ -227,6 +285,17 @@ static void deriv(const OrcParams* p, const R x[6], const R u[2], R xdot[6]) {
     xdot[0] = (Fxr - Fyf * sd) / R(p->m) + vy * r;
     xdot[1] = (Fyr + Fyf * cd) / R(p->m) - vx * r;
     xdot[2] = (R(p->lf) * Fyf * cd - R(p->lr) * Fyr) / R(p->Iz);
+    if (p->state_kind == 1) {
+        // curvilinear kinematics (reading c29): x[3] = s, x[4] = e_y, x[5] = e_psi
+        const R es = sin(x[5]), ec = cos(x[5]);
+        const R k = kappa_at<R>(p, x[3]);
+        R den = R(1.0) - k * x[4];
+        if (val(den) < 0.1) den = R(0.1);
+        xdot[3] = (vx * ec - vy * es) / den;
+        xdot[4] = vx * es + vy * ec;
+        xdot[5] = r - k * xdot[3];
+        return;
+    }
     R sp = sin(psi), cp = cos(psi);
     xdot[3] = vx * cp - vy * sp;
     xdot[4] = vx * sp + vy * cp;
@@ -357,8 +426,10 @@ double orc_rollout(const OrcParams* p, const double x0[6], const double* V, uint
                    uint32_t instance, uint32_t k, int noisy, double* traj, double* eps_out) {
     double x[6];
     for (int i = 0; i < 6; ++i) x[i] = x0[i];
-    double d2;
-    int seg = orc_track_nearest(p, x[3], x[4], &d2);
+    // e_y^2: the tracked polyline distance, or the curvilinear state's own e_y
+    const bool curv = p->state_kind == 1;
+    double d2 = x[4] * x[4];
+    int seg = curv ? 0 : orc_track_nearest(p, x[3], x[4], &d2);
     double h_prev = orc_h(p, d2);
     double S = orc_q(p, x, d2) + orc_cbf_penalty(p, h_prev, h_prev);
     if (traj) for (int i = 0; i < 6; ++i) traj[i] = x[i];
@@ -373,7 +444,8 @@ double orc_rollout(const OrcParams* p, const double x0[6], const double* V, uint
         double xn[6];
         step<double>(p, x, u, xn);
         for (int i = 0; i < 6; ++i) x[i] = xn[i];
-        seg = orc_track_follow(p, seg, x[3], x[4], &d2);
+        if (curv) d2 = x[4] * x[4];
+        else seg = orc_track_follow(p, seg, x[3], x[4], &d2);
         double h = orc_h(p, d2);
         // control term of Alg. 2 (absent when gamma = 0, also for a degenerate Sigma)
         if (p->gamma != 0.0)
@@ -446,9 +518,10 @@ static R det_cost(const OrcParams* p, const double x0[6], const R* V, int N, dou
     R x[6];
     for (int i = 0; i < 6; ++i) x[i] = R(x0[i]);
     double d2v;
-    int seg = orc_track_nearest(p, x0[3], x0[4], &d2v);
+    const bool curv = p->state_kind == 1;
+    int seg = curv ? 0 : orc_track_nearest(p, x0[3], x0[4], &d2v);
     const double w2 = p->half_width * p->half_width;
-    R d2 = seg_dist2<R>(p, seg, x[3], x[4]);
+    R d2 = curv ? x[4] * x[4] : seg_dist2<R>(p, seg, x[3], x[4]);
     R h_prev = R(w2) - d2;
     R J = R(0.0);
     if (w_run != 0.0) {
@@ -461,8 +534,12 @@ static R det_cost(const OrcParams* p, const double x0[6], const R* V, int N, dou
         R xn[6];
         step<R>(p, x, u, xn);
         for (int i = 0; i < 6; ++i) x[i] = xn[i];
-        seg = orc_track_follow(p, seg, val(x[3]), val(x[4]), &d2v);
-        d2 = seg_dist2<R>(p, seg, x[3], x[4]);
+        if (curv) {
+            d2 = x[4] * x[4];
+        } else {
+            seg = orc_track_follow(p, seg, val(x[3]), val(x[4]), &d2v);
+            d2 = seg_dist2<R>(p, seg, x[3], x[4]);
+        }
         R h = R(w2) - d2;
         if (w_run != 0.0) {
             R ev = x[0] - R(p->v_target);

@@ -1,0 +1,98 @@
+"""Pins of the oracle's curvilinear state variant (the (s, e_y, e_psi) state of
+the paper's AutoRally model, Sec. VI-A; readings c28, c29).
+
+  * the curvature table of a regular polygon inscribed in a circle of radius R
+    is the closed form (2 pi / n) / chord everywhere, and the track length is
+    n chords;
+  * on the ellipse track the table follows the ellipse's analytic curvature
+    ab / (a^2 sin^2 t + b^2 cos^2 t)^(3/2) at the same arc lengths (positive:
+    the counter-clockwise centreline turns left);
+  * on a circle the curvilinear model and the Cartesian model, started on the
+    centreline along the tangent and driven by the same controls, give the same
+    (s, e_y, e_psi) (the Cartesian state converted exactly), with a difference
+    that halves with dt (the two explicit Euler schemes agree to first order);
+    the velocity states are identical;
+  * the rollout cost takes e_y^2 from the state's own e_y.
+"""
+import numpy as np
+import pytest
+
+from paper_2302_11719_gb300 import inputs as I
+
+
+def _circle(R, n):
+    th = 2 * np.pi * np.arange(n) / n
+    return np.stack([R * np.cos(th), R * np.sin(th)], 1).astype(np.float32)
+
+
+def _curv(params):
+    p = dict(params)
+    p["state_kind"] = 1
+    return p
+
+
+def test_curvature_regular_polygon(orc):
+    R, n = 10.0, 256
+    m = orc.Model(_curv(I.make_params(K=1, T=10)), _circle(R, n))
+    k, L = orc.curvature_table(m)
+    chord = 2 * R * np.sin(np.pi / n)
+    assert np.max(np.abs(k / ((2 * np.pi / n) / chord) - 1)) < 5e-4   # float32 vertices
+    assert abs(L / (n * chord) - 1) < 1e-7
+
+
+def test_curvature_ellipse_analytic(orc):
+    a, b, n = 20.0, 12.0, 1024
+    tr = I.ellipse_track(a, b, n)
+    m = orc.Model(_curv(I.make_params(K=1, T=10)), tr)
+    k, L = orc.curvature_table(m)
+    seg = np.hypot(*(np.roll(tr, -1, 0) - tr).astype(np.float64).T)
+    st = np.concatenate([[0.0], np.cumsum(seg)])
+    t = np.interp(np.arange(n) * L / n, st, 2 * np.pi * np.arange(n + 1) / n)
+    ka = a * b / (a * a * np.sin(t) ** 2 + b * b * np.cos(t) ** 2) ** 1.5
+    assert np.all(k > 0)
+    assert np.max(np.abs(k / ka - 1)) < 1e-2
+    assert np.mean(np.abs(k / ka - 1)) < 2e-3
+
+
+def _circle_runs(orc, dt, R=10.0, n=256, tend=0.5):
+    T = int(round(tend / dt))
+    pc = I.make_params(K=1, T=T, dt=dt, half_width=2.0)
+    mc, mk = orc.Model(pc, _circle(R, n)), orc.Model(_curv(pc), _circle(R, n))
+    t = np.arange(T) * dt
+    V = np.stack([0.08 + 0.05 * np.sin(3 * t), 0.3 * np.cos(2 * t)], 1)
+    _, tc, _ = orc.rollout(mc, np.array([5.0, 0, 0, R, 0, np.pi / 2]), V, noisy=False)
+    _, tk, _ = orc.rollout(mk, np.array([5.0, 0, 0, 0, 0, 0]), V, noisy=False)
+    th = np.unwrap(np.arctan2(tc[:, 4], tc[:, 3]))
+    conv = np.stack([R * th, R - np.hypot(tc[:, 3], tc[:, 4]), tc[:, 5] - (th + np.pi / 2)], 1)
+    return np.abs(conv - tk[:, 3:6]).max(0), np.abs(tc[:, :3] - tk[:, :3]).max()
+
+
+def test_curvilinear_matches_cartesian_on_circle(orc):
+    e2, dv2 = _circle_runs(orc, 2e-3)
+    e1, dv1 = _circle_runs(orc, 1e-3)
+    assert dv1 == 0.0 and dv2 == 0.0                 # (v_x, v_y, r) do not depend on the pose
+    assert e1[0] < 2e-4 and e1[1] < 2e-3 and e1[2] < 1e-4
+    ratio = e2[:2] / e1[:2]                          # first-order agreement in s and e_y
+    assert np.all((ratio > 1.7) & (ratio < 2.3)), ratio
+    assert e1[1] > 1e-5                              # the trajectory really leaves the centreline
+
+
+def test_curvilinear_cost_uses_e_y(orc):
+    pr = I.single_problem(K=1, T=40)
+    p = _curv(pr.params)
+    m = orc.Model(p, pr.track)
+    x0 = np.array([6.0, 0.2, 0.1, 3.0, 0.7, 0.05])
+    V = np.tile([[0.05, 0.4]], (40, 1))
+    S, traj, _ = orc.rollout(m, x0, V, noisy=False)
+    w2 = np.float32(p["half_width"]) ** 2
+    a1 = 1 - float(np.float32(p["alpha"]))
+    ey2 = traj[:, 4] ** 2
+    h = w2 - ey2
+    q = float(np.float32(p["q_v"])) * (traj[:, 0] - float(np.float32(p["v_target"]))) ** 2 + \
+        float(np.float32(p["q_d"])) * ey2 / w2
+    cbf = np.maximum(a1 * np.concatenate([[h[0]], h[:-1]]) - h, 0) * float(np.float32(p["C_cbf"]))
+    gam = float(np.float32(p["gamma"]))
+    sig = np.array(p["sigma"], np.float32).astype(np.float64)
+    ctrl = gam * np.sum(V * V / sig ** 2)
+    assert S == pytest.approx(q.sum() + cbf.sum() + ctrl, rel=1e-12)
+    assert np.max(np.abs(traj[:, 4])) > 0.5          # e_y enters, not a polyline distance
