@@ -507,6 +507,58 @@ def run_sweep(args):
     return 0
 
 
+F_ALG_CURV = 260   # hand count per rollout step of the curvilinear model (design notes)
+
+
+def run_curv(args):
+    """The curvilinear state variant (s, e_y, e_psi) against the Cartesian model:
+    one MPPI iteration (rollouts + update) at K = 65536 and T in {50, 100, 200}
+    on the same ellipse track, both from the centreline start."""
+    import torch
+
+    import __graft_entry__
+    from paper_2302_11719_gb300 import inputs as I
+    from paper_2302_11719_gb300 import smppi as S
+    __graft_entry__.build()
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    rows = []
+    K = 65536
+    for T in (50, 100, 200):
+        for kind, flops in ((0, F_ALG), (1, F_ALG_CURV)):
+            pr = I.throughput_problem(K, T)
+            if kind == 1:
+                pr.params["state_kind"] = 1
+                pr.x0 = pr.x0.copy()
+                pr.x0[3:6] = 0.0          # s = 0, e_y = 0, e_psi = 0: the same start
+            ctl = S.Controller(pr.params, pr.track, device=dev)
+            x0, V0 = ctl.tensor(pr.x0), ctl.tensor(pr.V)
+            Vb = [V0.clone() for _ in range(args.warmup + 2 * args.steps)]
+            for i in range(args.warmup):
+                S.smppi_step(ctl.h, x0, Vb[i], i, 0)
+            t = _timed_steps(lambda i: S.smppi_step(ctl.h, x0, Vb[args.warmup + i], i, 0),
+                             args.steps, flush)
+            S.smppi_timing(ctl.h, True)
+            _timed_steps(lambda i: S.smppi_step(ctl.h, x0, Vb[args.warmup + args.steps + i], i, 0),
+                         args.steps, flush)
+            S.smppi_timing(ctl.h, False)
+            kt = S.smppi_timing_read(ctl.h)
+            st, bits = ctl.sync_status()
+            roll_s = kt["rollout"][0] / kt["rollout"][1] / 1e3
+            step_s = sum(t) / len(t) / 1e3
+            ach = flops * K * T / roll_s / 1e12
+            rows.append({"model": "curvilinear" if kind else "cartesian", "K": K, "T": T,
+                         "us_per_update": step_s * 1e6, "rollout_steps_per_s": K * T / step_s,
+                         "rollout_kernel_us": roll_s * 1e6, "flops_per_rollout_step": flops,
+                         "fp32_tflops": ach, "fp32_frac": ach / FP32_PEAK_TFLOPS,
+                         "device_status_bits": _status_names(bits)})
+            ctl.close()
+    print(json.dumps({"workload": "curvilinear vs Cartesian state, MPPI iteration, K = 65536",
+                      "peak_tflops": FP32_PEAK_TFLOPS, "l2": "flushed between steps",
+                      "rows": rows}), flush=True)
+    return 0
+
+
 def run_small(args):
     """The small configurations, GPU and FP64 oracle side by side: the K = 256,
     T = 50 Shield-MPPI update (10 Armijo iterations; also the MPPI iteration
@@ -676,7 +728,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="shield",
-                    choices=["shield", "batch", "sweep", "grad", "small", "compare"])
+                    choices=["shield", "batch", "sweep", "grad", "small", "compare", "curv"])
     ap.add_argument("--loop-updates", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -695,6 +747,8 @@ def main():
         return run_small(args)
     if args.workload == "compare":
         return run_compare(args)
+    if args.workload == "curv":
+        return run_curv(args)
     return run_ours(args)
 
 

@@ -95,7 +95,25 @@ typedef struct smppi_params {
     int n_track;                /* centreline points, 3..SMPPI_MAX_TRACK */
     const float* track_xy;      /* DEVICE, n_track x 2: closed centreline polyline */
     uint64_t seed;              /* Philox key */
+    int state_kind;             /* 0: x = (v_x, v_y, r, X, Y, psi), e_y = distance to the
+                                 * polyline (tracked); 1: curvilinear x = (v_x, v_y, r, s,
+                                 * e_y, e_psi) of the paper's AutoRally model (Sec. VI-A):
+                                 * s = arc length, e_y = lateral offset (left positive),
+                                 * e_psi = heading error, on the centreline's curvature
+                                 * kappa(s) (see below).  1 needs Ct = 1.5 and
+                                 * |steer| <= 1/2 and supports smppi_step, smppi_update,
+                                 * smppi_apply and smppi_debug_noise only. */
 } smppi_params;
+
+/* Curvilinear state (state_kind = 1):
+ *   kappa(s): at each vertex P_i the turning angle between P_i - P_{i-1} and
+ *   P_{i+1} - P_i over the mean length of the two segments; piecewise linear in
+ *   the arc length between the vertices; sampled at n_track uniform stations
+ *   s = j L / n_track (L = the closed polyline's length) and interpolated
+ *   linearly between the samples, s taken modulo L.
+ *   ds/dt = (v_x cos e_psi - v_y sin e_psi) / max(1 - kappa e_y, 0.1),
+ *   de_y/dt = v_x sin e_psi + v_y cos e_psi,  de_psi/dt = r - kappa ds/dt;
+ *   explicit Euler like the Cartesian model; h = w^2 - e_y^2 and q use e_y. */
 
 typedef struct smppi_handle smppi_handle;
 

@@ -33,6 +33,7 @@ struct smppi_handle {
     float* d_Vs = nullptr;
     double* d_merit = nullptr;
     int merit_cap = 0;
+    float* kappa = nullptr;          // curvature samples of the curvilinear state
     void* bfgs_ws = nullptr;         // BFGS repair workspace: counter + H slices (grown on use)
     size_t bfgs_ws_bytes = 0;
     int sms = 1;
@@ -96,7 +97,40 @@ smppi_status check_params(const smppi_params* p) {
     if (p->max_seq < 1 || p->max_seq > (1 << 20)) return bad("max_seq in [1, 2^20]");
     if (p->n_track < 3 || p->n_track > SMPPI_MAX_TRACK) return bad("n_track in [3, SMPPI_MAX_TRACK]");
     if (!p->track_xy) return bad("track_xy is NULL");
+    if (p->state_kind != 0 && p->state_kind != 1) return bad("state_kind must be 0 or 1");
+    if (p->state_kind == 1 &&
+        !(p->Ct == 1.5f && std::fabs(p->u_min[0]) <= 0.5f && std::fabs(p->u_max[0]) <= 0.5f))
+        return bad("state_kind 1 needs Ct = 1.5 and |steer| <= 1/2");
     return SMPPI_OK;
+}
+
+// Curvature samples of the curvilinear state (smppi.h, state_kind 1), in
+// double: the vertex curvatures (turning angle / mean adjacent segment
+// length), linear in arc length between the vertex stations, sampled at n
+// uniform stations; sample n repeats sample 0 for the interpolation.
+void curvature_samples(const std::vector<float>& xy, int n, std::vector<float>& out, double& L) {
+    std::vector<double> seg(n), station(n + 1, 0.0), kv(n);
+    for (int i = 0; i < n; ++i) {
+        const int j = (i + 1) % n;
+        seg[i] = std::hypot((double)xy[2 * j] - xy[2 * i], (double)xy[2 * j + 1] - xy[2 * i + 1]);
+        station[i + 1] = station[i] + seg[i];
+    }
+    L = station[n];
+    for (int i = 0; i < n; ++i) {
+        const int pv = (i + n - 1) % n, nx = (i + 1) % n;
+        const double ux = (double)xy[2 * i] - xy[2 * pv], uy = (double)xy[2 * i + 1] - xy[2 * pv + 1];
+        const double wx = (double)xy[2 * nx] - xy[2 * i], wy = (double)xy[2 * nx + 1] - xy[2 * i + 1];
+        kv[i] = std::atan2(ux * wy - uy * wx, ux * wx + uy * wy) / (0.5 * (seg[pv] + seg[i]));
+    }
+    out.assign(n + 1, 0.0f);
+    for (int j = 0; j < n; ++j) {
+        const double sj = L * j / n;
+        int i = (int)(std::upper_bound(station.begin(), station.begin() + n, sj) - station.begin()) - 1;
+        i = std::max(0, std::min(n - 1, i));
+        const double f = (sj - station[i]) / seg[i];
+        out[j] = (float)((1.0 - f) * kv[i] + f * kv[(i + 1) % n]);
+    }
+    out[n] = out[0];
 }
 
 DevParams derive(const smppi_params& p) {
@@ -128,6 +162,7 @@ DevParams derive(const smppi_params& p) {
     d.dsig0 = p.dist_sigma[0]; d.dsig1 = p.dist_sigma[1];
     d.ls_s0 = p.ls_s0; d.ls_c = p.ls_c; d.ls_max = p.ls_max_halvings;
     d.K = p.K; d.T = p.T; d.N_r = p.N_r; d.n_track = p.n_track;
+    d.state_kind = p.state_kind;   // the curvature table is set up by smppi_create
     d.key0 = (uint32_t)(p.seed & 0xFFFFFFFFull);
     d.key1 = (uint32_t)(p.seed >> 32);
     for (int i = 0; i < 10; ++i) {
@@ -147,7 +182,7 @@ void free_all(smppi_handle* h) {
                     h->status,
                     h->iter_dev,
                     h->rws.tape, h->rws.Vw, h->rws.G, h->rws.seg0, h->d_x0, h->d_V, h->d_Vs,
-                    h->d_merit, h->bfgs_ws};
+                    h->d_merit, h->bfgs_ws, h->kappa};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (h->cap) cudaStreamDestroy(h->cap);
@@ -182,6 +217,8 @@ void toc(smppi_handle* h, cudaStream_t st, int kind, int i0) {
 
 smppi_status check_seq_call(smppi_handle* h, int n_seq) {
     if (!h) return fail(nullptr, SMPPI_ERR_ARG, "handle is NULL");
+    if (h->p.state_kind != 0)
+        return fail(h, SMPPI_ERR_ARG, "the repair and the adjoint need state_kind 0");
     if (n_seq < 1 || n_seq > h->p.max_seq)
         return fail(h, SMPPI_ERR_ARG, "n_seq must be in [1, max_seq]");
     return SMPPI_OK;
@@ -311,6 +348,7 @@ void smppi_default_params(smppi_params* p) {
     p->n_track = 0;
     p->track_xy = nullptr;
     p->seed = 0;
+    p->state_kind = 0;
 }
 
 smppi_status smppi_create(const smppi_params* p, void* cuda_stream, smppi_handle** out) {
@@ -363,6 +401,21 @@ smppi_status smppi_create(const smppi_params* p, void* cuda_stream, smppi_handle
     if (e == cudaSuccess) e = cudaMemsetAsync(h->iter_dev, 0, sizeof(uint32_t), h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->ticket, 0, sizeof(unsigned), h->st);
     if (e == cudaSuccess) e = launch_rec_table(p->track_xy, p->n_track, h->rec, h->st);
+    if (e == cudaSuccess && p->state_kind == 1) {
+        std::vector<float> xy(2 * (size_t)p->n_track), ks;
+        double L = 0.0;
+        e = cudaMemcpy(xy.data(), p->track_xy, sizeof(float) * xy.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) {
+            curvature_samples(xy, p->n_track, ks, L);
+            e = alloc(&h->kappa, sizeof(float) * ks.size());
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpy(h->kappa, ks.data(), sizeof(float) * ks.size(), cudaMemcpyHostToDevice);
+        h->dp.kappa = h->kappa;
+        h->dp.kap_scale = (float)(p->n_track / L);
+        h->dp.track_len = (float)L;
+        h->dp.inv_len = (float)(1.0 / L);
+    }
     if (e != cudaSuccess) {
         const bool oom = (e == cudaErrorMemoryAllocation);
         fail(nullptr, oom ? SMPPI_ERR_NOMEM : SMPPI_ERR_CUDA,
@@ -498,6 +551,7 @@ smppi_status smppi_shield_update(smppi_handle* h, float* x0, float* V, float* V_
                                  uint32_t iter, uint32_t instance, int n_repair,
                                  double* merit_out, int host_buffers) {
     if (!h) return fail(nullptr, SMPPI_ERR_ARG, "handle is NULL");
+    if (h->p.state_kind != 0) return fail(h, SMPPI_ERR_ARG, "the shield needs state_kind 0");
     if (!x0 || !V || !V_safe) return fail(h, SMPPI_ERR_ARG, "x0, V, V_safe must not be NULL");
     if (n_repair < 0 || n_repair > 100000) return fail(h, SMPPI_ERR_ARG, "n_repair must be in [0, 1e5]");
     if (instance >= (1u << 24)) return fail(h, SMPPI_ERR_ARG, "instance must be < 2^24");
@@ -533,6 +587,7 @@ smppi_status smppi_shield_update(smppi_handle* h, float* x0, float* V, float* V_
 smppi_status smppi_shield_loop(smppi_handle* h, float* x0, float* V, float* V_safe,
                                uint32_t iter0, uint32_t instance, int n_repair, int n_updates) {
     if (!h) return fail(nullptr, SMPPI_ERR_ARG, "handle is NULL");
+    if (h->p.state_kind != 0) return fail(h, SMPPI_ERR_ARG, "the shield needs state_kind 0");
     if (!x0 || !V || !V_safe) return fail(h, SMPPI_ERR_ARG, "x0, V, V_safe must not be NULL");
     if (n_repair < 0 || n_repair > 100000 || n_updates < 0)
         return fail(h, SMPPI_ERR_ARG, "n_repair in [0, 1e5], n_updates >= 0");

@@ -594,6 +594,7 @@ smppi_status smppi_batch_create(const smppi_params* shared, int B, const smppi_i
     chk.half_width = 1.0f; chk.max_seq = 1;
     smppi_status s = validate_params(&chk);
     if (s != SMPPI_OK) return bfail(nullptr, s, "shared parameters rejected");
+    if (shared->state_kind != 0) return bfail(nullptr, SMPPI_ERR_ARG, "the batch needs state_kind 0");
     smppi_batch* b = new smppi_batch();
     b->shared = *shared;
     b->B = B;

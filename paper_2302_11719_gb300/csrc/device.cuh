@@ -47,6 +47,12 @@ struct DevParams {
     int steer_small;             // 1 when |steer| <= 1/2 on the whole control box
     uint32_t key0, key1;
     uint32_t rk0[10], rk1[10];   // Philox round keys key + i * Weyl
+    // curvilinear state (state_kind 1): x = (v_x, v_y, r, s, e_y, e_psi) held in
+    // State's (vx, vy, r, X, Y, psi) with (cp, sp) = (cos, sin) e_psi
+    int state_kind;
+    const float* kappa;          // n_track + 1 curvature samples (the last repeats the first)
+    float kap_scale;             // n_track / L
+    float track_len, inv_len;    // L, 1 / L
 };
 
 struct State {
@@ -247,6 +253,48 @@ __device__ __forceinline__ void model_step(const DevParams& P, State& x, float d
     x.psi += dpsi;
     x.cp = cp;
     x.sp = sp;
+}
+
+// ---------------------------------------------------------------------------
+// Curvilinear state (state_kind 1; smppi.h): x = (v_x, v_y, r, s, e_y, e_psi)
+// in State's (vx, vy, r, X, Y, psi), (cp, sp) = (cos e_psi, sin e_psi).
+// kappa(s) from the n_track + 1 samples (the last repeats the first), s taken
+// modulo the track length L.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float kappa_at(const DevParams& P, const float* kt, float s) {
+    const float sw = fmaf(floorf(s * P.inv_len), -P.track_len, s);
+    const float x = sw * P.kap_scale;
+    const int i = min(max((int)x, 0), P.n_track - 1);
+    const float f = x - (float)i;
+    const float k0 = kt[i], k1 = kt[i + 1];
+    return fmaf(f, k1 - k0, k0);
+}
+
+// One explicit Euler step of the curvilinear model (C = 1.5, |steer| <= 1/2):
+// the velocity part is the Cartesian model's; then
+//   s' = (v_x cos e_psi - v_y sin e_psi) / max(1 - kappa e_y, 0.1),
+//   e_y' = v_x sin e_psi + v_y cos e_psi,  e_psi' = r - kappa s',
+// with (cos, sin) e_psi rotated by the increment dt e_psi'.
+__device__ __forceinline__ void model_step_curv(const DevParams& P, const float* kt, State& x,
+                                                float d, float a) {
+    float sd, cd;
+    sincos_half(d, &sd, &cd);
+    const float vx = x.vx, vy = x.vy, r = x.r;
+    vel_step_fast(P, x.vx, x.vy, x.r, d, sd, cd, P.fx_gain * a);
+    const float k = kappa_at(P, kt, x.X);
+    const float den = fmaxf(fmaf(-k, x.Y, 1.0f), 0.1f);
+    const float sdot = __fdiv_rn(fmaf(vx, x.cp, -(vy * x.sp)), den);
+    const float eydot = fmaf(vx, x.sp, vy * x.cp);
+    const float epdot = fmaf(-k, sdot, r);
+    const float dpsi = P.dt * epdot;
+    float sa, ca;
+    sincos_any(dpsi, &sa, &ca);
+    x.X = fmaf(P.dt, sdot, x.X);
+    x.Y = fmaf(P.dt, eydot, x.Y);
+    x.psi += dpsi;
+    const float cp0 = x.cp;
+    x.cp = fmaf(x.cp, ca, -(x.sp * sa));
+    x.sp = fmaf(x.sp, ca, cp0 * sa);
 }
 
 // Reverse-mode adjoint of model_step at (x, d, a): given lb = dJ/dx_{t+1},

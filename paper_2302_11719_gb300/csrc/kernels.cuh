@@ -19,6 +19,12 @@ inline cudaError_t ensure_smem(const void* kernel, size_t bytes) {
 size_t rollout_smem_bytes(int n_track, int T);
 // Block minima the rollout launch writes (<= ceil(K / ROLL_BLK)).
 int rollout_blocks(const DevParams& P);
+// Rollouts of the curvilinear state (curv.cu; state_kind 1), same outputs as
+// launch_rollout (no nearest segment).
+cudaError_t launch_rollout_curv(const DevParams& P, bool dump, const float* x0, const float* V,
+                                uint32_t iter, uint32_t ctr3, const uint32_t* iter_dev,
+                                float* S_out, float* traj, float* blk_min, unsigned* status,
+                                cudaStream_t st);
 // Rollouts: S_out [K] and blk_min [rollout_blocks(P)]; traj (optional dump);
 // seg0_out (optional): nearest segment of x0.  rec: segment-pair table of
 // launch_rec_table.

@@ -65,6 +65,8 @@ extern "C" smppi_status smppi_step_noalloc(const smppi_params* p, const float* x
                                            uint32_t iter, uint32_t instance, float* S_out,
                                            void* cuda_stream) {
     smppi_status s = validate_params(p);
+    if (s == SMPPI_OK && p->state_kind != 0)
+        return report_error(SMPPI_ERR_ARG, "smppi_step_noalloc: needs state_kind 0");
     if (s != SMPPI_OK) return s;
     if (!x0 || !V) return report_error(SMPPI_ERR_ARG, "smppi_step_noalloc: x0 and V must not be NULL");
     if (p->K > NA_MAX_K)

@@ -404,7 +404,11 @@ __device__ double seq_cost_grad(const DevParams& P, const float4* rec,
 __device__ void closed_loop_step(const DevParams& P, const ApplyArgs& ap, float2 v_exec) {
     const uint32_t nn = ap.n + (ap.iter_dev ? *ap.iter_dev : 0u);
     State x = make_state(ap.x0);
-    model_step(P, x, clampf(v_exec.x, P.umin0, P.umax0), clampf(v_exec.y, P.umin1, P.umax1));
+    if (P.state_kind == 1)
+        model_step_curv(P, P.kappa, x, clampf(v_exec.x, P.umin0, P.umax0),
+                        clampf(v_exec.y, P.umin1, P.umax1));
+    else
+        model_step(P, x, clampf(v_exec.x, P.umin0, P.umax0), clampf(v_exec.y, P.umin1, P.umax1));
     const uint4 r = philox10(make_uint4(0u, 0u, nn, ap.ctr3), P);
     const float2 z = box_muller(r.x, r.y);
     ap.x0[0] = x.vx;

@@ -48,6 +48,7 @@ class Params(C.Structure):
         ("n_track", C.c_int),
         ("track_xy", C.c_void_p),
         ("seed", C.c_uint64),
+        ("state_kind", C.c_int),
     ]
 
 
@@ -157,6 +158,7 @@ def params_from_dict(d: dict, track_dev: torch.Tensor, max_seq: int = 1,
     p.n_track = int(track_dev.shape[0])
     p.track_xy = _ptr(track_dev)
     p.seed = int(d["seed"])
+    p.state_kind = int(d.get("state_kind", 0))
     return p
 
 

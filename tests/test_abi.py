@@ -68,6 +68,14 @@ def test_default_params_and_host_checks(lib):
     q.lam = 0.0
     assert L.smppi_create(C.byref(q), None, C.byref(h)) == smppi.ERR_ARG
     assert b"lambda" in L.smppi_last_error(None)
+    # the state kind: 0 or 1, and the curvilinear state needs C = 1.5 and |steer| <= 1/2
+    assert p.state_kind == 0
+    for kind, Ct, steer in ((2, 1.5, 0.5), (1, 1.2, 0.5), (1, 1.5, 0.6)):
+        q = smppi.default_params()
+        C.memmove(C.byref(q), C.byref(p), C.sizeof(p))
+        q.state_kind, q.Ct, q.u_max[0] = kind, Ct, steer
+        assert L.smppi_create(C.byref(q), None, C.byref(h)) == smppi.ERR_ARG
+        assert b"state_kind" in L.smppi_last_error(None)
     # calls on a NULL handle are rejected
     assert L.smppi_step(None, None, None, 0, 0, None, None) == smppi.ERR_ARG
     assert L.smppi_repair(None, 1, None, None, None, 1, 1, C.c_float(0), None, None) == smppi.ERR_ARG
