@@ -173,7 +173,7 @@ def cpu_threads() -> int:
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
+    _, rank, _ = dist_env()
     if rank != 0:
         return 0
     nth = cpu_threads()
@@ -207,6 +207,29 @@ def workload_config():
             "l2": "flushed between timed steps (256 MiB write, outside the timed events)"}
 
 
+def dist_env():
+    """(world size, rank, local rank) from the torchrun environment; (1, 0, 0) without it."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x, dist, device):
+    """The largest x over all ranks (x itself when there is no process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, max_seconds):
+    """Whole-job throughput under weak scaling: every rank runs its own problem of
+    the same size (replicas; rank r uses Philox instance r), so the job processed
+    world x units_per_rank in the slowest rank's time."""
+    return world * units_per_rank / max_seconds
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -215,9 +238,7 @@ def run_ours(args):
     from paper_2302_11719_gb300 import inputs as I
     from paper_2302_11719_gb300 import smppi as S
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = dist_env()
     __graft_entry__.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -276,11 +297,8 @@ def run_ours(args):
     st, bits = ctl.sync_status()
     if st not in (S.OK, S.ERR_STALLED):
         raise RuntimeError("device status %d (bits %d) in the timed region" % (st, bits))
-    if dist:
-        t = torch.tensor([total_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = world * K_ROLL * T_HOR * args.steps / total_s
+    total_s = max_over_ranks(total_s, dist, dev)
+    value = job_rate(world, K_ROLL * T_HOR * args.steps, total_s)
 
     # end to end through the host-buffer entry point (copies in the timed region)
     hx = torch.from_numpy(pr.x0.copy()).pin_memory()
@@ -299,11 +317,8 @@ def run_ours(args):
                               N_REPAIR, None, True)
         e2e_s += time.perf_counter() - a
         it += 1
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * K_ROLL * T_HOR * args.steps / e2e_s
+    e2e_s = max_over_ranks(e2e_s, dist, dev)
+    e2e_value = job_rate(world, K_ROLL * T_HOR * args.steps, e2e_s)
 
     if rank != 0:
         dist.barrier()
