@@ -135,7 +135,7 @@ __device__ double forward_cost(const DevParams& P, const float4* rec,
 // Progress is published every MERIT_PUB steps; every wait is bounded (past
 // the limit: SMPPI_DEV_TIMEOUT and the merit is reported as 0).
 // ---------------------------------------------------------------------------
-constexpr int MERIT_PUB = 4;
+constexpr int MERIT_PUB = 8;
 constexpr int MERIT_WAIT_LIMIT = 1 << 24;
 
 // The follower warp: positions pos[t - 1] = (X, Y) of x_t, t = 1..N, ready when
@@ -145,9 +145,11 @@ constexpr int MERIT_WAIT_LIMIT = 1 << 24;
 // c15 are then read off ballots of "the next segment is strictly closer"
 // position after position: the walk from window lane L moves forward to the
 // first lane above L whose successor is not closer, and stays at L when L + 1
-// is not closer and L - 1 is not closer either.  A backward step or a walk
-// that reaches the window's last lane is finished one segment at a time by
-// lane 0 (walk_seq_rec), for that position and the rest of the chunk.
+// is not closer and L - 1 is not closer either.  This decode is one dependent
+// chain per chunk, unrolled and free of calls so that it stays in registers.
+// A backward step or a walk that reaches the window's last lane is finished
+// one segment at a time by lane 0 (walk_seq_rec), for that position and the
+// rest of the chunk.
 // Returns J on every lane.
 __device__ __forceinline__ double merit_follow_warp(const DevParams& P, const float4* rec,
                                                     const State& x0, int s0, int N,
@@ -185,43 +187,51 @@ __device__ __forceinline__ double merit_follow_warp(const DevParams& P, const fl
             fw[q] = __ballot_sync(FULL, lane < 31 && dn < dq[q]);   // bit l: d(l+1) < d(l)
             bw[q] = __ballot_sync(FULL, lane < 31 && dq[q] < dn);   // bit l: d(l) < d(l+1)
         }
-        int L = 1, scur = s;
-        bool seq = false;
+        // DCBF term of x_t, in order (the sum of forward_cost)
+        auto take = [&](float dd, int t) {
+            const float h = P.w2 - dd;
+            const float a = cbf_arg(P, h_prev, h);
+            Jf = (a > 0.0f) ? fmaf(P.C_cbf, a, Jf) : Jf;
+            h_prev = h;
+            if ((t & 15) == 0) {
+                J += (double)Jf;
+                Jf = 0.0f;
+            }
+        };
+        // fast path, fully unrolled and without calls: the positions whose walk
+        // stays inside the window; qs = the first one that does not
+        int L = 1, qs = nq;
 #pragma unroll
         for (int q = 0; q < MERIT_PUB; ++q) {
-            if (q < nq) {
-                float dd = 0.0f;
-                if (!seq) {
-                    if ((fw[q] >> L) & 1u) {
-                        const int L2 = __ffs(~fw[q] & ~((2u << L) - 1u)) - 1;
-                        if (L2 >= 31) seq = true;
-                        else L = L2;
-                    } else if ((bw[q] >> (L - 1)) & 1u) {
-                        seq = true;
-                    }
-                    dd = __shfl_sync(FULL, dq[q], L);
-                    if (!seq) {
-                        scur = s - 1 + L;
-                        if (scur < 0) scur += n;
-                        while (scur >= n) scur -= n;
-                    }
+            if (q < qs) {
+                bool out;
+                int Ln = L;
+                if ((fw[q] >> L) & 1u) {
+                    Ln = __ffs(~fw[q] & ~((2u << L) - 1u)) - 1;
+                    out = Ln >= 31;
+                } else {
+                    out = ((bw[q] >> (L - 1)) & 1u) != 0u;
                 }
-                if (seq) {
-                    int sr = 0;
-                    float dr = 0.0f;
-                    if (lane == 0) sr = walk_seq_rec(rec, n, scur, xy[q].x, xy[q].y, dr);
-                    scur = __shfl_sync(FULL, sr, 0);
-                    dd = __shfl_sync(FULL, dr, 0);
-                }
-                const float h = P.w2 - dd;
-                const float a = cbf_arg(P, h_prev, h);
-                Jf = (a > 0.0f) ? fmaf(P.C_cbf, a, Jf) : Jf;
-                h_prev = h;
-                if (((t0 + q) & 15) == 0) {
-                    J += (double)Jf;
-                    Jf = 0.0f;
+                if (out) {
+                    qs = q;
+                } else {
+                    L = Ln;
+                    take(__shfl_sync(FULL, dq[q], L), t0 + q);
                 }
             }
+        }
+        int scur = s - 1 + L;
+        if (scur < 0) scur += n;
+        while (scur >= n) scur -= n;
+        // from qs on: lane 0 walks one segment at a time (rare)
+#pragma unroll 1
+        for (int q = qs; q < nq; ++q) {
+            const float2 p = pos[t0 - 1 + q];
+            int sr = 0;
+            float dr = 0.0f;
+            if (lane == 0) sr = walk_seq_rec(rec, n, scur, p.x, p.y, dr);
+            scur = __shfl_sync(FULL, sr, 0);
+            take(__shfl_sync(FULL, dr, 0), t0 + q);
         }
         s = scur;
     }
