@@ -516,9 +516,30 @@ def run_sweep(args):
                          "rollout_kernel_us": roll_s * 1e6, "update_kernel_us": upd_s * 1e6,
                          "fp32_tflops": ach, "fp32_frac": ach / FP32_PEAK_TFLOPS})
             ctl.close()
+    # the FP64 oracle's MPPI iteration at K = 4096 and 65536, T = 100 (host cores)
+    import numpy as np
+
+    import oracle as O
+    O.build()
+    oracle_rows = []
+    for K in (4096, 65536):
+        pr = I.throughput_problem(K, 100)
+        m = O.Model(pr.params, pr.track)
+        x0, V = pr.x0.astype(np.float64), pr.V.astype(np.float64)
+        for nth in (1, cpu_threads()):
+            reps = 1 if (nth == 1 and K > 4096) else 3
+            t = []
+            for r in range(reps):
+                a = time.perf_counter()
+                O.mppi_step(m, x0, V, r, 0, nthreads=nth)
+                t.append(time.perf_counter() - a)
+            us = 1e6 * sum(t) / len(t)
+            oracle_rows.append({"K": K, "T": 100, "threads": nth, "us_per_update": us,
+                                "rollout_steps_per_s": K * 100 / (us * 1e-6)})
     print(json.dumps({"workload": "MPPI iteration sweep (rollouts + softmin update)",
                       "peak_tflops": FP32_PEAK_TFLOPS, "flops_per_rollout_step": F_ALG,
-                      "l2": "flushed between steps", "rows": rows}), flush=True)
+                      "l2": "flushed between steps", "rows": rows,
+                      "oracle_fp64_host": oracle_rows}), flush=True)
     return 0
 
 
@@ -724,6 +745,23 @@ def run_grad(args):
                     "sequences_safe_after": int((m[:, -1] == 0).sum()),
                     "device_status_bits": _status_names(bits)}
     ctl.close()
+    # the FP64 oracle's repairs on a sample of the same sequences (one host core
+    # per sequence; sequences are independent, so the whole batch on all cores
+    # is extrapolated as sample time x 8192 / 64 / cores)
+    import oracle as O
+    O.build()
+    m = O.Model(sb.params, sb.track)
+    n_smp, cores = 64, cpu_threads()
+    for key, mode in (("repair_20", 1), ("bfgs_20", 2)):
+        a = time.perf_counter()
+        for q in range(n_smp):
+            O.repair(m, sb.x0[q], sb.V[q], 20, mode=mode)
+        dt = time.perf_counter() - a
+        out[key]["oracle_fp64_host"] = {
+            "sample": "first %d of the %d sequences, one core" % (n_smp, n),
+            "us_per_sequence": 1e6 * dt / n_smp,
+            "us_per_call_extrapolated_all_cores": 1e6 * dt / n_smp * n / cores,
+            "cores": cores}
     # a plain MPPI iteration of the same size (K = 8192 rollouts, T = 100)
     pr = I.throughput_problem(8192, 100)
     c2 = S.Controller(pr.params, pr.track, device=dev)
