@@ -228,8 +228,12 @@ smppi_status enqueue_rollout(smppi_handle* h, cudaStream_t st, const float* x0, 
                              uint32_t iter, uint32_t instance, float* S, float* traj_out,
                              uint32_t* iter_dev) {
     const int ev = tic(h, st);
-    CU(h, launch_rollout(h->dp, traj_out != nullptr, x0, V, h->rec, iter, instance << 8,
-                         iter_dev, S, traj_out, h->blk_min, h->rws.seg0, h->status, st));
+    if (h->p.state_kind == 1)
+        CU(h, launch_rollout_curv(h->dp, h->kappa, traj_out != nullptr, x0, V, iter, instance << 8,
+                                  iter_dev, S, traj_out, h->blk_min, h->status, st));
+    else
+        CU(h, launch_rollout(h->dp, traj_out != nullptr, x0, V, h->rec, iter, instance << 8,
+                             iter_dev, S, traj_out, h->blk_min, h->rws.seg0, h->status, st));
     toc(h, st, SMPPI_KERNEL_ROLLOUT, ev);
     return SMPPI_OK;
 }
@@ -309,7 +313,7 @@ smppi_status enqueue_shield(smppi_handle* h, cudaStream_t st, float* x0, float* 
     }
     smppi_status s = enqueue_step(h, st, x0, V, iter, instance, nullptr, nullptr, iter_dev);
     if (s != SMPPI_OK) return s;
-    const ApplyArgs ap{x0, V, iter, (instance << 8) | 1u, iter_dev};
+    const ApplyArgs ap{x0, V, iter, (instance << 8) | 1u, iter_dev, h->kappa};
     CU(h, cudaMemcpyAsync(Vs, V, sizeof(float) * 2 * h->p.T, cudaMemcpyDeviceToDevice, st));
     const int ev = tic(h, st);
     CU(h, launch_apply(h->dp, ap, Vs, st));
@@ -411,7 +415,6 @@ smppi_status smppi_create(const smppi_params* p, void* cuda_stream, smppi_handle
         }
         if (e == cudaSuccess)
             e = cudaMemcpy(h->kappa, ks.data(), sizeof(float) * ks.size(), cudaMemcpyHostToDevice);
-        h->dp.kappa = h->kappa;
         h->dp.kap_scale = (float)(p->n_track / L);
         h->dp.track_len = (float)L;
         h->dp.inv_len = (float)(1.0 / L);
@@ -540,7 +543,7 @@ smppi_status smppi_apply(smppi_handle* h, float* x0, float* V, const float* V_ex
     if (!h) return fail(nullptr, SMPPI_ERR_ARG, "handle is NULL");
     if (!x0 || !V || !V_exec) return fail(h, SMPPI_ERR_ARG, "x0, V, V_exec must not be NULL");
     if (instance >= (1u << 24)) return fail(h, SMPPI_ERR_ARG, "instance must be < 2^24");
-    const ApplyArgs ap{x0, V, n, (instance << 8) | 1u, nullptr};
+    const ApplyArgs ap{x0, V, n, (instance << 8) | 1u, nullptr, h->kappa};
     const int ev = tic(h, h->st);
     CU(h, launch_apply(h->dp, ap, V_exec, h->st));
     toc(h, h->st, SMPPI_KERNEL_APPLY, ev);

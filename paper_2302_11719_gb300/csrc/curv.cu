@@ -121,8 +121,9 @@ __device__ __forceinline__ f2 rollout2_curv(const DevParams& P, const float* kt,
 // thread; S_out [K], blk_min [blocks]; traj (DUMP) [K][T + 1][6].
 template <bool DUMP>
 __global__ void __launch_bounds__(ROLL2_BLK, 2) mppi_rollout_curv_kernel(
-    DevParams P, const float* __restrict__ x0g, const float* __restrict__ Vg, uint32_t iter,
-    uint32_t ctr3, const uint32_t* __restrict__ iter_dev, float* __restrict__ S_out,
+    DevParams P, const float* __restrict__ kappa, const float* __restrict__ x0g,
+    const float* __restrict__ Vg, uint32_t iter, uint32_t ctr3,
+    const uint32_t* __restrict__ iter_dev, float* __restrict__ S_out,
     float* __restrict__ traj, float* __restrict__ blk_min, unsigned* __restrict__ status) {
     constexpr int BLK = ROLL2_BLK, NW = BLK / 32;
     griddep_launch_dependents();
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(ROLL2_BLK, 2) mppi_rollout_curv_kernel(
         Vp[2 * t] = make_float4(v.x, v.x, v.y, v.y);
         Vp[2 * t + 1] = make_float4(g0, g0, g1, g1);
     }
-    for (int i = tid; i <= n; i += BLK) kt[i] = P.kappa[i];
+    for (int i = tid; i <= n; i += BLK) kt[i] = kappa[i];
     __syncthreads();
 
     const int ka = blockIdx.x * 2 * BLK + tid, kb = ka + BLK;
@@ -174,10 +175,10 @@ size_t curv_rollout_smem_bytes(int n_track, int T) {
     return (size_t)T * 2 * sizeof(float4) + (size_t)(n_track + 1) * sizeof(float);
 }
 
-cudaError_t launch_rollout_curv(const DevParams& P, bool dump, const float* x0, const float* V,
-                                uint32_t iter, uint32_t ctr3, const uint32_t* iter_dev,
-                                float* S_out, float* traj, float* blk_min, unsigned* status,
-                                cudaStream_t st) {
+cudaError_t launch_rollout_curv(const DevParams& P, const float* kappa, bool dump, const float* x0,
+                                const float* V, uint32_t iter, uint32_t ctr3,
+                                const uint32_t* iter_dev, float* S_out, float* traj,
+                                float* blk_min, unsigned* status, cudaStream_t st) {
     const size_t smem = curv_rollout_smem_bytes(P.n_track, P.T);
     auto kern = dump ? mppi_rollout_curv_kernel<true> : mppi_rollout_curv_kernel<false>;
     cudaError_t e = ensure_smem((const void*)kern, smem);
@@ -192,8 +193,8 @@ cudaError_t launch_rollout_curv(const DevParams& P, bool dump, const float* x0, 
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, P, x0, V, iter, ctr3, iter_dev, S_out, traj, blk_min,
-                              status);
+    return cudaLaunchKernelEx(&cfg, kern, P, kappa, x0, V, iter, ctr3, iter_dev, S_out, traj,
+                              blk_min, status);
 }
 
 }  // namespace smppi

@@ -48,9 +48,10 @@ struct DevParams {
     uint32_t key0, key1;
     uint32_t rk0[10], rk1[10];   // Philox round keys key + i * Weyl
     // curvilinear state (state_kind 1): x = (v_x, v_y, r, s, e_y, e_psi) held in
-    // State's (vx, vy, r, X, Y, psi) with (cp, sp) = (cos, sin) e_psi
+    // State's (vx, vy, r, X, Y, psi) with (cp, sp) = (cos, sin) e_psi; the
+    // curvature samples are passed to the kernels that need them (a pointer
+    // member here would change the register allocation of every kernel)
     int state_kind;
-    const float* kappa;          // n_track + 1 curvature samples (the last repeats the first)
     float kap_scale;             // n_track / L
     float track_len, inv_len;    // L, 1 / L
 };

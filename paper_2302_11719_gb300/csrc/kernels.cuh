@@ -21,10 +21,10 @@ size_t rollout_smem_bytes(int n_track, int T);
 int rollout_blocks(const DevParams& P);
 // Rollouts of the curvilinear state (curv.cu; state_kind 1), same outputs as
 // launch_rollout (no nearest segment).
-cudaError_t launch_rollout_curv(const DevParams& P, bool dump, const float* x0, const float* V,
-                                uint32_t iter, uint32_t ctr3, const uint32_t* iter_dev,
-                                float* S_out, float* traj, float* blk_min, unsigned* status,
-                                cudaStream_t st);
+cudaError_t launch_rollout_curv(const DevParams& P, const float* kappa, bool dump, const float* x0,
+                                const float* V, uint32_t iter, uint32_t ctr3,
+                                const uint32_t* iter_dev, float* S_out, float* traj,
+                                float* blk_min, unsigned* status, cudaStream_t st);
 // Rollouts: S_out [K] and blk_min [rollout_blocks(P)]; traj (optional dump);
 // seg0_out (optional): nearest segment of x0.  rec: segment-pair table of
 // launch_rec_table.
@@ -81,6 +81,7 @@ struct ApplyArgs {
     float* V;                  // in/out: shifted V+
     uint32_t n, ctr3;          // disturbance index and counter word
     uint32_t* iter_dev;        // graph replays: n += *iter_dev, then ++*iter_dev
+    const float* kappa;        // curvature samples (state_kind 1)
 };
 
 cudaError_t launch_seg0(const DevParams& P, const float4* rec, int n_seq,

@@ -583,9 +583,6 @@ cudaError_t launch_rollout(const DevParams& P, bool dump, const float* x0, const
                            const float4* rec, uint32_t iter, uint32_t ctr3,
                            const uint32_t* iter_dev, float* S_out, float* traj, float* blk_min,
                            int* seg0_out, unsigned* status, cudaStream_t st) {
-    if (P.state_kind == 1)
-        return launch_rollout_curv(P, dump, x0, V, iter, ctr3, iter_dev, S_out, traj, blk_min,
-                                   status, st);
     if (packed_rollout(P)) {
         const size_t smem = rec_table_bytes(P.n_track) + (size_t)P.T * 2 * sizeof(float4);
         auto kern = dump ? mppi_rollout2_kernel<true> : mppi_rollout2_kernel<false>;

@@ -415,7 +415,7 @@ __device__ void closed_loop_step(const DevParams& P, const ApplyArgs& ap, float2
     const uint32_t nn = ap.n + (ap.iter_dev ? *ap.iter_dev : 0u);
     State x = make_state(ap.x0);
     if (P.state_kind == 1)
-        model_step_curv(P, P.kappa, x, clampf(v_exec.x, P.umin0, P.umax0),
+        model_step_curv(P, ap.kappa, x, clampf(v_exec.x, P.umin0, P.umax0),
                         clampf(v_exec.y, P.umin1, P.umax1));
     else
         model_step(P, x, clampf(v_exec.x, P.umin0, P.umax0), clampf(v_exec.y, P.umin1, P.umax1));
