@@ -137,6 +137,25 @@ def test_repair_near_boundary_batch(S, orc, seqs):
     assert flips <= n // 8
 
 
+@pytest.mark.parametrize("T,N_r", [(40, 0), (1, 1)])
+def test_repair_degenerate_horizons(S, orc, T, N_r):
+    # N_r = 0: the objective of Eq. 22 is an empty sum, so P = 0 and nothing
+    # changes; T = N_r = 1: a one-step repair
+    pr = I.single_problem(K=64, T=T, N_r=N_r)
+    rng = np.random.default_rng(T)
+    x0 = np.tile(I.centreline_start(20.0, 12.0, 7.0), (4, 1))
+    x0[:, 4] += np.array([1.9, -1.9, 1.0, 0.0], np.float32)
+    V = np.stack([np.tile([[0.45, 1.0]], (T, 1)), np.tile([[-0.45, 1.0]], (T, 1)),
+                  rng.uniform(-0.5, 0.5, (T, 2)), np.zeros((T, 2))]).astype(np.float32)
+    flips, worst = repair_compare(S, orc, pr.params, pr.track, x0, V, 5)
+    assert flips == 0 and worst <= V_REP, (flips, worst)
+    if N_r == 0:
+        m = orc.Model(pr.params, pr.track)
+        for i in range(4):
+            Vo, mo, so, io = orc.repair(m, x0[i], V[i], 5)
+            assert io == 0 and np.all(mo == 0.0) and np.array_equal(Vo, V[i].astype(np.float64))
+
+
 def test_fixed_step_repair(S, orc, seqs):
     n = 8
     ctl = S.Controller(seqs.params, seqs.track, max_seq=n)

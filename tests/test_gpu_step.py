@@ -149,6 +149,41 @@ def test_long_horizon_reported(S, orc):
     assert rel_err(Sg, So) <= 1e-3
 
 
+def test_max_horizon(S, orc):
+    # T = SMPPI_MAX_T = 512: the error is reported and held to the T = 200 gate
+    pr = I.single_problem(K=256, T=512)
+    V = (0.05 * np.random.default_rng(5).uniform(-1, 1, (512, 2))).astype(np.float32)
+    Sg, Vg, _ = run_step(S, pr, it=1, V=V)
+    m, So, Vp, om, eps = oracle_step(orc, pr, 1, V=V)
+    print("T=512 max rel S err %.3e, max |V+ err| %.3e" % (rel_err(Sg, So), np.abs(Vg - Vp).max()))
+    assert rel_err(Sg, So) <= 1e-3
+    assert np.abs(Vg - Vp).max() <= 1e-3
+
+
+def test_max_rollouts(S, orc):
+    # K = 2^22 (the largest K a handle accepts), T = 20: every cost against the
+    # oracle's, and V+ within the update bound
+    K, T = 1 << 22, 20
+    pr = I.single_problem(K=K, T=T)
+    Sg, Vg, _ = run_step(S, pr, it=4)
+    m = orc.Model(pr.params, pr.track)
+    So, Vp = orc.mppi_step(m, pr.x0, pr.V, 4, 0, nthreads=orc.max_threads())
+    assert rel_err(Sg, So) <= S_REL
+    # the update bound over the rollouts that carry weight; the rest (total
+    # weight w_rest) add at most 2 w_rest tau_max (|eps|_max + |dV|) to it
+    _, om = orc.update(m, So, pr.V, 4, 0)
+    ks = np.nonzero(om > 1e-10)[0]
+    eps = orc.noise_block(m, 4, 0, ks, T)
+    tol = update_bound(So[ks], eps, om[ks], Vp, pr.V, pr.params["lam"])
+    tau_max = S_REL * (np.abs(So).max() + 1.0) / pr.params["lam"]
+    eps_max = np.sqrt(2 * 24 * np.log(2.0)) * max(pr.params["sigma"])
+    tol += 2.0 * (1.0 - om[ks].sum()) * tau_max * (eps_max + np.abs(Vp - pr.V).max())
+    err = np.abs(Vg - Vp)
+    assert np.all(err <= tol), (err.max(), tol.min())
+    print("K=2^22 T=20: max rel S err %.2e, max |V+ err| %.2e (%d weighted rollouts)"
+          % (rel_err(Sg, So), err.max(), len(ks)))
+
+
 def test_degenerate_updates(S, orc):
     base = I.single_step_small()
     V = np.full((base.T, 2), [0.1, 0.2], np.float32)
