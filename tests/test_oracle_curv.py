@@ -12,7 +12,11 @@ the paper's AutoRally model, Sec. VI-A; readings c28, c29).
     (s, e_y, e_psi) (the Cartesian state converted exactly), with a difference
     that halves with dt (the two explicit Euler schemes agree to first order);
     the velocity states are identical;
-  * the rollout cost takes e_y^2 from the state's own e_y.
+  * the rollout cost takes e_y^2 from the state's own e_y;
+  * the dual-number gradient of the repair objective through the Frenet
+    kinematics and kappa(s) equals central finite differences away from the
+    kinks, and the Armijo repair on the curvilinear state never increases the
+    merit and makes most near-edge sequences safe.
 """
 import numpy as np
 import pytest
@@ -96,3 +100,66 @@ def test_curvilinear_cost_uses_e_y(orc):
     ctrl = gam * np.sum(V * V / sig ** 2)
     assert S == pytest.approx(q.sum() + cbf.sum() + ctrl, rel=1e-12)
     assert np.max(np.abs(traj[:, 4])) > 0.5          # e_y enters, not a polyline distance
+
+
+def _curv_sequences(n=8, T=40, seed=3):
+    """Curvilinear starts near the track edge heading toward it, and smooth
+    control sequences that steer further out (the repair's inputs)."""
+    pr = I.single_problem(K=1, T=T)
+    p = _curv(pr.params)
+    rng = np.random.default_rng(seed)
+    x0s, Vs = [], []
+    for i in range(n):
+        side = 1.0 if i % 2 == 0 else -1.0
+        x0s.append([rng.uniform(5, 8), 0.0, 0.0, rng.uniform(0, 60), side * rng.uniform(1.4, 1.8),
+                    side * 0.08])
+        steer = side * 0.06 + 0.04 * rng.standard_normal(T)
+        thr = 0.2 + 0.2 * rng.standard_normal(T)
+        Vs.append(np.clip(np.stack([steer, thr], 1), [-0.45, -0.9], [0.45, 0.9]))
+    return p, pr.track, np.array(x0s), np.array(Vs)
+
+
+def _fd(orc, m, x0, V, w_run, w_cbf, h=1e-4):
+    g = np.zeros_like(V)
+    for t in range(V.shape[0]):
+        for j in range(2):
+            Vp, Vm = V.copy(), V.copy()
+            Vp[t, j] += h
+            Vm[t, j] -= h
+            g[t, j] = (orc.cost(m, x0, Vp, None, w_run, w_cbf) -
+                       orc.cost(m, x0, Vm, None, w_run, w_cbf)) / (2 * h)
+    return g
+
+
+def test_curvilinear_gradient_matches_fd(orc):
+    # the dual-number gradient through the Frenet kinematics and kappa(s), away from
+    # the kinks of max(0, .) (reading c12)
+    p, tr, x0s, Vs = _curv_sequences()
+    m = orc.Model(p, tr)
+    a1 = 1 - float(np.float32(p["alpha"]))
+    w2 = float(np.float32(p["half_width"])) ** 2
+    checked = 0
+    for i in range(len(x0s)):
+        _, traj, _ = orc.rollout(m, x0s[i], Vs[i], noisy=False)
+        h = w2 - traj[:, 4] ** 2
+        if np.any(np.abs(a1 * h[:-1] - h[1:]) < 1e-3):
+            continue
+        for w_run, w_cbf in ((1.0, 0.0), (0.0, 1.0), (1.0, 1.0)):
+            _, g = orc.cost_grad(m, x0s[i], Vs[i], None, w_run, w_cbf)
+            gfd = _fd(orc, m, x0s[i], Vs[i], w_run, w_cbf)
+            assert np.linalg.norm(g - gfd) <= 1e-6 * max(1.0, np.linalg.norm(gfd)), (i, w_run, w_cbf)
+        checked += 1
+    assert checked >= 3
+
+
+def test_curvilinear_repair_monotone_and_effective(orc):
+    p, tr, x0s, Vs = _curv_sequences()
+    m = orc.Model(p, tr)
+    unsafe, safe_after = 0, 0
+    for i in range(len(x0s)):
+        Vr, mer, st, it = orc.repair(m, x0s[i], Vs[i], 10)
+        assert np.all(np.diff(mer) <= 0.0)
+        if mer[0] > 0:
+            unsafe += 1
+            safe_after += mer[-1] == 0.0
+    assert unsafe >= 4 and safe_after >= unsafe // 2
