@@ -101,8 +101,8 @@ typedef struct smppi_params {
                                  * s = arc length, e_y = lateral offset (left positive),
                                  * e_psi = heading error, on the centreline's curvature
                                  * kappa(s) (see below).  1 needs Ct = 1.5 and
-                                 * |steer| <= 1/2 and supports smppi_step, smppi_update,
-                                 * smppi_apply and smppi_debug_noise only. */
+                                 * |steer| <= 1/2; smppi_cost_grad, the BFGS repair
+                                 * (mode 2), the batch and smppi_step_noalloc refuse it. */
 } smppi_params;
 
 /* Curvilinear state (state_kind = 1):

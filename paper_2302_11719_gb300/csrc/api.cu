@@ -217,8 +217,6 @@ void toc(smppi_handle* h, cudaStream_t st, int kind, int i0) {
 
 smppi_status check_seq_call(smppi_handle* h, int n_seq) {
     if (!h) return fail(nullptr, SMPPI_ERR_ARG, "handle is NULL");
-    if (h->p.state_kind != 0)
-        return fail(h, SMPPI_ERR_ARG, "the repair and the adjoint need state_kind 0");
     if (n_seq < 1 || n_seq > h->p.max_seq)
         return fail(h, SMPPI_ERR_ARG, "n_seq must be in [1, max_seq]");
     return SMPPI_OK;
@@ -259,6 +257,13 @@ smppi_status enqueue_repair(smppi_handle* h, cudaStream_t st, int n_seq, const f
                             double* merit_out, int* iters_out, bool seg0_known,
                             const ApplyArgs& ap) {
     int ev;
+    if (h->p.state_kind == 1) {
+        ev = tic(h, st);
+        CU(h, launch_repair_curv(h->dp, h->kappa, n_seq, x0, V_in, V_out, n_iters, mode, delta,
+                                 merit_out, iters_out, ap, h->status, st));
+        toc(h, st, SMPPI_KERNEL_REPAIR, ev);
+        return SMPPI_OK;
+    }
     if (!seg0_known) {
         ev = tic(h, st);
         CU(h, launch_seg0(h->dp, h->rec, n_seq, x0, h->rws.seg0, st));
@@ -300,6 +305,18 @@ smppi_status enqueue_repair(smppi_handle* h, cudaStream_t st, int n_seq, const f
 smppi_status enqueue_shield(smppi_handle* h, cudaStream_t st, float* x0, float* V, float* Vs,
                             uint32_t iter, uint32_t instance, int n_repair, double* merit,
                             uint32_t* iter_dev) {
+    if (h->p.state_kind == 1) {
+        // curvilinear state: the MPPI iteration (V <- V+), then the shield of V+ into
+        // Vs, whose block also takes the closed-loop step and shifts V
+        smppi_status s = enqueue_step(h, st, x0, V, iter, instance, nullptr, nullptr, iter_dev);
+        if (s != SMPPI_OK) return s;
+        const ApplyArgs ap{x0, V, iter, (instance << 8) | 1u, iter_dev, h->kappa};
+        const int ev = tic(h, st);
+        CU(h, launch_repair_curv(h->dp, h->kappa, 1, x0, V, Vs, n_repair, 1, 0.0f, merit, nullptr,
+                                 ap, h->status, st));
+        toc(h, st, SMPPI_KERNEL_REPAIR, ev);
+        return SMPPI_OK;
+    }
     if (n_repair > 0) {
         smppi_status s = enqueue_rollout(h, st, x0, V, iter, instance, h->S_ws, nullptr, iter_dev);
         if (s != SMPPI_OK) return s;
@@ -482,6 +499,7 @@ smppi_status smppi_cost_grad(smppi_handle* h, int n_seq, const float* x0, const 
     smppi_status s = check_seq_call(h, n_seq);
     if (s != SMPPI_OK) return s;
     if (!x0 || !V || !grad_out) return fail(h, SMPPI_ERR_ARG, "x0, V, grad_out must not be NULL");
+    if (h->p.state_kind != 0) return fail(h, SMPPI_ERR_ARG, "smppi_cost_grad needs state_kind 0");
     if (N < 0 || N > h->p.T) return fail(h, SMPPI_ERR_ARG, "N must be in [0, T]");
     if (!std::isfinite(w_run) || !std::isfinite(w_cbf)) return fail(h, SMPPI_ERR_ARG, "weights must be finite");
     if (checkpoint > h->p.T) return fail(h, SMPPI_ERR_ARG, "checkpoint must be <= T");
@@ -532,6 +550,7 @@ smppi_status smppi_repair(smppi_handle* h, int n_seq, const float* x0, const flo
     if (!x0 || !V_in || !V_out) return fail(h, SMPPI_ERR_ARG, "x0, V_in, V_out must not be NULL");
     if (n_iters < 0 || n_iters > 100000) return fail(h, SMPPI_ERR_ARG, "n_iters must be in [0, 1e5]");
     if (mode != 0 && mode != 1 && mode != 2) return fail(h, SMPPI_ERR_ARG, "mode must be 0, 1 or 2");
+    if (mode == 2 && h->p.state_kind != 0) return fail(h, SMPPI_ERR_ARG, "the BFGS repair needs state_kind 0");
     if (mode == 0 && !(std::isfinite(delta) && delta >= 0)) return fail(h, SMPPI_ERR_ARG, "delta must be >= 0");
     const ApplyArgs none{nullptr, nullptr, 0u, 0u, nullptr};
     return enqueue_repair(h, h->st, n_seq, x0, V_in, V_out, n_iters, mode, delta, merit_out,
@@ -554,7 +573,6 @@ smppi_status smppi_shield_update(smppi_handle* h, float* x0, float* V, float* V_
                                  uint32_t iter, uint32_t instance, int n_repair,
                                  double* merit_out, int host_buffers) {
     if (!h) return fail(nullptr, SMPPI_ERR_ARG, "handle is NULL");
-    if (h->p.state_kind != 0) return fail(h, SMPPI_ERR_ARG, "the shield needs state_kind 0");
     if (!x0 || !V || !V_safe) return fail(h, SMPPI_ERR_ARG, "x0, V, V_safe must not be NULL");
     if (n_repair < 0 || n_repair > 100000) return fail(h, SMPPI_ERR_ARG, "n_repair must be in [0, 1e5]");
     if (instance >= (1u << 24)) return fail(h, SMPPI_ERR_ARG, "instance must be < 2^24");
@@ -590,7 +608,6 @@ smppi_status smppi_shield_update(smppi_handle* h, float* x0, float* V, float* V_
 smppi_status smppi_shield_loop(smppi_handle* h, float* x0, float* V, float* V_safe,
                                uint32_t iter0, uint32_t instance, int n_repair, int n_updates) {
     if (!h) return fail(nullptr, SMPPI_ERR_ARG, "handle is NULL");
-    if (h->p.state_kind != 0) return fail(h, SMPPI_ERR_ARG, "the shield needs state_kind 0");
     if (!x0 || !V || !V_safe) return fail(h, SMPPI_ERR_ARG, "x0, V, V_safe must not be NULL");
     if (n_repair < 0 || n_repair > 100000 || n_updates < 0)
         return fail(h, SMPPI_ERR_ARG, "n_repair in [0, 1e5], n_updates >= 0");

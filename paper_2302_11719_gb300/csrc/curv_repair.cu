@@ -1,0 +1,308 @@
+// Safety shield (Alg. 1, Eq. 22) on the curvilinear state (state_kind 1;
+// smppi.h): the merit P = C sum_{t<N_r} max{(1 - alpha) h_t - h_{t+1}, 0} with
+// h = w^2 - e_y^2 (Eq. 17, 23), its gradient by a reverse-mode adjoint of the
+// curvilinear model step over a full tape of the N_r states (no recomputation:
+// 9 floats per state fit in shared memory for any T), projected gradient with
+// Armijo backtracking (mode 1) or the fixed step of Alg. 1 (mode 0).
+//
+// One block per sequence: thread 0 runs the forward pass and the adjoint, the
+// lanes of warp 0 evaluate the trial steps s, s/2, ... in parallel and the
+// largest accepted step is taken (the same iterate as sequential
+// backtracking).  The merit accumulates in float32 over blocks of 16 steps and
+// float64 across them.  The closed-loop step (Eq. 26) may follow in the tail
+// of the block of sequence 0.
+#include "shield.cuh"
+
+namespace smppi {
+namespace {
+
+constexpr int CR_BLK = 128;
+constexpr int CR_NF = 9;   // tape fields per state: v_x v_y r s e_y e_psi cos sin h
+
+__device__ __forceinline__ void tape_put(float* tp, int t, const State& x, float h) {
+    float* r = tp + (size_t)t * CR_NF;
+    r[0] = x.vx; r[1] = x.vy; r[2] = x.r; r[3] = x.X; r[4] = x.Y; r[5] = x.psi;
+    r[6] = x.cp; r[7] = x.sp; r[8] = h;
+}
+__device__ __forceinline__ State tape_state(const float* tp, int t) {
+    const float* r = tp + (size_t)t * CR_NF;
+    State x;
+    x.vx = r[0]; x.vy = r[1]; x.r = r[2]; x.X = r[3]; x.Y = r[4]; x.psi = r[5];
+    x.cp = r[6]; x.sp = r[7];
+    return x;
+}
+
+// Slope of kappa(s) on the interval of the samples that kappa_at uses.
+__device__ __forceinline__ float kappa_slope(const DevParams& P, const float* kt, float s) {
+    const float sw = fmaf(floorf(s * P.inv_len), -P.track_len, s);
+    const int i = min(max((int)(sw * P.kap_scale), 0), P.n_track - 1);
+    return (kt[i + 1] - kt[i]) * P.kap_scale;
+}
+
+// Merit of Vw (TRIAL: of clip(Vw - step G), with dec = G . (Vw - u')) from x0
+// over N steps; STORE: the states and h into the tape (N + 1 rows).
+template <bool STORE, bool TRIAL>
+__device__ double curv_forward(const DevParams& P, const float* kt, const State& x0, int N,
+                               const float2* Vw, const float2* G, float step, float* tape,
+                               double* dec_out) {
+    State x = x0;
+    float h_prev = P.w2 - x.Y * x.Y;
+    double J = 0.0, dec = 0.0;
+    float Jf = 0.0f, decf = 0.0f;
+    if (STORE) tape_put(tape, 0, x, h_prev);
+    for (int t = 0; t < N; ++t) {
+        const float2 v = Vw[t];
+        float2 u;
+        if (TRIAL) {
+            const float2 g = G[t];
+            u = clamp2(P, make_float2(fmaf(-step, g.x, v.x), fmaf(-step, g.y, v.y)));
+            decf = fmaf(g.x, v.x - u.x, fmaf(g.y, v.y - u.y, decf));
+        } else {
+            u = clamp2(P, v);
+        }
+        model_step_curv(P, kt, x, u.x, u.y);
+        const float h = P.w2 - x.Y * x.Y;
+        const float a = cbf_arg(P, h_prev, h);
+        Jf = (a > 0.0f) ? fmaf(P.C_cbf, a, Jf) : Jf;
+        h_prev = h;
+        if (STORE) tape_put(tape, t + 1, x, h);
+        if (((t + 1) & 15) == 0) {
+            J += (double)Jf;
+            dec += (double)decf;
+            Jf = 0.0f;
+            decf = 0.0f;
+        }
+    }
+    J += (double)Jf;
+    dec += (double)decf;
+    if (dec_out) *dec_out = dec;
+    return J;
+}
+
+// Adjoint of one curvilinear model step (model_step_curv): lb = dP/dx_{t+1} on
+// entry, dP/dx_t (through the step only) on exit; *gd, *ga = dP/du_t.  The
+// velocity part is the Cartesian model's (model_step_adjoint); the kinematics
+//   s' = s + dt num / den,  num = v_x cos e_psi - v_y sin e_psi,
+//   den = max(1 - kappa(s) e_y, 0.1),  e_y' = e_y + dt (v_x sin e_psi + v_y cos e_psi),
+//   e_psi' = e_psi + dt (r - kappa(s) num / den)
+// are differentiated with cos, sin e_psi as functions of e_psi.
+__device__ void model_step_adjoint_curv(const DevParams& P, const float* kt, const State& x,
+                                        float d, State& lb, float* gd, float* ga) {
+    const float yf = fmaf(P.lf, x.r, x.vy), yr = fmaf(-P.lr, x.r, x.vy);
+    const float bf = atan2_poly(yf, x.vx), br = atan2_poly(yr, x.vx);
+    const float af = d - bf, ar = -br;
+    float dphf, dphr;
+    const float Fyf = P.Fzf * tyre_shape(P, P.B * af, &dphf);
+    tyre_shape(P, P.B * ar, &dphr);
+    float sd, cd;
+    sincos_half(d, &sd, &cd);
+    const float cp = x.cp, sp = x.sp;
+    const float k = kappa_at(P, kt, x.X);
+    const float den_raw = fmaf(-k, x.Y, 1.0f);
+    const float den = fmaxf(den_raw, 0.1f);
+    const float num = x.vx * cp - x.vy * sp;
+    const float sdot = num / den;
+
+    const float gvx = P.dt * lb.vx, gvy = P.dt * lb.vy, gr = P.dt * lb.r;
+    const float gs = P.dt * lb.X, gey = P.dt * lb.Y, gep = P.dt * lb.psi;
+    State o = lb;   // identity part of x + dt F
+    // e_psi' : e_psi_dot = r - kappa sdot
+    o.r += gep;
+    float kb = -gep * sdot;
+    const float sdotb = gs - gep * k;
+    // e_y' : e_y_dot = v_x sin e_psi + v_y cos e_psi
+    o.vx += gey * sp;
+    o.vy += gey * cp;
+    float spb = gey * x.vx, cpb = gey * x.vy;
+    // s' : sdot = num / den
+    const float numb = sdotb / den, denb = -sdotb * sdot / den;
+    o.vx += numb * cp;
+    o.vy -= numb * sp;
+    cpb += numb * x.vx;
+    spb -= numb * x.vy;
+    if (den_raw > 0.1f) {   // den = 1 - kappa e_y (the guard has no derivative)
+        kb -= denb * x.Y;
+        o.Y -= denb * k;
+    }
+    o.X += kb * kappa_slope(P, kt, x.X);
+    o.psi += spb * cp - cpb * sp;
+    // velocity part: dvx = (Fx - Fyf sd)/m + vy r
+    const float Fxb = gvx * P.m_inv;
+    float Fyfb = -gvx * sd * P.m_inv;
+    float db = -gvx * Fyf * cd * P.m_inv;
+    o.vy += gvx * x.r;
+    o.r += gvx * x.vy;
+    // dvy = (Fyr + Fyf cd)/m - vx r
+    float Fyrb = gvy * P.m_inv;
+    Fyfb += gvy * cd * P.m_inv;
+    db -= gvy * Fyf * sd * P.m_inv;
+    o.vx -= gvy * x.r;
+    o.r -= gvy * x.vx;
+    // dr = (lf Fyf cd - lr Fyr)/Iz
+    Fyfb += gr * P.lf * cd * P.Iz_inv;
+    db -= gr * P.lf * Fyf * sd * P.Iz_inv;
+    Fyrb -= gr * P.lr * P.Iz_inv;
+    // tyres and slip angles
+    const float afb = Fyfb * P.Fzf * dphf * P.B;
+    const float arb = Fyrb * P.Fzr * dphr * P.B;
+    db += afb;
+    const float bfb = -afb, brb = -arb;
+    const float nf = fmaf(x.vx, x.vx, yf * yf), nr = fmaf(x.vx, x.vx, yr * yr);
+    const float yfb = nf > 0.0f ? bfb * x.vx / nf : 0.0f;
+    const float yrb = nr > 0.0f ? brb * x.vx / nr : 0.0f;
+    if (nf > 0.0f) o.vx -= bfb * yf / nf;
+    if (nr > 0.0f) o.vx -= brb * yr / nr;
+    o.vy += yfb + yrb;
+    o.r += P.lf * yfb - P.lr * yrb;
+    lb = o;
+    *gd = db;
+    *ga = P.fx_gain * Fxb;
+}
+
+// Gradient G of the merit of Vw (one thread): forward pass with the tape, then
+// the adjoint from x_N back to x_0.  G_t = 0 for N <= t < T and outside the box.
+__device__ double curv_merit_grad(const DevParams& P, const float* kt, const State& x0, int N,
+                                  int T, const float2* Vw, float2* G, float* tape) {
+    const double J = curv_forward<true, false>(P, kt, x0, N, Vw, nullptr, 0.0f, tape, nullptr);
+    for (int t = N; t < T; ++t) G[t] = make_float2(0.0f, 0.0f);
+    if (N == 0) return J;
+    State lam = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    auto h_at = [&](int t) { return tape[(size_t)t * CR_NF + 8]; };
+    // direct term of h_t (t >= 1): -C act(t-1, t) dh_t + C (1 - alpha) act(t, t+1) dh_t,
+    // dh_t / de_y = -2 e_y
+    auto direct = [&](int t) {
+        const float ey = tape[(size_t)t * CR_NF + 4];
+        const bool a0 = cbf_arg(P, h_at(t - 1), h_at(t)) > 0.0f;
+        const bool a1 = (t < N) && cbf_arg(P, h_at(t), h_at(t + 1)) > 0.0f;
+        const float w = (a0 ? -P.C_cbf : 0.0f) + (a1 ? P.C_cbf * P.one_m_alpha : 0.0f);
+        lam.Y += w * (-2.0f * ey);
+    };
+    direct(N);
+    for (int t = N - 1; t >= 0; --t) {
+        const State x = tape_state(tape, t);
+        const float2 v = Vw[t];
+        const float2 u = clamp2(P, v);
+        float gd, ga;
+        model_step_adjoint_curv(P, kt, x, u.x, lam, &gd, &ga);
+        const bool in0 = v.x >= P.umin0 && v.x <= P.umax0;
+        const bool in1 = v.y >= P.umin1 && v.y <= P.umax1;
+        G[t] = make_float2(in0 ? gd : 0.0f, in1 ? ga : 0.0f);
+        if (t >= 1) direct(t);
+    }
+    return J;
+}
+
+struct CurvSmem {
+    double P;
+    float red[CR_BLK / 32];
+    float step;
+    int ok;
+};
+
+}  // namespace
+
+__global__ void __launch_bounds__(CR_BLK) curv_repair_kernel(
+    DevParams P, const float* __restrict__ kappa, const float* __restrict__ x0g, const float* Vin,
+    float* Vout, int n_iters, int mode, float delta, double* __restrict__ merit_out,
+    int* __restrict__ iters_out, ApplyArgs ap, unsigned* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int T = P.T, N = P.N_r, n = P.n_track;
+    float2* Vw = reinterpret_cast<float2*>(smem_raw);
+    float2* G = Vw + T;
+    float* kt = reinterpret_cast<float*>(G + T);
+    float* tape = kt + ((n + 1 + 3) & ~3);
+    __shared__ CurvSmem sm;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = CR_BLK / 32;
+    const int q = blockIdx.x;
+    const float2* vin = reinterpret_cast<const float2*>(Vin) + (size_t)q * T;
+    for (int t = tid; t < T; t += CR_BLK) Vw[t] = vin[t];
+    for (int i = tid; i <= n; i += CR_BLK) kt[i] = kappa[i];
+    const State x0 = make_state(x0g + 6 * q);
+    __syncthreads();
+    double* mrow = merit_out ? merit_out + (size_t)q * (n_iters + 1) : nullptr;
+    if (tid == 0) sm.P = curv_forward<false, false>(P, kt, x0, N, Vw, nullptr, 0.0f, nullptr, nullptr);
+    __syncthreads();
+    double P0 = sm.P;
+    int it = 0;
+    bool stalled = false;
+    for (; it < n_iters; ++it) {
+        if (tid == 0 && mrow) mrow[it] = P0;
+        if (P0 == 0.0) break;
+        if (tid == 0) curv_merit_grad(P, kt, x0, N, T, Vw, G, tape);
+        __syncthreads();
+        if (mode == 0) {
+            for (int t = tid; t < N; t += CR_BLK)
+                Vw[t] = clamp2(P, make_float2(fmaf(-delta, G[t].x, Vw[t].x),
+                                              fmaf(-delta, G[t].y, Vw[t].y)));
+            __syncthreads();
+            if (tid == 0)
+                sm.P = curv_forward<false, false>(P, kt, x0, N, Vw, nullptr, 0.0f, nullptr, nullptr);
+            __syncthreads();
+            P0 = sm.P;
+            continue;
+        }
+        float gm = 0.0f;
+        for (int t = tid; t < N; t += CR_BLK) gm = fmaxf(gm, fmaxf(fabsf(G[t].x), fabsf(G[t].y)));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) gm = fmaxf(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+        if (lane == 0) sm.red[warp] = gm;
+        __syncthreads();
+        gm = sm.red[0];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) gm = fmaxf(gm, sm.red[w]);
+        if (!(gm > 0.0f)) { stalled = true; break; }
+        const float s_first = P.ls_s0 / gm;
+        if (warp == 0) {
+            int best = 0x7fffffff;
+            double best_P = 0.0;
+            for (int j = lane; j < P.ls_max; j += 32) {
+                const float sj = ldexpf(s_first, -j);
+                double dec;
+                const double Pt = curv_forward<false, true>(P, kt, x0, N, Vw, G, sj, nullptr, &dec);
+                if (Pt <= P0 - (double)P.ls_c * dec && j < best) { best = j; best_P = Pt; }
+            }
+            int bj = best;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) bj = min(bj, __shfl_xor_sync(0xffffffffu, bj, o));
+            if (best == bj && bj != 0x7fffffff) {
+                sm.P = best_P;
+                sm.step = ldexpf(s_first, -bj);
+            }
+            if (lane == 0) sm.ok = (bj != 0x7fffffff);
+        }
+        __syncthreads();
+        if (!sm.ok) { stalled = true; break; }
+        const float sa = sm.step;
+        for (int t = tid; t < N; t += CR_BLK)
+            Vw[t] = clamp2(P, make_float2(fmaf(-sa, G[t].x, Vw[t].x), fmaf(-sa, G[t].y, Vw[t].y)));
+        __syncthreads();
+        P0 = sm.P;
+    }
+    if (tid == 0) {
+        if (mrow)
+            for (int i = it; i <= n_iters; ++i) mrow[i] = P0;
+        if (iters_out) iters_out[q] = it;
+        if (stalled) atomicOr(status, SMPPI_DEV_STALLED);
+        if (!isfinite(P0)) atomicOr(status, SMPPI_DEV_NUMERIC);
+    }
+    __syncthreads();
+    float2* vout = reinterpret_cast<float2*>(Vout) + (size_t)q * T;
+    for (int t = tid; t < T; t += CR_BLK) vout[t] = Vw[t];
+    if (q == 0 && tid == 0 && ap.x0) closed_loop_step(P, ap, Vw[0]);
+}
+
+cudaError_t launch_repair_curv(const DevParams& P, const float* kappa, int n_seq,
+                               const float* x0, const float* V_in, float* V_out, int n_iters,
+                               int mode, float delta, double* merit_out, int* iters_out,
+                               const ApplyArgs& ap, unsigned* status, cudaStream_t st) {
+    const size_t smem = (size_t)P.T * 16 + (size_t)((P.n_track + 1 + 3) & ~3) * 4 +
+                        (size_t)(P.T + 1) * CR_NF * 4;
+    cudaError_t e = ensure_smem((const void*)curv_repair_kernel, smem);
+    if (e != cudaSuccess) return e;
+    curv_repair_kernel<<<n_seq, CR_BLK, smem, st>>>(P, kappa, x0, V_in, V_out, n_iters, mode,
+                                                    delta, merit_out, iters_out, ap, status);
+    return cudaGetLastError();
+}
+
+}  // namespace smppi

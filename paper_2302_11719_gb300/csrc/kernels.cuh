@@ -97,6 +97,13 @@ cudaError_t launch_repair(const DevParams& P, const float4* rec,
 cudaError_t launch_apply(const DevParams& P, const ApplyArgs& ap, const float* V_exec,
                          cudaStream_t st);
 
+// Shield on the curvilinear state (curv_repair.cu; state_kind 1): modes 0 and 1
+// of smppi_repair, one block per sequence, optional closed-loop tail (ap).
+cudaError_t launch_repair_curv(const DevParams& P, const float* kappa, int n_seq,
+                               const float* x0, const float* V_in, float* V_out, int n_iters,
+                               int mode, float delta, double* merit_out, int* iters_out,
+                               const ApplyArgs& ap, unsigned* status, cudaStream_t st);
+
 // BFGS repair (bfgs.cu): bfgs_grid() blocks of *wpb warps, one sequence per
 // warp at a time; the workspace (bfgs_ws_bytes()) holds a work counter and an
 // H slice of (2 N_r)^2 floats per warp slot.

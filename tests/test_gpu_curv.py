@@ -7,7 +7,11 @@ paper's AutoRally model, Sec. VI-A; readings c28, c29) against the FP64 oracle.
   * ragged sizes (K not a multiple of the block, odd T) and the full-size
     K = 65536, T = 100 launch (sampled rollouts, V+);
   * the closed-loop step (Eq. 26) on the curvilinear state;
-  * the repair, adjoint, shield and batch entry points refuse state_kind 1.
+  * the shield (Alg. 1, modes 1 and 0) on near-edge curvilinear sequences and
+    one whole Shield-MPPI update (rollouts, softmin, repair of V+, closed-loop
+    step) against the oracle, repaired controls within V_REP unless a
+    line-search decision differs between float32 and float64 (a flip);
+  * smppi_cost_grad and the BFGS repair refuse state_kind 1.
 Tolerances: tests/gpu_helpers.py.
 """
 import numpy as np
@@ -17,7 +21,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from paper_2302_11719_gb300 import inputs as I  # noqa: E402
-from tests.gpu_helpers import S_REL, X_REL, rel_err, update_bound  # noqa: E402
+from tests.gpu_helpers import (S_REL, V_REP, X_REL, rel_err, repair_compare,  # noqa: E402
+                                update_bound)
 
 
 @pytest.fixture(scope="module")
@@ -107,13 +112,113 @@ def test_curv_apply(S, orc):
     ctl.close()
 
 
+def near_edge(n=16, T=40, seed=3):
+    """Curvilinear starts near the track edge heading toward it, with smooth
+    controls that steer further out (the shield's inputs)."""
+    pr = curv_problem(1, T)
+    rng = np.random.default_rng(seed)
+    x0s, Vs = [], []
+    for i in range(n):
+        side = 1.0 if i % 2 == 0 else -1.0
+        x0s.append([rng.uniform(5, 8), 0.0, 0.0, rng.uniform(0, 60), side * rng.uniform(1.4, 1.8),
+                    side * 0.08])
+        steer = side * 0.06 + 0.04 * rng.standard_normal(T)
+        thr = 0.2 + 0.2 * rng.standard_normal(T)
+        Vs.append(np.clip(np.stack([steer, thr], 1), [-0.45, -0.9], [0.45, 0.9]))
+    return pr, np.array(x0s, np.float32), np.array(Vs, np.float32)
+
+
+@pytest.mark.parametrize("mode", [1, 0])
+def test_curv_repair_vs_oracle(S, orc, mode):
+    pr, x0s, Vs = near_edge()
+    if mode == 1:
+        flips, worst = repair_compare(S, orc, pr.params, pr.track, x0s, Vs, 10)
+        print("curvilinear repair (16 sequences, 10 Armijo iterations): %d flips, worst |dV| %.2e"
+              % (flips, worst))
+        assert worst <= V_REP and flips <= len(x0s) // 8
+        return
+    n = len(x0s)
+    ctl = S.Controller(pr.params, pr.track, max_seq=n)
+    Vout = torch.empty((n, pr.T, 2), device="cuda")
+    S.smppi_repair(ctl.h, n, ctl.tensor(x0s), ctl.tensor(Vs), Vout, 1, 0, 1e-6)
+    assert ctl.sync_status()[0] == S.OK
+    m = orc.Model(pr.params, pr.track)
+    for i in range(n):
+        Vo = orc.repair(m, x0s[i], Vs[i], 1, mode=0, delta=1e-6)[0]
+        assert np.max(np.abs(Vout[i].cpu().numpy() - Vo)) <= V_REP
+    ctl.close()
+
+
+@pytest.mark.parametrize("ey,ep", [(1.7, 0.25), (-1.6, -0.3), (0.0, 0.0)])
+def test_curv_shield_update_vs_oracle(S, orc, ey, ep):
+    # one whole Shield-MPPI update on the curvilinear state from a start near the
+    # edge and heading out, against the oracle's mppi_step -> repair -> apply -> shift
+    pr = curv_problem(512, 50, (6.0, 0.0, 0.0, 5.0, ey, ep))
+    x0 = pr.x0
+    V = np.tile(np.array([[0.0, 0.3]], np.float32), (pr.T, 1))
+    it, inst = 3, 2
+    ctl = S.Controller(pr.params, pr.track)
+    xg, Vg, Vsg = ctl.tensor(x0), ctl.tensor(V), torch.empty((pr.T, 2), device="cuda")
+    mer_g = torch.empty(11, dtype=torch.float64, device="cuda")
+    S.smppi_shield_update(ctl.h, xg, Vg, Vsg, it, inst, 10, mer_g)
+    st, bits = ctl.sync_status()
+    assert st in (S.OK, S.ERR_STALLED), (st, bits)
+    m = orc.Model(pr.params, pr.track)
+    So, Vp = orc.mppi_step(m, x0, V, it, inst, nthreads=8)
+    Vsafe, mer, ost, its = orc.repair(m, x0, Vp.astype(np.float32), 10)
+    x1 = orc.apply(m, x0, Vsafe[0], it, inst)
+    print("curvilinear e_y %.1f: oracle repair iterations %d, merit %.4g -> %.4g"
+          % (ey, its, mer[0], mer[its]))
+    _, om = orc.update(m, So, V, it, inst)
+    eps = orc.noise_block(m, it, inst, range(m.K))
+    tol = update_bound(So, eps, om, Vp, V, pr.params["lam"])
+    tol_sh = np.concatenate([tol[1:], tol[-1:]])
+    assert np.all(np.abs(Vg.cpu().numpy() - orc.shift(m, Vp)) <= tol_sh)
+    assert np.max(np.abs(Vsg.cpu().numpy() - Vsafe)) <= V_REP
+    assert rel_err(xg.cpu().numpy(), x1) <= X_REL
+    assert mer_g.cpu().numpy()[0] == pytest.approx(mer[0], rel=S_REL, abs=1e-2)
+    ctl.close()
+
+
+def test_curv_shield_device_host_graph_agree(S):
+    pr = curv_problem(256, 30, (6.0, 0.0, 0.0, 5.0, 1.5, 0.2))
+    ctl = S.Controller(pr.params, pr.track)
+    ref = None
+    for how in ("device", "host", "graph"):
+        x0 = ctl.tensor(pr.x0)
+        V = ctl.tensor(pr.V)
+        Vs = torch.empty_like(V)
+        if how == "device":
+            for n in range(3):
+                S.smppi_shield_update(ctl.h, x0, V, Vs, n, 0, 5)
+            out = (x0.cpu().numpy(), V.cpu().numpy(), Vs.cpu().numpy())
+        elif how == "host":
+            hx, hV = pr.x0.copy(), pr.V.copy()
+            hVs = np.empty_like(hV)
+            for n in range(3):
+                S.smppi_shield_update(ctl.h, hx.ctypes.data, hV.ctypes.data, hVs.ctypes.data, n, 0,
+                                      5, None, True)
+            out = (hx, hV, hVs)
+        else:
+            S.smppi_shield_loop(ctl.h, x0, V, Vs, 0, 0, 5, 3)
+            out = (x0.cpu().numpy(), V.cpu().numpy(), Vs.cpu().numpy())
+        assert ctl.sync_status()[0] in (S.OK, S.ERR_STALLED)
+        if ref is None:
+            ref = out
+        else:
+            for a, b in zip(out, ref):
+                assert np.array_equal(a, b), how
+    ctl.close()
+
+
 def test_curv_refused_entry_points(S):
     pr = curv_problem(64, 20)
     ctl = S.Controller(pr.params, pr.track)
     x0, V = ctl.tensor(pr.x0), ctl.tensor(pr.V)
     Vs = torch.empty_like(V)
     with pytest.raises(RuntimeError):
-        S.smppi_repair(ctl.h, 1, x0, V, Vs, 5, 1)
+        S.smppi_repair(ctl.h, 1, x0, V, Vs, 5, 2)
+    J = torch.empty(1, dtype=torch.float64, device="cuda")
     with pytest.raises(RuntimeError):
-        S.smppi_shield_update(ctl.h, x0, V, Vs, 0, 0, 5)
+        S.smppi_cost_grad(ctl.h, 1, x0, V, 20, 0.0, 1.0, 0, J, Vs)
     ctl.close()
