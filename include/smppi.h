@@ -101,8 +101,9 @@ typedef struct smppi_params {
                                  * s = arc length, e_y = lateral offset (left positive),
                                  * e_psi = heading error, on the centreline's curvature
                                  * kappa(s) (see below).  1 needs Ct = 1.5 and
-                                 * |steer| <= 1/2; smppi_cost_grad, the BFGS repair
-                                 * (mode 2), the batch and smppi_step_noalloc refuse it. */
+                                 * |steer| <= 1/2; the BFGS repair (mode 2), the batch
+                                 * and smppi_step_noalloc refuse it; smppi_cost_grad
+                                 * keeps the whole trajectory (no checkpoints). */
 } smppi_params;
 
 /* Curvilinear state (state_kind = 1):

@@ -499,10 +499,16 @@ smppi_status smppi_cost_grad(smppi_handle* h, int n_seq, const float* x0, const 
     smppi_status s = check_seq_call(h, n_seq);
     if (s != SMPPI_OK) return s;
     if (!x0 || !V || !grad_out) return fail(h, SMPPI_ERR_ARG, "x0, V, grad_out must not be NULL");
-    if (h->p.state_kind != 0) return fail(h, SMPPI_ERR_ARG, "smppi_cost_grad needs state_kind 0");
     if (N < 0 || N > h->p.T) return fail(h, SMPPI_ERR_ARG, "N must be in [0, T]");
     if (!std::isfinite(w_run) || !std::isfinite(w_cbf)) return fail(h, SMPPI_ERR_ARG, "weights must be finite");
     if (checkpoint > h->p.T) return fail(h, SMPPI_ERR_ARG, "checkpoint must be <= T");
+    if (h->p.state_kind == 1) {   // full tape: the checkpoint interval does not apply
+        const int ev = tic(h, h->st);
+        CU(h, launch_cost_grad_curv(h->dp, h->kappa, n_seq, x0, V, N, w_run, w_cbf, J_out,
+                                    grad_out, h->status, h->st));
+        toc(h, h->st, SMPPI_KERNEL_COST_GRAD, ev);
+        return SMPPI_OK;
+    }
     const int ck = checkpoint == 0 ? h->p.checkpoint : (checkpoint < 0 ? 0 : checkpoint);
     int ev = tic(h, h->st);
     CU(h, launch_seg0(h->dp, h->rec, n_seq, x0, h->rws.seg0, h->st));

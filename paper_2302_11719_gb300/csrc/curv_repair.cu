@@ -39,16 +39,19 @@ __device__ __forceinline__ float kappa_slope(const DevParams& P, const float* kt
     return (kt[i + 1] - kt[i]) * P.kap_scale;
 }
 
-// Merit of Vw (TRIAL: of clip(Vw - step G), with dec = G . (Vw - u')) from x0
-// over N steps; STORE: the states and h into the tape (N + 1 rows).
+// J = w_run sum_{t=0}^{N} q(x_t) + w_cbf sum_{t<N} C max{(1-alpha) h_t - h_{t+1}, 0}
+// of Vw (TRIAL: of clip(Vw - step G), with dec = G . (Vw - u')) from x0 over N
+// steps; (0, 1) is the merit P.  STORE: the states and h into the tape (N + 1 rows).
 template <bool STORE, bool TRIAL>
 __device__ double curv_forward(const DevParams& P, const float* kt, const State& x0, int N,
                                const float2* Vw, const float2* G, float step, float* tape,
-                               double* dec_out) {
+                               double* dec_out, float w_run = 0.0f, float w_cbf = 1.0f) {
     State x = x0;
     float h_prev = P.w2 - x.Y * x.Y;
-    double J = 0.0, dec = 0.0;
+    double J = (w_run != 0.0f) ? (double)(w_run * run_cost(P, x.vx, x.Y * x.Y)) : 0.0;
+    double dec = 0.0;
     float Jf = 0.0f, decf = 0.0f;
+    const float wc = w_cbf * P.C_cbf;
     if (STORE) tape_put(tape, 0, x, h_prev);
     for (int t = 0; t < N; ++t) {
         const float2 v = Vw[t];
@@ -61,9 +64,11 @@ __device__ double curv_forward(const DevParams& P, const float* kt, const State&
             u = clamp2(P, v);
         }
         model_step_curv(P, kt, x, u.x, u.y);
-        const float h = P.w2 - x.Y * x.Y;
+        const float d2 = x.Y * x.Y;
+        const float h = P.w2 - d2;
+        if (w_run != 0.0f) Jf = fmaf(w_run, run_cost(P, x.vx, d2), Jf);
         const float a = cbf_arg(P, h_prev, h);
-        Jf = (a > 0.0f) ? fmaf(P.C_cbf, a, Jf) : Jf;
+        Jf = (a > 0.0f) ? fmaf(wc, a, Jf) : Jf;
         h_prev = h;
         if (STORE) tape_put(tape, t + 1, x, h);
         if (((t + 1) & 15) == 0) {
@@ -159,22 +164,31 @@ __device__ void model_step_adjoint_curv(const DevParams& P, const float* kt, con
     *ga = P.fx_gain * Fxb;
 }
 
-// Gradient G of the merit of Vw (one thread): forward pass with the tape, then
-// the adjoint from x_N back to x_0.  G_t = 0 for N <= t < T and outside the box.
+// Gradient G of J (w_run, w_cbf; (0, 1) = the merit) of Vw (one thread): forward
+// pass with the tape, then the adjoint from x_N back to x_0.  G_t = 0 for
+// N <= t < T and outside the box.
 __device__ double curv_merit_grad(const DevParams& P, const float* kt, const State& x0, int N,
-                                  int T, const float2* Vw, float2* G, float* tape) {
-    const double J = curv_forward<true, false>(P, kt, x0, N, Vw, nullptr, 0.0f, tape, nullptr);
+                                  int T, const float2* Vw, float2* G, float* tape,
+                                  float w_run = 0.0f, float w_cbf = 1.0f) {
+    const double J = curv_forward<true, false>(P, kt, x0, N, Vw, nullptr, 0.0f, tape, nullptr,
+                                               w_run, w_cbf);
     for (int t = N; t < T; ++t) G[t] = make_float2(0.0f, 0.0f);
     if (N == 0) return J;
     State lam = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     auto h_at = [&](int t) { return tape[(size_t)t * CR_NF + 8]; };
-    // direct term of h_t (t >= 1): -C act(t-1, t) dh_t + C (1 - alpha) act(t, t+1) dh_t,
+    // direct terms of x_t (t >= 1): w_run dq/dx_t (q = q_v (v_x - v*)^2 + q_d e_y^2 / w^2
+    // + C_obs 1(outside), Eq. 24-25) and w_cbf C [-act(t-1, t) + (1 - alpha) act(t, t+1)] dh_t,
     // dh_t / de_y = -2 e_y
+    const float wc = w_cbf * P.C_cbf;
     auto direct = [&](int t) {
-        const float ey = tape[(size_t)t * CR_NF + 4];
+        const float vx = tape[(size_t)t * CR_NF + 0], ey = tape[(size_t)t * CR_NF + 4];
+        if (w_run != 0.0f) {
+            lam.vx += w_run * 2.0f * P.q_v * (vx - P.v_target);
+            lam.Y += w_run * 2.0f * P.qd_w2 * ey;
+        }
         const bool a0 = cbf_arg(P, h_at(t - 1), h_at(t)) > 0.0f;
         const bool a1 = (t < N) && cbf_arg(P, h_at(t), h_at(t + 1)) > 0.0f;
-        const float w = (a0 ? -P.C_cbf : 0.0f) + (a1 ? P.C_cbf * P.one_m_alpha : 0.0f);
+        const float w = (a0 ? -wc : 0.0f) + (a1 ? wc * P.one_m_alpha : 0.0f);
         lam.Y += w * (-2.0f * ey);
     };
     direct(N);
@@ -290,6 +304,49 @@ __global__ void __launch_bounds__(CR_BLK) curv_repair_kernel(
     float2* vout = reinterpret_cast<float2*>(Vout) + (size_t)q * T;
     for (int t = tid; t < T; t += CR_BLK) vout[t] = Vw[t];
     if (q == 0 && tid == 0 && ap.x0) closed_loop_step(P, ap, Vw[0]);
+}
+
+// J and dJ/dV of n_seq sequences (smppi_cost_grad on the curvilinear state):
+// one warp per sequence, lane 0 runs the forward pass into the warp's tape and
+// the adjoint; the tape keeps every state (the checkpoint argument does not
+// apply).  Gradients of the controls t >= N are 0.
+__global__ void __launch_bounds__(32) curv_cost_grad_kernel(
+    DevParams P, const float* __restrict__ kappa, int n_seq, const float* __restrict__ x0g,
+    const float* __restrict__ Vg, int N, float w_run, float w_cbf, double* __restrict__ J_out,
+    float* __restrict__ grad_out, unsigned* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int T = P.T, n = P.n_track, q = blockIdx.x, lane = threadIdx.x;
+    float2* Vw = reinterpret_cast<float2*>(smem_raw);
+    float2* G = Vw + T;
+    float* kt = reinterpret_cast<float*>(G + T);
+    float* tape = kt + ((n + 1 + 3) & ~3);
+    if (q >= n_seq) return;
+    const float2* vin = reinterpret_cast<const float2*>(Vg) + (size_t)q * T;
+    for (int t = lane; t < T; t += 32) Vw[t] = vin[t];
+    for (int i = lane; i <= n; i += 32) kt[i] = kappa[i];
+    __syncwarp();
+    if (lane == 0) {
+        const State x0 = make_state(x0g + 6 * q);
+        const double J = curv_merit_grad(P, kt, x0, N, T, Vw, G, tape, w_run, w_cbf);
+        if (J_out) J_out[q] = J;
+        if (!isfinite(J)) atomicOr(status, SMPPI_DEV_NUMERIC);
+    }
+    __syncwarp();
+    float2* gout = reinterpret_cast<float2*>(grad_out) + (size_t)q * T;
+    for (int t = lane; t < T; t += 32) gout[t] = G[t];
+}
+
+cudaError_t launch_cost_grad_curv(const DevParams& P, const float* kappa, int n_seq,
+                                  const float* x0, const float* V, int N, float w_run, float w_cbf,
+                                  double* J_out, float* grad_out, unsigned* status,
+                                  cudaStream_t st) {
+    const size_t smem = (size_t)P.T * 16 + (size_t)((P.n_track + 1 + 3) & ~3) * 4 +
+                        (size_t)(P.T + 1) * CR_NF * 4;
+    cudaError_t e = ensure_smem((const void*)curv_cost_grad_kernel, smem);
+    if (e != cudaSuccess) return e;
+    curv_cost_grad_kernel<<<n_seq, 32, smem, st>>>(P, kappa, n_seq, x0, V, N, w_run, w_cbf, J_out,
+                                                   grad_out, status);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_repair_curv(const DevParams& P, const float* kappa, int n_seq,

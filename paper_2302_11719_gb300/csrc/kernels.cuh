@@ -104,6 +104,13 @@ cudaError_t launch_repair_curv(const DevParams& P, const float* kappa, int n_seq
                                int mode, float delta, double* merit_out, int* iters_out,
                                const ApplyArgs& ap, unsigned* status, cudaStream_t st);
 
+// smppi_cost_grad on the curvilinear state (curv_repair.cu): full tape, one warp
+// per sequence (the checkpoint interval does not apply).
+cudaError_t launch_cost_grad_curv(const DevParams& P, const float* kappa, int n_seq,
+                                  const float* x0, const float* V, int N, float w_run, float w_cbf,
+                                  double* J_out, float* grad_out, unsigned* status,
+                                  cudaStream_t st);
+
 // BFGS repair (bfgs.cu): bfgs_grid() blocks of *wpb warps, one sequence per
 // warp at a time; the workspace (bfgs_ws_bytes()) holds a work counter and an
 // H slice of (2 N_r)^2 floats per warp slot.

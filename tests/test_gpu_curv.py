@@ -11,7 +11,9 @@ paper's AutoRally model, Sec. VI-A; readings c28, c29) against the FP64 oracle.
     one whole Shield-MPPI update (rollouts, softmin, repair of V+, closed-loop
     step) against the oracle, repaired controls within V_REP unless a
     line-search decision differs between float32 and float64 (a flip);
-  * smppi_cost_grad and the BFGS repair refuse state_kind 1.
+  * smppi_cost_grad (full tape) against the oracle's dual-number gradient:
+    J within S_REL, the gradient within G_REL on kink-free sequences;
+  * the BFGS repair refuses state_kind 1.
 Tolerances: tests/gpu_helpers.py.
 """
 import numpy as np
@@ -21,8 +23,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from paper_2302_11719_gb300 import inputs as I  # noqa: E402
-from tests.gpu_helpers import (S_REL, V_REP, X_REL, rel_err, repair_compare,  # noqa: E402
-                                update_bound)
+from tests.gpu_helpers import (G_REL, S_REL, V_REP, X_REL, rel_err,  # noqa: E402
+                                repair_compare, update_bound)
 
 
 @pytest.fixture(scope="module")
@@ -211,6 +213,38 @@ def test_curv_shield_device_host_graph_agree(S):
     ctl.close()
 
 
+@pytest.mark.parametrize("w_run,w_cbf", [(1.0, 1.0), (0.0, 1.0), (1.0, 0.0)])
+def test_curv_cost_grad_vs_oracle(S, orc, w_run, w_cbf):
+    # J within S_REL and the adjoint gradient within G_REL (relative l2) of the
+    # oracle's dual-number gradient on sequences with no max(0, .) kink within 1e-3
+    pr, x0s, Vs = near_edge(n=24, T=40, seed=7)
+    n = len(x0s)
+    ctl = S.Controller(pr.params, pr.track, max_seq=n)
+    J = torch.empty(n, dtype=torch.float64, device="cuda")
+    g = torch.empty((n, pr.T, 2), device="cuda")
+    S.smppi_cost_grad(ctl.h, n, ctl.tensor(x0s), ctl.tensor(Vs), pr.T, w_run, w_cbf, 0, J, g)
+    assert ctl.sync_status()[0] == S.OK
+    J, g = J.cpu().numpy(), g.cpu().numpy().astype(np.float64)
+    ctl.close()
+    m = orc.Model(pr.params, pr.track)
+    a1 = 1 - float(np.float32(pr.params["alpha"]))
+    w2 = float(np.float32(pr.params["half_width"])) ** 2
+    clean, worst = 0, 0.0
+    for i in range(n):
+        Jo, go = orc.cost_grad(m, x0s[i], Vs[i], None, w_run, w_cbf)
+        assert abs(J[i] - Jo) <= S_REL * (abs(Jo) + 1), (i, J[i], Jo)
+        _, traj, _ = orc.rollout(m, x0s[i], Vs[i], noisy=False)
+        h = w2 - traj[:, 4] ** 2
+        if w_cbf != 0.0 and np.any(np.abs(a1 * h[:-1] - h[1:]) < 1e-3):
+            continue
+        e = np.linalg.norm(g[i] - go) / max(np.linalg.norm(go), 1e-12)
+        worst = max(worst, e)
+        clean += 1
+    print("curvilinear cost_grad (%g, %g): %d kink-free of %d, worst rel l2 %.2e"
+          % (w_run, w_cbf, clean, n, worst))
+    assert clean >= 8 and worst <= G_REL
+
+
 def test_curv_refused_entry_points(S):
     pr = curv_problem(64, 20)
     ctl = S.Controller(pr.params, pr.track)
@@ -218,7 +252,4 @@ def test_curv_refused_entry_points(S):
     Vs = torch.empty_like(V)
     with pytest.raises(RuntimeError):
         S.smppi_repair(ctl.h, 1, x0, V, Vs, 5, 2)
-    J = torch.empty(1, dtype=torch.float64, device="cuda")
-    with pytest.raises(RuntimeError):
-        S.smppi_cost_grad(ctl.h, 1, x0, V, 20, 0.0, 1.0, 0, J, Vs)
     ctl.close()
