@@ -101,9 +101,9 @@ typedef struct smppi_params {
                                  * s = arc length, e_y = lateral offset (left positive),
                                  * e_psi = heading error, on the centreline's curvature
                                  * kappa(s) (see below).  1 needs Ct = 1.5 and
-                                 * |steer| <= 1/2; the BFGS repair (mode 2), the batch
-                                 * and smppi_step_noalloc refuse it; smppi_cost_grad
-                                 * keeps the whole trajectory (no checkpoints). */
+                                 * |steer| <= 1/2; the batch and smppi_step_noalloc
+                                 * refuse it; smppi_cost_grad and the repair keep the
+                                 * whole trajectory (no checkpoints). */
 } smppi_params;
 
 /* Curvilinear state (state_kind = 1):
@@ -197,8 +197,8 @@ smppi_status smppi_cost_grad(smppi_handle* h, int n_seq, const float* x0, const 
  *           unset again when g'd >= 0).  Trials clip(V + a d), a = 1, 1/2, ...
  *           (ls_max_halvings), accepted when g'(V - V') > 0 and
  *           P' <= P - ls_c g'(V - V'); if none is and d came from H, the search
- *           is repeated along the gradient step.  One warp per sequence; a
- *           mode-2 call that needs more workspace than the handle holds
+ *           is repeated along the gradient step.  One warp per sequence (both
+ *           state kinds); a mode-2 call that needs more workspace than the handle holds
  *           allocates it (a work counter and (2 N_r)^2 floats per resident
  *           warp, about 256 MB at most).
  *   x0 [n_seq x 6]; V_in, V_out [n_seq x T x 2] (may alias);

@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "bfgs_launch.cuh"
 #include "kernels.cuh"
 
 using namespace smppi;
@@ -257,21 +258,23 @@ smppi_status enqueue_repair(smppi_handle* h, cudaStream_t st, int n_seq, const f
                             double* merit_out, int* iters_out, bool seg0_known,
                             const ApplyArgs& ap) {
     int ev;
-    if (h->p.state_kind == 1) {
+    const bool curv = h->p.state_kind == 1;
+    if (curv && mode != 2) {
         ev = tic(h, st);
         CU(h, launch_repair_curv(h->dp, h->kappa, n_seq, x0, V_in, V_out, n_iters, mode, delta,
                                  merit_out, iters_out, ap, h->status, st));
         toc(h, st, SMPPI_KERNEL_REPAIR, ev);
         return SMPPI_OK;
     }
-    if (!seg0_known) {
+    if (!curv && !seg0_known) {
         ev = tic(h, st);
         CU(h, launch_seg0(h->dp, h->rec, n_seq, x0, h->rws.seg0, st));
         toc(h, st, SMPPI_KERNEL_SEG0, ev);
     }
     if (mode == 2) {
         int wpb = 0;
-        const int grid = bfgs_grid(h->dp, n_seq, h->sms, &wpb);
+        const int grid = curv ? curv_bfgs_grid(h->dp, n_seq, h->sms, &wpb)
+                              : bfgs_grid(h->dp, n_seq, h->sms, &wpb);
         if (grid < 1) return fail(h, SMPPI_ERR_CUDA, "BFGS repair: no launch shape fits");
         const size_t need = bfgs_ws_bytes(h->dp, grid, wpb);
         if (need > h->bfgs_ws_bytes) {
@@ -288,8 +291,15 @@ smppi_status enqueue_repair(smppi_handle* h, cudaStream_t st, int n_seq, const f
             h->bfgs_ws_bytes = need;
         }
         ev = tic(h, st);
-        CU(h, launch_repair_bfgs(h->dp, h->rec, n_seq, x0, V_in, V_out, n_iters, h->rws.ck,
-                                 h->bfgs_ws, grid, wpb, merit_out, iters_out, ap, h->status, st));
+        if (curv) {
+            CU(h, launch_repair_bfgs_curv(h->dp, h->kappa, n_seq, x0, V_in, V_out, n_iters,
+                                          h->bfgs_ws, grid, wpb, merit_out, iters_out, ap,
+                                          h->status, st));
+        } else {
+            CU(h, launch_repair_bfgs(h->dp, h->rec, n_seq, x0, V_in, V_out, n_iters, h->rws.ck,
+                                     h->bfgs_ws, grid, wpb, merit_out, iters_out, ap, h->status,
+                                     st));
+        }
         toc(h, st, SMPPI_KERNEL_REPAIR, ev);
         return SMPPI_OK;
     }
@@ -556,7 +566,6 @@ smppi_status smppi_repair(smppi_handle* h, int n_seq, const float* x0, const flo
     if (!x0 || !V_in || !V_out) return fail(h, SMPPI_ERR_ARG, "x0, V_in, V_out must not be NULL");
     if (n_iters < 0 || n_iters > 100000) return fail(h, SMPPI_ERR_ARG, "n_iters must be in [0, 1e5]");
     if (mode != 0 && mode != 1 && mode != 2) return fail(h, SMPPI_ERR_ARG, "mode must be 0, 1 or 2");
-    if (mode == 2 && h->p.state_kind != 0) return fail(h, SMPPI_ERR_ARG, "the BFGS repair needs state_kind 0");
     if (mode == 0 && !(std::isfinite(delta) && delta >= 0)) return fail(h, SMPPI_ERR_ARG, "delta must be >= 0");
     const ApplyArgs none{nullptr, nullptr, 0u, 0u, nullptr};
     return enqueue_repair(h, h->st, n_seq, x0, V_in, V_out, n_iters, mode, delta, merit_out,

@@ -1,0 +1,238 @@
+// BFGS repair of one sequence on one warp: the solver Sec. IV-B names for the
+// local problem of Eq. 22, run for a fixed number of iterations.  The variant
+// (box projection, Armijo on the projected path, binding coordinates held,
+// gradient-step restarts) is stated with smppi_repair's mode 2 in smppi.h.
+// Shared by the kernels of the two state kinds (bfgs.cu: Cartesian state,
+// curv_repair.cu: curvilinear state); what differs between them is the merit,
+// supplied as an object with
+//   double merit(P, Vw)                         lane 0: P(Vw)
+//   void   grad(P, Vw, G)                       lane 0: G = dP/dV at Vw, 0 past N_r
+//                                               and for controls outside the box
+//   double trial(P, Vw, G, Dn, a, &dec)         any lane: P(u), u = clip(Vw - a Dn),
+//                                               dec = G . (Vw - u)
+//
+// Lane 0 computes the gradient (a serial chain), the lanes evaluate the
+// line-search trials a = 1, 1/2, ... in parallel (the largest accepted a is
+// taken: the same iterate as sequential backtracking), and the O(n^2) parts
+// (H y, H_FF g_F, the rank-two update, n = 2 N_r) are spread over the lanes.
+//
+// H lives in the warp's slice of a global workspace, small enough to stay in
+// L2.  The update is evaluated in a form that is symmetric in (i, j) operation
+// by operation (no fused multiply-add), so H stays exactly symmetric; products
+// with H then read it by columns, H[j][i] = H[i][j], so that the lanes' loads
+// of one j coalesce.
+#pragma once
+
+#include "shield.cuh"
+
+namespace smppi {
+
+constexpr int BFGS_WPB_MAX = 4;                      // warps (sequences) per block
+constexpr size_t BFGS_WS_MAX = size_t(256) << 20;    // bytes of H slices at most
+constexpr int BFGS_ROWS = 8;                         // rows per lane per pass of a product
+
+namespace {
+
+__device__ __forceinline__ double bfgs_warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// out_i = sum_j H_ji x_j (= (H x)_i, H symmetric) for i < n, lanes over i;
+// with mask, only the flagged rows and columns (other rows give 0).
+__device__ __forceinline__ void warp_symv(const float* __restrict__ H, const float* x, int n,
+                                          const unsigned char* mask, float* out) {
+    const int lane = threadIdx.x & 31;
+    for (int i0 = lane; i0 < n; i0 += 32 * BFGS_ROWS) {
+        float acc[BFGS_ROWS];
+#pragma unroll
+        for (int r = 0; r < BFGS_ROWS; ++r) acc[r] = 0.0f;
+        for (int j = 0; j < n; ++j) {
+            if (mask && !mask[j]) continue;          // the same j on every lane
+            const float xj = x[j];
+            const float* col = H + (size_t)j * n;
+#pragma unroll
+            for (int r = 0; r < BFGS_ROWS; ++r) {
+                const int i = i0 + 32 * r;
+                if (i < n) acc[r] = fmaf(col[i], xj, acc[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < BFGS_ROWS; ++r) {
+            const int i = i0 + 32 * r;
+            if (i < n) out[i] = (mask && !mask[i]) ? 0.0f : acc[r];
+        }
+    }
+    __syncwarp();
+}
+
+// The warp's working arrays for horizon T: five float2 arrays of T, two float
+// arrays of 2T and 2T flag bytes (padded to 16 bytes).
+struct BfgsArrays {
+    float2* Vw;          // iterate z (first N_r controls; the rest are carried)
+    float2* G;           // gradient at z
+    float2* Gp;          // gradient at the previous z
+    float2* Sv;          // last step s = z' - z
+    float2* Dn;          // negated direction
+    float* Yv;           // y = g - g_prev (n)
+    float* Hy;           // H y (n)
+    unsigned char* fr;   // free coordinate flags (n)
+};
+
+__host__ __device__ inline size_t bfgs_array_bytes(int T) {
+    const size_t t = (size_t)T;
+    return 5 * t * 8 + 2 * t * 8 + ((2 * t + 15) & ~size_t(15));
+}
+
+__device__ __forceinline__ BfgsArrays bfgs_arrays(unsigned char* base, int T) {
+    BfgsArrays a;
+    a.Vw = reinterpret_cast<float2*>(base);
+    a.G = a.Vw + T;
+    a.Gp = a.G + T;
+    a.Sv = a.Gp + T;
+    a.Dn = a.Sv + T;
+    a.Yv = reinterpret_cast<float*>(a.Dn + T);
+    a.Hy = a.Yv + 2 * T;
+    a.fr = reinterpret_cast<unsigned char*>(a.Hy + 2 * T);
+    return a;
+}
+
+// Runs up to n_iters BFGS iterations on a.Vw (all lanes of the warp).  mrow:
+// P before each iteration and after the last (n_iters + 1 values, repeated
+// after an early stop) or null.  Returns the iterations run; *P_out is the
+// final merit on every lane, *stalled_out whether the search gave up (no
+// accepted step, or a zero gradient with P > 0).
+template <class Merit>
+__device__ __forceinline__ int bfgs_solve(const DevParams& P, const Merit& f, const BfgsArrays& a,
+                                          float* __restrict__ H, int n_iters, double* mrow,
+                                          double* P_out, bool* stalled_out) {
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, N = P.N_r, n = 2 * N;
+    const float* zf = reinterpret_cast<const float*>(a.Vw);
+    const float* gf = reinterpret_cast<const float*>(a.G);
+    const float* gpf = reinterpret_cast<const float*>(a.Gp);
+    const float* sf = reinterpret_cast<const float*>(a.Sv);
+    float* dnf = reinterpret_cast<float*>(a.Dn);
+    double P0 = 0.0;
+    if (lane == 0) P0 = f.merit(P, a.Vw);
+    P0 = __shfl_sync(FULL, P0, 0);
+    bool H_set = false, have_step = false, stalled = false;
+    int it = 0;
+    for (; it < n_iters; ++it) {
+        if (lane == 0 && mrow) mrow[it] = P0;
+        if (P0 == 0.0) break;
+        if (lane == 0) f.grad(P, a.Vw, a.G);
+        __syncwarp();
+        // curvature pair of the last accepted step and the inverse update
+        //   H <- (I - rho s y') H (I - rho y s') + rho s s'
+        //      = H - rho (s (Hy)' + (Hy) s') + (rho^2 y'Hy + rho) s s'   (H symmetric)
+        if (have_step) {
+            double sy = 0.0, yy = 0.0, ss = 0.0;
+            for (int i = lane; i < n; i += 32) {
+                const float y = gf[i] - gpf[i];
+                a.Yv[i] = y;
+                sy += (double)sf[i] * y;
+                yy += (double)y * y;
+                ss += (double)sf[i] * sf[i];
+            }
+            sy = bfgs_warp_sum(sy);
+            yy = bfgs_warp_sum(yy);
+            ss = bfgs_warp_sum(ss);
+            __syncwarp();
+            if (sy > 1e-5 * sqrt(ss * yy)) {
+                if (!H_set) {
+                    const float h0 = (float)(sy / yy);
+                    for (int k = lane; k < n * n; k += 32) H[k] = (k % (n + 1) == 0) ? h0 : 0.0f;
+                    __syncwarp();
+                    H_set = true;
+                }
+                warp_symv(H, a.Yv, n, nullptr, a.Hy);
+                double yHy = 0.0;
+                for (int i = lane; i < n; i += 32) yHy += (double)a.Yv[i] * a.Hy[i];
+                yHy = bfgs_warp_sum(yHy);
+                const float rho = (float)(1.0 / sy);
+                const float cs = (float)(yHy / (sy * sy) + 1.0 / sy);
+                for (int k = lane; k < n * n; k += 32) {
+                    const int i = k / n, j = k - i * n;
+                    const float si = sf[i], sj = sf[j];
+                    const float cross = __fadd_rn(__fmul_rn(si, a.Hy[j]), __fmul_rn(sj, a.Hy[i]));
+                    const float delta = __fsub_rn(__fmul_rn(cs, __fmul_rn(si, sj)), __fmul_rn(rho, cross));
+                    H[k] = __fadd_rn(H[k], delta);
+                }
+                __syncwarp();
+            }
+        }
+        // |g|_inf and the binding coordinates (at a bound, gradient pushing outward)
+        float gm = 0.0f;
+        for (int i = lane; i < n; i += 32) {
+            const float g = gf[i], z = zf[i];
+            const float lo = (i & 1) ? P.umin1 : P.umin0, hi = (i & 1) ? P.umax1 : P.umax0;
+            a.fr[i] = !((z <= lo && g > 0.0f) || (z >= hi && g < 0.0f));
+            gm = fmaxf(gm, fabsf(g));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) gm = fmaxf(gm, __shfl_xor_sync(FULL, gm, o));
+        __syncwarp();
+        if (!(gm > 0.0f)) { stalled = true; break; }
+        const float s_first = P.ls_s0 / gm;
+        // direction (negated): Dn = H_FF g_F, or the scaled gradient step
+        if (H_set) {
+            warp_symv(H, gf, n, a.fr, dnf);
+            double gHg = 0.0;
+            for (int i = lane; i < n; i += 32) gHg += (double)gf[i] * dnf[i];
+            gHg = bfgs_warp_sum(gHg);
+            if (!(gHg > 0.0)) H_set = false;      // g'd = -g'Dn >= 0: not a descent direction
+        }
+        if (!H_set) {
+            for (int i = lane; i < n; i += 32) dnf[i] = a.fr[i] ? s_first * gf[i] : 0.0f;
+            __syncwarp();
+        }
+        // Armijo on the projected path (trials in parallel on the lanes); if the
+        // direction came from H and nothing is accepted, once more along the
+        // gradient step
+        int bj = 0x7fffffff;
+        double best_P = 0.0;
+        for (int pass = 0; pass < 2; ++pass) {
+            int best = 0x7fffffff;
+            double bp = 0.0;
+            for (int j = lane; j < P.ls_max; j += 32) {
+                double dec;
+                const double Pt = f.trial(P, a.Vw, a.G, a.Dn, ldexpf(1.0f, -j), &dec);
+                if (dec > 0.0 && Pt <= P0 - (double)P.ls_c * dec && j < best) {
+                    best = j;
+                    bp = Pt;
+                }
+            }
+            bj = best;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) bj = min(bj, __shfl_xor_sync(FULL, bj, o));
+            // the lane that owns trial bj (j = lane + 32 m) holds its merit
+            best_P = __shfl_sync(FULL, bp, (bj == 0x7fffffff) ? 0 : (bj & 31));
+            if (bj != 0x7fffffff || !H_set) break;
+            H_set = false;
+            for (int i = lane; i < n; i += 32) dnf[i] = a.fr[i] ? s_first * gf[i] : 0.0f;
+            __syncwarp();
+        }
+        if (bj == 0x7fffffff) { stalled = true; break; }
+        const float al = ldexpf(1.0f, -bj);
+        for (int t = lane; t < N; t += 32) {
+            const float2 v = a.Vw[t], dn = a.Dn[t];
+            const float2 u = clamp2(P, make_float2(fmaf(-al, dn.x, v.x), fmaf(-al, dn.y, v.y)));
+            a.Sv[t] = make_float2(u.x - v.x, u.y - v.y);
+            a.Gp[t] = a.G[t];
+            a.Vw[t] = u;
+        }
+        __syncwarp();
+        P0 = best_P;
+        have_step = true;
+    }
+    if (lane == 0 && mrow)
+        for (int i = it; i <= n_iters; ++i) mrow[i] = P0;
+    *P_out = P0;
+    *stalled_out = stalled;
+    return it;
+}
+
+}  // namespace
+}  // namespace smppi

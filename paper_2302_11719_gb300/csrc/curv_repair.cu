@@ -11,7 +11,10 @@
 // backtracking).  The merit accumulates in float32 over blocks of 16 steps and
 // float64 across them.  The closed-loop step (Eq. 26) may follow in the tail
 // of the block of sequence 0.
-#include "shield.cuh"
+#include <algorithm>
+
+#include "bfgs.cuh"
+#include "bfgs_launch.cuh"
 
 namespace smppi {
 namespace {
@@ -40,12 +43,14 @@ __device__ __forceinline__ float kappa_slope(const DevParams& P, const float* kt
 }
 
 // J = w_run sum_{t=0}^{N} q(x_t) + w_cbf sum_{t<N} C max{(1-alpha) h_t - h_{t+1}, 0}
-// of Vw (TRIAL: of clip(Vw - step G), with dec = G . (Vw - u')) from x0 over N
-// steps; (0, 1) is the merit P.  STORE: the states and h into the tape (N + 1 rows).
+// of Vw (TRIAL: of u' = clip(Vw - step Dn), with dec = G . (Vw - u'); Dn = G when
+// no search direction is given) from x0 over N steps; (0, 1) is the merit P.
+// STORE: the states and h into the tape (N + 1 rows).
 template <bool STORE, bool TRIAL>
 __device__ double curv_forward(const DevParams& P, const float* kt, const State& x0, int N,
                                const float2* Vw, const float2* G, float step, float* tape,
-                               double* dec_out, float w_run = 0.0f, float w_cbf = 1.0f) {
+                               double* dec_out, float w_run = 0.0f, float w_cbf = 1.0f,
+                               const float2* Dn = nullptr) {
     State x = x0;
     float h_prev = P.w2 - x.Y * x.Y;
     double J = (w_run != 0.0f) ? (double)(w_run * run_cost(P, x.vx, x.Y * x.Y)) : 0.0;
@@ -58,7 +63,8 @@ __device__ double curv_forward(const DevParams& P, const float* kt, const State&
         float2 u;
         if (TRIAL) {
             const float2 g = G[t];
-            u = clamp2(P, make_float2(fmaf(-step, g.x, v.x), fmaf(-step, g.y, v.y)));
+            const float2 dn = Dn ? Dn[t] : g;
+            u = clamp2(P, make_float2(fmaf(-step, dn.x, v.x), fmaf(-step, dn.y, v.y)));
             decf = fmaf(g.x, v.x - u.x, fmaf(g.y, v.y - u.y, decf));
         } else {
             u = clamp2(P, v);
@@ -204,6 +210,33 @@ __device__ double curv_merit_grad(const DevParams& P, const float* kt, const Sta
         if (t >= 1) direct(t);
     }
     return J;
+}
+
+// The merit of the curvilinear state from x0 for the BFGS solver (bfgs.cuh):
+// curv_forward and curv_merit_grad with the warp's full tape.
+struct CurvMerit {
+    const float* kt;
+    State x0;
+    float* tape;
+    __device__ __forceinline__ double merit(const DevParams& P, const float2* Vw) const {
+        return curv_forward<false, false>(P, kt, x0, P.N_r, Vw, nullptr, 0.0f, nullptr, nullptr);
+    }
+    __device__ __forceinline__ void grad(const DevParams& P, const float2* Vw, float2* G) const {
+        curv_merit_grad(P, kt, x0, P.N_r, P.T, Vw, G, tape);
+    }
+    __device__ __forceinline__ double trial(const DevParams& P, const float2* Vw, const float2* G,
+                                            const float2* Dn, float a, double* dec) const {
+        return curv_forward<false, true>(P, kt, x0, P.N_r, Vw, G, a, nullptr, dec, 0.0f, 1.0f, Dn);
+    }
+};
+
+// Bytes of the staged curvature samples (n_track + 1 floats, padded to 16).
+__host__ __device__ inline size_t kappa_bytes(int n) { return (size_t)((n + 1 + 3) & ~3) * 4; }
+
+// Bytes of one warp's region of the BFGS kernel: the solver's arrays and a full
+// tape of T + 1 states, padded to 16 (a multiple of 8: float2 arrays stay aligned).
+__host__ __device__ inline size_t curv_bfgs_warp_bytes(int T) {
+    return bfgs_array_bytes(T) + (((size_t)(T + 1) * CR_NF * 4 + 15) & ~size_t(15));
 }
 
 struct CurvSmem {
@@ -359,6 +392,74 @@ cudaError_t launch_repair_curv(const DevParams& P, const float* kappa, int n_seq
     if (e != cudaSuccess) return e;
     curv_repair_kernel<<<n_seq, CR_BLK, smem, st>>>(P, kappa, x0, V_in, V_out, n_iters, mode,
                                                     delta, merit_out, iters_out, ap, status);
+    return cudaGetLastError();
+}
+
+
+// BFGS repair (mode 2) on the curvilinear state: the solver of bfgs.cuh with
+// the curvilinear merit.  A block holds a few warps that share the staged
+// curvature samples; warps take sequences from an atomic counter.
+__global__ void __launch_bounds__(32 * BFGS_WPB_MAX) curv_repair_bfgs_kernel(
+    DevParams P, const float* __restrict__ kappa, const float* __restrict__ x0g, const float* Vin,
+    float* Vout, int n_seq, int n_iters, float* __restrict__ Hws, unsigned* __restrict__ next,
+    double* __restrict__ merit_out, int* __restrict__ iters_out, ApplyArgs ap,
+    unsigned* __restrict__ status) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int T = P.T, nt = P.n_track, n = 2 * P.N_r;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    float* kt = reinterpret_cast<float*>(smem_raw);
+    unsigned char* wbase = smem_raw + kappa_bytes(nt) + (size_t)warp * curv_bfgs_warp_bytes(T);
+    const BfgsArrays a = bfgs_arrays(wbase, T);
+    float* tape = reinterpret_cast<float*>(wbase + bfgs_array_bytes(T));
+    float* H = Hws + ((size_t)blockIdx.x * wpb + warp) * n * n;
+
+    for (int i = threadIdx.x; i <= nt; i += blockDim.x) kt[i] = kappa[i];
+    __syncthreads();
+
+    for (;;) {
+        int q = 0;
+        if (lane == 0) q = (int)atomicAdd(next, 1u);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if (q >= n_seq) break;
+        const float2* vin = reinterpret_cast<const float2*>(Vin) + (size_t)q * T;
+        for (int t = lane; t < T; t += 32) a.Vw[t] = vin[t];
+        __syncwarp();
+        const CurvMerit f{kt, make_state(x0g + 6 * q), tape};
+        double P0;
+        bool stalled;
+        const int it = bfgs_solve(P, f, a, H, n_iters,
+                                  merit_out ? merit_out + (size_t)q * (n_iters + 1) : nullptr, &P0,
+                                  &stalled);
+        if (lane == 0) {
+            if (iters_out) iters_out[q] = it;
+            if (stalled) atomicOr(status, SMPPI_DEV_STALLED);
+            if (!isfinite(P0)) atomicOr(status, SMPPI_DEV_NUMERIC);
+        }
+        float2* vout = reinterpret_cast<float2*>(Vout) + (size_t)q * T;
+        for (int t = lane; t < T; t += 32) vout[t] = a.Vw[t];
+        if (q == 0 && lane == 0 && ap.x0) closed_loop_step(P, ap, a.Vw[0]);
+        __syncwarp();   // the warp's shared memory is reused by its next sequence
+    }
+}
+
+int curv_bfgs_grid(const DevParams& P, int n_seq, int sms, int* wpb_out) {
+    return bfgs_shape((const void*)curv_repair_bfgs_kernel, kappa_bytes(P.n_track),
+                      curv_bfgs_warp_bytes(P.T), P.N_r, n_seq, sms, wpb_out);
+}
+
+cudaError_t launch_repair_bfgs_curv(const DevParams& P, const float* kappa, int n_seq,
+                                    const float* x0, const float* V_in, float* V_out, int n_iters,
+                                    void* ws, int grid, int wpb, double* merit_out, int* iters_out,
+                                    const ApplyArgs& ap, unsigned* status, cudaStream_t st) {
+    const size_t smem = kappa_bytes(P.n_track) + (size_t)wpb * curv_bfgs_warp_bytes(P.T);
+    cudaError_t e = ensure_smem((const void*)curv_repair_bfgs_kernel, smem);
+    if (e != cudaSuccess) return e;
+    unsigned* next = static_cast<unsigned*>(ws);
+    float* H = reinterpret_cast<float*>(static_cast<unsigned char*>(ws) + 16);
+    e = cudaMemsetAsync(next, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    curv_repair_bfgs_kernel<<<grid, 32 * wpb, smem, st>>>(P, kappa, x0, V_in, V_out, n_seq, n_iters,
+                                                          H, next, merit_out, iters_out, ap, status);
     return cudaGetLastError();
 }
 

@@ -80,3 +80,25 @@ def test_default_params_and_host_checks(lib):
     assert L.smppi_step(None, None, None, 0, 0, None, None) == smppi.ERR_ARG
     assert L.smppi_repair(None, 1, None, None, None, 1, 1, C.c_float(0), None, None) == smppi.ERR_ARG
     assert L.smppi_destroy(None) == smppi.OK
+
+
+def test_curvilinear_state_refused_where_unsupported(lib):
+    """The batch and smppi_step_noalloc take the Cartesian state only: a valid
+    state_kind 1 parameter set is refused on the host, before any device work."""
+    from paper_2302_11719_gb300 import smppi
+    smppi.load_library(os.path.join(ROOT, "paper_2302_11719_gb300", "libsmppi.so"))
+    L = smppi.load_library()
+    p = smppi.default_params()
+    p.track_xy = 1234          # never dereferenced: the state kind is refused first
+    p.n_track = 64
+    p.state_kind = 1
+    assert L.smppi_step_noalloc(C.byref(p), None, None, 0, 0, None, None) == smppi.ERR_ARG
+    assert b"state_kind" in L.smppi_last_error(None)
+    descs = (smppi.InstanceDesc * 1)()
+    b = C.c_void_p()
+    assert L.smppi_batch_create(C.byref(p), 1, descs, 1234, 0, None, C.byref(b)) == smppi.ERR_ARG
+    assert b.value is None
+    assert b"state_kind" in L.smppi_batch_last_error(None)
+    p.state_kind = 0           # the same set passes the checks that come before
+    assert L.smppi_step_noalloc(C.byref(p), None, None, 0, 0, None, None) == smppi.ERR_ARG
+    assert b"NULL" in L.smppi_last_error(None)

@@ -13,7 +13,11 @@ paper's AutoRally model, Sec. VI-A; readings c28, c29) against the FP64 oracle.
     line-search decision differs between float32 and float64 (a flip);
   * smppi_cost_grad (full tape) against the oracle's dual-number gradient:
     J within S_REL, the gradient within G_REL on kink-free sequences;
-  * the BFGS repair refuses state_kind 1.
+  * the BFGS repair (mode 2, reading c27) against the oracle's BFGS on
+    near-edge curvilinear sequences (controls within V_REP unless a flip, at
+    most 1/8), and a batch larger than the resident warps (warps take several
+    sequences and reuse their H slice) bit-identical to a small batch on the
+    sequences they share.
 Tolerances: tests/gpu_helpers.py.
 """
 import numpy as np
@@ -245,11 +249,35 @@ def test_curv_cost_grad_vs_oracle(S, orc, w_run, w_cbf):
     assert clean >= 8 and worst <= G_REL
 
 
-def test_curv_refused_entry_points(S):
-    pr = curv_problem(64, 20)
-    ctl = S.Controller(pr.params, pr.track)
-    x0, V = ctl.tensor(pr.x0), ctl.tensor(pr.V)
-    Vs = torch.empty_like(V)
-    with pytest.raises(RuntimeError):
-        S.smppi_repair(ctl.h, 1, x0, V, Vs, 5, 2)
+def test_curv_bfgs_vs_oracle(S, orc):
+    pr, x0s, Vs = near_edge(n=64, T=40, seed=7)
+    flips, worst = repair_compare(S, orc, pr.params, pr.track, x0s, Vs, 10, mode=2)
+    print("curvilinear BFGS repair (64 sequences, 10 iterations): %d flips, worst |dV| %.2e"
+          % (flips, worst))
+    assert worst <= V_REP and flips <= len(x0s) // 8
+
+
+def _bfgs_run(S, ctl, x0, V, n, n_iters):
+    Vout = torch.empty((n, ctl.T, 2), device="cuda")
+    mer = torch.empty((n, n_iters + 1), dtype=torch.float64, device="cuda")
+    its = torch.empty(n, dtype=torch.int32, device="cuda")
+    S.smppi_repair(ctl.h, n, x0[:n], V[:n], Vout, n_iters, 2, 0.0, mer, its)
+    st, _ = ctl.sync_status()
+    assert st in (S.OK, S.ERR_STALLED)
+    return Vout.cpu().numpy(), mer.cpu().numpy(), its.cpu().numpy()
+
+
+def test_curv_bfgs_independent_of_batch(S):
+    n = 8192          # more than the resident warps of the T = 40 launch
+    pr, x0s, Vs = near_edge(n=n, T=40, seed=11)
+    ctl = S.Controller(pr.params, pr.track, max_seq=n)
+    x0, V = ctl.tensor(x0s), ctl.tensor(Vs)
+    big = _bfgs_run(S, ctl, x0, V, n, 10)
+    small = _bfgs_run(S, ctl, x0, V, 256, 10)
     ctl.close()
+    for a, b in zip(big, small):
+        assert np.array_equal(a[:256], b)
+    mer = big[1]
+    assert np.all(mer[:, -1] <= mer[:, 0])
+    print("curvilinear BFGS, %d sequences: safe after %d of %d unsafe"
+          % (n, int(((mer[:, 0] > 0) & (mer[:, -1] == 0)).sum()), int((mer[:, 0] > 0).sum())))

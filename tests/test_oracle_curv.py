@@ -16,7 +16,11 @@ the paper's AutoRally model, Sec. VI-A; readings c28, c29).
   * the dual-number gradient of the repair objective through the Frenet
     kinematics and kappa(s) equals central finite differences away from the
     kinks, and the Armijo repair on the curvilinear state never increases the
-    merit and makes most near-edge sequences safe.
+    merit and makes most near-edge sequences safe;
+  * the BFGS repair (reading c27) on the curvilinear state: its first
+    iteration is the gradient repair's (H is unset), its merit never
+    increases, its iterates stay in the control box, and ten iterations make
+    at least half of the unsafe near-edge sequences safe.
 """
 import numpy as np
 import pytest
@@ -159,6 +163,23 @@ def test_curvilinear_repair_monotone_and_effective(orc):
     for i in range(len(x0s)):
         Vr, mer, st, it = orc.repair(m, x0s[i], Vs[i], 10)
         assert np.all(np.diff(mer) <= 0.0)
+        if mer[0] > 0:
+            unsafe += 1
+            safe_after += mer[-1] == 0.0
+    assert unsafe >= 4 and safe_after >= unsafe // 2
+
+
+def test_curvilinear_bfgs_first_step_and_descent(orc):
+    p, tr, x0s, Vs = _curv_sequences()
+    m = orc.Model(p, tr)
+    unsafe, safe_after = 0, 0
+    for i in range(len(x0s)):
+        Va = orc.repair(m, x0s[i], Vs[i], 1, mode=1)[0]
+        Vb = orc.repair(m, x0s[i], Vs[i], 1, mode=2)[0]
+        assert np.array_equal(Va, Vb)
+        Vr, mer, st, it = orc.repair(m, x0s[i], Vs[i], 10, mode=2)
+        assert np.all(np.diff(mer) <= 0.0)
+        assert np.all((Vr[:, 0] >= -0.5) & (Vr[:, 0] <= 0.5) & (Vr[:, 1] >= -1) & (Vr[:, 1] <= 1))
         if mer[0] > 0:
             unsafe += 1
             safe_after += mer[-1] == 0.0
