@@ -546,10 +546,44 @@ def run_sweep(args):
 F_ALG_CURV = 260   # hand count per rollout step of the curvilinear model (design notes)
 
 
+def _time_repairs(S, ctl, n, x0, V, n_iters, args, flush):
+    """smppi_repair of n sequences, n_iters iterations, in modes 1 (projected
+    gradient + Armijo) and 2 (BFGS): time per call and what the repair achieved."""
+    import torch
+    dev = x0.device
+    Vout = torch.empty_like(V)
+    its = torch.empty(n, dtype=torch.int32, device=dev)
+    mer = torch.empty((n, n_iters + 1), dtype=torch.float64, device=dev)
+    out = {}
+    for key, mode in (("repair_%d" % n_iters, 1), ("bfgs_%d" % n_iters, 2)):
+        for _ in range(2):
+            S.smppi_repair(ctl.h, n, x0, V, Vout, n_iters, mode, 0.0, mer, its)
+        t = _timed_steps(lambda i: S.smppi_repair(ctl.h, n, x0, V, Vout, n_iters, mode, 0.0, mer,
+                                                  its),
+                         max(3, args.steps // 4), flush)
+        st, bits = ctl.sync_status()
+        iters = its.cpu().numpy()
+        m = mer.cpu().numpy()
+        us = 1e3 * sum(t) / len(t)
+        out[key] = {"us_per_call": us,
+                    "mean_iterations_run": float(iters.mean()),
+                    "us_per_iteration_run": us / max(1.0, iters.max()),
+                    "merit_before_mean": float(m[:, 0].mean()),
+                    "merit_after_mean": float(m[:, -1].mean()),
+                    "merit_reduction_per_us": float((m[:, 0] - m[:, -1]).sum()) / us,
+                    "sequences_unsafe_before": int((m[:, 0] > 0).sum()),
+                    "sequences_safe_after": int((m[:, -1] == 0).sum()),
+                    "device_status_bits": _status_names(bits)}
+    return out
+
+
 def run_curv(args):
     """The curvilinear state variant (s, e_y, e_psi) against the Cartesian model:
     one MPPI iteration (rollouts + update) at K = 65536 and T in {50, 100, 200}
-    on the same ellipse track, both from the centreline start."""
+    on the same ellipse track, both from the centreline start; then the shield
+    on the curvilinear state: 8192 near-edge sequences, T = 100, 20 iterations
+    of the gradient repair (one block per sequence) and of BFGS (one warp per
+    sequence), and the full-tape merit gradient."""
     import torch
 
     import __graft_entry__
@@ -589,9 +623,24 @@ def run_curv(args):
                          "fp32_tflops": ach, "fp32_frac": ach / FP32_PEAK_TFLOPS,
                          "device_status_bits": _status_names(bits)})
             ctl.close()
+    sb = I.near_edge_curvilinear(8192, 100, seed=0)
+    n = sb.x0.shape[0]
+    ctl = S.Controller(sb.params, sb.track, max_seq=n, device=dev)
+    x0, V = ctl.tensor(sb.x0), ctl.tensor(sb.V)
+    shield = _time_repairs(S, ctl, n, x0, V, 20, args, flush)
+    J = torch.empty(n, dtype=torch.float64, device=dev)
+    g = torch.empty_like(V)
+    for _ in range(args.warmup):
+        S.smppi_cost_grad(ctl.h, n, x0, V, 100, 0.0, 1.0, -1, J, g)
+    t = _timed_steps(lambda i: S.smppi_cost_grad(ctl.h, n, x0, V, 100, 0.0, 1.0, -1, J, g),
+                     args.steps, flush)
+    shield["merit_grad_full_tape"] = {"us_per_call": 1e3 * sum(t) / len(t),
+                                      "sequence_steps_per_s": n * 100 / (sum(t) / len(t) / 1e3)}
+    ctl.close()
     print(json.dumps({"workload": "curvilinear vs Cartesian state, MPPI iteration, K = 65536",
                       "peak_tflops": FP32_PEAK_TFLOPS, "l2": "flushed between steps",
-                      "rows": rows}), flush=True)
+                      "rows": rows,
+                      "shield_8192_near_edge_T100": shield}), flush=True)
     return 0
 
 
@@ -722,28 +771,9 @@ def run_grad(args):
                          args.steps, flush)
         out[name] = {"us_per_call": 1e3 * sum(t) / len(t),
                      "sequence_steps_per_s": n * 100 / (sum(t) / len(t) / 1e3)}
-    Vout = torch.empty_like(V)
-    its = torch.empty(n, dtype=torch.int32, device=dev)
-    mer = torch.empty((n, 21), dtype=torch.float64, device=dev)
     # 20 repair iterations: projected gradient + Armijo (mode 1, one thread per
-    # sequence at this size) and BFGS (mode 2, one block per sequence)
-    for key, mode in (("repair_20", 1), ("bfgs_20", 2)):
-        for _ in range(2):
-            S.smppi_repair(ctl.h, n, x0, V, Vout, 20, mode, 0.0, mer, its)
-        t = _timed_steps(lambda i: S.smppi_repair(ctl.h, n, x0, V, Vout, 20, mode, 0.0, mer, its),
-                         max(3, args.steps // 4), flush)
-        st, bits = ctl.sync_status()
-        iters = its.cpu().numpy()
-        m = mer.cpu().numpy()
-        us = 1e3 * sum(t) / len(t)
-        out[key] = {"us_per_call": us,
-                    "mean_iterations_run": float(iters.mean()),
-                    "us_per_iteration_run": us / max(1.0, iters.max()),
-                    "merit_before_mean": float(m[:, 0].mean()),
-                    "merit_after_mean": float(m[:, -1].mean()),
-                    "merit_reduction_per_us": float((m[:, 0] - m[:, -1]).sum()) / us,
-                    "sequences_safe_after": int((m[:, -1] == 0).sum()),
-                    "device_status_bits": _status_names(bits)}
+    # sequence at this size) and BFGS (mode 2, one warp per sequence)
+    out.update(_time_repairs(S, ctl, n, x0, V, 20, args, flush))
     ctl.close()
     # the FP64 oracle's repairs on a sample of the same sequences (one host core
     # per sequence; sequences are independent, so the whole batch on all cores

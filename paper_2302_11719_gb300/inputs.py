@@ -119,6 +119,10 @@ class SequenceBatch:
     V: np.ndarray         # (n_seq, T, 2) float32
     side: np.ndarray      # (n_seq,) +1 = offset to the left of the centreline, -1 right
 
+    @property
+    def T(self) -> int:
+        return int(self.params["T"])
+
 
 def near_boundary_sequences(n_seq: int = 8192, T: int = 100, seed: int = 0,
                             a: float = 20.0, b: float = 12.0, w: float = 2.0) -> SequenceBatch:
@@ -167,6 +171,34 @@ def near_boundary_sequences(n_seq: int = 8192, T: int = 100, seed: int = 0,
     thr = 0.2 + ar1(0.2)
     V = np.stack([np.clip(steer, -0.5, 0.5), np.clip(thr, -1.0, 1.0)], axis=2).astype(np.float32)
     return SequenceBatch(params=p, track=ellipse_track(a, b), x0=x0, V=V, side=side)
+
+
+def near_edge_curvilinear(n_seq: int = 16, T: int = 40, seed: int = 3) -> SequenceBatch:
+    """Curvilinear-state starts (state_kind 1) near the edge of the single-problem
+    track, heading toward it, with smooth controls that steer further out.
+
+    Sequence i takes side +1 (left) for even i, -1 for odd i; x0 = (v_x, 0, 0,
+    s, side e_y, side 0.08) with v_x ~ U[5, 8] m/s, s ~ U[0, 60] m and
+    e_y ~ U[1.4, 1.8] m (half-width 2); steering side 0.06 + N(0, 0.04^2) and
+    throttle 0.2 + N(0, 0.2^2) per step, independent, clipped to
+    [-0.45, 0.45] x [-0.9, 0.9].  The draws are taken sequence by sequence
+    from default_rng(seed).
+    """
+    pr = single_problem(K=1, T=T)
+    p = dict(pr.params)
+    p["state_kind"] = 1
+    rng = np.random.default_rng(seed)
+    x0s, Vs, sides = [], [], []
+    for i in range(n_seq):
+        side = 1.0 if i % 2 == 0 else -1.0
+        x0s.append([rng.uniform(5, 8), 0.0, 0.0, rng.uniform(0, 60), side * rng.uniform(1.4, 1.8),
+                    side * 0.08])
+        steer = side * 0.06 + 0.04 * rng.standard_normal(T)
+        thr = 0.2 + 0.2 * rng.standard_normal(T)
+        Vs.append(np.clip(np.stack([steer, thr], 1), [-0.45, -0.9], [0.45, 0.9]))
+        sides.append(side)
+    return SequenceBatch(params=p, track=pr.track, x0=np.array(x0s, np.float32),
+                         V=np.array(Vs, np.float32), side=np.array(sides))
 
 
 @dataclasses.dataclass

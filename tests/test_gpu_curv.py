@@ -121,17 +121,8 @@ def test_curv_apply(S, orc):
 def near_edge(n=16, T=40, seed=3):
     """Curvilinear starts near the track edge heading toward it, with smooth
     controls that steer further out (the shield's inputs)."""
-    pr = curv_problem(1, T)
-    rng = np.random.default_rng(seed)
-    x0s, Vs = [], []
-    for i in range(n):
-        side = 1.0 if i % 2 == 0 else -1.0
-        x0s.append([rng.uniform(5, 8), 0.0, 0.0, rng.uniform(0, 60), side * rng.uniform(1.4, 1.8),
-                    side * 0.08])
-        steer = side * 0.06 + 0.04 * rng.standard_normal(T)
-        thr = 0.2 + 0.2 * rng.standard_normal(T)
-        Vs.append(np.clip(np.stack([steer, thr], 1), [-0.45, -0.9], [0.45, 0.9]))
-    return pr, np.array(x0s, np.float32), np.array(Vs, np.float32)
+    sb = I.near_edge_curvilinear(n, T, seed)
+    return sb, sb.x0, sb.V
 
 
 @pytest.mark.parametrize("mode", [1, 0])

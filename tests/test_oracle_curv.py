@@ -109,18 +109,8 @@ def test_curvilinear_cost_uses_e_y(orc):
 def _curv_sequences(n=8, T=40, seed=3):
     """Curvilinear starts near the track edge heading toward it, and smooth
     control sequences that steer further out (the repair's inputs)."""
-    pr = I.single_problem(K=1, T=T)
-    p = _curv(pr.params)
-    rng = np.random.default_rng(seed)
-    x0s, Vs = [], []
-    for i in range(n):
-        side = 1.0 if i % 2 == 0 else -1.0
-        x0s.append([rng.uniform(5, 8), 0.0, 0.0, rng.uniform(0, 60), side * rng.uniform(1.4, 1.8),
-                    side * 0.08])
-        steer = side * 0.06 + 0.04 * rng.standard_normal(T)
-        thr = 0.2 + 0.2 * rng.standard_normal(T)
-        Vs.append(np.clip(np.stack([steer, thr], 1), [-0.45, -0.9], [0.45, 0.9]))
-    return p, pr.track, np.array(x0s), np.array(Vs)
+    sb = I.near_edge_curvilinear(n, T, seed)
+    return sb.params, sb.track, sb.x0.astype(np.float64), sb.V.astype(np.float64)
 
 
 def _fd(orc, m, x0, V, w_run, w_cbf, h=1e-4):
