@@ -355,6 +355,19 @@ smppi_status smppi_timing_read(smppi_handle* h, double* ms_out, int* count_out, 
 smppi_status smppi_debug_noise(smppi_handle* h, uint32_t iter, uint32_t instance, int K, int T,
                                float* eps_out, uint32_t* raw_out);
 
+/*
+ * Failure-detection self-test (no handle): launches one block of 32 threads on
+ * cuda_stream that waits, through the library's bounded device waits, on
+ * something nothing completes: which = 0: an mbarrier phase that no thread
+ * arrives at (the wait of the bulk-copy staging; gives up after 0.25 s of the
+ * global timer); which = 1: a shared-memory counter that no warp advances (the
+ * wait of the split merit pass; gives up after 2^24 tries).  The block then ORs
+ * SMPPI_DEV_TIMEOUT into *status (DEVICE, one word, not cleared) and returns;
+ * the context stays usable.  Asynchronous; SMPPI_ERR_ARG for another `which`
+ * or a NULL status.
+ */
+smppi_status smppi_debug_wait_timeout(int which, uint32_t* status, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

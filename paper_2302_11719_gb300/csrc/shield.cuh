@@ -138,6 +138,16 @@ __device__ double forward_cost(const DevParams& P, const float4* rec,
 constexpr int MERIT_PUB = 8;
 constexpr int MERIT_WAIT_LIMIT = 1 << 24;
 
+// Bounded spin of one thread on a shared-memory counter that another warp of
+// the block advances: true once *flag >= target, false after MERIT_WAIT_LIMIT
+// tries (about a quarter of a second), when the caller records
+// SMPPI_DEV_TIMEOUT and goes on without the value.
+__device__ __forceinline__ bool spin_until_geq(const volatile int* flag, int target) {
+    int tries = 0;
+    while (*flag < target && tries <= MERIT_WAIT_LIMIT) ++tries;
+    return tries <= MERIT_WAIT_LIMIT;
+}
+
 // The follower warp: positions pos[t - 1] = (X, Y) of x_t, t = 1..N, ready when
 // *prog >= t (published in chunks of MERIT_PUB).  For a chunk, lane l
 // evaluates segment s - 1 + l of the window around the segment s where the
@@ -165,9 +175,8 @@ __device__ __forceinline__ double merit_follow_warp(const DevParams& P, const fl
     bool timed_out = false;
     for (int t0 = 1; t0 <= N; t0 += MERIT_PUB) {
         const int t1 = min(N, t0 + MERIT_PUB - 1), nq = t1 - t0 + 1;
-        int tries = 0;
-        while (*prog < t1 && tries <= MERIT_WAIT_LIMIT) ++tries;
-        if (__any_sync(FULL, tries > MERIT_WAIT_LIMIT)) {   // warp-uniform
+        const bool ok = spin_until_geq(prog, t1);
+        if (__any_sync(FULL, !ok)) {   // warp-uniform
             if (lane == 0) atomicOr(status, SMPPI_DEV_TIMEOUT);
             timed_out = true;
             break;
@@ -317,9 +326,7 @@ __device__ __forceinline__ void merit_split3(const DevParams& P, const float4* r
     } else if (tid == 32) {
         float X = x0.X, Y = x0.Y, psi = x0.psi, cp = x0.cp, sp = x0.sp;
         for (int t = 0; t < N; ++t) {
-            int tries = 0;
-            while (prog[0] <= t && tries <= MERIT_WAIT_LIMIT) ++tries;
-            if (tries > MERIT_WAIT_LIMIT) {
+            if (!spin_until_geq(prog, t + 1)) {
                 atomicOr(status, SMPPI_DEV_TIMEOUT);
                 break;
             }
@@ -468,10 +475,7 @@ __device__ double repair_in_block(const DevParams& P, const float4* rec,
         else
             merit_split<FAST>(P, rec, x0, s0, N, Vw, tape_s, sm.prog, &sm.P, &sm.done, status);
         __syncthreads();
-        int tries = 0;
-        while (*reinterpret_cast<volatile int*>(&sm.done) == 0 && tries <= MERIT_WAIT_LIMIT)
-            ++tries;
-        if (tries > MERIT_WAIT_LIMIT && tid == 0) atomicOr(status, SMPPI_DEV_TIMEOUT);
+        if (!spin_until_geq(&sm.done, 1) && tid == 0) atomicOr(status, SMPPI_DEV_TIMEOUT);
         __threadfence_block();
         __syncthreads();
     };

@@ -73,6 +73,7 @@ _SIGS = {
     "smppi_shield_update": ([_vp, _vp, _vp, _vp, _u32, _u32, _i, _vp, _i], _i),
     "smppi_shield_loop": ([_vp, _vp, _vp, _vp, _u32, _u32, _i, _i], _i),
     "smppi_debug_noise": ([_vp, _u32, _u32, _i, _i, _vp, _vp], _i),
+    "smppi_debug_wait_timeout": ([_i, _vp, _vp], _i),
     "smppi_step_noalloc": ([C.POINTER(Params), _vp, _vp, _u32, _u32, _vp, _vp], _i),
     "smppi_batch_create": ([C.POINTER(Params), _i, C.POINTER(InstanceDesc), _vp, _i, _vp,
                             C.POINTER(_vp)], _i),
@@ -224,6 +225,13 @@ def smppi_shield_loop(h, x0, V, V_safe, iter0, instance=0, n_repair=10, n_update
 def smppi_debug_noise(h, iter, instance, K, T, eps_out=None, raw_out=None):
     _check(load_library().smppi_debug_noise(h, iter, instance, K, T, _ptr(eps_out),
                                             _ptr(raw_out)), h)
+
+
+def smppi_debug_wait_timeout(which, status, stream=None):
+    """Self-test of the bounded device waits: a block waits on something nothing
+    completes (0: an mbarrier phase, 1: a shared-memory counter), gives up and
+    ORs DEV_TIMEOUT into the device word `status`."""
+    _check(load_library().smppi_debug_wait_timeout(int(which), _ptr(status), _stream(stream)))
 
 
 def smppi_step_noalloc(params: Params, x0, V, iter=0, instance=0, S_out=None, stream=None):

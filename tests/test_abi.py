@@ -102,3 +102,15 @@ def test_curvilinear_state_refused_where_unsupported(lib):
     p.state_kind = 0           # the same set passes the checks that come before
     assert L.smppi_step_noalloc(C.byref(p), None, None, 0, 0, None, None) == smppi.ERR_ARG
     assert b"NULL" in L.smppi_last_error(None)
+
+
+def test_wait_timeout_self_test_host_checks(lib):
+    """The failure-detection self-test rejects a bad `which` and a NULL status
+    word on the host, before any launch."""
+    from paper_2302_11719_gb300 import smppi
+    smppi.load_library(os.path.join(ROOT, "paper_2302_11719_gb300", "libsmppi.so"))
+    L = smppi.load_library()
+    assert L.smppi_debug_wait_timeout(2, 1234, None) == smppi.ERR_ARG
+    assert b"which" in L.smppi_last_error(None)
+    assert L.smppi_debug_wait_timeout(0, None, None) == smppi.ERR_ARG
+    assert b"NULL" in L.smppi_last_error(None)
