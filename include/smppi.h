@@ -114,7 +114,9 @@ typedef struct smppi_params {
  *   linearly between the samples, s taken modulo L.
  *   ds/dt = (v_x cos e_psi - v_y sin e_psi) / max(1 - kappa e_y, 0.1),
  *   de_y/dt = v_x sin e_psi + v_y cos e_psi,  de_psi/dt = r - kappa ds/dt;
- *   explicit Euler like the Cartesian model; h = w^2 - e_y^2 and q use e_y. */
+ *   explicit Euler like the Cartesian model; h = w^2 - e_y^2 and q use e_y.
+ *   smppi_create returns SMPPI_ERR_ARG when two consecutive vertices of the
+ *   track coincide (the curvature is undefined there). */
 
 typedef struct smppi_handle smppi_handle;
 

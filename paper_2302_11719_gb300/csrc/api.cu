@@ -108,12 +108,15 @@ smppi_status check_params(const smppi_params* p) {
 // Curvature samples of the curvilinear state (smppi.h, state_kind 1), in
 // double: the vertex curvatures (turning angle / mean adjacent segment
 // length), linear in arc length between the vertex stations, sampled at n
-// uniform stations; sample n repeats sample 0 for the interpolation.
-void curvature_samples(const std::vector<float>& xy, int n, std::vector<float>& out, double& L) {
+// uniform stations; sample n repeats sample 0 for the interpolation.  False
+// (nothing written) when two consecutive vertices coincide: the turning angle
+// and the interpolation are then undefined.
+bool curvature_samples(const std::vector<float>& xy, int n, std::vector<float>& out, double& L) {
     std::vector<double> seg(n), station(n + 1, 0.0), kv(n);
     for (int i = 0; i < n; ++i) {
         const int j = (i + 1) % n;
         seg[i] = std::hypot((double)xy[2 * j] - xy[2 * i], (double)xy[2 * j + 1] - xy[2 * i + 1]);
+        if (!(seg[i] > 0.0) || !std::isfinite(seg[i])) return false;
         station[i + 1] = station[i] + seg[i];
     }
     L = station[n];
@@ -132,6 +135,7 @@ void curvature_samples(const std::vector<float>& xy, int n, std::vector<float>& 
         out[j] = (float)((1.0 - f) * kv[i] + f * kv[(i + 1) % n]);
     }
     out[n] = out[0];
+    return true;
 }
 
 DevParams derive(const smppi_params& p) {
@@ -432,19 +436,26 @@ smppi_status smppi_create(const smppi_params* p, void* cuda_stream, smppi_handle
     if (e == cudaSuccess) e = cudaMemsetAsync(h->iter_dev, 0, sizeof(uint32_t), h->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->ticket, 0, sizeof(unsigned), h->st);
     if (e == cudaSuccess) e = launch_rec_table(p->track_xy, p->n_track, h->rec, h->st);
+    bool track_ok = true;
     if (e == cudaSuccess && p->state_kind == 1) {
         std::vector<float> xy(2 * (size_t)p->n_track), ks;
         double L = 0.0;
         e = cudaMemcpy(xy.data(), p->track_xy, sizeof(float) * xy.size(), cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess) {
-            curvature_samples(xy, p->n_track, ks, L);
+        if (e == cudaSuccess) track_ok = curvature_samples(xy, p->n_track, ks, L);
+        if (e == cudaSuccess && track_ok) {
             e = alloc(&h->kappa, sizeof(float) * ks.size());
+            if (e == cudaSuccess)
+                e = cudaMemcpy(h->kappa, ks.data(), sizeof(float) * ks.size(), cudaMemcpyHostToDevice);
+            h->dp.kap_scale = (float)(p->n_track / L);
+            h->dp.track_len = (float)L;
+            h->dp.inv_len = (float)(1.0 / L);
         }
-        if (e == cudaSuccess)
-            e = cudaMemcpy(h->kappa, ks.data(), sizeof(float) * ks.size(), cudaMemcpyHostToDevice);
-        h->dp.kap_scale = (float)(p->n_track / L);
-        h->dp.track_len = (float)L;
-        h->dp.inv_len = (float)(1.0 / L);
+    }
+    if (e == cudaSuccess && !track_ok) {
+        free_all(h);
+        delete h;
+        return fail(nullptr, SMPPI_ERR_ARG,
+                    "state_kind 1 needs a track whose consecutive vertices differ (finite curvature)");
     }
     if (e != cudaSuccess) {
         const bool oom = (e == cudaErrorMemoryAllocation);

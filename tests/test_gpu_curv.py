@@ -17,7 +17,10 @@ paper's AutoRally model, Sec. VI-A; readings c28, c29) against the FP64 oracle.
     near-edge curvilinear sequences (controls within V_REP unless a flip, at
     most 1/8), and a batch larger than the resident warps (warps take several
     sequences and reuse their H slice) bit-identical to a small batch on the
-    sequences they share.
+    sequences they share;
+  * a track with two coinciding consecutive vertices (undefined curvature) is
+    refused at smppi_create for the curvilinear state and accepted for the
+    Cartesian one.
 Tolerances: tests/gpu_helpers.py.
 """
 import numpy as np
@@ -272,3 +275,19 @@ def test_curv_bfgs_independent_of_batch(S):
     assert np.all(mer[:, -1] <= mer[:, 0])
     print("curvilinear BFGS, %d sequences: safe after %d of %d unsafe"
           % (n, int(((mer[:, 0] > 0) & (mer[:, -1] == 0)).sum()), int((mer[:, 0] > 0).sum())))
+
+
+def test_curv_degenerate_track_refused(S):
+    pr = curv_problem(64, 20)
+    tr = pr.track.copy()
+    tr[5] = tr[4]
+    with pytest.raises(S.SmppiError) as ei:
+        S.Controller(pr.params, tr)
+    assert ei.value.status == S.ERR_ARG and "vertices" in str(ei.value)
+    p0 = dict(pr.params)
+    p0["state_kind"] = 0
+    ctl = S.Controller(p0, tr)
+    x0, V = ctl.tensor(I.single_problem(K=64, T=20).x0), ctl.tensor(pr.V)
+    ctl.step(x0, V)
+    assert ctl.sync_status()[0] == S.OK
+    ctl.close()
