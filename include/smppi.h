@@ -137,7 +137,9 @@ smppi_status smppi_create(const smppi_params* p, void* cuda_stream, smppi_handle
 /* Free the workspace after synchronising the handle's stream.  NULL is a no-op. */
 smppi_status smppi_destroy(smppi_handle* h);
 
-/* Message of the last failure on h (or of the last failed create when h is NULL). */
+/* Message of the last failure on h; with h NULL, of the last failed call
+ * without a handle (create, smppi_step_noalloc, smppi_debug_wait_timeout) on
+ * the calling host thread.  Valid until the next failing call. */
 const char* smppi_last_error(const smppi_handle* h);
 
 /* Synchronise the stream, read and clear the device status word; returns
@@ -275,6 +277,8 @@ smppi_status smppi_batch_create(const smppi_params* shared, int B,
                                 const smppi_instance_desc* desc, const float* tracks_xy,
                                 int block_rollouts, void* cuda_stream, smppi_batch** out);
 smppi_status smppi_batch_destroy(smppi_batch* b);
+/* Message of the last failure on b; with b NULL, of the last failed
+ * smppi_batch_create on the calling host thread. */
 const char* smppi_batch_last_error(const smppi_batch* b);
 
 /* One closed-loop Shield-MPPI update of all B problems (device arrays):

@@ -50,7 +50,8 @@ struct smppi_handle {
 
 namespace {
 
-std::string g_create_err;
+// the message of the last failure outside a handle, per host thread
+thread_local std::string g_create_err;
 
 smppi_status fail(smppi_handle* h, smppi_status s, const std::string& msg) {
     if (h) h->err = msg;

@@ -403,7 +403,8 @@ struct smppi_batch {
 
 namespace {
 
-std::string g_batch_err;
+// the message of the last failure outside a batch handle, per host thread
+thread_local std::string g_batch_err;
 
 smppi_status bfail(smppi_batch* b, smppi_status s, const std::string& m) {
     if (b) b->err = m;

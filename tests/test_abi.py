@@ -114,3 +114,23 @@ def test_wait_timeout_self_test_host_checks(lib):
     assert b"which" in L.smppi_last_error(None)
     assert L.smppi_debug_wait_timeout(0, None, None) == smppi.ERR_ARG
     assert b"NULL" in L.smppi_last_error(None)
+
+
+def test_last_error_is_per_thread(lib):
+    """A handle-less failure on one host thread does not overwrite the message
+    another thread reads."""
+    import threading
+    from paper_2302_11719_gb300 import smppi
+    smppi.load_library(os.path.join(ROOT, "paper_2302_11719_gb300", "libsmppi.so"))
+    L = smppi.load_library()
+    assert L.smppi_debug_wait_timeout(2, 1234, None) == smppi.ERR_ARG
+    other = []
+
+    def worker():
+        other.append(L.smppi_debug_wait_timeout(0, None, None))
+        other.append(L.smppi_last_error(None))
+    th = threading.Thread(target=worker)
+    th.start()
+    th.join()
+    assert other[0] == smppi.ERR_ARG and b"NULL" in other[1]
+    assert b"which" in L.smppi_last_error(None)
