@@ -23,7 +23,7 @@
 //   local repair of the CBF objective              Eq. 22, Alg. 1 (Sec. IV-B)
 //   disturbed closed loop                          Eq. 26 (Sec. VI-F), Alg. 2
 //
-// Where the paper is silent the readings are (numbered as in the design notes):
+// Where the paper is silent these readings are taken (their labels are used below):
 //   c2  control term gamma * v_t' Sigma^-1 (v_t + eps_t), gamma a parameter;
 //   c3  terminal cost phi = q, so S sums q over x_0..x_T;
 //   c4  the k = 0 CBF term uses x_{-1} = x_0 (Eq. 20);
@@ -36,6 +36,7 @@
 //       backtracking on the projected path, see bfgs_box below;
 //   c12 max(0, .) has derivative 0 at a non-positive argument; clamp(v) has
 //       derivative 1 on the closed box and 0 strictly outside it;
+//   c13 warm start V <- shift(V^+): drop v_0 and repeat the last control;
 //   c15 e_y is the distance to the centreline polyline, tracked continuously
 //       from the previous step's segment (the curvilinear coordinate of the
 //       paper's model); the first segment is the global nearest one.

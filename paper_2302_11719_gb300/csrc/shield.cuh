@@ -152,7 +152,7 @@ __device__ __forceinline__ bool spin_until_geq(const volatile int* flag, int tar
 // *prog >= t (published in chunks of MERIT_PUB).  For a chunk, lane l
 // evaluates segment s - 1 + l of the window around the segment s where the
 // chunk starts, for every position of the chunk at once; the descent walks of
-// c15 are then read off ballots of "the next segment is strictly closer"
+// the tracked projection are then read off ballots of "the next segment is strictly closer"
 // position after position: the walk from window lane L moves forward to the
 // first lane above L whose successor is not closer, and stays at L when L + 1
 // is not closer and L - 1 is not closer either.  This decode is one dependent

@@ -1,5 +1,6 @@
 """GPU BFGS repair (smppi_repair mode 2: the solver Sec. IV-B names for
-Eq. 22, variant = reading c27) against the FP64 oracle's BFGS.
+Eq. 22; box-projected, Armijo on the projected path, binding coordinates held,
+restarts along the gradient step) against the FP64 oracle's BFGS.
 
   * the K = 256, T = 50 problem's repair starts (its V+ and sequences that
     leave the track): repaired controls within V_REP of the oracle, no flip;

@@ -1,5 +1,6 @@
 """GPU curvilinear state variant (state_kind 1: the (s, e_y, e_psi) state of the
-paper's AutoRally model, Sec. VI-A; readings c28, c29) against the FP64 oracle.
+paper's AutoRally model, Sec. VI-A, on the curvature of the centreline's
+turning angles, Frenet kinematics) against the FP64 oracle.
 
   * K = 256, T = 50 on the ellipse track, from the centreline and from an
     off-centre start: every rollout cost and every trajectory state within
@@ -13,7 +14,7 @@ paper's AutoRally model, Sec. VI-A; readings c28, c29) against the FP64 oracle.
     line-search decision differs between float32 and float64 (a flip);
   * smppi_cost_grad (full tape) against the oracle's dual-number gradient:
     J within S_REL, the gradient within G_REL on kink-free sequences;
-  * the BFGS repair (mode 2, reading c27) against the oracle's BFGS on
+  * the BFGS repair (mode 2) against the oracle's BFGS on
     near-edge curvilinear sequences (controls within V_REP unless a flip, at
     most 1/8), and a batch larger than the resident warps (warps take several
     sequences and reuse their H slice) bit-identical to a small batch on the

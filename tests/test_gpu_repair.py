@@ -4,7 +4,7 @@
     forward-mode dual gradient on near-boundary sequences (T = 100,
     checkpoint every 10): cost within 1e-4 relative, gradient within 1e-3
     relative l2 on sequences with no max(0, .) or clamp kink within 1e-3
-    (reading c12), reported for the rest; checkpointed == full tape exactly;
+    (where the derivative is taken as 0), reported for the rest; checkpointed == full tape exactly;
   * the autograd wrapper returns the same gradient;
   * smppi_repair (Armijo) on the K = 256, T = 50 problem's V+ and on
     near-boundary sequences: repaired controls within 1e-4 of the oracle

@@ -1,5 +1,5 @@
 """Pins of the oracle's BFGS repair (the solver Sec. IV-B names for Eq. 22;
-variant = reading c27: box projection, Armijo on the projected path, binding
+variant: box projection, Armijo on the projected path, binding
 coordinates held, restarts along the gradient step).
 
   * the inverse update H+ = (I - rho s y') H (I - rho y s') + rho s s' meets

@@ -1,5 +1,6 @@
 """Pins of the oracle's curvilinear state variant (the (s, e_y, e_psi) state of
-the paper's AutoRally model, Sec. VI-A; readings c28, c29).
+the paper's AutoRally model, Sec. VI-A, on the curvature of the centreline's
+turning angles, Frenet kinematics).
 
   * the curvature table of a regular polygon inscribed in a circle of radius R
     is the closed form (2 pi / n) / chord everywhere, and the track length is
@@ -17,7 +18,7 @@ the paper's AutoRally model, Sec. VI-A; readings c28, c29).
     kinematics and kappa(s) equals central finite differences away from the
     kinks, and the Armijo repair on the curvilinear state never increases the
     merit and makes most near-edge sequences safe;
-  * the BFGS repair (reading c27) on the curvilinear state: its first
+  * the BFGS repair (mode 2) on the curvilinear state: its first
     iteration is the gradient repair's (H is unset), its merit never
     increases, its iterates stay in the control box, and ten iterations make
     at least half of the unsafe near-edge sequences safe.
@@ -127,7 +128,7 @@ def _fd(orc, m, x0, V, w_run, w_cbf, h=1e-4):
 
 def test_curvilinear_gradient_matches_fd(orc):
     # the dual-number gradient through the Frenet kinematics and kappa(s), away from
-    # the kinks of max(0, .) (reading c12)
+    # the kinks of max(0, .) (derivative 0 on the inactive side)
     p, tr, x0s, Vs = _curv_sequences()
     m = orc.Model(p, tr)
     a1 = 1 - float(np.float32(p["alpha"]))

@@ -2,7 +2,8 @@
 
   * the forward-mode (dual number) gradient agrees with central finite
     differences (h = 1e-4, FP64) on the smooth running cost and, away from the
-    kinks of max(0, .) and of the clamp (reading c12), on the CBF objective;
+    kinks of max(0, .) and of the clamp (derivative 0 on the inactive side),
+    on the CBF objective;
   * an already-safe sequence has zero objective and zero gradient and is a
     fixed point of the shield (the objective of Eq. 22 is 0 iff the CBF
     condition holds on every pair);
