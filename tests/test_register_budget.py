@@ -1,0 +1,60 @@
+"""Register budgets of the rollout kernels (ptxas report, no GPU needed).
+
+The rollout launch is issue-bound with few warps per scheduler, and its
+residency beyond one wave depends on the register count: registers are
+granted per warp in multiples of 8 per thread, so up to 168 registers three
+128-thread blocks fit on an SM (65536 / (168 x 128) = 3.05) and from 169 on
+only two (a 170-register build ran 6 % slower at K = 262144).  A change that
+raises the count or makes the kernel spill is a performance regression even
+when every parity test passes, so the counts are held at what the kernels use
+now: the packed Cartesian kernel at <= 160, the packed curvilinear kernel at
+<= 104, neither spilling.
+"""
+import os
+import re
+import shutil
+import subprocess
+
+import pytest
+
+from paper_2302_11719_gb300 import build as B
+
+BUDGET = {
+    # (source, mangled-name fragment): max registers
+    ("rollout.cu", "mppi_rollout2_kernelILb0E"): 160,
+    ("curv.cu", "mppi_rollout_curv_kernelILb0E"): 104,
+}
+
+
+def _ptxas_report(src, tmp_path):
+    exe = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(exe):
+        pytest.skip("nvcc not available")
+    cmd = [exe, *B.ARCH, *B.FLAGS, "-Xptxas", "-v", "-c", os.path.join(B.CSRC, src),
+           "-o", str(tmp_path / (src + ".o"))]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+    out, name, res = r.stderr, None, {}
+    for line in out.splitlines():
+        m = re.search(r"Compiling entry function '(\S+)'", line)
+        if m:
+            name = m.group(1)
+            continue
+        m = re.search(r"(\d+) bytes spill stores, (\d+) bytes spill loads", line)
+        if m and name:
+            res.setdefault(name, {})["spill"] = int(m.group(1)) + int(m.group(2))
+        m = re.search(r"Used (\d+) registers", line)
+        if m and name:
+            res.setdefault(name, {})["regs"] = int(m.group(1))
+    return res
+
+
+@pytest.mark.parametrize("src,frag", sorted(BUDGET))
+def test_rollout_kernel_register_budget(src, frag, tmp_path):
+    res = _ptxas_report(src, tmp_path)
+    hits = {k: v for k, v in res.items() if frag in k}
+    assert len(hits) == 1, sorted(res)
+    (name, r), = hits.items()
+    print("%s: %d registers, %d bytes spilled" % (frag, r["regs"], r.get("spill", 0)))
+    assert r["regs"] <= BUDGET[(src, frag)]
+    assert r.get("spill", 0) == 0
