@@ -23,6 +23,11 @@
  *     which must stay valid until smppi_destroy.
  *   - State x = (v_x, v_y, r, X, Y, psi) (6 floats); control u = (delta, a)
  *     (steer in rad, throttle in [-1, 1]); a control sequence is T x 2.
+ *     Precondition: the position of every start state passed in is finite
+ *     (|X|, |Y| well below 1e19).  The search for the nearest centreline
+ *     segment that starts each rollout and repair has no answer otherwise,
+ *     and device values are not checked before it; NaN or Inf arising later
+ *     (in velocities, costs, merits) is flagged as described below.
  *   - All work is enqueued on the handle's CUDA stream and is asynchronous;
  *     no entry point synchronises unless it says so.  Argument errors are
  *     found on the host before anything is enqueued and return SMPPI_ERR_ARG;
