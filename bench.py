@@ -34,8 +34,11 @@ sys.path.insert(0, ROOT)
 METRIC = "rollout-steps/s & µs per MPPI update (batched+adjoint vs plain), % FP32 roofline"
 UNIT = "rollout-steps/s"
 K_ROLL, T_HOR, N_REPAIR = 65536, 100, 10
-# FP32 flops of one rollout step (FMA = 2), hand count of the forward model,
-# noise, track projection and cost; see the design notes.
+# FP32 flops of one rollout step (FMA = 2), hand count: Box-Muller pair and
+# uniforms 44, perturbation and control-cost term 10, two slip angles 48, two
+# lateral forces 34, steer sin/cos 28, force balance 20, heading increment 32,
+# Euler update 12, track projection (about three segments) 39, running cost and
+# DCBF penalty 13.
 F_ALG = 280
 # FP32 peak: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (maximum SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
@@ -543,7 +546,11 @@ def run_sweep(args):
     return 0
 
 
-F_ALG_CURV = 260   # hand count per rollout step of the curvilinear model (design notes)
+# The same count for the curvilinear model: noise 44, perturbation 10, slip angles
+# 48, lateral forces 34, steer sin/cos 28, force balance 20, curvature lookup 8,
+# 1 - kappa e_y and its reciprocal 4, s' e_y' e_psi' 10, heading rotation 27,
+# Euler update 10, cost and DCBF penalty 17.
+F_ALG_CURV = 260
 
 
 def _time_repairs(S, ctl, n, x0, V, n_iters, args, flush):
