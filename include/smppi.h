@@ -68,7 +68,7 @@ typedef enum {
 #define SMPPI_DEV_TIMEOUT 2u
 #define SMPPI_DEV_STALLED 4u
 
-/* Limits of this build. */
+/* Limits of the library. */
 #define SMPPI_MAX_T 512        /* horizon */
 #define SMPPI_MAX_TRACK 2048   /* centreline points (staged in shared memory) */
 

@@ -265,7 +265,7 @@ static R kappa_at(const OrcParams* p, R s) {
 // ---------------------------------------------------------------------------
 // Vehicle model (Sec. VI-A uses a single-track model; its parameters are not
 // given, so the dynamic single-track model with Pacejka-type lateral tyre
-// forces below is the model this build fixes).  State x = (v_x, v_y, r, X, Y,
+// forces below is the model this implementation fixes).  State x = (v_x, v_y, r, X, Y,
 // psi), control u = (delta, a).  Static axle loads, no drag.
 // ---------------------------------------------------------------------------
 template <class R>

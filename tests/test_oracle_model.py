@@ -1,6 +1,6 @@
 """Pins of the oracle's vehicle model, track distance, cost and DCBF penalty.
 
-Dynamics (single-track model of Sec. VI-A, the equations this build fixes):
+Dynamics (single-track model of Sec. VI-A, the equations this implementation fixes):
   * straight running (delta = 0, v_y = r = 0) is a linear ODE that explicit
     Euler integrates exactly: v_x' = v_x + dt 60 a / m, X, Y advance along psi;
   * mirror symmetry about the heading axis (delta, v_y, r, Y, psi -> -);
