@@ -3,14 +3,21 @@
 // h = w^2 - e_y^2 (Eq. 17, 23), its gradient by a reverse-mode adjoint of the
 // curvilinear model step over a full tape of the N_r states (no recomputation:
 // 9 floats per state fit in shared memory for any T), projected gradient with
-// Armijo backtracking (mode 1) or the fixed step of Alg. 1 (mode 0).
+// Armijo backtracking (mode 1), the fixed step of Alg. 1 (mode 0) or BFGS
+// (mode 2, the solver of bfgs.cuh).
 //
-// One block per sequence: thread 0 runs the forward pass and the adjoint, the
-// lanes of warp 0 evaluate the trial steps s, s/2, ... in parallel and the
-// largest accepted step is taken (the same iterate as sequential
-// backtracking).  The merit accumulates in float32 over blocks of 16 steps and
-// float64 across them.  The closed-loop step (Eq. 26) may follow in the tail
-// of the block of sequence 0.
+// Kernels:
+//   curv_repair_kernel       modes 0 and 1, one block per sequence: thread 0
+//                            runs the forward pass and the adjoint, the lanes of
+//                            warp 0 evaluate the trial steps s, s/2, ... in
+//                            parallel and the largest accepted step is taken
+//                            (the same iterate as sequential backtracking);
+//   curv_repair_bfgs_kernel  mode 2, one warp per sequence from a work counter;
+//   curv_cost_grad_kernel    J and dJ/dV with running-cost and CBF weights
+//                            (smppi_cost_grad), one warp per sequence.
+// The merit accumulates in float32 over blocks of 16 steps and float64 across
+// them.  The closed-loop step (Eq. 26) may follow in the tail of the block or
+// warp that repaired sequence 0.
 #include <algorithm>
 
 #include "bfgs.cuh"
