@@ -134,3 +134,31 @@ def test_last_error_is_per_thread(lib):
     th.join()
     assert other[0] == smppi.ERR_ARG and b"NULL" in other[1]
     assert b"which" in L.smppi_last_error(None)
+
+
+def test_header_is_plain_c_and_links_from_c(lib, tmp_path):
+    """include/smppi.h is a C header (strict C99, no C++ constructs) and a C
+    program links against libsmppi.so and calls it; the call here needs no GPU
+    (default parameters, then a create that fails its host-side check)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    src = tmp_path / "t.c"
+    src.write_text(
+        '#include <stdio.h>\n#include "smppi.h"\n'
+        "int main(void) {\n"
+        "    smppi_params p;\n    smppi_handle* h = 0;\n"
+        "    smppi_default_params(&p);\n"
+        "    smppi_status s = smppi_create(&p, 0, &h);\n"
+        '    printf("%d %d\\n", p.K, (int)s);\n'
+        "    return (s == SMPPI_ERR_ARG && h == 0) ? 0 : 1;\n}\n")
+    libdir = os.path.join(ROOT, "paper_2302_11719_gb300")
+    exe = tmp_path / "t"
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic",
+                        "-I", os.path.join(ROOT, "include"), str(src), "-L", libdir, "-lsmppi",
+                        "-Wl,-rpath," + libdir, "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0 and r.stdout.split() == ["256", "1"], (r.stdout, r.stderr)
