@@ -4,7 +4,7 @@ turning angles, Frenet kinematics).
 
   * the curvature table of a regular polygon inscribed in a circle of radius R
     is the closed form (2 pi / n) / chord everywhere, and the track length is
-    n chords;
+    n chords; traversed clockwise, the samples change sign;
   * on the ellipse track the table follows the ellipse's analytic curvature
     ab / (a^2 sin^2 t + b^2 cos^2 t)^(3/2) at the same arc lengths (positive:
     the counter-clockwise centreline turns left);
@@ -47,6 +47,17 @@ def test_curvature_regular_polygon(orc):
     chord = 2 * R * np.sin(np.pi / n)
     assert np.max(np.abs(k / ((2 * np.pi / n) / chord) - 1)) < 5e-4   # float32 vertices
     assert abs(L / (n * chord) - 1) < 1e-7
+
+
+def test_curvature_sign_follows_orientation(orc):
+    # the same polygon traversed clockwise turns right at every vertex: the
+    # samples change sign, the length does not
+    R, n = 10.0, 256
+    ccw = _circle(R, n)
+    k1, L1 = orc.curvature_table(orc.Model(_curv(I.make_params(K=1, T=10)), ccw))
+    k2, L2 = orc.curvature_table(orc.Model(_curv(I.make_params(K=1, T=10)), ccw[::-1].copy()))
+    assert np.all(k1 > 0) and np.all(k2 < 0)
+    assert np.allclose(k2, -k1[0], rtol=5e-4) and abs(L2 / L1 - 1) < 1e-12
 
 
 def test_curvature_ellipse_analytic(orc):
