@@ -23,11 +23,13 @@
  *     which must stay valid until smppi_destroy.
  *   - State x = (v_x, v_y, r, X, Y, psi) (6 floats); control u = (delta, a)
  *     (steer in rad, throttle in [-1, 1]); a control sequence is T x 2.
- *     Precondition: the position of every start state passed in is finite
- *     (|X|, |Y| well below 1e19).  The search for the nearest centreline
- *     segment that starts each rollout and repair has no answer otherwise,
- *     and device values are not checked before it; NaN or Inf arising later
- *     (in velocities, costs, merits) is flagged as described below.
+ *     A start state whose position is not finite (or beyond ~1e19 m) has no
+ *     nearest centreline segment: the kernels then start from segment 0, set
+ *     SMPPI_DEV_NUMERIC and produce NaN costs (V+ then lies on the lower
+ *     corner of the control box); the handle stays usable.  Host-buffer calls
+ *     refuse a non-finite x0 with SMPPI_ERR_ARG before anything is enqueued.
+ *     NaN or Inf arising later (in velocities, costs, merits) is flagged as
+ *     described below.
  *   - All work is enqueued on the handle's CUDA stream and is asynchronous;
  *     no entry point synchronises unless it says so.  Argument errors are
  *     found on the host before anything is enqueued and return SMPPI_ERR_ARG;
@@ -302,7 +304,11 @@ smppi_status smppi_batch_loop(smppi_batch* b, float* x0, float* V, float* V_safe
 /* Synchronise the batch stream and read / clear its device status word.
  * After SMPPI_DEV_TIMEOUT (a block gave up on a bounded wait and left the
  * launch) the problems' completion counters are cleared as well; the state
- * of the problems that block held (x0, V, V_safe) is then undefined. */
+ * of the problems that block held (x0, V, V_safe) is then undefined.  While
+ * the TIMEOUT bit is set (until this call reads it), batch launches take no
+ * further work items, so a launch, and every later replay of a loop, ends
+ * within about one wait limit; the problems they do not reach keep their
+ * state. */
 smppi_status smppi_batch_sync_status(smppi_batch* b, uint32_t* bits_out);
 
 /* The launch shape in use (after autotuning): rollouts per item and grid size. */
@@ -331,9 +337,13 @@ smppi_status smppi_batch_monitor(smppi_batch* b, uint32_t* viol_out, uint32_t* o
  * for smppi_last_error(NULL)), T <= SMPPI_MAX_T, n_track <= SMPPI_MAX_TRACK.
  * Scratch: one fixed 1.4 MB array per GPU inside the library, held until the
  * process exits.  The first call on a device looks up that array's device
- * address; make it before any stream capture.  Every call on a device shares
- * the array and leaves its contents behind; calls that overlap on the GPU
- * race on it.  Device-side NaN checks are not reported (NaN reaches V).
+ * address; make it before any stream capture.  Later calls outside a capture
+ * look the address up again (it does not survive a device reset); calls
+ * inside a capture reuse the last one.  Every call on a device shares the
+ * array and leaves its contents behind; calls that overlap on the GPU race on
+ * it.  Device-side checks are not reported: with a NaN in x0 or in the costs
+ * the call still returns SMPPI_OK and V+ lies on the lower corner of the
+ * control box.
  */
 smppi_status smppi_step_noalloc(const smppi_params* p, const float* x0, float* V, uint32_t iter,
                                 uint32_t instance, float* S_out, void* cuda_stream);

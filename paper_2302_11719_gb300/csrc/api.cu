@@ -273,7 +273,7 @@ smppi_status enqueue_repair(smppi_handle* h, cudaStream_t st, int n_seq, const f
     }
     if (!curv && !seg0_known) {
         ev = tic(h, st);
-        CU(h, launch_seg0(h->dp, h->rec, n_seq, x0, h->rws.seg0, st));
+        CU(h, launch_seg0(h->dp, h->rec, n_seq, x0, h->rws.seg0, h->status, st));
         toc(h, st, SMPPI_KERNEL_SEG0, ev);
     }
     if (mode == 2) {
@@ -533,7 +533,7 @@ smppi_status smppi_cost_grad(smppi_handle* h, int n_seq, const float* x0, const 
     }
     const int ck = checkpoint == 0 ? h->p.checkpoint : (checkpoint < 0 ? 0 : checkpoint);
     int ev = tic(h, h->st);
-    CU(h, launch_seg0(h->dp, h->rec, n_seq, x0, h->rws.seg0, h->st));
+    CU(h, launch_seg0(h->dp, h->rec, n_seq, x0, h->rws.seg0, h->status, h->st));
     toc(h, h->st, SMPPI_KERNEL_SEG0, ev);
     ev = tic(h, h->st);
     CU(h, launch_cost_grad(h->dp, h->rec, h->rws, n_seq, x0, V, N, w_run, w_cbf, ck, J_out,
@@ -605,6 +605,10 @@ smppi_status smppi_shield_update(smppi_handle* h, float* x0, float* V, float* V_
     if (instance >= (1u << 24)) return fail(h, SMPPI_ERR_ARG, "instance must be < 2^24");
     if (!host_buffers)
         return enqueue_shield(h, h->st, x0, V, V_safe, iter, instance, n_repair, merit_out, nullptr);
+    // host state: the start position is checked here (the device search for the
+    // nearest segment has no answer for a non-finite one)
+    for (int j = 0; j < 6; ++j)
+        if (!std::isfinite(x0[j])) return fail(h, SMPPI_ERR_ARG, "x0 must be finite");
     const size_t vb = sizeof(float) * 2 * h->p.T;
     double* dm = nullptr;
     if (merit_out && n_repair > 0) {

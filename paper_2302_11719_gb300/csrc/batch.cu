@@ -100,7 +100,14 @@ __global__ void __launch_bounds__(RB) batch_kernel(DevParams P0, BatchArgs a) {
     float d20 = 0.0f;
 
     for (;;) {
-        if (tid == 0) s_item = (int)atomicAdd(a.head, 1u);
+        // after any block of the launch (or of an earlier replay not yet read by
+        // the host) gave up on a bounded wait, no block takes further items: the
+        // launch then ends within one item's time instead of every later item
+        // waiting out its own limit
+        if (tid == 0)
+            s_item = (*reinterpret_cast<volatile unsigned*>(a.status) & SMPPI_DEV_TIMEOUT)
+                         ? a.n_items
+                         : (int)atomicAdd(a.head, 1u);
         __syncthreads();
         const int item = s_item;
         if (item >= a.n_items) break;
@@ -132,6 +139,9 @@ __global__ void __launch_bounds__(RB) batch_kernel(DevParams P0, BatchArgs a) {
                     Vs4[t] = make_float4(v.x, v.y, g0, g1);
                 }
             }
+            // thread 0 has armed the barrier (arrive.expect_tx) before any thread
+            // of the block, its own warp's lanes included, starts to wait on it
+            __syncthreads();
             // a failed wait ends the whole block (block-uniform decision), after
             // thread 0 has let the copy in flight land
             const bool ok = mbar_wait_bounded(&bar, phase);
@@ -143,7 +153,7 @@ __global__ void __launch_bounds__(RB) batch_kernel(DevParams P0, BatchArgs a) {
                 return;
             }
             phase ^= 1u;
-            s0 = block_nearest_segment<RB>(rec, n, x.X, x.Y, red_f, red_i, &d20);
+            s0 = block_nearest_segment<RB>(rec, n, x.X, x.Y, red_f, red_i, &d20, a.status);
             staged = i;
         }
 

@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(32 * BFGS_WPB_MAX) repair_bfgs_kernel(
             if (d < bd) { bd = d; s0 = i; }
         }
         warp_argmin(bd, s0);
+        s0 = seg_or_zero(s0, nt, lane == 0 ? status : nullptr);
         __syncwarp();
         const CartMerit<FAST> f{rec, x0, s0, ck, Tape{tape_s, 1, 0}};
         double P0;

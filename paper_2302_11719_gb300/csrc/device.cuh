@@ -671,6 +671,17 @@ __device__ __forceinline__ float rollout_sample(const DevParams& P, const float4
     return acc;
 }
 
+// Result of a nearest-segment search.  The search starts its argmin at an
+// out-of-range index, which survives only when no squared distance is below
+// 3e38 (a start position that is NaN, infinite or beyond ~1.8e19 m): segment 0
+// is taken instead, so that every later table access stays in bounds, and the
+// NUMERIC bit of the status word reports the state.
+__device__ __forceinline__ int seg_or_zero(int s, int n, unsigned* status) {
+    if ((unsigned)s < (unsigned)n) return s;
+    if (status) atomicOr(status, SMPPI_DEV_NUMERIC);
+    return 0;
+}
+
 // Warp-level argmin of (d2, index) with lowest index on ties.
 __device__ __forceinline__ void warp_argmin(float& d, int& i) {
 #pragma unroll

@@ -85,7 +85,7 @@ struct ApplyArgs {
 };
 
 cudaError_t launch_seg0(const DevParams& P, const float4* rec, int n_seq,
-                        const float* x0, int* seg0, cudaStream_t st);
+                        const float* x0, int* seg0, unsigned* status, cudaStream_t st);
 cudaError_t launch_cost_grad(const DevParams& P, const float4* rec,
                              const RepairWs& ws, int n_seq, const float* x0, const float* V, int N,
                              float w_run, float w_cbf, int ck, double* J_out, float* grad_out,

@@ -5,12 +5,13 @@
 // The iteration's scratch (segment-pair table, rollout costs, block minima, the
 // update kernel's partials and counters) lives in one file-scope __device__
 // array of fixed size, so the call allocates nothing.  Host code cannot use
-// the array's name as a device address: its device address is looked up once
-// per device with cudaGetSymbolAddress (the first call on a device does this,
-// so that call should come before any stream capture) and passed to the
-// kernels.  Every call on a device shares the same array and leaves the last
-// call's contents in it; calls whose work overlaps on the GPU (different
-// streams, host threads) race on it and must be serialised by the caller.
+// the array's name as a device address: its device address is looked up with
+// cudaGetSymbolAddress (the first call on a device does this, so that call
+// should come before any stream capture; later calls outside a capture look it
+// up again) and passed to the kernels.  Every call on a device shares the
+// same array and leaves the last call's contents in it; calls whose work
+// overlaps on the GPU (different streams, host threads) race on it and must be
+// serialised by the caller.
 #include <mutex>
 
 #include "kernels.cuh"
@@ -40,15 +41,21 @@ constexpr int MAX_DEVICES = 64;
 std::mutex g_mu;
 unsigned char* g_scratch_dev[MAX_DEVICES] = {};
 
-// Device address of g_scratch on the current device (looked up once per device).
-smppi_status scratch_address(unsigned char** out) {
+// Device address of g_scratch on the current device.  Looked up again on
+// every call made outside a stream capture (the address does not survive a
+// device reset, after which the module is loaded anew); a call inside a
+// capture uses the address of the last call on the device.
+smppi_status scratch_address(cudaStream_t st, unsigned char** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return report_error(SMPPI_ERR_CUDA, cudaGetErrorString(e));
     if (dev < 0 || dev >= MAX_DEVICES)
         return report_error(SMPPI_ERR_ARG, "smppi_step_noalloc: device ordinal out of range");
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return report_error(SMPPI_ERR_CUDA, cudaGetErrorString(e));
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_dev[dev]) {
+    if (!g_scratch_dev[dev] || cs == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess || !p)
@@ -75,10 +82,10 @@ extern "C" smppi_status smppi_step_noalloc(const smppi_params* p, const float* x
         return report_error(SMPPI_ERR_ARG, "smppi_step_noalloc: instance must be < 2^24");
     if (rollout_smem_bytes(p->n_track, p->T) > 200 * 1024)
         return report_error(SMPPI_ERR_ARG, "smppi_step_noalloc: n_track and T exceed shared memory");
-    unsigned char* base = nullptr;
-    s = scratch_address(&base);
-    if (s != SMPPI_OK) return s;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    unsigned char* base = nullptr;
+    s = scratch_address(st, &base);
+    if (s != SMPPI_OK) return s;
     const DevParams dp = derive_params(*p);
     float4* rec = reinterpret_cast<float4*>(base + OFF_REC);
     float* S = S_out ? S_out : reinterpret_cast<float*>(base + OFF_S);

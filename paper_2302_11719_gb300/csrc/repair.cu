@@ -15,7 +15,8 @@ namespace smppi {
 
 // Global nearest segment of each x0 (one warp per sequence; lowest index on ties).
 __global__ void seg0_kernel(DevParams P, const float4* __restrict__ rec, int n_seq,
-                            const float* __restrict__ x0, int* __restrict__ seg0) {
+                            const float* __restrict__ x0, int* __restrict__ seg0,
+                            unsigned* __restrict__ status) {
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     if (w >= n_seq) return;
     const float X = x0[6 * w + 3], Y = x0[6 * w + 4];
@@ -26,7 +27,7 @@ __global__ void seg0_kernel(DevParams P, const float4* __restrict__ rec, int n_s
         if (d < bd) { bd = d; bi = i; }
     }
     warp_argmin(bd, bi);
-    if (lane == 0) seg0[w] = bi;
+    if (lane == 0) seg0[w] = seg_or_zero(bi, P.n_track, status);
 }
 
 constexpr int REP_BLK = 64;
@@ -177,7 +178,8 @@ __global__ void __launch_bounds__(REPB_BLK) repair_block_kernel(
         }
         return;
     }
-    const int s0 = block_nearest_segment<REPB_BLK>(rec, n, x0.X, x0.Y, s_red, s_redi, nullptr);
+    const int s0 = block_nearest_segment<REPB_BLK>(rec, n, x0.X, x0.Y, s_red, s_redi, nullptr,
+                                                   status);
     repair_in_block<REPB_BLK, FAST>(P, rec, x0, s0, Vw, G, tape_s, n_iters, mode, delta, ck,
                               merit_out ? merit_out + (size_t)q * (n_iters + 1) : nullptr,
                               iters_out ? iters_out + q : nullptr, status, sm);
@@ -194,10 +196,10 @@ __global__ void apply_kernel(DevParams P, ApplyArgs ap, const float* V_exec) {
 
 // ----------------------------------------------------------------------------
 cudaError_t launch_seg0(const DevParams& P, const float4* rec, int n_seq, const float* x0,
-                        int* seg0, cudaStream_t st) {
+                        int* seg0, unsigned* status, cudaStream_t st) {
     const int warps_per_block = 4;
     seg0_kernel<<<(n_seq + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, st>>>(
-        P, rec, n_seq, x0, seg0);
+        P, rec, n_seq, x0, seg0, status);
     return cudaGetLastError();
 }
 

@@ -18,6 +18,8 @@
 //   these problems that leaves a small fraction of K.  The last block to
 //   finish (device-scope ticket) sums the non-empty block partials in float64
 //   and writes V+ = clamp(V + A / eta).
+#include <atomic>
+
 #include "rollout2.cuh"
 #include "shield.cuh"
 
@@ -81,8 +83,9 @@ __device__ __forceinline__ bool stage_problem(const DevParams& P, const float4* 
     if (tid == 0) {
         for (int w = 1; w < BLK / 32; ++w)
             if (red_f[w] < bd || (red_f[w] == bd && red_i[w] < bi)) { bd = red_f[w]; bi = red_i[w]; }
-        *s_seg0 = bi;
-        *s_d20 = bd;
+        const int s0 = seg_or_zero(bi, n, status);
+        *s_seg0 = s0;
+        *s_d20 = (s0 == bi) ? bd : rec_d2_seg(rec, s0, X0, Y0);
     }
     __syncthreads();
     return true;
@@ -196,9 +199,10 @@ __global__ void __launch_bounds__(ROLL2_BLK, 2) mppi_rollout2_kernel(
     if (tid == 0) {
         for (int w = 1; w < NW; ++w)
             if (red_f[w] < bd || (red_f[w] == bd && red_i[w] < bi)) { bd = red_f[w]; bi = red_i[w]; }
-        s_seg0 = bi;
-        s_d20 = bd;
-        if (blockIdx.x == 0 && seg0_out) *seg0_out = bi;
+        const int s0 = seg_or_zero(bi, n, status);
+        s_seg0 = s0;
+        s_d20 = (s0 == bi) ? bd : rec_d2_seg(rec, s0, X0, Y0);
+        if (blockIdx.x == 0 && seg0_out) *seg0_out = s0;
     }
     __syncthreads();
 
@@ -566,13 +570,18 @@ cudaError_t launch_rec_table(const float* track_xy, int n, float4* rec, cudaStre
 }
 
 int update_grid(int K) {
-    static int sms = 0;
-    if (sms == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
+    // SM count of the current device, cached per device ordinal (every thread
+    // that fills an entry writes the same value)
+    constexpr int MAX_DEV = 64;
+    static std::atomic<int> sms_of[MAX_DEV];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+    int sms = dev < MAX_DEV ? sms_of[dev].load(std::memory_order_relaxed) : 0;
+    if (sms < 1) {
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
             sms < 1)
             sms = 1;
+        if (dev < MAX_DEV) sms_of[dev].store(sms, std::memory_order_relaxed);
     }
     const int by_k = (K + UPD_BLK - 1) / UPD_BLK;
     int g = by_k < sms ? by_k : sms;

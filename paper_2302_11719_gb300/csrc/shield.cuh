@@ -549,10 +549,11 @@ __device__ double repair_in_block(const DevParams& P, const float4* rec,
 }
 
 // Nearest segment of (X, Y) over the whole track by one block (lowest index on
-// ties); every thread gets the result.
+// ties); every thread gets the result (segment 0 and the NUMERIC bit when no
+// distance is finite, seg_or_zero).
 template <int BLK>
 __device__ int block_nearest_segment(const float4* rec, int n, float X, float Y,
-                                     float* red_f, int* red_i, float* d2_out) {
+                                     float* red_f, int* red_i, float* d2_out, unsigned* status) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     float bd = 3.0e38f;
     int bi = 0x7fffffff;
@@ -568,8 +569,9 @@ __device__ int block_nearest_segment(const float4* rec, int n, float X, float Y,
     for (int w = 1; w < BLK / 32; ++w)
         if (red_f[w] < bd || (red_f[w] == bd && red_i[w] < bi)) { bd = red_f[w]; bi = red_i[w]; }
     __syncthreads();
-    if (d2_out) *d2_out = bd;
-    return bi;
+    const int s0 = seg_or_zero(bi, n, tid == 0 ? status : nullptr);
+    if (d2_out) *d2_out = (s0 == bi) ? bd : rec_d2_seg(rec, s0, X, Y);
+    return s0;
 }
 
 }  // namespace
