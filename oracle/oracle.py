@@ -74,6 +74,8 @@ def lib():
                                       _dp]
         L.orc_seg_dist2.argtypes = [_PP, C.c_int, C.c_double, C.c_double]
         L.orc_seg_dist2.restype = C.c_double
+        L.orc_kappa_at.argtypes = [_PP, C.c_double]
+        L.orc_kappa_at.restype = C.c_double
         L.orc_track_nearest.argtypes = [_PP, C.c_double, C.c_double, _dp]
         L.orc_track_nearest.restype = C.c_int
         L.orc_track_follow.argtypes = [_PP, C.c_int, C.c_double, C.c_double, _dp]
@@ -256,6 +258,13 @@ def step(m: Model, x, u):
 
 def seg_dist2(m: Model, i, X, Y):
     return lib().orc_seg_dist2(m.ptr, int(i), float(X), float(Y))
+
+
+def kappa_at(m: Model, s):
+    """kappa(s) of the curvilinear model (state_kind 1): the curvature samples
+    interpolated linearly in arc length, s taken modulo the track length."""
+    assert m.kappa is not None, "kappa(s) needs a curvilinear model (state_kind 1)"
+    return lib().orc_kappa_at(m.ptr, float(s))
 
 
 def track_nearest(m: Model, X, Y):

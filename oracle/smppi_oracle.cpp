@@ -351,6 +351,9 @@ double orc_seg_dist2(const OrcParams* p, int i, double X, double Y) {
     return seg_dist2<double>(p, i, X, Y);
 }
 
+// kappa(s) of the curvilinear model (the interpolation above), for the pins.
+double orc_kappa_at(const OrcParams* p, double s) { return kappa_at<double>(p, s); }
+
 // Global nearest segment (brute force over all segments, lowest index on ties).
 int orc_track_nearest(const OrcParams* p, double X, double Y, double* d2_out) {
     int best = 0;

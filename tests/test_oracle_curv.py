@@ -7,7 +7,12 @@ turning angles, Frenet kinematics).
     n chords; traversed clockwise, the samples change sign;
   * on the ellipse track the table follows the ellipse's analytic curvature
     ab / (a^2 sin^2 t + b^2 cos^2 t)^(3/2) at the same arc lengths (positive:
-    the counter-clockwise centreline turns left);
+    the counter-clockwise centreline turns left), and so does kappa(s), the
+    interpolation the model evaluates, at arbitrary arc lengths (between the
+    stations, across the wrap, whole laps forward and backward);
+  * on the ellipse, where the curvature varies, the curvilinear and Cartesian
+    models agree in (s, e_y, e_psi) with respect to the exact ellipse to first
+    order in dt;
   * on a circle the curvilinear model and the Cartesian model, started on the
     centreline along the tangent and driven by the same controls, give the same
     (s, e_y, e_psi) (the Cartesian state converted exactly), with a difference
@@ -72,6 +77,104 @@ def test_curvature_ellipse_analytic(orc):
     assert np.all(k > 0)
     assert np.max(np.abs(k / ka - 1)) < 1e-2
     assert np.mean(np.abs(k / ka - 1)) < 2e-3
+
+
+def _ellipse_curv_model(orc):
+    a, b, n = 20.0, 12.0, 1024
+    tr = I.ellipse_track(a, b, n)
+    m = orc.Model(_curv(I.make_params(K=1, T=10)), tr)
+    seg = np.hypot(*(np.roll(tr, -1, 0) - tr).astype(np.float64).T)
+    st = np.concatenate([[0.0], np.cumsum(seg)])
+    return m, a, b, n, st
+
+
+def _ellipse_kappa(a, b, n, st, s):
+    """Analytic curvature of the ellipse at the parameter whose polyline arc
+    length is s (0 <= s < L)."""
+    t = np.interp(s, st, 2 * np.pi * np.arange(n + 1) / n)
+    return a * b / (a * a * np.sin(t) ** 2 + b * b * np.cos(t) ** 2) ** 1.5
+
+
+def test_kappa_at_interpolates_ellipse_curvature(orc):
+    """kappa(s), the function the curvilinear model evaluates, at arbitrary arc
+    lengths (between the stations, in the last interval that wraps to sample 0,
+    shifted by whole laps forward and backward) against the ellipse's analytic
+    curvature.  The interpolation error is below 0.3 %; taking one station's
+    sample instead of interpolating would miss by 0.8 % between stations."""
+    m, a, b, n, st = _ellipse_curv_model(orc)
+    k, L = orc.curvature_table(m)
+    rng = np.random.default_rng(5)
+    s = rng.uniform(0.0, L, 3000)
+    ka = _ellipse_kappa(a, b, n, st, s)
+    kk = np.array([orc.kappa_at(m, x) for x in s])
+    assert np.max(np.abs(kk / ka - 1)) < 4e-3
+    assert np.mean(np.abs(kk / ka - 1)) < 1e-3
+    # midway between stations, where a wrong station index or slope errs most
+    mid = (np.arange(n) + 0.5) * L / n
+    kmid = np.array([orc.kappa_at(m, x) for x in mid])
+    assert np.max(np.abs(kmid / _ellipse_kappa(a, b, n, st, mid) - 1)) < 4e-3
+    # the last interval interpolates towards sample 0 (the wrap)
+    last = np.linspace((n - 1) * L / n, L, 25, endpoint=False)
+    kl = np.array([orc.kappa_at(m, x) for x in last])
+    assert np.max(np.abs(kl / _ellipse_kappa(a, b, n, st, last) - 1)) < 4e-3
+    # periodic in s with period L, for s >= L and s < 0
+    for shift in (L, 3 * L, -L, -2 * L):
+        ks = np.array([orc.kappa_at(m, x + shift) for x in s[:300]])
+        assert np.max(np.abs(ks - kk[:300])) <= 1e-12 * np.max(np.abs(kk))
+
+
+def _ellipse_frenet(a, b, X, Y, psi, t):
+    """(s, e_y, e_psi) of a Cartesian pose with respect to the exact ellipse
+    (a cos t, b sin t): the foot point by Newton from parameter t, the arc
+    length from t = 0 by quadrature, e_y positive to the left."""
+    from scipy.integrate import quad
+    for _ in range(50):
+        ex, ey = a * np.cos(t) - X, b * np.sin(t) - Y
+        dx, dy = -a * np.sin(t), b * np.cos(t)
+        t -= (ex * dx + ey * dy) / (dx * dx + dy * dy - ex * a * np.cos(t) - ey * b * np.sin(t))
+    ex, ey = a * np.cos(t), b * np.sin(t)
+    dx, dy = -a * np.sin(t), b * np.cos(t)
+    nn = np.hypot(dx, dy)
+    s = quad(lambda u: np.hypot(a * np.sin(u), b * np.cos(u)), 0.0, t)[0]
+    e_psi = (psi - np.arctan2(dy, dx) + np.pi) % (2 * np.pi) - np.pi
+    return (s, (-(X - ex) * dy + (Y - ey) * dx) / nn, e_psi), t
+
+
+def _ellipse_runs(orc, dt, tend=1.0):
+    a, b, n = 20.0, 12.0, 1024
+    tr = I.ellipse_track(a, b, n)
+    T = int(round(tend / dt))
+    pc = I.make_params(K=1, T=T, dt=dt, half_width=2.0)
+    mc, mk = orc.Model(pc, tr), orc.Model(_curv(pc), tr)
+    t = np.arange(T) * dt
+    V = np.stack([0.08 + 0.05 * np.sin(3 * t), 0.3 * np.cos(2 * t)], 1)
+    _, tc, _ = orc.rollout(mc, np.array([5.0, 0, 0, a, 0, np.pi / 2]), V, noisy=False)
+    _, tk, _ = orc.rollout(mk, np.array([5.0, 0, 0, 0, 0, 0]), V, noisy=False)
+    conv, tp = [], 0.0
+    for row in tc:
+        f, tp = _ellipse_frenet(a, b, row[3], row[4], row[5], tp)
+        conv.append(f)
+    return (np.abs(np.array(conv) - tk[:, 3:6]).max(0), np.abs(tc[:, :3] - tk[:, :3]).max(),
+            np.abs(tk[:, 4]).max())
+
+
+def test_curvilinear_matches_cartesian_on_ellipse(orc):
+    """Where the curvature varies (the first 5 m from the end of the major axis,
+    kappa from 0.139 /m down): the curvilinear model on the interpolated kappa(s)
+    and the Cartesian model on the polyline, same start and controls, agree in
+    (s, e_y, e_psi) against the exact ellipse to first order in dt (each
+    halving of dt halves the gap; a wrong kappa(s) would leave a gap that does
+    not shrink), with identical velocity states."""
+    e4, dv4, _ = _ellipse_runs(orc, 4e-3)
+    e2, dv2, _ = _ellipse_runs(orc, 2e-3)
+    e1, dv1, ey_max = _ellipse_runs(orc, 1e-3)
+    assert dv1 == 0.0 and dv2 == 0.0 and dv4 == 0.0
+    assert ey_max > 0.3                              # the path really leaves the centreline
+    assert e1[0] < 5e-4 and e1[1] < 2e-3 and e1[2] < 2e-4
+    for hi, lo in ((e4, e2), (e2, e1)):
+        r = hi / lo
+        assert np.all((r[:2] > 1.7) & (r[:2] < 2.3)), r
+        assert 1.5 < r[2] < 2.6, r
 
 
 def _circle_runs(orc, dt, R=10.0, n=256, tend=0.5):

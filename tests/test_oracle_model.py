@@ -143,6 +143,39 @@ def test_ellipse_distance_and_tracking(orc, model):
             assert dd2 == pytest.approx(d2, abs=1e-12)
 
 
+def test_tracked_projection_outside_track(orc, model):
+    """The tracked nearest segment (reading c15) followed along continuous paths
+    that leave the track by up to twice the half-width, inward and outward: at
+    every point it equals the global nearest segment (same squared distance;
+    the segment itself up to equal-distance ties).  The ellipse's smallest
+    radius of curvature b^2/a = 7.2 m exceeds 2w = 4 m, so no path crosses the
+    inner cut locus (the part of the major axis between the centres of
+    curvature).  Past it the two differ: a path from the top of the track
+    straight down to (0, -1) keeps the top as its (local) nearest point at
+    13 m while the bottom, at 11 m, is the global one."""
+    a, b, n = 20.0, 12.0, 1024
+    rng = np.random.default_rng(11)
+    for _ in range(60):
+        th = rng.uniform(0, 2 * np.pi)
+        tx, ty = -a * math.sin(th), b * math.cos(th)
+        nn = math.hypot(tx, ty)
+        d_end = rng.choice([-1.0, 1.0]) * rng.uniform(2.0, 4.0)
+        seg, _ = orc.track_nearest(model, a * math.cos(th), b * math.sin(th))
+        for d in np.linspace(0.0, d_end, 41)[1:]:
+            X, Y = a * math.cos(th) - d * ty / nn, b * math.sin(th) + d * tx / nn
+            seg, d2 = orc.track_follow(model, seg, X, Y)
+            gseg, gd2 = orc.track_nearest(model, X, Y)
+            assert d2 == gd2, (th, d)
+            assert seg == gseg or orc.seg_dist2(model, gseg, X, Y) == d2
+    # past the inner cut locus the tracked and the global projection differ
+    seg, _ = orc.track_nearest(model, 0.0, b)
+    for Y in np.linspace(b, -1.0, 131)[1:]:
+        seg, d2 = orc.track_follow(model, seg, 0.0, Y)
+    _, gd2 = orc.track_nearest(model, 0.0, -1.0)
+    assert math.sqrt(d2) == pytest.approx(13.0, abs=1e-3)
+    assert math.sqrt(gd2) == pytest.approx(11.0, abs=1e-3)
+
+
 def test_segment_distance_endpoints(orc, model):
     A = model.track[0].astype(np.float64)
     Bp = model.track[1].astype(np.float64)
