@@ -27,7 +27,8 @@
  *     nearest centreline segment: the kernels then start from segment 0, set
  *     SMPPI_DEV_NUMERIC and produce NaN costs (V+ then lies on the lower
  *     corner of the control box); the handle stays usable.  Host-buffer calls
- *     refuse a non-finite x0 with SMPPI_ERR_ARG before anything is enqueued.
+ *     refuse an x0 with a non-finite entry or a position beyond 1e18 m with
+ *     SMPPI_ERR_ARG before anything is enqueued.
  *     NaN or Inf arising later (in velocities, costs, merits) is flagged as
  *     described below.
  *   - All work is enqueued on the handle's CUDA stream and is asynchronous;
@@ -167,6 +168,36 @@ smppi_status smppi_sync_status(smppi_handle* h, uint32_t* bits_out);
  */
 smppi_status smppi_step(smppi_handle* h, const float* x0, float* V, uint32_t iter,
                         uint32_t instance, float* S_out, float* traj_out);
+
+/*
+ * Rollouts sharded over several devices or calls (Eq. 10-11 over a partition of
+ * the K rollouts; Alg. 2's sampling loop is a parallel loop over them).  The
+ * weights are min-shifted per slice and rescaled at the merge, a log-sum-exp
+ * merge: omega_k = exp(-(S_k - m)/lambda) = c_g exp(-(S_k - m_g)/lambda) with
+ * m = min_g m_g and c_g = exp(-(m_g - m)/lambda).
+ *
+ * smppi_step_partial runs rollouts k_lo .. k_hi - 1 of iteration (iter,
+ * instance) (their Philox counters, so slices of one iteration on different
+ * devices draw exactly the noise of the unsharded iteration) and writes
+ *   partial_out [2T + 2] (DEVICE, float64) = (m_g, eta_g, A_g[0 .. 2T - 1]):
+ *   m_g = min S_k over the slice, eta_g = sum exp(-(S_k - m_g)/lambda) and
+ *   A_g[2t + j] = sum exp(-(S_k - m_g)/lambda) eps_{k,t,j} (the noise sum of
+ *   rollouts whose slice weight exceeds the skip threshold of all K rollouts).
+ * V [T x 2] is read, not written.  0 <= k_lo < k_hi <= K (the handle's K),
+ * else SMPPI_ERR_ARG.  Uses the handle's workspace (one slice at a time per
+ * handle).
+ *
+ * smppi_merge_partials forms V <- clamp(V + A / eta) from n_parts partials
+ * [n_parts x (2T + 2)] (DEVICE, float64, e.g. gathered from every device by
+ * an all-gather), with eta = sum_g c_g eta_g and A = sum_g c_g A_g summed in
+ * float64 in slice order, so every device that merges the same partials gets
+ * the same V+.  One partial covering all K gives smppi_step's V+ bit for bit.
+ * n_parts in [1, 1024], else SMPPI_ERR_ARG.
+ */
+smppi_status smppi_step_partial(smppi_handle* h, const float* x0, const float* V, uint32_t iter,
+                                uint32_t instance, int k_lo, int k_hi, double* partial_out);
+smppi_status smppi_merge_partials(smppi_handle* h, int n_parts, const double* partials,
+                                  float* V);
 
 /* The control update alone (Eq. 10-11) from given rollout costs S [K]: the
  * noise of iteration (iter, instance) is regenerated.  V [T x 2] in/out as
@@ -362,7 +393,8 @@ smppi_status smppi_step_noalloc(const smppi_params* p, const float* x0, float* V
 #define SMPPI_KERNEL_APPLY 4      /* closed-loop step */
 #define SMPPI_KERNEL_COST_GRAD 5  /* cost + adjoint gradient */
 #define SMPPI_KERNEL_UPDATE_SHIELD 6  /* update -> V+, then (last block) shield and closed-loop step */
-#define SMPPI_KERNEL_KINDS 7
+#define SMPPI_KERNEL_MERGE 7      /* merge of slice partials -> V+ */
+#define SMPPI_KERNEL_KINDS 8
 smppi_status smppi_timing(smppi_handle* h, int enable);
 smppi_status smppi_timing_read(smppi_handle* h, double* ms_out, int* count_out, int n_kinds);
 

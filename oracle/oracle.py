@@ -91,6 +91,8 @@ def lib():
         L.orc_rollout.restype = C.c_double
         L.orc_update.argtypes = [_PP, _dp, _dp, C.c_uint32, C.c_uint32, _dp, _dp]
         L.orc_mppi_step.argtypes = [_PP, _dp, _dp, C.c_uint32, C.c_uint32, _dp, _dp, C.c_int]
+        L.orc_partial.argtypes = [_PP, _dp, C.c_uint32, C.c_uint32, C.c_int, C.c_int, _dp]
+        L.orc_merge.argtypes = [_PP, C.c_int, _dp, _dp, _dp]
         L.orc_cost.argtypes = [_PP, _dp, _dp, C.c_int, C.c_double, C.c_double]
         L.orc_cost.restype = C.c_double
         L.orc_merit.argtypes = [_PP, _dp, _dp]; L.orc_merit.restype = C.c_double
@@ -308,6 +310,25 @@ def update(m: Model, S, V, it=0, instance=0):
     lib().orc_update(m.ptr, sp, vp, int(it), int(instance), vplus.ctypes.data_as(_dp),
                      om.ctypes.data_as(_dp))
     return vplus, om
+
+
+def partial(m: Model, S_slice, k_lo, it=0, instance=0):
+    """(m_g, eta_g, A_g) of rollouts k_lo .. k_lo + len(S_slice) - 1 from their
+    costs: a float64 array of 2T + 2 values."""
+    S, sp = _d(S_slice)
+    out = np.zeros(2 * m.T + 2)
+    lib().orc_partial(m.ptr, sp, int(it), int(instance), int(k_lo), int(k_lo + S.size),
+                      out.ctypes.data_as(_dp))
+    return out
+
+
+def merge(m: Model, parts, V):
+    """V+ (T, 2) from slice partials (n_parts, 2T + 2)."""
+    P = np.ascontiguousarray(parts, np.float64).reshape(-1, 2 * m.T + 2)
+    V, vp = _d(V, 2 * m.T)
+    out = np.zeros((m.T, 2))
+    lib().orc_merge(m.ptr, P.shape[0], P.ctypes.data_as(_dp), vp, out.ctypes.data_as(_dp))
+    return out
 
 
 def mppi_step(m: Model, x0, V, it=0, instance=0, nthreads=1):

@@ -488,6 +488,55 @@ void orc_update(const OrcParams* p, const double* S, const double* V, uint32_t i
     if (omega_out) for (int k = 0; k < K; ++k) omega_out[k] = omega[k] / eta;
 }
 
+// The update of Eq. 10-11 over a partition of the rollouts (the sampling loop
+// of Alg. 2 is a loop over independent rollouts, so its K rollouts can be
+// split into slices): for the slice k_lo .. k_hi - 1 with costs S[0 ..],
+//   m_g = min S_k,  eta_g = sum_k exp(-(S_k - m_g) / lambda),
+//   A_g[2t + j] = sum_k exp(-(S_k - m_g) / lambda) eps_{k,t,j},
+// written to out [2T + 2] = (m_g, eta_g, A_g).
+void orc_partial(const OrcParams* p, const double* S, uint32_t iter, uint32_t instance, int k_lo,
+                 int k_hi, double* out) {
+    const int T = p->T, n = k_hi - k_lo;
+    double m = S[0];
+    for (int i = 1; i < n; ++i) if (S[i] < m) m = S[i];
+    double eta = 0.0;
+    std::vector<double> acc(2 * T, 0.0);
+    for (int i = 0; i < n; ++i) {
+        const double w = std::exp(-(S[i] - m) / p->lambda);
+        eta += w;
+        for (int t = 0; t < T; ++t) {
+            double eps[2];
+            orc_noise(p, iter, instance, (uint32_t)(k_lo + i), (uint32_t)t, eps);
+            acc[2 * t] += w * eps[0];
+            acc[2 * t + 1] += w * eps[1];
+        }
+    }
+    out[0] = m;
+    out[1] = eta;
+    for (int j = 0; j < 2 * T; ++j) out[2 + j] = acc[j];
+}
+
+// V+ from the slices' partials (n_parts x (2T + 2)): with m = min_g m_g the
+// weights of slice g are its own times c_g = exp(-(m_g - m) / lambda), so
+//   v_t^+ = clamp(v_t + sum_g c_g A_g[t] / sum_g c_g eta_g)
+// is the update of Eq. 10-11 over all rollouts of the slices.
+void orc_merge(const OrcParams* p, int n_parts, const double* parts, const double* V,
+               double* Vplus) {
+    const int T = p->T, W = 2 * T + 2;
+    double m = parts[0];
+    for (int g = 1; g < n_parts; ++g) if (parts[g * W] < m) m = parts[g * W];
+    double eta = 0.0;
+    std::vector<double> c(n_parts), acc(2 * T, 0.0);
+    for (int g = 0; g < n_parts; ++g) {
+        c[g] = std::exp(-(parts[g * W] - m) / p->lambda);
+        eta += c[g] * parts[g * W + 1];
+        for (int j = 0; j < 2 * T; ++j) acc[j] += c[g] * parts[g * W + 2 + j];
+    }
+    for (int t = 0; t < T; ++t)
+        for (int j = 0; j < 2; ++j)
+            Vplus[2 * t + j] = clamp_ctrl<double>(p, j, V[2 * t + j] + acc[2 * t + j] / eta);
+}
+
 // One MPPI iteration (Alg. 2, the sampling loop and OptimalControl): K noisy
 // rollouts, then the update.  The per-rollout costs are computed in parallel
 // over k with `nthreads` threads; every reduction runs in index order, so the

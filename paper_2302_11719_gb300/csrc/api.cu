@@ -503,6 +503,48 @@ smppi_status smppi_step(smppi_handle* h, const float* x0, float* V, uint32_t ite
     return enqueue_step(h, h->st, x0, V, iter, instance, S_out, traj_out, nullptr);
 }
 
+smppi_status smppi_step_partial(smppi_handle* h, const float* x0, const float* V, uint32_t iter,
+                                uint32_t instance, int k_lo, int k_hi, double* partial_out) {
+    if (!h) return fail(nullptr, SMPPI_ERR_ARG, "handle is NULL");
+    if (!x0 || !V || !partial_out)
+        return fail(h, SMPPI_ERR_ARG, "x0, V and partial_out must not be NULL");
+    if (instance >= (1u << 24)) return fail(h, SMPPI_ERR_ARG, "instance must be < 2^24");
+    if (k_lo < 0 || k_lo >= k_hi || k_hi > h->p.K)
+        return fail(h, SMPPI_ERR_ARG, "need 0 <= k_lo < k_hi <= K");
+    // the slice's rollouts as a problem of k_hi - k_lo rollouts whose Philox
+    // counters start at k_lo; the noise-skip threshold stays the one of all K
+    DevParams dp = h->dp;
+    dp.K = k_hi - k_lo;
+    const uint32_t ctr3 = instance << 8;
+    cudaStream_t st = h->st;
+    int ev = tic(h, st);
+    if (h->p.state_kind == 1)
+        CU(h, launch_rollout_curv(dp, h->kappa, false, x0, V, iter, ctr3, nullptr, h->S_ws,
+                                  nullptr, h->blk_min, h->status, st, (uint32_t)k_lo));
+    else
+        CU(h, launch_rollout(dp, false, x0, V, h->rec, iter, ctr3, nullptr, h->S_ws, nullptr,
+                             h->blk_min, nullptr, h->status, st, (uint32_t)k_lo));
+    toc(h, st, SMPPI_KERNEL_ROLLOUT, ev);
+    ev = tic(h, st);
+    CU(h, launch_update_partial(dp, h->S_ws, h->blk_min, rollout_blocks(dp), V, iter, ctr3,
+                                h->part_acc, h->part_eta, h->part_has, h->ticket, h->status,
+                                (uint32_t)k_lo, partial_out, st));
+    toc(h, st, SMPPI_KERNEL_UPDATE, ev);
+    return SMPPI_OK;
+}
+
+smppi_status smppi_merge_partials(smppi_handle* h, int n_parts, const double* partials,
+                                  float* V) {
+    if (!h) return fail(nullptr, SMPPI_ERR_ARG, "handle is NULL");
+    if (!partials || !V) return fail(h, SMPPI_ERR_ARG, "partials and V must not be NULL");
+    if (n_parts < 1 || n_parts > MERGE_MAX_PARTS)
+        return fail(h, SMPPI_ERR_ARG, "n_parts must be in [1, 1024]");
+    const int ev = tic(h, h->st);
+    CU(h, launch_merge(h->dp, n_parts, partials, V, h->status, h->st));
+    toc(h, h->st, SMPPI_KERNEL_MERGE, ev);
+    return SMPPI_OK;
+}
+
 smppi_status smppi_update(smppi_handle* h, const float* S, float* V, uint32_t iter,
                           uint32_t instance) {
     if (!h) return fail(nullptr, SMPPI_ERR_ARG, "handle is NULL");
@@ -605,10 +647,12 @@ smppi_status smppi_shield_update(smppi_handle* h, float* x0, float* V, float* V_
     if (instance >= (1u << 24)) return fail(h, SMPPI_ERR_ARG, "instance must be < 2^24");
     if (!host_buffers)
         return enqueue_shield(h, h->st, x0, V, V_safe, iter, instance, n_repair, merit_out, nullptr);
-    // host state: the start position is checked here (the device search for the
-    // nearest segment has no answer for a non-finite one)
+    // host state: checked here (the device search for the nearest segment has no
+    // answer for a position whose squared distances overflow float32)
     for (int j = 0; j < 6; ++j)
         if (!std::isfinite(x0[j])) return fail(h, SMPPI_ERR_ARG, "x0 must be finite");
+    if (std::fabs(x0[3]) > 1e18f || std::fabs(x0[4]) > 1e18f)
+        return fail(h, SMPPI_ERR_ARG, "x0 position beyond 1e18 m");
     const size_t vb = sizeof(float) * 2 * h->p.T;
     double* dm = nullptr;
     if (merit_out && n_repair > 0) {

@@ -124,7 +124,8 @@ __global__ void __launch_bounds__(ROLL2_BLK, 2) mppi_rollout_curv_kernel(
     DevParams P, const float* __restrict__ kappa, const float* __restrict__ x0g,
     const float* __restrict__ Vg, uint32_t iter, uint32_t ctr3,
     const uint32_t* __restrict__ iter_dev, float* __restrict__ S_out,
-    float* __restrict__ traj, float* __restrict__ blk_min, unsigned* __restrict__ status) {
+    float* __restrict__ traj, float* __restrict__ blk_min, unsigned* __restrict__ status,
+    uint32_t k_off) {
     constexpr int BLK = ROLL2_BLK, NW = BLK / 32;
     griddep_launch_dependents();
     griddep_wait();
@@ -148,8 +149,8 @@ __global__ void __launch_bounds__(ROLL2_BLK, 2) mppi_rollout_curv_kernel(
     const bool act_a = ka < P.K, act_b = kb < P.K;
     float* ta = (DUMP && act_a) ? traj + (size_t)ka * (T + 1) * 6 : nullptr;
     float* tb = (DUMP && act_b) ? traj + (size_t)kb * (T + 1) * 6 : nullptr;
-    const float2 S = x2::rollout2_curv<DUMP>(P, kt, Vp, make_state(x0g), (uint32_t)ka,
-                                             (uint32_t)kb, iter, ctr3, ta, tb);
+    const float2 S = x2::rollout2_curv<DUMP>(P, kt, Vp, make_state(x0g), (uint32_t)ka + k_off,
+                                             (uint32_t)kb + k_off, iter, ctr3, ta, tb);
     if (act_a) {
         S_out[ka] = S.x;
         if (!isfinite(S.x)) atomicOr(status, SMPPI_DEV_NUMERIC);
@@ -178,7 +179,8 @@ size_t curv_rollout_smem_bytes(int n_track, int T) {
 cudaError_t launch_rollout_curv(const DevParams& P, const float* kappa, bool dump, const float* x0,
                                 const float* V, uint32_t iter, uint32_t ctr3,
                                 const uint32_t* iter_dev, float* S_out, float* traj,
-                                float* blk_min, unsigned* status, cudaStream_t st) {
+                                float* blk_min, unsigned* status, cudaStream_t st,
+                                uint32_t k_off) {
     const size_t smem = curv_rollout_smem_bytes(P.n_track, P.T);
     auto kern = dump ? mppi_rollout_curv_kernel<true> : mppi_rollout_curv_kernel<false>;
     cudaError_t e = ensure_smem((const void*)kern, smem);
@@ -194,7 +196,7 @@ cudaError_t launch_rollout_curv(const DevParams& P, const float* kappa, bool dum
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, P, kappa, x0, V, iter, ctr3, iter_dev, S_out, traj,
-                              blk_min, status);
+                              blk_min, status, k_off);
 }
 
 }  // namespace smppi

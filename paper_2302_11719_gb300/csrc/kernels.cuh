@@ -24,14 +24,16 @@ int rollout_blocks(const DevParams& P);
 cudaError_t launch_rollout_curv(const DevParams& P, const float* kappa, bool dump, const float* x0,
                                 const float* V, uint32_t iter, uint32_t ctr3,
                                 const uint32_t* iter_dev, float* S_out, float* traj,
-                                float* blk_min, unsigned* status, cudaStream_t st);
+                                float* blk_min, unsigned* status, cudaStream_t st,
+                                uint32_t k_off = 0);
 // Rollouts: S_out [K] and blk_min [rollout_blocks(P)]; traj (optional dump);
 // seg0_out (optional): nearest segment of x0.  rec: segment-pair table of
-// launch_rec_table.
+// launch_rec_table.  The P.K rollouts are rollouts k_off .. k_off + P.K - 1 of
+// the problem (their Philox counters); outputs are indexed from 0.
 cudaError_t launch_rollout(const DevParams& P, bool dump, const float* x0, const float* V,
                            const float4* rec, uint32_t iter, uint32_t ctr3,
                            const uint32_t* iter_dev, float* S_out, float* traj, float* blk_min,
-                           int* seg0_out, unsigned* status, cudaStream_t st);
+                           int* seg0_out, unsigned* status, cudaStream_t st, uint32_t k_off = 0);
 // Segment-pair table of a closed polyline (layout in device.cuh): n + 5
 // records of three float4.
 __host__ __device__ inline size_t rec_table_bytes(int n) { return (size_t)(n + 5) * 3 * sizeof(float4); }
@@ -57,6 +59,21 @@ cudaError_t launch_update_shield(const DevParams& P, const float* S, const float
                                  const float4* rec, const int* seg0, float* x0, float* V_safe,
                                  int n_repair, int ck, double* merit_out, uint32_t ctr3_dist,
                                  cudaStream_t st);
+// The update over a slice of rollouts (P.K of them, rollouts k_off ..) without
+// touching V: partial_out [2T + 2] (float64) = (m, eta, A) with m the slice's
+// minimum cost, eta = sum exp(-(S - m)/lambda) and A [2T] = sum exp(-(S - m)
+// /lambda) eps over the slice.
+cudaError_t launch_update_partial(const DevParams& P, const float* S, const float* blk_min,
+                                  int n_min, const float* V, uint32_t iter, uint32_t ctr3,
+                                  float* part_acc, double* part_eta, int* part_has,
+                                  unsigned* ticket, unsigned* status, uint32_t k_off,
+                                  double* partial_out, cudaStream_t st);
+// V <- clamp(V + A / eta) from n_parts slice partials [n_parts][2T + 2]: with
+// m = min_g m_g and c_g = exp(-(m_g - m)/lambda), eta = sum_g c_g eta_g and
+// A = sum_g c_g A_g, summed in float64 in slice order.
+constexpr int MERGE_MAX_PARTS = 1024;
+cudaError_t launch_merge(const DevParams& P, int n_parts, const double* parts, float* V,
+                         unsigned* status, cudaStream_t st);
 cudaError_t launch_debug_noise(const DevParams& P, uint32_t iter, uint32_t ctr3, int K, int T,
                                float* eps, uint32_t* raw, cudaStream_t st);
 

@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(BLK) mppi_rollout_kernel(
     DevParams P, const float* __restrict__ x0g, const float* __restrict__ Vg,
     const float4* __restrict__ recg, uint32_t iter, uint32_t ctr3,
     const uint32_t* __restrict__ iter_dev, float* __restrict__ S_out, float* __restrict__ traj,
-    float* __restrict__ blk_min, int* __restrict__ seg0_out, unsigned* __restrict__ status) {
+    float* __restrict__ blk_min, int* __restrict__ seg0_out, unsigned* __restrict__ status,
+    uint32_t k_off) {
     constexpr int NW = BLK / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int T = P.T;
@@ -122,7 +123,7 @@ __global__ void __launch_bounds__(BLK) mppi_rollout_kernel(
     float S = 3.0e38f;
     if (active) {
         S = rollout_sample<FAST, DUMP>(P, rec, Vs, make_state(x0g), s_seg0, s_d20,
-                                       (uint32_t)k, iter, ctr3,
+                                       (uint32_t)k + k_off, iter, ctr3,
                                        DUMP ? traj + (size_t)k * (T + 1) * 6 : nullptr);
         S_out[k] = S;
         if (!isfinite(S)) atomicOr(status, SMPPI_DEV_NUMERIC);
@@ -146,7 +147,8 @@ __global__ void __launch_bounds__(ROLL2_BLK, 2) mppi_rollout2_kernel(
     DevParams P, const float* __restrict__ x0g, const float* __restrict__ Vg,
     const float4* __restrict__ recg, uint32_t iter, uint32_t ctr3,
     const uint32_t* __restrict__ iter_dev, float* __restrict__ S_out, float* __restrict__ traj,
-    float* __restrict__ blk_min, int* __restrict__ seg0_out, unsigned* __restrict__ status) {
+    float* __restrict__ blk_min, int* __restrict__ seg0_out, unsigned* __restrict__ status,
+    uint32_t k_off) {
     constexpr int BLK = ROLL2_BLK, NW = BLK / 32;
     griddep_launch_dependents();
     griddep_wait();
@@ -211,7 +213,8 @@ __global__ void __launch_bounds__(ROLL2_BLK, 2) mppi_rollout2_kernel(
     float* ta = (DUMP && act_a) ? traj + (size_t)ka * (T + 1) * 6 : nullptr;
     float* tb = (DUMP && act_b) ? traj + (size_t)kb * (T + 1) * 6 : nullptr;
     const float2 S = x2::rollout2<DUMP>(P, rec, Vp, make_state(x0g), s_seg0, s_d20,
-                                        (uint32_t)ka, (uint32_t)kb, iter, ctr3, ta, tb);
+                                        (uint32_t)ka + k_off, (uint32_t)kb + k_off, iter, ctr3,
+                                        ta, tb);
     if (act_a) {
         S_out[ka] = S.x;
         if (!isfinite(S.x)) atomicOr(status, SMPPI_DEV_NUMERIC);
@@ -280,7 +283,8 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_update_kernel(
     DevParams P, const float* __restrict__ S, const float* __restrict__ blk_min, int n_min,
     float* V, uint32_t iter, uint32_t ctr3, uint32_t* __restrict__ iter_dev,
     float* __restrict__ part_acc, double* __restrict__ part_eta, int* __restrict__ part_has,
-    unsigned* __restrict__ ticket, unsigned* __restrict__ status, ShieldTail sh) {
+    unsigned* __restrict__ ticket, unsigned* __restrict__ status, ShieldTail sh,
+    uint32_t k_off, double* __restrict__ partial_out) {
     constexpr int NW = UPD_BLK / 32;
     constexpr int PER_T = UPD_PER_T;
     griddep_launch_dependents();
@@ -365,7 +369,8 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_update_kernel(
         has |= (nl > 0);
         if (worker) {
             for (int i = c; i < nl; i += C) {
-                const uint4 r = philox10(make_uint4((uint32_t)l_k[i], (uint32_t)p, iter, ctr3), P);
+                const uint4 r =
+                    philox10(make_uint4((uint32_t)l_k[i] + k_off, (uint32_t)p, iter, ctr3), P);
                 const float2 ze = box_muller(r.x, r.y), zo = box_muller(r.z, r.w);
                 const float w0 = l_w[i] * P.sig0, w1 = l_w[i] * P.sig1;
                 a0 = fmaf(w0, ze.x, a0);
@@ -435,7 +440,13 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_update_kernel(
         for (int b = lane; b < G; b += 32) e_sum += __ldcg(&part_eta[b]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) e_sum += __shfl_xor_sync(0xffffffffu, e_sum, o);
-        if (lane == 0) s_inv_eta = 1.0 / e_sum;
+        if (lane == 0) {
+            s_inv_eta = 1.0 / e_sum;
+            if (partial_out) {
+                partial_out[0] = (double)m;
+                partial_out[1] = e_sum;
+            }
+        }
     }
     __syncthreads();
     const double inv_eta = s_inv_eta;
@@ -450,6 +461,10 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_update_kernel(
             for (int u = 0; u < 8; ++u) A += (double)v[u];
         }
         for (; i < nz; ++i) A += (double)__ldcg(&part_acc[(size_t)l_k[i] * T2 + j]);
+        if (partial_out) {          // slice partial: V is left as it is
+            partial_out[2 + j] = A;
+            continue;
+        }
         const float lo = (j & 1) ? P.umin1 : P.umin0, hi = (j & 1) ? P.umax1 : P.umax0;
         const float v = (float)fma(A, inv_eta, (double)V[j]);
         if (!isfinite(v)) atomicOr(status, SMPPI_DEV_NUMERIC);
@@ -457,7 +472,7 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_update_kernel(
         if (SHIELD) acc_s[j] = V[j];    // V+ (the merge no longer needs acc_s)
     }
     if (tid == 0) *ticket = 0u;
-    if (!SHIELD) return;
+    if (!SHIELD || partial_out) return;
 
     // ---- safety shield on V+ (Alg. 1) and closed-loop step (Eq. 26) ----
     __shared__ int s_fail;
@@ -533,6 +548,42 @@ __global__ void debug_noise_kernel(DevParams P, uint32_t iter, uint32_t ctr3, in
     }
 }
 
+// Merge of slice partials (m_g, eta_g, A_g) into V+ (Eq. 10-11 over the union
+// of the slices): omega_k = exp(-(S_k - m)/lambda) = c_g exp(-(S_k - m_g)/lambda)
+// for k in slice g, c_g = exp(-(m_g - m)/lambda), m = min_g m_g, so eta and the
+// weighted noise sum are the c_g-weighted sums of the slices' (float64, in
+// slice order).  With one slice c_0 = 1 and V+ is the single update's, bit for
+// bit.
+__global__ void __launch_bounds__(UPD_BLK) mppi_merge_kernel(DevParams P, int n_parts,
+                                                             const double* __restrict__ parts,
+                                                             float* V, unsigned* status) {
+    __shared__ double s_c[MERGE_MAX_PARTS];
+    __shared__ double s_inv_eta;
+    const int T2 = 2 * P.T, W = T2 + 2, tid = threadIdx.x;
+    if (tid == 0) {
+        double m = parts[0];
+        for (int g = 1; g < n_parts; ++g) m = fmin(m, parts[(size_t)g * W]);
+        const double lam_inv = (double)P.lam_inv;
+        double eta = 0.0;
+        for (int g = 0; g < n_parts; ++g) {
+            const double c = exp(-(parts[(size_t)g * W] - m) * lam_inv);
+            s_c[g] = c;
+            eta += c * parts[(size_t)g * W + 1];
+        }
+        s_inv_eta = 1.0 / eta;
+    }
+    __syncthreads();
+    const double inv_eta = s_inv_eta;
+    for (int j = tid; j < T2; j += UPD_BLK) {
+        double A = 0.0;
+        for (int g = 0; g < n_parts; ++g) A += s_c[g] * parts[(size_t)g * W + 2 + j];
+        const float lo = (j & 1) ? P.umin1 : P.umin0, hi = (j & 1) ? P.umax1 : P.umax0;
+        const float v = (float)fma(A, inv_eta, (double)V[j]);
+        if (!isfinite(v)) atomicOr(status, SMPPI_DEV_NUMERIC);
+        V[j] = clampf(v, lo, hi);
+    }
+}
+
 // ----------------------------------------------------------------------------
 // Host-side launchers
 // ----------------------------------------------------------------------------
@@ -591,14 +642,14 @@ int update_grid(int K) {
 cudaError_t launch_rollout(const DevParams& P, bool dump, const float* x0, const float* V,
                            const float4* rec, uint32_t iter, uint32_t ctr3,
                            const uint32_t* iter_dev, float* S_out, float* traj, float* blk_min,
-                           int* seg0_out, unsigned* status, cudaStream_t st) {
+                           int* seg0_out, unsigned* status, cudaStream_t st, uint32_t k_off) {
     if (packed_rollout(P)) {
         const size_t smem = rec_table_bytes(P.n_track) + (size_t)P.T * 2 * sizeof(float4);
         auto kern = dump ? mppi_rollout2_kernel<true> : mppi_rollout2_kernel<false>;
         cudaError_t e = ensure_smem((const void*)kern, smem);
         if (e != cudaSuccess) return e;
         return launch_pdl(kern, rollout_blocks(P), ROLL2_BLK, smem, st, P, x0, V, rec, iter, ctr3,
-                          iter_dev, S_out, traj, blk_min, seg0_out, status);
+                          iter_dev, S_out, traj, blk_min, seg0_out, status, k_off);
     }
     const int nblk = (P.K + ROLL_BLK - 1) / ROLL_BLK;
     const size_t smem = rec_table_bytes(P.n_track) + (size_t)P.T * sizeof(float4);
@@ -607,7 +658,7 @@ cudaError_t launch_rollout(const DevParams& P, bool dump, const float* x0, const
     cudaError_t e = ensure_smem((const void*)kern, smem);
     if (e != cudaSuccess) return e;
     return launch_pdl(kern, nblk, ROLL_BLK, smem, st, P, x0, V, rec, iter, ctr3, iter_dev, S_out,
-                      traj, blk_min, seg0_out, status);
+                      traj, blk_min, seg0_out, status, k_off);
 }
 
 cudaError_t launch_update(const DevParams& P, const float* S, const float* blk_min, int n_min,
@@ -616,7 +667,26 @@ cudaError_t launch_update(const DevParams& P, const float* S, const float* blk_m
                           unsigned* status, cudaStream_t st) {
     return launch_pdl(mppi_update_kernel<false, false>, update_grid(P.K), UPD_BLK, 0, st, P, S,
                       blk_min, n_min, V, iter, ctr3, iter_dev, part_acc, part_eta, part_has, ticket,
-                      status, ShieldTail{});
+                      status, ShieldTail{}, 0u, (double*)nullptr);
+}
+
+cudaError_t launch_update_partial(const DevParams& P, const float* S, const float* blk_min,
+                                  int n_min, const float* V, uint32_t iter, uint32_t ctr3,
+                                  float* part_acc, double* part_eta, int* part_has,
+                                  unsigned* ticket, unsigned* status, uint32_t k_off,
+                                  double* partial_out, cudaStream_t st) {
+    // V is only read when partial_out is given
+    return launch_pdl(mppi_update_kernel<false, false>, update_grid(P.K), UPD_BLK, 0, st, P, S,
+                      blk_min, n_min, const_cast<float*>(V), iter, ctr3, (uint32_t*)nullptr,
+                      part_acc, part_eta, part_has, ticket, status, ShieldTail{}, k_off,
+                      partial_out);
+}
+
+cudaError_t launch_merge(const DevParams& P, int n_parts, const double* parts, float* V,
+                         unsigned* status, cudaStream_t st) {
+    // an ordinary launch: the partials may come from another library's kernels (a collective)
+    mppi_merge_kernel<<<1, UPD_BLK, 0, st>>>(P, n_parts, parts, V, status);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_update_shield(const DevParams& P, const float* S, const float* blk_min,
@@ -634,7 +704,8 @@ cudaError_t launch_update_shield(const DevParams& P, const float* S, const float
     cudaError_t e = ensure_smem((const void*)kern, smem);
     if (e != cudaSuccess) return e;
     return launch_pdl(kern, update_grid(P.K), UPD_BLK, smem, st, P, S, blk_min, n_min, V, iter,
-                      ctr3, iter_dev, part_acc, part_eta, part_has, ticket, status, sh);
+                      ctr3, iter_dev, part_acc, part_eta, part_has, ticket, status, sh, 0u,
+                      (double*)nullptr);
 }
 
 cudaError_t launch_debug_noise(const DevParams& P, uint32_t iter, uint32_t ctr3, int K, int T,

@@ -67,6 +67,8 @@ _SIGS = {
     "smppi_sync_status": ([_vp, C.POINTER(_u32)], _i),
     "smppi_step": ([_vp, _vp, _vp, _u32, _u32, _vp, _vp], _i),
     "smppi_update": ([_vp, _vp, _vp, _u32, _u32], _i),
+    "smppi_step_partial": ([_vp, _vp, _vp, _u32, _u32, _i, _i, _vp], _i),
+    "smppi_merge_partials": ([_vp, _i, _vp, _vp], _i),
     "smppi_cost_grad": ([_vp, _i, _vp, _vp, _i, _f, _f, _i, _vp, _vp], _i),
     "smppi_repair": ([_vp, _i, _vp, _vp, _vp, _i, _i, _f, _vp, _vp], _i),
     "smppi_apply": ([_vp, _vp, _vp, _vp, _u32, _u32], _i),
@@ -88,7 +90,8 @@ _SIGS = {
     "smppi_timing_read": ([_vp, C.POINTER(C.c_double), C.POINTER(C.c_int), _i], _i),
 }
 
-KERNEL_KINDS = ("rollout", "update", "seg0", "repair", "apply", "cost_grad", "update_shield")
+KERNEL_KINDS = ("rollout", "update", "seg0", "repair", "apply", "cost_grad", "update_shield",
+                "merge")
 
 _lib = None
 
@@ -193,6 +196,27 @@ def smppi_step(h, x0, V, iter=0, instance=0, S_out=None, traj_out=None):
 
 def smppi_update(h, S, V, iter=0, instance=0):
     _check(load_library().smppi_update(h, _ptr(S), _ptr(V), iter, instance), h)
+
+
+def smppi_step_partial(h, x0, V, iter, instance, k_lo, k_hi, partial_out):
+    """Rollouts k_lo .. k_hi - 1 -> partial_out (float64, 2T + 2): (m, eta, A)."""
+    _check(load_library().smppi_step_partial(h, _ptr(x0), _ptr(V), iter, instance, int(k_lo),
+                                             int(k_hi), _ptr(partial_out)), h)
+
+
+def smppi_merge_partials(h, n_parts, partials, V):
+    """V <- V+ from n_parts slice partials (float64, n_parts x (2T + 2))."""
+    _check(load_library().smppi_merge_partials(h, int(n_parts), _ptr(partials), _ptr(V)), h)
+
+
+def shard_range(K: int, world: int, rank: int) -> tuple[int, int]:
+    """The contiguous slice [k_lo, k_hi) of K rollouts that rank `rank` of
+    `world` runs: sizes differ by at most one, lower ranks take the larger."""
+    if world < 1 or not 0 <= rank < world or K < world:
+        raise ValueError("need 1 <= world <= K and 0 <= rank < world")
+    q, r = divmod(K, world)
+    lo = rank * q + min(rank, r)
+    return lo, lo + q + (1 if rank < r else 0)
 
 
 def smppi_cost_grad(h, n_seq, x0, V, N, w_run, w_cbf, checkpoint, J_out, grad_out):
