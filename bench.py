@@ -1,14 +1,18 @@
 #!/usr/bin/env python3
 """Throughput of the Shield-MPPI hot path on GB300.
 
-One step = one whole Shield-MPPI control update (Alg. 2 body) of the K = 65536,
-T = 100 problem (elliptical 20 x 12 m track, half-width 2 m): K sampled
-rollouts with the DCBF cost and the softmin update (smppi_step), 10 Armijo
-repair iterations of V+ (smppi_repair), then the disturbed closed-loop step
-and warm start (smppi_apply), all through smppi_shield_update.  The metric is
-rollout-steps/s = K T / (time per update); the line also carries the
-microseconds per update, the roofline of the dominant kernel, the end-to-end
-rate through the host-buffer API and the FP64 oracle timed on the host cores.
+The unit of work is one whole Shield-MPPI control update (Alg. 2 body) of the
+K = 65536, T = 100 problem (elliptical 20 x 12 m track, half-width 2 m): K
+sampled rollouts with the DCBF cost and the softmin update, up to 10 Armijo
+repair iterations of V+ (they run while V+ breaks the DCBF condition), then
+the disturbed closed-loop step and warm start, all through
+smppi_shield_update.  One timed step is R such updates back to back (R chosen
+so that the timed region lasts over a second), each bracketed by CUDA events
+with the L2 flushed before it.  The metric is rollout-steps/s = K T / (time
+per update); the line also carries the microseconds per update, the repair
+iterations that ran, a second workload whose near-boundary starts make the
+shield iterate, the roofline of the dominant kernel, the end-to-end rate
+through the host-buffer API and the FP64 oracle timed on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -21,6 +25,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -201,13 +206,77 @@ def run_reference(args):
     return 0
 
 
-def workload_config():
-    return {"workload": "Shield-MPPI control update, K=%d rollouts, T=%d, %d Armijo repair "
-                        "iterations, closed loop" % (K_ROLL, T_HOR, N_REPAIR),
-            "K": K_ROLL, "T": T_HOR, "n_repair": N_REPAIR,
+def workload_config(updates_per_step=1):
+    return {"workload": "Shield-MPPI control update, K=%d rollouts, T=%d, up to %d Armijo repair "
+                        "iterations (they run only while V+ breaks the DCBF condition), closed "
+                        "loop" % (K_ROLL, T_HOR, N_REPAIR),
+            "K": K_ROLL, "T": T_HOR, "n_repair_max": N_REPAIR,
+            "updates_per_step": updates_per_step,
             "track": "ellipse 20 x 12 m, half-width 2 m, 1024 points",
             "model": "6-state dynamic single-track car, dt 0.02 s",
-            "l2": "flushed between timed steps (256 MiB write, outside the timed events)"}
+            "l2": "flushed before every timed update (256 MiB write, outside the timed events)"}
+
+
+def updates_per_step(steps, est_update_s, min_timed_s):
+    """Updates per timed step so that steps x R updates last at least min_timed_s."""
+    return max(1, int(math.ceil(min_timed_s / (steps * max(est_update_s, 1e-6)))))
+
+
+def iterations_run(merit_row, n_repair):
+    """Repair iterations one update ran, from its merit row (P before each
+    iteration and after the last, repeated after an early stop: a safe V,
+    P = 0, or a line search that accepted nothing)."""
+    for i in range(n_repair):
+        if merit_row[i] == 0.0 or merit_row[i + 1] == merit_row[i]:
+            return i
+    return n_repair
+
+
+def shield_active_workload(S, I, dev, flush, n_updates, inst):
+    """Updates in which the shield works: each starts from a near-boundary state
+    (offset 1.5-1.95 m of the 2 m half-width, heading 0.1 rad outward) with a
+    warm start that steers further out (inputs.near_boundary_sequences), so V+
+    often breaks the DCBF condition and the Armijo repair iterates.  Same K, T
+    and track as the headline; every update is timed with its own events."""
+    import numpy as np
+    import torch
+    sb = I.near_boundary_sequences(n_updates, T_HOR, seed=1)
+    pr = I.throughput_problem(K_ROLL, T_HOR)
+    ctl = S.Controller(pr.params, pr.track, device=dev)
+    xs, Vs_all = ctl.tensor(sb.x0), ctl.tensor(sb.V)
+    x0, V = ctl.tensor(pr.x0), ctl.tensor(pr.V)
+    Vs = torch.empty_like(V)
+    merits = torch.zeros((n_updates, N_REPAIR + 1), dtype=torch.float64, device=dev)
+    for j in range(3):                                  # warm-up
+        x0.copy_(xs[j]); V.copy_(Vs_all[j])
+        S.smppi_shield_update(ctl.h, x0, V, Vs, j, inst, N_REPAIR)
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(n_updates)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(n_updates)]
+    for j in range(n_updates):
+        x0.copy_(xs[j]); V.copy_(Vs_all[j])
+        flush.zero_()
+        e0[j].record()
+        S.smppi_shield_update(ctl.h, x0, V, Vs, 100 + j, inst, N_REPAIR, merits[j])
+        e1[j].record()
+    torch.cuda.synchronize()
+    st, bits = ctl.sync_status()
+    ms = np.array([a.elapsed_time(b) for a, b in zip(e0, e1)])
+    mer = merits.cpu().numpy()
+    it = np.array([iterations_run(r, N_REPAIR) for r in mer])
+    ctl.close()
+    rep = it > 0
+    return {"workload": "near-boundary starts (offset 1.5-1.95 m, heading 0.1 rad outward, warm "
+                        "start steering outward), K=%d, T=%d, up to %d Armijo iterations"
+                        % (K_ROLL, T_HOR, N_REPAIR),
+            "updates": n_updates, "us_per_update": 1e3 * float(ms.mean()),
+            "us_per_update_with_repair": 1e3 * float(ms[rep].mean()) if rep.any() else None,
+            "us_per_update_without_repair": 1e3 * float(ms[~rep].mean()) if (~rep).any() else None,
+            "repair_iterations_run_mean": float(it.mean()),
+            "updates_with_repair": int(rep.sum()),
+            "merit_before_mean": float(mer[:, 0].mean()),
+            "merit_after_mean": float(mer[:, -1].mean()),
+            "safe_after": int((mer[:, -1] == 0.0).sum()),
+            "status_bits": int(bits)}
 
 
 def dist_env():
@@ -259,30 +328,41 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     it = 0
+    wu0 = time.perf_counter()
     for _ in range(args.warmup):
         S.smppi_shield_update(ctl.h, x0, V, Vs, it, inst, N_REPAIR)
         it += 1
+    torch.cuda.synchronize()
+    est_s = (time.perf_counter() - wu0) / args.warmup
     st, bits = ctl.sync_status()
     if st not in (S.OK, S.ERR_STALLED):
         raise RuntimeError("device status %d (bits %d) in warm-up" % (st, bits))
 
-    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    # one step = R back-to-back control updates (R chosen so that the timed
+    # region lasts at least --min-timed-seconds; each update is bracketed by its
+    # own events with the L2 flush before it, outside the events)
+    R = updates_per_step(args.steps, est_s, args.min_timed_seconds)
+    n_upd = args.steps * R
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(n_upd)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(n_upd)]
+    merits = torch.zeros((n_upd, N_REPAIR + 1), dtype=torch.float64, device=dev)
     sampler = ClockSampler(gpu_index(local))
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
     wall0 = time.perf_counter()
-    for i in range(args.steps):
+    for j in range(n_upd):
         flush.zero_()
-        e0[i].record()
-        S.smppi_shield_update(ctl.h, x0, V, Vs, it, inst, N_REPAIR)
-        e1[i].record()
+        e0[j].record()
+        S.smppi_shield_update(ctl.h, x0, V, Vs, it, inst, N_REPAIR, merits[j])
+        e1[j].record()
         it += 1
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
-    step_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
+    upd_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
+    step_ms = [sum(upd_ms[i * R:(i + 1) * R]) for i in range(args.steps)]
+    iters = [iterations_run(row, N_REPAIR) for row in merits.cpu().numpy()]
     # per-kernel durations: the same steps again with CUDA events around every
     # launch (on the library's stream).  Events between the launches cost time
     # and stop a launch from overlapping its predecessor's tail, so the step
@@ -301,7 +381,7 @@ def run_ours(args):
     if st not in (S.OK, S.ERR_STALLED):
         raise RuntimeError("device status %d (bits %d) in the timed region" % (st, bits))
     total_s = max_over_ranks(total_s, dist, dev)
-    value = job_rate(world, K_ROLL * T_HOR * args.steps, total_s)
+    value = job_rate(world, K_ROLL * T_HOR * n_upd, total_s)
 
     # end to end through the host-buffer entry point (copies in the timed region)
     hx = torch.from_numpy(pr.x0.copy()).pin_memory()
@@ -312,7 +392,7 @@ def run_ours(args):
                               N_REPAIR, None, True)
         it += 1
     e2e_s = 0.0
-    for i in range(args.steps):
+    for i in range(n_upd):
         flush.zero_()
         torch.cuda.synchronize()
         a = time.perf_counter()
@@ -321,7 +401,8 @@ def run_ours(args):
         e2e_s += time.perf_counter() - a
         it += 1
     e2e_s = max_over_ranks(e2e_s, dist, dev)
-    e2e_value = job_rate(world, K_ROLL * T_HOR * args.steps, e2e_s)
+    e2e_value = job_rate(world, K_ROLL * T_HOR * n_upd, e2e_s)
+    active = shield_active_workload(S, I, dev, flush, args.active_updates, inst)
 
     if rank != 0:
         dist.barrier()
@@ -353,15 +434,21 @@ def run_ours(args):
                "kind": "oracle",
                "sample": "%d whole Shield-MPPI updates (K=%d, T=%d, %d repair iterations) of "
                          "the FP64 oracle, %.1f s" % (n, K_ROLL, T_HOR, N_REPAIR, sum(times))}
-    launches = sum(v[1] for v in kt.values())
+    launches = 2 * n_upd        # rollout + update/shield launch per update in the timed region
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": workload_config(),
-        "us_per_update": 1e6 * total_s / args.steps,
+        "data": "synthetic", "config": workload_config(R),
+        "updates_per_step": R,
+        "us_per_update": 1e6 * total_s / n_upd,
+        "update_us_median": 1e3 * statistics.median(upd_ms),
         "step_ms_median": statistics.median(step_ms),
         "wall_s_timed_loop": wall,
+        "repair_iterations_run": {"mean": float(np.mean(iters)), "max": int(max(iters)),
+                                  "updates_with_repair": int(sum(i > 0 for i in iters)),
+                                  "updates": n_upd},
+        "shield_active": active,
         "kernel_share": {k: round(v / tot_k, 4) for k, v in shares.items()},
         "kernel_avg_us": {k: 1e3 * v[0] / v[1] for k, v in kt.items() if v[1]},
         "kernel_timing": "CUDA events around every launch on the library stream, in a second "
@@ -372,6 +459,7 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 4 * (6 + 2 * T_HOR),
                 "d2h_bytes_per_step": 4 * (6 + 4 * T_HOR)},
         "gpu_launches": launches,
+        "gpu_launches_kernel_pass": sum(v[1] for v in kt.values()),
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -822,6 +910,11 @@ def main():
     ap.add_argument("--loop-updates", type=int, default=500)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--min-timed-seconds", type=float, default=1.2,
+                    help="each timed step repeats the update so that the timed region lasts "
+                         "at least this long (clock samples under load)")
+    ap.add_argument("--active-updates", type=int, default=100,
+                    help="updates of the near-boundary (shield-active) workload")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -51,3 +51,18 @@ def test_status_names():
     assert bench._status_names(0) == ["ok"]
     names = bench._status_names(1 | 2 | 4)
     assert len(names) == 3 and "ok" not in names
+
+
+def test_updates_per_step_covers_min_time():
+    import bench
+    assert bench.updates_per_step(50, 120e-6, 1.2) == 200
+    assert bench.updates_per_step(50, 1.0, 1.2) == 1
+    assert bench.updates_per_step(3, 0.0, 0.1) >= 1
+
+
+def test_iterations_run_from_merits():
+    import bench
+    assert bench.iterations_run([0.0] * 11, 10) == 0                 # safe V+
+    assert bench.iterations_run([5.0, 2.0, 0.0] + [0.0] * 8, 10) == 2
+    assert bench.iterations_run([5.0, 4.0, 4.0] + [4.0] * 8, 10) == 1  # line search stalled
+    assert bench.iterations_run([float(10 - i) for i in range(11)], 10) == 10

@@ -10,8 +10,9 @@
   * the batch of 512 uneven problems (K log-uniform in [64, 16384], T in
     [20, 150]): 20 closed-loop updates in one persistent launch each, 16
     problems spread over the K and T range resynced to the oracle at every
-    update and compared (V+ within the update bound, V_safe within 1e-4 unless
-    flipped, next state within 1e-4 relative).
+    update and compared: V+ within the update bound; V_safe within 1e-4 plus
+    the bound of the V+ it starts from (else a flip); the executed closed-loop
+    step, from the control the GPU executed, within 1e-4 relative.
 The oracle runs on host threads (its C routines release the interpreter lock).
 Tolerances: tests/gpu_helpers.py.
 """
@@ -63,9 +64,10 @@ def test_update_error_full_size(S, orc, K):
     assert es <= S_REL
     tol = _bound_top(orc, m, So, pr.V, Vp, 1, 0, pr.params["lam"])
     e = np.abs(Vg - Vp)
-    print("K=%d T=100: max rel S err %.2e, max |V+ err| %.2e (north-star gate %.0e; update "
-          "bound here %.2e..%.2e)" % (K, es, e.max(), V_UPD, tol.min(), tol.max()))
+    print("K=%d T=100: max rel S err %.2e, max |V+ err| %.2e (gate %.0e; update bound "
+          "here %.2e..%.2e)" % (K, es, e.max(), V_UPD, tol.min(), tol.max()))
     assert np.all(e <= tol)
+    assert e.max() <= V_UPD
 
 
 def _repair_sample(S, orc, mode):
@@ -150,12 +152,15 @@ def test_batch_512_spot_check(S, orc):
                 assert np.all(eV <= tol_sh), (n, i, eV.max())
                 worst_V = max(worst_V, eV.max())
                 compared += 1
-                if np.max(np.abs(Vsg[i] - Vso)) > V_REP:
+                # V_safe starts from a V+ that may differ by the update bound: the repair
+                # tolerance is added to it; beyond that a line-search decision differs
+                if np.any(np.abs(Vsg[i] - Vso) > V_REP + tol):
                     flips += 1
-                else:
-                    ex_ = rel_err(xg[i], x1)
-                    assert ex_ <= X_REL, (n, i, ex_)
-                    worst_x = max(worst_x, ex_)
+                # the executed step, from the control the GPU executed
+                x1g = orc.apply(models[i], xs[i].astype(np.float32), Vsg[i][0], n, i)
+                ex_ = rel_err(xg[i], x1g)
+                assert ex_ <= X_REL, (n, i, ex_)
+                worst_x = max(worst_x, ex_)
                 xs[i], Vs[i] = x1, Vsh
     rb, grid = S.smppi_batch_config(bt.b)
     bt.close()
