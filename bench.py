@@ -520,7 +520,7 @@ def run_batch(args):
     t_b = _timed_steps(batched, args.steps, flush)
     it += args.steps
     # graph replays of the whole closed loop (no flush between replays)
-    n_loop = args.loop_updates
+    n_loop = args.loop_updates or 500
     a0 = torch.cuda.Event(enable_timing=True)
     a1 = torch.cuda.Event(enable_timing=True)
     S.smppi_batch_loop(bt.b, bt.x0, bt.V, bt.V_safe, it, n_rep, 1)
@@ -786,17 +786,78 @@ def run_small(args):
     return 0
 
 
-COMPARE_MAX_UPDATES = 50
+COMPARE_K = (16, 32, 64, 128, 256, 1024)      # rollouts (the paper's samples M)
+COMPARE_T = (10, 20, 40, 75)                   # horizon steps of 0.02 s (0.2 .. 1.5 s)
+COMPARE_CHUNK = 25                             # updates per graph replay chunk
+# narrow tracks (half-width 1-1.5 m), target speed 10 m/s, centring weight 50 and
+# disturbances of std 0.2 on (v_y, r): crash rates then span the grid from most
+# problems (few rollouts, short horizons) to none (long horizons)
+COMPARE_SETTING = dict(w=(1.0, 1.5), v_target=10.0, q_d=50.0, dist_sigma=(0.2, 0.2))
+
+
+def compare_controllers(S, I, dev, K, T, n_updates, B=128, seed=7, setting=None):
+    """One (K, T) cell of the closed-loop comparison: plain MPPI (no DCBF cost,
+    no shield), MPPI with the DCBF cost of Eq. 17-20, and Shield-MPPI (DCBF
+    cost + up to 10 Armijo repair iterations, Alg. 1), each on the same B
+    narrow-track problems from the same starts with the same disturbances
+    (Eq. 26), n_updates closed-loop updates in graph replays of COMPARE_CHUNK.
+    Returns one row per controller; the device status is checked after every
+    chunk."""
+    import numpy as np
+    import torch
+    ctrls = (("plain MPPI", 0.0, 0), ("MPPI + DCBF cost", 1000.0, 0),
+             ("Shield-MPPI", 1000.0, N_REPAIR))
+    rows = []
+    for name, c_cbf, n_rep in ctrls:
+        st_ = dict(COMPARE_SETTING if setting is None else setting)
+        w_lo, w_hi = st_.pop("w")
+        ib = I.uneven_instances(n_inst=B, seed=seed, K_lo=K, K_hi=K, T_lo=T, T_hi=T,
+                                w_lo=w_lo, w_hi=w_hi, C_cbf=c_cbf, **st_)
+        bt = S.Batch(ib, block_rollouts=0, device=dev)
+        S.smppi_batch_loop(bt.b, bt.x0, bt.V, bt.V_safe, 0, n_rep, 1)   # autotune
+        S.smppi_batch_sync_status(bt.b)
+        bt.x0.copy_(torch.as_tensor(ib.x0, device=dev))
+        bt.V.zero_()
+        S.smppi_batch_monitor(bt.b, B, reset=True)
+        viol = np.zeros(B, np.int64)
+        out = np.zeros(B, np.int64)
+        ms, bits_seen, done = 0.0, 0, 0
+        while done < n_updates:
+            n = min(COMPARE_CHUNK, n_updates - done)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record()
+            S.smppi_batch_loop(bt.b, bt.x0, bt.V, bt.V_safe, done, n_rep, n)
+            a1.record()
+            torch.cuda.synchronize()
+            ms += a0.elapsed_time(a1)
+            st, bits = S.smppi_batch_sync_status(bt.b)
+            bits_seen |= bits
+            if bits & 2:
+                raise RuntimeError("device wait timed out in the %s loop (K=%d, T=%d) after "
+                                   "%d updates" % (name, K, T, done + n))
+            v, o = S.smppi_batch_monitor(bt.b, B, reset=True)
+            viol += v
+            out += o
+            done += n
+        rows.append({"K": K, "T": T, "controller": name,
+                     "violation_rate": float(viol.sum()) / (B * n_updates),
+                     "outside_rate": float(out.sum()) / (B * n_updates),
+                     "crash_rate": float((out > 0).mean()),
+                     "ms_per_update_all": ms / n_updates,
+                     "status": _status_names(bits_seen)})
+        bt.close()
+    return rows
 
 
 def run_compare(args):
     """Closed-loop controller comparison on synthetic tracks (the analogue of the
-    paper's Sec. VI closed-loop experiments, which need the AutoRally simulator):
-    plain MPPI (no DCBF cost, no shield), MPPI with the DCBF cost (Eq. 17-20) and
-    Shield-MPPI (DCBF cost + 10 Armijo repair iterations), each on the same 128
-    narrow-track problems with the same disturbances, for a grid of (K, T).
-    Rates come from the batch's safety monitor (executed steps that break the
-    DCBF condition / end outside the track)."""
+    paper's Sec. VI-E, whose heat maps cover samples and horizon; the AutoRally
+    simulator is not available): plain MPPI, MPPI with the DCBF cost and
+    Shield-MPPI on the same 128 narrow-track problems for a grid of rollouts K
+    and horizons T.  Rates come from the batch's safety monitor: executed steps
+    that break the DCBF condition or end outside the track, and the fraction
+    of problems that ever leave the track (a crash)."""
     import torch
 
     import __graft_entry__
@@ -804,39 +865,19 @@ def run_compare(args):
     from paper_2302_11719_gb300 import smppi as S
     __graft_entry__.build()
     dev = torch.device("cuda", 0)
-    # the narrow-track Shield-MPPI loop has stalled the batch kernel for minutes past
-    # about 100 updates (cause not yet found): this workload runs at most 50
-    B, steps = 128, min(args.loop_updates, COMPARE_MAX_UPDATES)
-    ctrls = (("plain MPPI", 0.0, 0), ("MPPI + DCBF cost", 1000.0, 0),
-             ("Shield-MPPI", 1000.0, N_REPAIR))
+    B, steps = 128, args.loop_updates or 300
     rows = []
-    for K in (64, 256, 1024, 4096):
-        for T in (20, 40):
-            for name, c_cbf, n_rep in ctrls:
-                ib = I.uneven_instances(n_inst=B, seed=7, K_lo=K, K_hi=K, T_lo=T, T_hi=T,
-                                        w_lo=1.0, w_hi=1.5, C_cbf=c_cbf, **I.HARSH)
-                bt = S.Batch(ib, block_rollouts=0, device=dev)
-                S.smppi_batch_loop(bt.b, bt.x0, bt.V, bt.V_safe, 0, n_rep, 1)   # autotune
-                bt.x0.copy_(torch.as_tensor(ib.x0, device=dev))
-                bt.V.zero_()
-                S.smppi_batch_monitor(bt.b, B, reset=True)
-                a0 = torch.cuda.Event(enable_timing=True)
-                a1 = torch.cuda.Event(enable_timing=True)
-                a0.record()
-                S.smppi_batch_loop(bt.b, bt.x0, bt.V, bt.V_safe, 0, n_rep, steps)
-                a1.record()
-                torch.cuda.synchronize()
-                viol, out = S.smppi_batch_monitor(bt.b, B, reset=True)
-                rows.append({"K": K, "T": T, "controller": name,
-                             "violation_rate": float(viol.sum()) / (B * steps),
-                             "outside_rate": float(out.sum()) / (B * steps),
-                             "problems_ever_outside": int((out > 0).sum()),
-                             "ms_per_update_all": a0.elapsed_time(a1) / steps})
-                bt.close()
-    print(json.dumps({"workload": "closed-loop controller comparison, %d problems x %d updates, "
-                                  "narrow tracks (w in [1, 1.5] m), v_target 14 m/s, q_d 10, "
-                                  "disturbance std 0.6" % (B, steps),
-                      "rows": rows}), flush=True)
+    Ks = COMPARE_K if not args.compare_k else tuple(args.compare_k)
+    Ts = COMPARE_T if not args.compare_t else tuple(args.compare_t)
+    setting = dict(COMPARE_SETTING)
+    if args.compare_setting:
+        setting.update(json.loads(args.compare_setting))
+    for K in Ks:
+        for T in Ts:
+            rows.extend(compare_controllers(S, I, dev, K, T, steps, B, setting=setting))
+    print(json.dumps({"workload": "closed-loop controller comparison, %d problems x %d updates"
+                                  % (B, steps),
+                      "setting": setting, "rows": rows}), flush=True)
     return 0
 
 
@@ -907,7 +948,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="shield",
                     choices=["shield", "batch", "sweep", "grad", "small", "compare", "curv"])
-    ap.add_argument("--loop-updates", type=int, default=500)
+    ap.add_argument("--loop-updates", type=int, default=None,
+                    help="closed-loop updates per problem (batch workload: 500, compare: 300)")
+    ap.add_argument("--compare-k", type=int, nargs="*", help="rollouts of the comparison grid")
+    ap.add_argument("--compare-t", type=int, nargs="*", help="horizons of the comparison grid")
+    ap.add_argument("--compare-setting", default=None,
+                    help="JSON overrides of the comparison's track and cost setting")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--min-timed-seconds", type=float, default=1.2,
