@@ -470,6 +470,82 @@ def run_ours(args):
     return 0
 
 
+def run_sharded(args):
+    """--shard-rollouts: the ranks split the K rollouts of ONE problem (strong
+    scaling).  Each update: every rank runs its slice (smppi_step_partial, the
+    slice's Philox counters), one all-gather of the (2T + 2)-value partials
+    over NCCL, the merge into V+ on every rank (smppi_merge_partials), then the
+    shield and the closed-loop step, replicated (smppi_repair, smppi_apply)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    from paper_2302_11719_gb300 import inputs as I
+    from paper_2302_11719_gb300 import smppi as S
+
+    world, rank, local = dist_env()
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    pr = I.throughput_problem(K_ROLL, T_HOR)
+    ctl = S.Controller(pr.params, pr.track, device=dev)
+    k_lo, k_hi = S.shard_range(K_ROLL, world, rank)
+    x0, V = ctl.tensor(pr.x0), ctl.tensor(pr.V)
+    Vs = torch.empty_like(V)
+    W = 2 * T_HOR + 2
+    mine = torch.empty(W, dtype=torch.float64, device=dev)
+    parts = torch.empty((world, W), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def update(it):
+        S.smppi_step_partial(ctl.h, x0, V, it, 0, k_lo, k_hi, mine)
+        if dist:
+            dist.all_gather_into_tensor(parts, mine)
+        else:
+            parts[0].copy_(mine)
+        S.smppi_merge_partials(ctl.h, world, parts, V)
+        S.smppi_repair(ctl.h, 1, x0, V, Vs, N_REPAIR, 1)
+        S.smppi_apply(ctl.h, x0, V, Vs, it, 0)
+
+    for it in range(args.warmup):
+        update(it)
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        e0[i].record()
+        update(args.warmup + i)
+        e1[i].record()
+    torch.cuda.synchronize()
+    st, bits = ctl.sync_status()
+    if st not in (S.OK, S.ERR_STALLED):
+        raise RuntimeError("device status %d (bits %d)" % (st, bits))
+    total_s = sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / 1e3
+    total_s = max_over_ranks(total_s, dist, dev)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": K_ROLL * T_HOR * args.steps / total_s, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(workload_config(), parallelism="rollouts sharded over %d ranks, "
+                           "all-gather of the slice partials" % world),
+            "rollouts_per_rank": k_hi - k_lo,
+            "gpu_launches": 6 * args.steps}), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    ctl.close()
+    return 0
+
+
 def _timed_steps(fn, steps, flush):
     """Per-step CUDA-event times (ms) of fn(i), L2 flushed before each step."""
     import torch
@@ -952,6 +1028,9 @@ def main():
                     help="closed-loop updates per problem (batch workload: 500, compare: 300)")
     ap.add_argument("--compare-k", type=int, nargs="*", help="rollouts of the comparison grid")
     ap.add_argument("--compare-t", type=int, nargs="*", help="horizons of the comparison grid")
+    ap.add_argument("--shard-rollouts", action="store_true",
+                    help="split the K rollouts of one problem over the ranks (strong scaling; "
+                         "default: one independent replica per rank)")
     ap.add_argument("--compare-setting", default=None,
                     help="JSON overrides of the comparison's track and cost setting")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -978,6 +1057,8 @@ def main():
         return run_compare(args)
     if args.workload == "curv":
         return run_curv(args)
+    if args.shard_rollouts:
+        return run_sharded(args)
     return run_ours(args)
 
 
