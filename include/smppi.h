@@ -409,6 +409,24 @@ smppi_status smppi_debug_noise(smppi_handle* h, uint32_t iter, uint32_t instance
                                float* eps_out, uint32_t* raw_out);
 
 /*
+ * Test access to the hand-written elementary functions of the rollout and
+ * repair kernels (no handle; not part of the method): for i < n, out[i] = the
+ * library's function and ref[i] = CUDA's own function of the same arguments:
+ *   fn 0: atan2(a, b), scalar form      ref atan2f(a, b)
+ *   fn 1: atan2(a, b), packed pair form  ref atan2f(a, b)
+ *   fn 2: sin(1.5 atan a), scalar        ref sinf(1.5f atanf(a))
+ *   fn 3: sin(1.5 atan a), packed        ref sinf(1.5f atanf(a))
+ *   fn 4 / 5: sin / cos of a, |a| <= 1/2, scalar   ref sinf / cosf
+ *   fn 6 / 7: sin / cos of a, |a| <= 1/2, packed   ref sinf / cosf
+ * (b is read by fn 0 and 1 only but must not be NULL).  Packed forms evaluate
+ * elements 2i and 2i + 1 as the two halves of one instruction.  All arrays
+ * DEVICE, float32; asynchronous on cuda_stream; SMPPI_ERR_ARG for another fn,
+ * n < 0 or a NULL array.
+ */
+smppi_status smppi_debug_elementary(int fn, int n, const float* a, const float* b, float* out,
+                                    float* ref, void* cuda_stream);
+
+/*
  * Failure-detection self-test (no handle): launches one block of 32 threads on
  * cuda_stream that waits, through the library's bounded device waits, on
  * something nothing completes: which = 0: an mbarrier phase that no thread

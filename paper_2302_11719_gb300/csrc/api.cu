@@ -715,6 +715,18 @@ smppi_status smppi_shield_loop(smppi_handle* h, float* x0, float* V, float* V_sa
     return SMPPI_OK;
 }
 
+smppi_status smppi_debug_elementary(int fn, int n, const float* a, const float* b, float* out,
+                                    float* ref, void* cuda_stream) {
+    if (fn < 0 || fn > 7) return fail(nullptr, SMPPI_ERR_ARG, "fn must be in [0, 7]");
+    if (n < 0) return fail(nullptr, SMPPI_ERR_ARG, "n must be >= 0");
+    if (n == 0) return SMPPI_OK;
+    if (!a || !b || !out || !ref) return fail(nullptr, SMPPI_ERR_ARG, "NULL array");
+    const cudaError_t e =
+        launch_debug_elementary(fn, n, a, b, out, ref, static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return fail(nullptr, SMPPI_ERR_CUDA, cudaGetErrorString(e));
+    return SMPPI_OK;
+}
+
 smppi_status smppi_debug_noise(smppi_handle* h, uint32_t iter, uint32_t instance, int K, int T,
                                float* eps_out, uint32_t* raw_out) {
     if (!h) return fail(nullptr, SMPPI_ERR_ARG, "handle is NULL");

@@ -10,8 +10,10 @@
 // Elementary functions on the hot path are written here so that each step
 // costs few instructions while staying within a few ulp:
 //   atan2   -- octant reduction + a degree-8 polynomial in a^2 for atan(a)/a on
-//              [0, 1], coefficients from a Remez (minimax, absolute error)
-//              fit done for this file (max error 1e-7, <= 3 ulp in float32);
+//              [0, 1]: the minimax fit (Remez exchange, absolute error of
+//              atan(a) = a p(a^2)) of csrc/atan_minimax.py: 5.8e-9 with exact
+//              coefficients, 2.2e-8 with the float32 ones below (ATAN_P0..8);
+//              valid for finite arguments with max(|x|, |y|) below 2^126;
 //   tyre    -- for C = 1.5, sin(1.5 atan z) by the half-angle identities
 //              cos t = 1/sqrt(1+z^2), sin(3t/2) = sin t cos(t/2) + cos t sin(t/2)
 //              (no atan, no sin); other C use the library atanf / sinf;
@@ -104,21 +106,33 @@ __device__ __forceinline__ float clampf(float v, float lo, float hi) {
     return fminf(fmaxf(v, lo), hi);
 }
 
-// atan2 by octant reduction and a minimax polynomial for atan(a)/a, a in [0, 1].
+// atan(a) ~ a p(a^2) on [0, 1]: the coefficients of p, highest degree first
+// (csrc/atan_minimax.py prints them; a CPU test regenerates and compares them).
+constexpr float ATAN_P8 = 2.456725575e-03f;
+constexpr float ATAN_P7 = -1.440136135e-02f;
+constexpr float ATAN_P6 = 3.978123143e-02f;
+constexpr float ATAN_P5 = -7.234857976e-02f;
+constexpr float ATAN_P4 = 1.049894616e-01f;
+constexpr float ATAN_P3 = -1.416122913e-01f;
+constexpr float ATAN_P2 = 1.998590678e-01f;
+constexpr float ATAN_P1 = -3.333259821e-01f;
+constexpr float ATAN_P0 = 9.999998808e-01f;
+
+// atan2 by octant reduction and the minimax polynomial for atan(a)/a, a in [0, 1].
 __device__ __forceinline__ float atan2_poly(float y, float x) {
     const float ax = fabsf(x), ay = fabsf(y);
     const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
     const float a = mx > 0.0f ? __fdividef(mn, mx) : 0.0f;
     const float s = a * a;
-    float p = 2.456725575e-03f;
-    p = fmaf(p, s, -1.440136135e-02f);
-    p = fmaf(p, s, 3.978123143e-02f);
-    p = fmaf(p, s, -7.234857976e-02f);
-    p = fmaf(p, s, 1.049894616e-01f);
-    p = fmaf(p, s, -1.416122913e-01f);
-    p = fmaf(p, s, 1.998590678e-01f);
-    p = fmaf(p, s, -3.333259821e-01f);
-    p = fmaf(p, s, 9.999998808e-01f);
+    float p = ATAN_P8;
+    p = fmaf(p, s, ATAN_P7);
+    p = fmaf(p, s, ATAN_P6);
+    p = fmaf(p, s, ATAN_P5);
+    p = fmaf(p, s, ATAN_P4);
+    p = fmaf(p, s, ATAN_P3);
+    p = fmaf(p, s, ATAN_P2);
+    p = fmaf(p, s, ATAN_P1);
+    p = fmaf(p, s, ATAN_P0);
     float r = a * p;
     if (ay > ax) r = 1.57079632679f - r;
     if (x < 0.0f) r = 3.14159265359f - r;

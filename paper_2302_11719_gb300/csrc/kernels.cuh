@@ -74,6 +74,8 @@ cudaError_t launch_update_partial(const DevParams& P, const float* S, const floa
 constexpr int MERGE_MAX_PARTS = 1024;
 cudaError_t launch_merge(const DevParams& P, int n_parts, const double* parts, float* V,
                          unsigned* status, cudaStream_t st);
+cudaError_t launch_debug_elementary(int fn, int n, const float* a, const float* b, float* out,
+                                   float* ref, cudaStream_t st);
 cudaError_t launch_debug_noise(const DevParams& P, uint32_t iter, uint32_t ctr3, int K, int T,
                                float* eps, uint32_t* raw, cudaStream_t st);
 

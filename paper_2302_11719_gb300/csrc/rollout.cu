@@ -548,6 +548,39 @@ __global__ void debug_noise_kernel(DevParams P, uint32_t iter, uint32_t ctr3, in
     }
 }
 
+// The library's hand-written elementary functions on given arguments (test
+// access).  Packed forms (fn 1, 3, 6, 7) take elements 2i and 2i + 1 as the two
+// halves of one register pair.  ref receives CUDA's own function of the same
+// arguments.
+__global__ void debug_elementary_kernel(int fn, int n, const float* __restrict__ a,
+                                        const float* __restrict__ b, float* __restrict__ out,
+                                        float* __restrict__ ref) {
+    using namespace x2;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool packed = fn == 1 || fn == 3 || fn == 6 || fn == 7;
+    const int i0 = packed ? 2 * i : i;
+    if (i0 >= n) return;
+    const int i1 = (packed && i0 + 1 < n) ? i0 + 1 : i0;
+    const f2 A = make_float2(a[i0], a[i1]), B = make_float2(b[i0], b[i1]);
+    f2 o = A, r = A;
+    switch (fn) {
+        case 0: o.x = atan2_poly(A.x, B.x); r.x = atan2f(A.x, B.x); break;
+        case 1: o = atan2_2(A, B); r = make_float2(atan2f(A.x, B.x), atan2f(A.y, B.y)); break;
+        case 2: o.x = tyre15(A.x); r.x = sinf(1.5f * atanf(A.x)); break;
+        case 3: o = tyre15_2(A); r = make_float2(sinf(1.5f * atanf(A.x)), sinf(1.5f * atanf(A.y))); break;
+        case 4: { float sn, cs; sincos_half(A.x, &sn, &cs); o.x = sn; r.x = sinf(A.x); } break;
+        case 5: { float sn, cs; sincos_half(A.x, &sn, &cs); o.x = cs; r.x = cosf(A.x); } break;
+        case 6: { f2 sn, cs; sincos_half2(A, sn, cs); o = sn; r = make_float2(sinf(A.x), sinf(A.y)); } break;
+        default: { f2 sn, cs; sincos_half2(A, sn, cs); o = cs; r = make_float2(cosf(A.x), cosf(A.y)); } break;
+    }
+    out[i0] = o.x;
+    ref[i0] = r.x;
+    if (packed && i1 != i0) {
+        out[i1] = o.y;
+        ref[i1] = r.y;
+    }
+}
+
 // Merge of slice partials (m_g, eta_g, A_g) into V+ (Eq. 10-11 over the union
 // of the slices): omega_k = exp(-(S_k - m)/lambda) = c_g exp(-(S_k - m_g)/lambda)
 // for k in slice g, c_g = exp(-(m_g - m)/lambda), m = min_g m_g, so eta and the
@@ -706,6 +739,13 @@ cudaError_t launch_update_shield(const DevParams& P, const float* S, const float
     return launch_pdl(kern, update_grid(P.K), UPD_BLK, smem, st, P, S, blk_min, n_min, V, iter,
                       ctr3, iter_dev, part_acc, part_eta, part_has, ticket, status, sh, 0u,
                       (double*)nullptr);
+}
+
+cudaError_t launch_debug_elementary(int fn, int n, const float* a, const float* b, float* out,
+                                   float* ref, cudaStream_t st) {
+    const int items = (fn == 1 || fn == 3 || fn == 6 || fn == 7) ? (n + 1) / 2 : n;
+    debug_elementary_kernel<<<(items + 255) / 256, 256, 0, st>>>(fn, n, a, b, out, ref);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_debug_noise(const DevParams& P, uint32_t iter, uint32_t ctr3, int K, int T,

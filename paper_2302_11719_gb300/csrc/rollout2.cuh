@@ -38,7 +38,7 @@ __device__ __forceinline__ State2 broadcast(const State& s) {
 }
 
 // atan2 of both halves: octant reduction and the degree-8 minimax polynomial
-// of atan2_poly.  x = y = 0 gives 0 (mx is kept at or above the smallest
+// of atan2_poly (ATAN_P0..8).  x = y = 0 gives 0 (mx is kept at or above the smallest
 // normal float, so a = 0 there).
 __device__ __forceinline__ f2 atan2_2(f2 y, f2 x) {
     const float ax0 = fabsf(x.x), ay0 = fabsf(y.x), ax1 = fabsf(x.y), ay1 = fabsf(y.y);
@@ -47,14 +47,14 @@ __device__ __forceinline__ f2 atan2_2(f2 y, f2 x) {
     const float mx1 = fmaxf(fmaxf(ax1, ay1), 1.17549435e-38f);
     const f2 a = mul(mn, make_float2(rcp_approx(mx0), rcp_approx(mx1)));
     const f2 s = mul(a, a);
-    f2 p = fma(bc(2.456725575e-03f), s, bc(-1.440136135e-02f));
-    p = fma(p, s, bc(3.978123143e-02f));
-    p = fma(p, s, bc(-7.234857976e-02f));
-    p = fma(p, s, bc(1.049894616e-01f));
-    p = fma(p, s, bc(-1.416122913e-01f));
-    p = fma(p, s, bc(1.998590678e-01f));
-    p = fma(p, s, bc(-3.333259821e-01f));
-    p = fma(p, s, bc(9.999998808e-01f));
+    f2 p = fma(bc(ATAN_P8), s, bc(ATAN_P7));
+    p = fma(p, s, bc(ATAN_P6));
+    p = fma(p, s, bc(ATAN_P5));
+    p = fma(p, s, bc(ATAN_P4));
+    p = fma(p, s, bc(ATAN_P3));
+    p = fma(p, s, bc(ATAN_P2));
+    p = fma(p, s, bc(ATAN_P1));
+    p = fma(p, s, bc(ATAN_P0));
     f2 r = mul(a, p);
     const f2 r1 = fma(r, bc(-1.0f), bc(1.57079632679f));
     r.x = (ay0 > ax0) ? r1.x : r.x;

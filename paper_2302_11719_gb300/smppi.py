@@ -76,6 +76,7 @@ _SIGS = {
     "smppi_shield_loop": ([_vp, _vp, _vp, _vp, _u32, _u32, _i, _i], _i),
     "smppi_debug_noise": ([_vp, _u32, _u32, _i, _i, _vp, _vp], _i),
     "smppi_debug_wait_timeout": ([_i, _vp, _vp], _i),
+    "smppi_debug_elementary": ([_i, _i, _vp, _vp, _vp, _vp, _vp], _i),
     "smppi_step_noalloc": ([C.POINTER(Params), _vp, _vp, _u32, _u32, _vp, _vp], _i),
     "smppi_batch_create": ([C.POINTER(Params), _i, C.POINTER(InstanceDesc), _vp, _i, _vp,
                             C.POINTER(_vp)], _i),
@@ -256,6 +257,13 @@ def smppi_debug_wait_timeout(which, status, stream=None):
     completes (0: an mbarrier phase, 1: a shared-memory counter), gives up and
     ORs DEV_TIMEOUT into the device word `status`."""
     _check(load_library().smppi_debug_wait_timeout(int(which), _ptr(status), _stream(stream)))
+
+
+def smppi_debug_elementary(fn, a, b, out, ref, stream=None):
+    """The library's elementary function `fn` (smppi.h) of a (and b) into out,
+    CUDA's own into ref; device float32 tensors of equal length."""
+    _check(load_library().smppi_debug_elementary(int(fn), int(a.numel()), _ptr(a), _ptr(b),
+                                                 _ptr(out), _ptr(ref), _stream(stream)))
 
 
 def smppi_step_noalloc(params: Params, x0, V, iter=0, instance=0, S_out=None, stream=None):
