@@ -8,7 +8,9 @@
 // is a dense contraction; the hot loop is FP32 FMA/ALU/SFU work in registers.
 //
 // Elementary functions on the hot path are written here so that each step
-// costs few instructions while staying within a few ulp:
+// costs few instructions while staying within a few ulp (measured on dense grids
+// against float64: atan2 <= 3.8 ulp, the C = 1.5 tyre <= 5.0 ulp, the short
+// sin / cos <= 0.8 ulp):
 //   atan2   -- octant reduction + a degree-8 polynomial in a^2 for atan(a)/a on
 //              [0, 1]: the minimax fit (Remez exchange, absolute error of
 //              atan(a) = a p(a^2)) of csrc/atan_minimax.py: 5.8e-9 with exact
