@@ -332,6 +332,21 @@ smppi_status enqueue_shield(smppi_handle* h, cudaStream_t st, float* x0, float* 
         toc(h, st, SMPPI_KERNEL_REPAIR, ev);
         return SMPPI_OK;
     }
+    if (n_repair > 0 && merge_shield_applies(h->dp)) {
+        // rollouts whose blocks each write their min-shifted partial of the update,
+        // then one block that merges them into V+ and runs the shield
+        const BlockPartials part{h->part_acc, h->part_eta, h->part_has};
+        int ev = tic(h, st);
+        CU(h, launch_rollout(h->dp, false, x0, V, h->rec, iter, instance << 8, iter_dev, h->S_ws,
+                             nullptr, h->blk_min, h->rws.seg0, h->status, st, 0u, part));
+        toc(h, st, SMPPI_KERNEL_ROLLOUT, ev);
+        ev = tic(h, st);
+        CU(h, launch_merge_shield(h->dp, rollout_blocks(h->dp), h->blk_min, part, V, iter,
+                                  iter_dev, h->status, h->rec, h->rws.seg0, x0, Vs, n_repair,
+                                  h->rws.ck, merit, (instance << 8) | 1u, st));
+        toc(h, st, SMPPI_KERNEL_UPDATE_SHIELD, ev);
+        return SMPPI_OK;
+    }
     if (n_repair > 0) {
         smppi_status s = enqueue_rollout(h, st, x0, V, iter, instance, h->S_ws, nullptr, iter_dev);
         if (s != SMPPI_OK) return s;
@@ -418,9 +433,11 @@ smppi_status smppi_create(const smppi_params* p, void* cuda_stream, smppi_handle
     ALLOC(h->rec, rec_table_bytes(p->n_track));
     ALLOC(h->S_ws, sizeof(float) * p->K);
     ALLOC(h->blk_min, sizeof(float) * h->nblk);
-    ALLOC(h->part_acc, sizeof(float) * 2 * T * (size_t)UPD_BLK);
-    ALLOC(h->part_eta, sizeof(double) * UPD_BLK);
-    ALLOC(h->part_has, sizeof(int) * UPD_BLK);
+    // partials of the update kernel's blocks or of the packed rollout blocks
+    const size_t n_part = (size_t)std::max(UPD_BLK, (p->K + 2 * ROLL2_BLK - 1) / (2 * ROLL2_BLK));
+    ALLOC(h->part_acc, sizeof(float) * 2 * T * n_part);
+    ALLOC(h->part_eta, sizeof(double) * n_part);
+    ALLOC(h->part_has, sizeof(int) * n_part);
     ALLOC(h->ticket, sizeof(unsigned));
     ALLOC(h->status, sizeof(unsigned));
     ALLOC(h->iter_dev, sizeof(uint32_t));

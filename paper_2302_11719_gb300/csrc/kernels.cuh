@@ -15,6 +15,18 @@ inline cudaError_t ensure_smem(const void* kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Per-block partials of the update (Eq. 10-11 min-shifted by each rollout
+// block's own minimum, which blk_min holds) written by the packed rollout
+// kernel: acc [blocks][2T], eta [blocks], has [blocks].  All null: none written.
+struct BlockPartials {
+    float* acc;
+    double* eta;
+    int* has;
+};
+// Largest number of rollout blocks the single-block merge takes (2 * ROLL2_BLK
+// rollouts each: K <= 2^19).
+constexpr int MERGE_MAX_BLOCKS = 2048;
+
 // Dynamic shared memory of the rollout launch (the larger of its two kernels).
 size_t rollout_smem_bytes(int n_track, int T);
 // Block minima the rollout launch writes (<= ceil(K / ROLL_BLK)).
@@ -33,7 +45,11 @@ cudaError_t launch_rollout_curv(const DevParams& P, const float* kappa, bool dum
 cudaError_t launch_rollout(const DevParams& P, bool dump, const float* x0, const float* V,
                            const float4* rec, uint32_t iter, uint32_t ctr3,
                            const uint32_t* iter_dev, float* S_out, float* traj, float* blk_min,
-                           int* seg0_out, unsigned* status, cudaStream_t st, uint32_t k_off = 0);
+                           int* seg0_out, unsigned* status, cudaStream_t st, uint32_t k_off = 0,
+                           BlockPartials part = BlockPartials{nullptr, nullptr, nullptr});
+// True when the rollout launch can write block partials for launch_merge_shield
+// (the packed kernel applies and the blocks are few enough).
+bool merge_shield_applies(const DevParams& P);
 // Segment-pair table of a closed polyline (layout in device.cuh): n + 5
 // records of three float4.
 __host__ __device__ inline size_t rec_table_bytes(int n) { return (size_t)(n + 5) * 3 * sizeof(float4); }
@@ -68,6 +84,15 @@ cudaError_t launch_update_partial(const DevParams& P, const float* S, const floa
                                   float* part_acc, double* part_eta, int* part_has,
                                   unsigned* ticket, unsigned* status, uint32_t k_off,
                                   double* partial_out, cudaStream_t st);
+// The update from the rollout launch's block partials (one block: the block
+// minima, m = min, c_b = exp(-(m_b - m)/lambda), eta = sum c_b eta_b, A = sum
+// c_b A_b in float64 in block order), then the shield and the closed-loop step
+// as launch_update_shield.  nb = rollout_blocks(P) <= MERGE_MAX_BLOCKS.
+cudaError_t launch_merge_shield(const DevParams& P, int nb, const float* blk_min,
+                                BlockPartials part, float* V, uint32_t iter, uint32_t* iter_dev,
+                                unsigned* status, const float4* rec, const int* seg0, float* x0,
+                                float* V_safe, int n_repair, int ck, double* merit_out,
+                                uint32_t ctr3_dist, cudaStream_t st);
 // V <- clamp(V + A / eta) from n_parts slice partials [n_parts][2T + 2]: with
 // m = min_g m_g and c_g = exp(-(m_g - m)/lambda), eta = sum_g c_g eta_g and
 // A = sum_g c_g A_g, summed in float64 in slice order.

@@ -139,16 +139,108 @@ __global__ void __launch_bounds__(BLK) mppi_rollout_kernel(
     }
 }
 
+// Partial of one rollout block (Eq. 10-11 over its rollouts, min-shifted by its
+// own minimum m_b; the merge rescales it by exp(-(m_b - m)/lambda)):
+// part_eta = sum_k exp(-(S_k - m_b)/lambda) and part_acc[2t + j] = the same
+// weights times eps_{k,t,j}, summed over the rollouts whose weight exceeds
+// w_skip, with the noise regenerated.  The taken rollouts are listed in thread
+// order (rollout a, then b, of each thread); thread (slot c, pair p)
+// accumulates list items c, c + C, ... for pair p and the slots are added in
+// slot order: a fixed summation order.  smem: l_k, l_w [2 BLK], acc_s [2T].
+template <int BLK>
+__device__ __forceinline__ void block_partial(const DevParams& P, float m_b, float2 S, bool act_a,
+                                              bool act_b, uint32_t ka, uint32_t kb, uint32_t iter,
+                                              uint32_t ctr3, int* l_k, float* l_w, float* acc_s,
+                                              float* red, int* w_cnt, float* part_acc,
+                                              double* part_eta, int* part_has) {
+    constexpr int NW = BLK / 32;
+    constexpr int PP = (SMPPI_MAX_T / 2 + BLK - 1) / BLK;   // pairs per thread at most
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int T = P.T, T2 = 2 * T, npair = (T + 1) >> 1;
+    const float wa = act_a ? expf((m_b - S.x) * P.lam_inv) : 0.0f;
+    const float wb = act_b ? expf((m_b - S.y) * P.lam_inv) : 0.0f;
+    const bool ta = wa > P.w_skip, tb = wb > P.w_skip;
+    const int ntake = (int)ta + (int)tb;
+    int incl = ntake;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    float e = wa + wb;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if (lane == 31) w_cnt[warp] = incl;
+    if (lane == 0) red[warp] = e;
+    for (int j = tid; j < T2; j += BLK) acc_s[j] = 0.0f;
+    __syncthreads();
+    int off = incl - ntake, tot = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        if (w < warp) off += w_cnt[w];
+        tot += w_cnt[w];
+    }
+    if (ta) { l_k[off] = (int)ka; l_w[off] = wa; ++off; }
+    if (tb) { l_k[off] = (int)kb; l_w[off] = wb; }
+    __syncthreads();
+    const int C = npair <= BLK ? BLK / npair : 1;
+    const int c = npair <= BLK ? tid / npair : 0;
+    const int pb = npair <= BLK ? tid % npair : tid;
+    float ac[PP][4];
+#pragma unroll
+    for (int u = 0; u < PP; ++u) ac[u][0] = ac[u][1] = ac[u][2] = ac[u][3] = 0.0f;
+    if (c < C) {
+        for (int i = c; i < tot; i += C) {
+#pragma unroll
+            for (int u = 0; u < PP; ++u) {
+                const int p = pb + u * BLK;
+                if ((u > 0 && npair <= BLK) || p >= npair) break;
+                const uint4 r = philox10(make_uint4((uint32_t)l_k[i], (uint32_t)p, iter, ctr3), P);
+                const float2 ze = box_muller(r.x, r.y), zo = box_muller(r.z, r.w);
+                const float w0 = l_w[i] * P.sig0, w1 = l_w[i] * P.sig1;
+                ac[u][0] = fmaf(w0, ze.x, ac[u][0]);
+                ac[u][1] = fmaf(w1, ze.y, ac[u][1]);
+                ac[u][2] = fmaf(w0, zo.x, ac[u][2]);
+                ac[u][3] = fmaf(w1, zo.y, ac[u][3]);
+            }
+        }
+    }
+    for (int cc = 0; cc < C; ++cc) {
+        if (c == cc) {
+#pragma unroll
+            for (int u = 0; u < PP; ++u) {
+                const int p = pb + u * BLK;
+                if ((u > 0 && npair <= BLK) || p >= npair) break;
+                acc_s[4 * p] += ac[u][0];
+                acc_s[4 * p + 1] += ac[u][1];
+                if (2 * p + 1 < T) {
+                    acc_s[4 * p + 2] += ac[u][2];
+                    acc_s[4 * p + 3] += ac[u][3];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    for (int j = tid; j < T2; j += BLK) part_acc[j] = acc_s[j];
+    if (tid == 0) {
+        float eta = red[0];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) eta += red[w];
+        *part_eta = (double)eta;
+        *part_has = tot > 0;
+    }
+}
+
 // Launch 1, packed form: thread t of block b steps rollouts 2 b BLK + t and
 // 2 b BLK + BLK + t together (rollout2.cuh).  The segment-pair table arrives
 // by one bulk copy; V is laid out as broadcast pairs.
-template <bool DUMP>
+template <bool DUMP, bool PART>
 __global__ void __launch_bounds__(ROLL2_BLK, 2) mppi_rollout2_kernel(
     DevParams P, const float* __restrict__ x0g, const float* __restrict__ Vg,
     const float4* __restrict__ recg, uint32_t iter, uint32_t ctr3,
     const uint32_t* __restrict__ iter_dev, float* __restrict__ S_out, float* __restrict__ traj,
     float* __restrict__ blk_min, int* __restrict__ seg0_out, unsigned* __restrict__ status,
-    uint32_t k_off) {
+    uint32_t k_off, BlockPartials part) {
     constexpr int BLK = ROLL2_BLK, NW = BLK / 32;
     griddep_launch_dependents();
     griddep_wait();
@@ -226,11 +318,24 @@ __global__ void __launch_bounds__(ROLL2_BLK, 2) mppi_rollout2_kernel(
     const float m = warp_min(fminf(act_a ? S.x : 3.0e38f, act_b ? S.y : 3.0e38f));
     if (lane == 0) red_f[warp] = m;
     __syncthreads();
+    __shared__ float s_mb;
     if (tid == 0) {
         float mb = red_f[0];
 #pragma unroll
         for (int w = 1; w < NW; ++w) mb = fminf(mb, red_f[w]);
         blk_min[blockIdx.x] = mb;
+        s_mb = mb;
+    }
+    if (PART) {   // this block's min-shifted partial of the update (merged by the next launch)
+        __shared__ int w_cnt[NW];
+        __syncthreads();
+        float* acc_s = reinterpret_cast<float*>(Vp + 2 * T);
+        int* l_k = reinterpret_cast<int*>(acc_s + 2 * T);
+        float* l_w = reinterpret_cast<float*>(l_k + 2 * BLK);
+        block_partial<BLK>(P, s_mb, S, act_a, act_b, (uint32_t)ka + k_off, (uint32_t)kb + k_off,
+                           iter, ctr3, l_k, l_w, acc_s, red_f, w_cnt,
+                           part.acc + (size_t)blockIdx.x * 2 * T, part.eta + blockIdx.x,
+                           part.has + blockIdx.x);
     }
 }
 
@@ -277,6 +382,62 @@ struct ShieldTail {
     double* merit_out;      // optional: n_repair + 1 merits
     uint32_t ctr3_dist;     // counter word of the disturbance
 };
+
+// The safety shield on V+ (Alg. 1 with Armijo backtracking, repair_in_block;
+// V_safe out) and the closed-loop step (x0 <- f(x0, v_0^safe) + w, V <- shift(V+),
+// Eq. 26) by one block of BLK threads.  smem_raw: the segment-pair table, whose
+// bulk copy completes on bar, then room for the repair's controls, gradient and
+// tape; Vplus: V+ in shared memory.
+template <int BLK, bool FAST>
+__device__ __forceinline__ void shield_tail(const DevParams& P, unsigned char* smem_raw,
+                                            uint64_t* bar, const float2* Vplus, float* V,
+                                            uint32_t iter, uint32_t n_upd, uint32_t* iter_dev,
+                                            const ShieldTail& sh, unsigned* status) {
+    __shared__ int s_fail;
+    __shared__ RepairSmem rsm;
+    const int tid = threadIdx.x, T = P.T;
+    float4* rec = reinterpret_cast<float4*>(smem_raw);
+    float2* Vw = reinterpret_cast<float2*>(rec + 3 * (P.n_track + 5));
+    float2* G2 = Vw + T;
+    float* tape_s = reinterpret_cast<float*>(G2 + T);
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    if (!mbar_wait_bounded(bar, 0u)) s_fail = 1;
+    __syncthreads();
+    if (s_fail) {
+        if (tid == 0) {
+            atomicOr(status, SMPPI_DEV_TIMEOUT);
+            mbar_wait_bounded(bar, 0u);
+        }
+        return;
+    }
+    for (int t = tid; t < T; t += BLK) Vw[t] = Vplus[t];
+    __syncthreads();
+    const State x0 = make_state(sh.x0);
+    if (sh.n_repair > 0)
+        repair_in_block<BLK, FAST>(P, rec, x0, sh.seg0[0], Vw, G2, tape_s, sh.n_repair, 1, 0.0f,
+                                   sh.ck, sh.merit_out, nullptr, status, rsm);
+    float2* Vs_out = reinterpret_cast<float2*>(sh.V_safe);
+    float2* V2 = reinterpret_cast<float2*>(V);
+    for (int t = tid; t < T; t += BLK) {
+        Vs_out[t] = Vw[t];
+        V2[t] = Vplus[t + 1 < T ? t + 1 : T - 1];   // warm start: shift(V+)
+    }
+    if (tid == 0) {   // x0 <- f(x0, clamp(v_0^safe)) + w_n
+        State x = x0;
+        const float2 v0 = Vw[0];
+        model_step(P, x, clampf(v0.x, P.umin0, P.umax0), clampf(v0.y, P.umin1, P.umax1));
+        const uint4 r = philox10(make_uint4(0u, 0u, iter, sh.ctr3_dist), P);
+        const float2 z = box_muller(r.x, r.y);
+        sh.x0[0] = x.vx;
+        sh.x0[1] = fmaf(P.dsig0, z.x, x.vy);
+        sh.x0[2] = fmaf(P.dsig1, z.y, x.r);
+        sh.x0[3] = x.X;
+        sh.x0[4] = x.Y;
+        sh.x0[5] = x.psi;
+        if (iter_dev) *iter_dev = n_upd + 1u;
+    }
+}
 
 template <bool SHIELD, bool FAST>
 __global__ void __launch_bounds__(UPD_BLK) mppi_update_kernel(
@@ -475,50 +636,123 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_update_kernel(
     if (!SHIELD || partial_out) return;
 
     // ---- safety shield on V+ (Alg. 1) and closed-loop step (Eq. 26) ----
-    __shared__ int s_fail;
-    __shared__ RepairSmem rsm;
-    float4* rec = reinterpret_cast<float4*>(smem_raw);
-    float2* Vw = reinterpret_cast<float2*>(rec + 3 * (P.n_track + 5));
-    float2* G2 = Vw + T;
-    float* tape_s = reinterpret_cast<float*>(G2 + T);
-    if (tid == 0) s_fail = 0;
+    shield_tail<UPD_BLK, FAST>(P, smem_raw, &bar, reinterpret_cast<const float2*>(acc_s), V, iter,
+                               n_upd, iter_dev, sh, status);
+}
+
+// One control update after a rollout launch that wrote block partials: the
+// merge of the partials into V+ (Eq. 10-11; the log-sum-exp rescaling
+// c_b = exp(-(m_b - m)/lambda) with m the smallest block minimum, the sums in
+// float64 in block order; blocks whose whole contribution c_b eta_b is below w_skip are
+// left out of the noise sum, which moves V+ by at most w_skip max|eps| each),
+// then the shield and the closed-loop step (shield_tail).  One block; the
+// track table is staged before the wait on the rollout launch.
+template <bool FAST>
+__global__ void __launch_bounds__(UPD_BLK) mppi_merge_shield_kernel(
+    DevParams P, int nb, const float* __restrict__ blk_min, BlockPartials part, float* V,
+    uint32_t iter, uint32_t* __restrict__ iter_dev, unsigned* __restrict__ status,
+    ShieldTail sh) {
+    constexpr int NW = UPD_BLK / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ double s_c[MERGE_MAX_BLOCKS];
+    __shared__ int l_b[MERGE_MAX_BLOCKS];
+    __shared__ float vplus[2 * SMPPI_MAX_T];
+    __shared__ float red_f[NW];
+    __shared__ double red_d[NW];
+    __shared__ int w_cnt[NW];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int T2 = 2 * P.T;
+    griddep_launch_dependents();
+    if (tid == 0) {   // the track table is constant: staged before the wait
+        mbar_init(&bar, 1);
+        const uint32_t bytes = (uint32_t)rec_table_bytes(P.n_track);
+        mbar_expect_tx(&bar, bytes);
+        bulk_g2s(reinterpret_cast<float4*>(smem_raw), sh.rec, bytes, &bar);
+    }
+    griddep_wait();
+    const uint32_t n_upd = iter_dev ? *iter_dev : 0u;
+    iter += n_upd;
+    // every block's (m_b, eta_b, has_b) loaded at once into registers (one round trip)
+    constexpr int PB = MERGE_MAX_BLOCKS / UPD_BLK;
+    float mb[PB];
+    double eb[PB];
+    int hb[PB];
+#pragma unroll
+    for (int u = 0; u < PB; ++u) {
+        const int b = tid + u * UPD_BLK;
+        mb[u] = b < nb ? __ldcg(&blk_min[b]) : 3.0e38f;
+        eb[u] = b < nb ? __ldcg(&part.eta[b]) : 0.0;
+        hb[u] = b < nb ? __ldcg(&part.has[b]) : 0;
+    }
+    // m = min_b m_b
+    float m = mb[0];
+#pragma unroll
+    for (int u = 1; u < PB; ++u) m = fminf(m, mb[u]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) red_f[warp] = m;
     __syncthreads();
-    if (!mbar_wait_bounded(&bar, 0u)) s_fail = 1;
-    __syncthreads();
-    if (s_fail) {
-        if (tid == 0) {
-            atomicOr(status, SMPPI_DEV_TIMEOUT);
-            mbar_wait_bounded(&bar, 0u);
+    m = red_f[0];
+#pragma unroll
+    for (int w = 1; w < NW; ++w) m = fminf(m, red_f[w]);
+    // c_b (float32: its rounding rescales eta_b and A_b alike) and eta = sum c_b eta_b
+    // in float64 (fixed order: thread-strided, then the warps' sums in order)
+    double eta = 0.0;
+#pragma unroll
+    for (int u = 0; u < PB; ++u) {
+        const int b = tid + u * UPD_BLK;
+        if (b < nb) {
+            const double c = (double)expf((m - mb[u]) * P.lam_inv);
+            const double ce = c * eb[u];
+            eta += ce;
+            s_c[b] = (hb[u] && ce > (double)P.w_skip) ? c : 0.0;
         }
-        return;
     }
-    const float2* Vplus = reinterpret_cast<const float2*>(acc_s);
-    for (int t = tid; t < T; t += UPD_BLK) Vw[t] = Vplus[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) eta += __shfl_xor_sync(0xffffffffu, eta, o);
+    if (lane == 0) red_d[warp] = eta;
     __syncthreads();
-    const State x0 = make_state(sh.x0);
-    if (sh.n_repair > 0)
-        repair_in_block<UPD_BLK, FAST>(P, rec, x0, sh.seg0[0], Vw, G2, tape_s, sh.n_repair, 1,
-                                       0.0f, sh.ck, sh.merit_out, nullptr, status, rsm);
-    float2* Vs_out = reinterpret_cast<float2*>(sh.V_safe);
-    float2* V2 = reinterpret_cast<float2*>(V);
-    for (int t = tid; t < T; t += UPD_BLK) {
-        Vs_out[t] = Vw[t];
-        V2[t] = Vplus[t + 1 < T ? t + 1 : T - 1];   // warm start: shift(V+)
+    if (tid == 0) {
+        double e = red_d[0];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) e += red_d[w];
+        red_d[0] = 1.0 / e;          // one float64 division for the block
     }
-    if (tid == 0) {   // x0 <- f(x0, clamp(v_0^safe)) + w_n
-        State x = x0;
-        const float2 v0 = Vw[0];
-        model_step(P, x, clampf(v0.x, P.umin0, P.umax0), clampf(v0.y, P.umin1, P.umax1));
-        const uint4 r = philox10(make_uint4(0u, 0u, iter, sh.ctr3_dist), P);
-        const float2 z = box_muller(r.x, r.y);
-        sh.x0[0] = x.vx;
-        sh.x0[1] = fmaf(P.dsig0, z.x, x.vy);
-        sh.x0[2] = fmaf(P.dsig1, z.y, x.r);
-        sh.x0[3] = x.X;
-        sh.x0[4] = x.Y;
-        sh.x0[5] = x.psi;
-        if (iter_dev) *iter_dev = n_upd + 1u;
+    __syncthreads();
+    const double inv_eta = red_d[0];
+    // the blocks that enter the noise sum, in block order
+    int nz = 0;
+    for (int b0 = 0; b0 < nb; b0 += UPD_BLK) {
+        const int b = b0 + tid;
+        const bool sel = b < nb && s_c[b] != 0.0;
+        const unsigned bal = __ballot_sync(0xffffffffu, sel);
+        if (lane == 0) w_cnt[warp] = __popc(bal);
+        __syncthreads();
+        int off = nz;
+        for (int w = 0; w < warp; ++w) off += w_cnt[w];
+        if (sel) l_b[off + __popc(bal & ((1u << lane) - 1u))] = b;
+        for (int w = 0; w < NW; ++w) nz += w_cnt[w];
+        __syncthreads();
     }
+    for (int j = tid; j < T2; j += UPD_BLK) {
+        double A = 0.0;
+        int i = 0;
+        for (; i + 8 <= nz; i += 8) {      // 8 independent loads in flight, summed in order
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = __ldcg(&part.acc[(size_t)l_b[i + u] * T2 + j]);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) A = fma(s_c[l_b[i + u]], (double)v[u], A);
+        }
+        for (; i < nz; ++i) A = fma(s_c[l_b[i]], (double)__ldcg(&part.acc[(size_t)l_b[i] * T2 + j]), A);
+        const float lo = (j & 1) ? P.umin1 : P.umin0, hi = (j & 1) ? P.umax1 : P.umax0;
+        const float v = (float)fma(A, inv_eta, (double)V[j]);
+        if (!isfinite(v)) atomicOr(status, SMPPI_DEV_NUMERIC);
+        vplus[j] = clampf(v, lo, hi);
+    }
+    shield_tail<UPD_BLK, FAST>(P, smem_raw, &bar, reinterpret_cast<const float2*>(vplus), V, iter,
+                               n_upd, iter_dev, sh, status);
 }
 
 // Control noise exactly as the rollout kernels draw it (test access).
@@ -637,8 +871,10 @@ static cudaError_t launch_pdl(void (*kern)(KArgs...), int grid, int block, size_
     return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 size_t rollout_smem_bytes(int n_track, int T) {
-    // the packed kernel's V pairs take two float4 per step, the scalar kernel's one
-    return rec_table_bytes(n_track) + (size_t)T * 2 * sizeof(float4);
+    // the packed kernel's V pairs take two float4 per step, the scalar kernel's one;
+    // the block partials add 2T floats and the list of taken rollouts
+    return rec_table_bytes(n_track) + (size_t)T * 2 * sizeof(float4) +
+           (size_t)T * 2 * sizeof(float) + (size_t)ROLL2_BLK * 4 * sizeof(float);
 }
 
 static bool packed_rollout(const DevParams& P) { return P.tyre15 && P.steer_small; }
@@ -672,17 +908,26 @@ int update_grid(int K) {
     return g < UPD_BLK ? g : UPD_BLK;   // the merge lists at most UPD_BLK partials
 }
 
+bool merge_shield_applies(const DevParams& P) {
+    return packed_rollout(P) && rollout_blocks(P) <= MERGE_MAX_BLOCKS;
+}
+
 cudaError_t launch_rollout(const DevParams& P, bool dump, const float* x0, const float* V,
                            const float4* rec, uint32_t iter, uint32_t ctr3,
                            const uint32_t* iter_dev, float* S_out, float* traj, float* blk_min,
-                           int* seg0_out, unsigned* status, cudaStream_t st, uint32_t k_off) {
+                           int* seg0_out, unsigned* status, cudaStream_t st, uint32_t k_off,
+                           BlockPartials part) {
     if (packed_rollout(P)) {
-        const size_t smem = rec_table_bytes(P.n_track) + (size_t)P.T * 2 * sizeof(float4);
-        auto kern = dump ? mppi_rollout2_kernel<true> : mppi_rollout2_kernel<false>;
+        const bool with_part = part.acc != nullptr;
+        size_t smem = rec_table_bytes(P.n_track) + (size_t)P.T * 2 * sizeof(float4);
+        if (with_part) smem += (size_t)P.T * 2 * sizeof(float) + (size_t)ROLL2_BLK * 4 * sizeof(float);
+        auto kern = dump ? mppi_rollout2_kernel<true, false>
+                         : (with_part ? mppi_rollout2_kernel<false, true>
+                                      : mppi_rollout2_kernel<false, false>);
         cudaError_t e = ensure_smem((const void*)kern, smem);
         if (e != cudaSuccess) return e;
         return launch_pdl(kern, rollout_blocks(P), ROLL2_BLK, smem, st, P, x0, V, rec, iter, ctr3,
-                          iter_dev, S_out, traj, blk_min, seg0_out, status, k_off);
+                          iter_dev, S_out, traj, blk_min, seg0_out, status, k_off, part);
     }
     const int nblk = (P.K + ROLL_BLK - 1) / ROLL_BLK;
     const size_t smem = rec_table_bytes(P.n_track) + (size_t)P.T * sizeof(float4);
@@ -739,6 +984,22 @@ cudaError_t launch_update_shield(const DevParams& P, const float* S, const float
     return launch_pdl(kern, update_grid(P.K), UPD_BLK, smem, st, P, S, blk_min, n_min, V, iter,
                       ctr3, iter_dev, part_acc, part_eta, part_has, ticket, status, sh, 0u,
                       (double*)nullptr);
+}
+
+cudaError_t launch_merge_shield(const DevParams& P, int nb, const float* blk_min,
+                                BlockPartials part, float* V, uint32_t iter, uint32_t* iter_dev,
+                                unsigned* status, const float4* rec, const int* seg0, float* x0,
+                                float* V_safe, int n_repair, int ck, double* merit_out,
+                                uint32_t ctr3_dist, cudaStream_t st) {
+    const size_t smem = rec_table_bytes(P.n_track) + (size_t)P.T * 16 +
+                        (size_t)(P.T + 2) * NFIELD * 4;
+    const ShieldTail sh{rec, seg0, x0, V_safe, n_repair, ck, merit_out, ctr3_dist};
+    auto kern = (P.tyre15 && P.steer_small) ? mppi_merge_shield_kernel<true>
+                                             : mppi_merge_shield_kernel<false>;
+    cudaError_t e = ensure_smem((const void*)kern, smem);
+    if (e != cudaSuccess) return e;
+    return launch_pdl(kern, 1, UPD_BLK, smem, st, P, nb, blk_min, part, V, iter, iter_dev, status,
+                      sh);
 }
 
 cudaError_t launch_debug_elementary(int fn, int n, const float* a, const float* b, float* out,

@@ -37,43 +37,6 @@ __device__ __forceinline__ State2 broadcast(const State& s) {
     return x;
 }
 
-// atan2 of both halves: octant reduction and the degree-8 minimax polynomial
-// of atan2_poly (ATAN_P0..8).  x = y = 0 gives 0 (mx is kept at or above the smallest
-// normal float, so a = 0 there).
-__device__ __forceinline__ f2 atan2_2(f2 y, f2 x) {
-    const float ax0 = fabsf(x.x), ay0 = fabsf(y.x), ax1 = fabsf(x.y), ay1 = fabsf(y.y);
-    const f2 mn = make_float2(fminf(ax0, ay0), fminf(ax1, ay1));
-    const float mx0 = fmaxf(fmaxf(ax0, ay0), 1.17549435e-38f);
-    const float mx1 = fmaxf(fmaxf(ax1, ay1), 1.17549435e-38f);
-    const f2 a = mul(mn, make_float2(rcp_approx(mx0), rcp_approx(mx1)));
-    const f2 s = mul(a, a);
-    f2 p = fma(bc(ATAN_P8), s, bc(ATAN_P7));
-    p = fma(p, s, bc(ATAN_P6));
-    p = fma(p, s, bc(ATAN_P5));
-    p = fma(p, s, bc(ATAN_P4));
-    p = fma(p, s, bc(ATAN_P3));
-    p = fma(p, s, bc(ATAN_P2));
-    p = fma(p, s, bc(ATAN_P1));
-    p = fma(p, s, bc(ATAN_P0));
-    f2 r = mul(a, p);
-    const f2 r1 = fma(r, bc(-1.0f), bc(1.57079632679f));
-    r.x = (ay0 > ax0) ? r1.x : r.x;
-    r.y = (ay1 > ax1) ? r1.y : r.y;
-    const f2 r2 = fma(r, bc(-1.0f), bc(3.14159265359f));
-    r.x = (x.x < 0.0f) ? r2.x : r.x;
-    r.y = (x.y < 0.0f) ? r2.y : r.y;
-    return make_float2(copysignf(r.x, y.x), copysignf(r.y, y.y));
-}
-
-// sin(1.5 atan z) of both halves (half-angle identities, as tyre15).
-__device__ __forceinline__ f2 tyre15_2(f2 z) {
-    const f2 q = fma(z, z, bc(1.0f));
-    const f2 c = make_float2(rsqrtf(q.x), rsqrtf(q.y));
-    const f2 u = fma(bc(0.5f), c, bc(0.5f));
-    const f2 ru = make_float2(rsqrtf(u.x), rsqrtf(u.y));
-    return mul(mul(mul(z, c), ru), fma(bc(0.5f), c, u));
-}
-
 // sin and cos of |x| <= 1/2 by Taylor series to x^7 / x^8: the remainders are
 // below 0.5^9 / 9! = 5.4e-9 and 0.5^10 / 10! = 2.7e-10, under half an ulp of
 // the results (|sin x| >= 0.96 |x|, cos x >= 0.87).

@@ -149,22 +149,27 @@ __device__ __forceinline__ bool spin_until_geq(const volatile int* flag, int tar
 }
 
 // The follower warp: positions pos[t - 1] = (X, Y) of x_t, t = 1..N, ready when
-// *prog >= t (published in chunks of MERIT_PUB).  For a chunk, lane l
-// evaluates segment s - 1 + l of the window around the segment s where the
-// chunk starts, for every position of the chunk at once; the descent walks of
-// the tracked projection are then read off ballots of "the next segment is strictly closer"
-// position after position: the walk from window lane L moves forward to the
-// first lane above L whose successor is not closer, and stays at L when L + 1
-// is not closer and L - 1 is not closer either.  This decode is one dependent
-// chain per chunk, unrolled and free of calls so that it stays in registers.
-// A backward step or a walk that reaches the window's last lane is finished
-// one segment at a time by lane 0 (walk_seq_rec), for that position and the
-// rest of the chunk.
+// *prog >= t (published in chunks of MERIT_PUB).  For a chunk, lane l holds the
+// segment s - 1 + l of the window around the segment s where the chunk starts
+// and evaluates its squared distance to every position of the chunk; the
+// descent walks of the tracked projection are then read off ballots of "the
+// next segment is strictly closer", position after position: the walk from
+// window lane L moves forward to the first lane above L whose successor is not
+// closer, and stays at L when L + 1 is not closer and L - 1 is not closer
+// either.  The decode is one branch-free dependent chain per chunk, unrolled
+// so that it stays in registers.  A backward step or a walk that reaches the
+// window's last lane is finished one segment at a time by lane 0
+// (walk_seq_rec), for that position and the rest of the chunk.
+// The DCBF terms are summed as forward_cost sums them: float32 over blocks of
+// 16 steps, then each block's sum added to a float64 total in order.  With
+// chunks of 8 starting at t = 1 a block ends only at a chunk's last position,
+// so the float64 add runs once per block, after that chunk.
 // Returns J on every lane.
 __device__ __forceinline__ double merit_follow_warp(const DevParams& P, const float4* rec,
                                                     const State& x0, int s0, int N,
                                                     const float2* pos, volatile int* prog,
                                                     unsigned* status) {
+    static_assert(MERIT_PUB == 8, "the float64 adds assume chunks of 8 steps starting at t = 1");
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, n = P.n_track;
     int s = s0;
@@ -185,49 +190,37 @@ __device__ __forceinline__ double merit_follow_warp(const DevParams& P, const fl
         int j = s - 1 + lane;
         if (j < 0) j += n;
         while (j >= n) j -= n;
-        float2 xy[MERIT_PUB];
+        // this lane's segment j (first half of record j + 1), loaded once per chunk
+        const float4 nA = rec[3 * (j + 1)], nD = rec[3 * (j + 1) + 1], Dn = rec[3 * (j + 1) + 2];
         float dq[MERIT_PUB];
         unsigned fw[MERIT_PUB], bw[MERIT_PUB];
 #pragma unroll
         for (int q = 0; q < MERIT_PUB; ++q) {
-            xy[q] = pos[t0 - 1 + min(q, nq - 1)];
-            dq[q] = rec_d2_seg(rec, j, xy[q].x, xy[q].y);
+            const float2 xy = pos[t0 - 1 + min(q, nq - 1)];
+            const float ex = xy.x + nA.x, ey = xy.y + nA.z;   // rec_d2_seg's arithmetic
+            const float tt = __saturatef(fmaf(ex, Dn.x, ey * Dn.z));
+            const float rx = fmaf(tt, nD.x, ex), ry = fmaf(tt, nD.z, ey);
+            dq[q] = fmaf(rx, rx, ry * ry);
             const float dn = __shfl_down_sync(FULL, dq[q], 1);
             fw[q] = __ballot_sync(FULL, lane < 31 && dn < dq[q]);   // bit l: d(l+1) < d(l)
             bw[q] = __ballot_sync(FULL, lane < 31 && dq[q] < dn);   // bit l: d(l) < d(l+1)
         }
-        // DCBF term of x_t, in order (the sum of forward_cost)
-        auto take = [&](float dd, int t) {
-            const float h = P.w2 - dd;
-            const float a = cbf_arg(P, h_prev, h);
-            Jf = (a > 0.0f) ? fmaf(P.C_cbf, a, Jf) : Jf;
-            h_prev = h;
-            if ((t & 15) == 0) {
-                J += (double)Jf;
-                Jf = 0.0f;
-            }
-        };
-        // fast path, fully unrolled and without calls: the positions whose walk
-        // stays inside the window; qs = the first one that does not
+        // fast path: the positions whose walk stays inside the window, in order, up
+        // to qs = the first one that does not; each position's DCBF term of Eq. 17
+        // (C max(a, 0) equals forward_cost's conditional term exactly)
         int L = 1, qs = nq;
 #pragma unroll
         for (int q = 0; q < MERIT_PUB; ++q) {
-            if (q < qs) {
-                bool out;
-                int Ln = L;
-                if ((fw[q] >> L) & 1u) {
-                    Ln = __ffs(~fw[q] & ~((2u << L) - 1u)) - 1;
-                    out = Ln >= 31;
-                } else {
-                    out = ((bw[q] >> (L - 1)) & 1u) != 0u;
-                }
-                if (out) {
-                    qs = q;
-                } else {
-                    L = Ln;
-                    take(__shfl_sync(FULL, dq[q], L), t0 + q);
-                }
-            }
+            const bool fwd = (fw[q] >> L) & 1u;
+            const int Lf = __ffs(~fw[q] & ~((2u << L) - 1u)) - 1;
+            const bool out = fwd ? (Lf < 0 || Lf >= 31) : (((bw[q] >> (L - 1)) & 1u) != 0u);
+            const bool go = q < qs && !out;
+            qs = (q < qs && out) ? q : qs;
+            L = (go && fwd) ? Lf : L;
+            const float h = P.w2 - __shfl_sync(FULL, dq[q], L);
+            const float a = cbf_arg(P, h_prev, h);
+            Jf = go ? fmaf(P.C_cbf, fmaxf(a, 0.0f), Jf) : Jf;
+            h_prev = go ? h : h_prev;
         }
         int scur = s - 1 + L;
         if (scur < 0) scur += n;
@@ -240,9 +233,16 @@ __device__ __forceinline__ double merit_follow_warp(const DevParams& P, const fl
             float dr = 0.0f;
             if (lane == 0) sr = walk_seq_rec(rec, n, scur, p.x, p.y, dr);
             scur = __shfl_sync(FULL, sr, 0);
-            take(__shfl_sync(FULL, dr, 0), t0 + q);
+            const float h = P.w2 - __shfl_sync(FULL, dr, 0);
+            const float a = cbf_arg(P, h_prev, h);
+            Jf = fmaf(P.C_cbf, fmaxf(a, 0.0f), Jf);
+            h_prev = h;
         }
         s = scur;
+        if (nq == MERIT_PUB && ((t1 & 15) == 0)) {   // a block of 16 steps ends here
+            J += (double)Jf;
+            Jf = 0.0f;
+        }
     }
     J += (double)Jf;
     return timed_out ? 0.0 : J;
@@ -326,11 +326,14 @@ __device__ __forceinline__ void merit_split3(const DevParams& P, const float4* r
     } else if (tid == 32) {
         float X = x0.X, Y = x0.Y, psi = x0.psi, cp = x0.cp, sp = x0.sp;
         for (int t = 0; t < N; ++t) {
-            if (!spin_until_geq(prog, t + 1)) {
-                atomicOr(status, SMPPI_DEV_TIMEOUT);
-                break;
+            // the velocities arrive MERIT_PUB at a time: wait at the start of each chunk
+            if (t % MERIT_PUB == 0) {
+                if (!spin_until_geq(prog, min(N, t + MERIT_PUB))) {
+                    atomicOr(status, SMPPI_DEV_TIMEOUT);
+                    break;
+                }
+                __threadfence_block();
             }
-            __threadfence_block();
             const float4 v = vel[t];
             pose_step_fast(P, v.x, v.y, v.z, X, Y, psi, cp, sp);
             pos[t] = make_float2(X, Y);

@@ -1,8 +1,7 @@
 """The atan polynomial of the rollout kernels is reproducible: the minimax fit
 (csrc/atan_minimax.py, Remez exchange for the absolute error of
-atan(a) = a p(a^2) on [0, 1]) regenerates the float32 literals of both the
-scalar (device.cuh) and the packed (rollout2.cuh, through the same constants)
-atan2, its error equioscillates as a minimax error must (Chebyshev's
+atan(a) = a p(a^2) on [0, 1]) regenerates the float32 literals that the
+scalar and the packed atan2 (device.cuh) share, its error equioscillates as a minimax error must (Chebyshev's
 alternation theorem: at least degree + 2 extrema of equal size and
 alternating sign), and the float32 coefficients stay within 2.2e-8."""
 import importlib.util
@@ -35,9 +34,12 @@ def test_fit_regenerates_the_kernel_coefficients():
     lit = _literals()
     assert len(lit) == 9
     assert A.float32_coefficients() == [float(np.float32(v)) for v in lit]
-    # the packed atan2 uses the same constants, not literals of its own
-    packed = open(os.path.join(CSRC, "rollout2.cuh")).read()
-    assert "ATAN_P8" in packed and "2.588483738e-03" not in packed
+    # the scalar and the packed atan2 use these constants; no source holds a copy
+    dev = open(os.path.join(CSRC, "device.cuh")).read()
+    assert dev.count("ATAN_P8") == 3          # defined, used by atan2_poly and atan2_2
+    for f in os.listdir(CSRC):
+        if f.endswith((".cu", ".cuh")):
+            assert open(os.path.join(CSRC, f)).read().count("%.9e" % lit[0]) == (f == "device.cuh")
 
 
 def test_fit_is_minimax_and_accurate():

@@ -7,8 +7,9 @@ granted per warp in multiples of 8 per thread, so up to 168 registers three
 only two (a 170-register build ran 6 % slower at K = 262144).  A change that
 raises the count or makes the kernel spill is a performance regression even
 when every parity test passes, so the counts are held at what the kernels use
-now: the packed Cartesian kernel at <= 160, the packed curvilinear kernel at
-<= 104, neither spilling.
+now: the packed Cartesian kernel at <= 160, its variant that also writes the
+block partials of the update at <= 168 (three blocks per SM still fit), the
+packed curvilinear kernel at <= 104, none spilling.
 """
 import os
 import re
@@ -21,7 +22,8 @@ from paper_2302_11719_gb300 import build as B
 
 BUDGET = {
     # (source, mangled-name fragment): max registers
-    ("rollout.cu", "mppi_rollout2_kernelILb0E"): 160,
+    ("rollout.cu", "mppi_rollout2_kernelILb0ELb0E"): 160,
+    ("rollout.cu", "mppi_rollout2_kernelILb0ELb1E"): 168,
     ("curv.cu", "mppi_rollout_curv_kernelILb0E"): 104,
 }
 
