@@ -418,7 +418,11 @@ smppi_status smppi_debug_noise(smppi_handle* h, uint32_t iter, uint32_t instance
  *   fn 3: sin(1.5 atan a), packed        ref sinf(1.5f atanf(a))
  *   fn 4 / 5: sin / cos of a, |a| <= 1/2, scalar   ref sinf / cosf
  *   fn 6 / 7: sin / cos of a, |a| <= 1/2, packed   ref sinf / cosf
- * (b is read by fn 0 and 1 only but must not be NULL).  Packed forms evaluate
+ *   fn 8: atan2(a, b), packed pair form of the one-thread recurrences
+ *         (Estrin's scheme, octant folded into one FMA)   ref atan2f(a, b)
+ *   fn 9: 1 / sqrt(a) without the denormal path, as the tyre and
+ *         Box-Muller use it (arguments never denormal)     ref rsqrtf(a)
+ * (b is read by fn 0, 1 and 8 only but must not be NULL).  Packed forms evaluate
  * elements 2i and 2i + 1 as the two halves of one instruction.  All arrays
  * DEVICE, float32; asynchronous on cuda_stream; SMPPI_ERR_ARG for another fn,
  * n < 0 or a NULL array.

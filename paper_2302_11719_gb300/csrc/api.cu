@@ -734,7 +734,7 @@ smppi_status smppi_shield_loop(smppi_handle* h, float* x0, float* V, float* V_sa
 
 smppi_status smppi_debug_elementary(int fn, int n, const float* a, const float* b, float* out,
                                     float* ref, void* cuda_stream) {
-    if (fn < 0 || fn > 7) return fail(nullptr, SMPPI_ERR_ARG, "fn must be in [0, 7]");
+    if (fn < 0 || fn > 9) return fail(nullptr, SMPPI_ERR_ARG, "fn must be in [0, 9]");
     if (n < 0) return fail(nullptr, SMPPI_ERR_ARG, "n must be >= 0");
     if (n == 0) return SMPPI_OK;
     if (!a || !b || !out || !ref) return fail(nullptr, SMPPI_ERR_ARG, "NULL array");

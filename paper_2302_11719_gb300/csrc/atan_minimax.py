@@ -1,5 +1,5 @@
 """Minimax fit of the polynomial behind the kernels' atan2 (device.cuh
-atan2_poly, rollout2.cuh atan2_2).
+atan2_poly, atan2_2 and atan2_2_lat).
 
 After the octant reduction the kernels need atan(a) for a in [0, 1]; they
 evaluate it as a p(a^2) with p of degree 8.  This script finds p by the Remez
@@ -10,8 +10,8 @@ weight sqrt(s).
 
     python atan_minimax.py      # prints the nine coefficients, highest first
 
-The printed values, rounded to float32, are the literals in the kernels;
-tests/test_atan_fit.py regenerates them and checks both copies.
+The printed values, rounded to float32, are the ATAN_P0..8 constants of
+device.cuh (the one copy); tests/test_atan_fit.py regenerates and compares them.
 """
 from __future__ import annotations
 

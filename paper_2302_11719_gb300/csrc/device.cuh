@@ -95,10 +95,21 @@ __device__ __forceinline__ float u01(uint32_t x) {
     return fmaf(__uint2float_rn(x >> 9), 0x1p-23f, 0x1p-24f);
 }
 
-// Box-Muller pair (library logf and sincospif; r = sqrt(q) as q rsqrt(q), q > 0).
+// 1 / sqrt(x) by the SFU approximation without the denormal path
+// (rsqrt.approx.ftz.f32), for arguments that cannot be denormal: for a normal
+// x > 0 it is rsqrtf(x) bit for bit (tests/test_gpu_elementary.py checks every
+// float in [1/2, 2) and samples of every binade), at about half the latency.
+__device__ __forceinline__ float rsqrt_n(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Box-Muller pair (library logf and sincospif; r = sqrt(q) as q rsqrt(q), with
+// q = -2 ln u in [1.2e-7, 33.3] for the u of u01).
 __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b) {
     const float q = -2.0f * logf(u01(a));
-    const float r = q * rsqrtf(q);
+    const float r = q * rsqrt_n(q);
     float s, c;
     sincospif(2.0f * u01(b), &s, &c);
     return make_float2(r * c, r * s);
@@ -213,32 +224,80 @@ __device__ __forceinline__ f2 atan2_2(f2 y, f2 x) {
     return make_float2(copysignf(r.x, y.x), copysignf(r.y, y.y));
 }
 
-// sin(1.5 atan z) of both halves (half-angle identities, as tyre15).
-__device__ __forceinline__ f2 tyre15_2(f2 z) {
+// atan2 of both halves for one-thread recurrences, where the dependent chain
+// rather than the instruction count sets the time: the polynomial of atan2_2
+// by Estrin's scheme (depth 4 instead of 8, two more products), and the
+// octant's fix-up folded into one FMA after it, atan2(y, x) = O + (S a) p(a^2)
+// with the offset O in {0, pi/2, pi} and the sign S = +-1 (both carrying the
+// sign of y) picked from the comparisons while the reciprocal is in flight.
+// One rounding follows the polynomial (atan2_2 has up to three there).
+__device__ __forceinline__ f2 atan2_2_lat(f2 y, f2 x) {
+    const float ax0 = fabsf(x.x), ay0 = fabsf(y.x), ax1 = fabsf(x.y), ay1 = fabsf(y.y);
+    const float mn0 = fminf(ax0, ay0), mn1 = fminf(ax1, ay1);
+    const float mx0 = fmaxf(fmaxf(ax0, ay0), 1.17549435e-38f);
+    const float mx1 = fmaxf(fmaxf(ax1, ay1), 1.17549435e-38f);
+    const f2 rc = make_float2(rcp_approx(mx0), rcp_approx(mx1));
+    // ay > ax reflects the result about pi/4 (pi/2 - r), x < 0 about pi/2 (pi - r)
+    const bool sw0 = ay0 > ax0, sw1 = ay1 > ax1, ng0 = x.x < 0.0f, ng1 = x.y < 0.0f;
+    const unsigned sy0 = __float_as_uint(y.x) & 0x80000000u;
+    const unsigned sy1 = __float_as_uint(y.y) & 0x80000000u;
+    const float o0 = sw0 ? 1.57079632679f : (ng0 ? 3.14159265359f : 0.0f);
+    const float o1 = sw1 ? 1.57079632679f : (ng1 ? 3.14159265359f : 0.0f);
+    const f2 O = make_float2(__uint_as_float(__float_as_uint(o0) | sy0),
+                             __uint_as_float(__float_as_uint(o1) | sy1));
+    const f2 mS = make_float2(
+        __uint_as_float(__float_as_uint(mn0) ^ sy0 ^ (sw0 != ng0 ? 0x80000000u : 0u)),
+        __uint_as_float(__float_as_uint(mn1) ^ sy1 ^ (sw1 != ng1 ? 0x80000000u : 0u)));
+    const f2 a = mul(make_float2(mn0, mn1), rc);
+    const f2 aS = mul(mS, rc);
+    const f2 s = mul(a, a);
+    const f2 s2 = mul(s, s), s4 = mul(s2, s2);
+    const f2 q0 = fma(bc(ATAN_P1), s, bc(ATAN_P0));
+    const f2 q1 = fma(bc(ATAN_P3), s, bc(ATAN_P2));
+    const f2 q2 = fma(bc(ATAN_P5), s, bc(ATAN_P4));
+    const f2 q3 = fma(bc(ATAN_P7), s, bc(ATAN_P6));
+    const f2 lo4 = fma(q1, s2, q0);                             // P0 + .. + P3 s^3
+    const f2 hi4 = fma(fma(bc(ATAN_P8), s2, q3), s2, q2);      // P4 + .. + P8 s^4
+    return fma(aS, fma(hi4, s4, lo4), O);
+}
+
+// sin(1.5 atan z) of both halves (half-angle identities, as tyre15) as the
+// product w ru, with t = atan z, c = cos t = 1 / sqrt(1 + z^2),
+// u = cos^2(t/2) = (1 + c) / 2, ru = 1 / cos(t/2) and w = sin t (c/2 + u):
+// sin t cos(t/2) + cos t sin(t/2) = (sin t / cos(t/2)) (cos^2(t/2) + cos t / 2).
+// A caller can scale w while the second reciprocal square root is in flight.
+// (q = 1 + z^2 >= 1 and u in [1/2, 1] are never denormal: rsqrt_n.)
+__device__ __forceinline__ void tyre15_2_parts(f2 z, f2& w, f2& ru) {
     const f2 q = fma(z, z, bc(1.0f));
-    const f2 c = make_float2(rsqrtf(q.x), rsqrtf(q.y));
+    const f2 c = make_float2(rsqrt_n(q.x), rsqrt_n(q.y));
     const f2 u = fma(bc(0.5f), c, bc(0.5f));
-    const f2 ru = make_float2(rsqrtf(u.x), rsqrtf(u.y));
-    return mul(mul(mul(z, c), ru), fma(bc(0.5f), c, u));
+    ru = make_float2(rsqrt_n(u.x), rsqrt_n(u.y));
+    w = mul(mul(z, c), fma(bc(0.5f), c, u));
+}
+
+__device__ __forceinline__ f2 tyre15_2(f2 z) {
+    f2 w, ru;
+    tyre15_2_parts(z, w, ru);
+    return mul(w, ru);
 }
 
 }  // namespace x2
 
 // sin(1.5 atan z) by the half-angle identities (no branch).
 __device__ __forceinline__ float tyre15(float z) {
-    const float c = rsqrtf(fmaf(z, z, 1.0f));        // cos t, t = atan z
+    const float c = rsqrt_n(fmaf(z, z, 1.0f));       // cos t, t = atan z
     const float u = fmaf(0.5f, c, 0.5f);             // cos^2(t/2)
-    return z * c * rsqrtf(u) * fmaf(0.5f, c, u);     // sin t cos(t/2) + cos t sin(t/2)
+    return z * c * rsqrt_n(u) * fmaf(0.5f, c, u);    // sin t cos(t/2) + cos t sin(t/2)
 }
 
 // Lateral tyre force shape sin(Ct atan(z)) and, if dz != nullptr, its
 // derivative Ct cos(Ct atan z) / (1 + z^2).
 __device__ __forceinline__ float tyre_shape(const DevParams& P, float z, float* dz) {
     if (P.tyre15) {
-        const float c = rsqrtf(fmaf(z, z, 1.0f));    // cos t, t = atan z
+        const float c = rsqrt_n(fmaf(z, z, 1.0f));   // cos t, t = atan z
         const float s = z * c;                       // sin t
         const float u = fmaf(0.5f, c, 0.5f);         // cos^2(t/2)
-        const float ru = rsqrtf(u);                  // 1 / cos(t/2)
+        const float ru = rsqrt_n(u);                 // 1 / cos(t/2)
         if (dz) *dz = 1.5f * ru * fmaf(c, u, -0.5f * s * s) * c * c;   // 1.5 cos(1.5 t) cos^2 t
         return s * ru * fmaf(0.5f, c, u);            // sin t cos(t/2) + cos t sin(t/2)
     }
@@ -258,24 +317,44 @@ __device__ __forceinline__ float tyre_shape(const DevParams& P, float z, float* 
 // the velocities of the same step) so that the repair's merit pass can run the
 // two recurrences on different threads; explicit fmaf fixes the rounding.
 //
-// Velocity part: (v_x, v_y, r) <- Euler update at steer d (sd, cd = sin, cos d)
-// with rear force Fx.  The front and rear axle (slip angle, lateral force) run
-// as the two halves of packed instructions (atan2_2, tyre15_2 above): this
-// step is the dependent chain of every one-thread recurrence (the merit pass,
-// the repair's forward and adjoint sweeps), and pairing the axles shortens it
-// from about 350 to 250 cycles.
+// Velocity part: (v_x, v_y, r) <- Euler update at steer d with throttle a.
+// The per-step factors that depend on the control alone (vel_coef) are formed
+// apart from the recurrence; the front and rear axle (slip angle, lateral force)
+// run as the two halves of packed instructions (atan2_2_lat, tyre15_2_parts),
+// and the lateral forces Fz w ru enter the update as (dt-scaled w) x ru, so
+// that two FMAs follow the last reciprocal square root.  This step is the
+// dependent chain of every one-thread recurrence (the merit pass, the repair's
+// forward and adjoint sweeps).
+struct VelCoef {
+    float Bd;   // B d
+    float kx;   // -dt Fzf sin(d) / m
+    float ky;   //  dt Fzf cos(d) / m
+    float kr;   //  dt lf Fzf cos(d) / Iz
+    float bx;   //  dt fx_gain a / m
+};
+
+__device__ __forceinline__ VelCoef vel_coef(const DevParams& P, float d, float sd, float cd,
+                                            float a) {
+    const float gm = P.dt * P.Fzf * P.m_inv, gi = P.dt * P.lf * P.Fzf * P.Iz_inv;
+    return VelCoef{P.B * d, -gm * sd, gm * cd, gi * cd, (P.dt * P.fx_gain * P.m_inv) * a};
+}
+
 __device__ __forceinline__ void vel_step_fast(const DevParams& P, float& vx, float& vy, float& r,
-                                              float d, float sd, float cd, float Fx) {
-    const float2 b = x2::atan2_2(make_float2(fmaf(P.lf, r, vy), fmaf(-P.lr, r, vy)),
-                                 make_float2(vx, vx));
-    const float2 t = x2::tyre15_2(make_float2(P.B * (d - b.x), -P.B * b.y));
-    const float Fyf = P.Fzf * t.x, Fyr = P.Fzr * t.y;
-    const float dvx = fmaf(fmaf(-Fyf, sd, Fx), P.m_inv, vy * r);
-    const float dvy = fmaf(fmaf(Fyf, cd, Fyr), P.m_inv, -(vx * r));
-    const float dr = fmaf(P.lf * Fyf, cd, -(P.lr * Fyr)) * P.Iz_inv;
-    vx = fmaf(P.dt, dvx, vx);
-    vy = fmaf(P.dt, dvy, vy);
-    r = fmaf(P.dt, dr, r);
+                                              const VelCoef& k) {
+    const float2 b = x2::atan2_2_lat(make_float2(fmaf(P.lf, r, vy), fmaf(-P.lr, r, vy)),
+                                     make_float2(vx, vx));
+    float2 w, ru;
+    x2::tyre15_2_parts(make_float2(fmaf(-P.B, b.x, k.Bd), -P.B * b.y), w, ru);
+    const float gyr = P.dt * P.Fzr * P.m_inv, grr = -(P.dt * P.lr * P.Fzr * P.Iz_inv);
+    // dv_x = (Fx - Fyf sin d) / m + v_y r, dv_y = (Fyf cos d + Fyr) / m - v_x r,
+    // dr = (lf Fyf cos d - lr Fyr) / Iz, with Fy = Fz w ru
+    // __fadd_rn: the product in bx is never contracted into this add, so a step
+    // with vel_coef inline rounds as one with the factors read from memory
+    const float bxv = fmaf(P.dt * vy, r, __fadd_rn(vx, k.bx));
+    const float byv = fmaf(-(P.dt * vx), r, vy);
+    vx = fmaf(w.x * k.kx, ru.x, bxv);
+    vy = fmaf(w.x * k.ky, ru.x, fmaf(w.y * gyr, ru.y, byv));
+    r = fmaf(w.x * k.kr, ru.x, fmaf(w.y * grr, ru.y, r));
 }
 
 // Pose part, from the velocities (vx, vy, r) of the same step: (X, Y) by Euler,
@@ -304,7 +383,7 @@ __device__ __forceinline__ void model_step(const DevParams& P, State& x, float d
         float sd, cd;
         sincos_half(d, &sd, &cd);
         const float vx = x.vx, vy = x.vy, r = x.r;
-        vel_step_fast(P, x.vx, x.vy, x.r, d, sd, cd, P.fx_gain * a);
+        vel_step_fast(P, x.vx, x.vy, x.r, vel_coef(P, d, sd, cd, a));
         pose_step_fast(P, vx, vy, r, x.X, x.Y, x.psi, x.cp, x.sp);
         return;
     }
@@ -362,7 +441,7 @@ __device__ __forceinline__ void model_step_curv(const DevParams& P, const float*
     float sd, cd;
     sincos_half(d, &sd, &cd);
     const float vx = x.vx, vy = x.vy, r = x.r;
-    vel_step_fast(P, x.vx, x.vy, x.r, d, sd, cd, P.fx_gain * a);
+    vel_step_fast(P, x.vx, x.vy, x.r, vel_coef(P, d, sd, cd, a));
     const float k = kappa_at(P, kt, x.X);
     const float den = fmaxf(fmaf(-k, x.Y, 1.0f), 0.1f);
     const float sdot = __fdiv_rn(fmaf(vx, x.cp, -(vy * x.sp)), den);

@@ -233,9 +233,13 @@ __device__ __forceinline__ void block_partial(const DevParams& P, float m_b, flo
 
 // Launch 1, packed form: thread t of block b steps rollouts 2 b BLK + t and
 // 2 b BLK + BLK + t together (rollout2.cuh).  The segment-pair table arrives
-// by one bulk copy; V is laid out as broadcast pairs.
-template <bool DUMP, bool PART>
-__global__ void __launch_bounds__(ROLL2_BLK, 2) mppi_rollout2_kernel(
+// by one bulk copy; V is laid out as broadcast pairs.  Built for MINB = 2 and
+// 3 resident blocks per SM: a grid that fits in one wave at two blocks per SM
+// runs the MINB = 2 build (the compiler keeps more values in registers: 4 %
+// faster at K = 65536), a larger one the MINB = 3 build (<= 168 registers, a
+// third block per SM: 1 % faster at K = 262144 than MINB = 2).
+template <bool DUMP, bool PART, int MINB>
+__global__ void __launch_bounds__(ROLL2_BLK, MINB) mppi_rollout2_kernel(
     DevParams P, const float* __restrict__ x0g, const float* __restrict__ Vg,
     const float4* __restrict__ recg, uint32_t iter, uint32_t ctr3,
     const uint32_t* __restrict__ iter_dev, float* __restrict__ S_out, float* __restrict__ traj,
@@ -783,15 +787,15 @@ __global__ void debug_noise_kernel(DevParams P, uint32_t iter, uint32_t ctr3, in
 }
 
 // The library's hand-written elementary functions on given arguments (test
-// access).  Packed forms (fn 1, 3, 6, 7) take elements 2i and 2i + 1 as the two
-// halves of one register pair.  ref receives CUDA's own function of the same
-// arguments.
+// access).  Packed forms (fn 1, 3, 6, 7, 8) take elements 2i and 2i + 1 as the
+// two halves of one register pair.  ref receives CUDA's own function of the
+// same arguments.
 __global__ void debug_elementary_kernel(int fn, int n, const float* __restrict__ a,
                                         const float* __restrict__ b, float* __restrict__ out,
                                         float* __restrict__ ref) {
     using namespace x2;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool packed = fn == 1 || fn == 3 || fn == 6 || fn == 7;
+    const bool packed = fn == 1 || fn == 3 || (fn >= 6 && fn <= 8);
     const int i0 = packed ? 2 * i : i;
     if (i0 >= n) return;
     const int i1 = (packed && i0 + 1 < n) ? i0 + 1 : i0;
@@ -805,7 +809,9 @@ __global__ void debug_elementary_kernel(int fn, int n, const float* __restrict__
         case 4: { float sn, cs; sincos_half(A.x, &sn, &cs); o.x = sn; r.x = sinf(A.x); } break;
         case 5: { float sn, cs; sincos_half(A.x, &sn, &cs); o.x = cs; r.x = cosf(A.x); } break;
         case 6: { f2 sn, cs; sincos_half2(A, sn, cs); o = sn; r = make_float2(sinf(A.x), sinf(A.y)); } break;
-        default: { f2 sn, cs; sincos_half2(A, sn, cs); o = cs; r = make_float2(cosf(A.x), cosf(A.y)); } break;
+        case 7: { f2 sn, cs; sincos_half2(A, sn, cs); o = cs; r = make_float2(cosf(A.x), cosf(A.y)); } break;
+        case 8: o = atan2_2_lat(A, B); r = make_float2(atan2f(A.x, B.x), atan2f(A.y, B.y)); break;
+        default: o.x = rsqrt_n(A.x); r.x = rsqrtf(A.x); break;
     }
     out[i0] = o.x;
     ref[i0] = r.x;
@@ -889,9 +895,9 @@ cudaError_t launch_rec_table(const float* track_xy, int n, float4* rec, cudaStre
     return cudaGetLastError();
 }
 
-int update_grid(int K) {
-    // SM count of the current device, cached per device ordinal (every thread
-    // that fills an entry writes the same value)
+// SM count of the current device, cached per device ordinal (every thread
+// that fills an entry writes the same value).
+static int device_sms() {
     constexpr int MAX_DEV = 64;
     static std::atomic<int> sms_of[MAX_DEV];
     int dev = 0;
@@ -903,6 +909,11 @@ int update_grid(int K) {
             sms = 1;
         if (dev < MAX_DEV) sms_of[dev].store(sms, std::memory_order_relaxed);
     }
+    return sms;
+}
+
+int update_grid(int K) {
+    const int sms = device_sms();
     const int by_k = (K + UPD_BLK - 1) / UPD_BLK;
     int g = by_k < sms ? by_k : sms;
     return g < UPD_BLK ? g : UPD_BLK;   // the merge lists at most UPD_BLK partials
@@ -921,9 +932,12 @@ cudaError_t launch_rollout(const DevParams& P, bool dump, const float* x0, const
         const bool with_part = part.acc != nullptr;
         size_t smem = rec_table_bytes(P.n_track) + (size_t)P.T * 2 * sizeof(float4);
         if (with_part) smem += (size_t)P.T * 2 * sizeof(float) + (size_t)ROLL2_BLK * 4 * sizeof(float);
-        auto kern = dump ? mppi_rollout2_kernel<true, false>
-                         : (with_part ? mppi_rollout2_kernel<false, true>
-                                      : mppi_rollout2_kernel<false, false>);
+        const bool one_wave = rollout_blocks(P) <= 2 * device_sms();
+        auto kern = dump ? mppi_rollout2_kernel<true, false, 3>
+                    : with_part ? (one_wave ? mppi_rollout2_kernel<false, true, 2>
+                                            : mppi_rollout2_kernel<false, true, 3>)
+                                : (one_wave ? mppi_rollout2_kernel<false, false, 2>
+                                            : mppi_rollout2_kernel<false, false, 3>);
         cudaError_t e = ensure_smem((const void*)kern, smem);
         if (e != cudaSuccess) return e;
         return launch_pdl(kern, rollout_blocks(P), ROLL2_BLK, smem, st, P, x0, V, rec, iter, ctr3,
@@ -1004,7 +1018,7 @@ cudaError_t launch_merge_shield(const DevParams& P, int nb, const float* blk_min
 
 cudaError_t launch_debug_elementary(int fn, int n, const float* a, const float* b, float* out,
                                    float* ref, cudaStream_t st) {
-    const int items = (fn == 1 || fn == 3 || fn == 6 || fn == 7) ? (n + 1) / 2 : n;
+    const int items = (fn == 1 || fn == 3 || (fn >= 6 && fn <= 8)) ? (n + 1) / 2 : n;
     debug_elementary_kernel<<<(items + 255) / 256, 256, 0, st>>>(fn, n, a, b, out, ref);
     return cudaGetLastError();
 }

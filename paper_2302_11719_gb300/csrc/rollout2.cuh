@@ -117,7 +117,7 @@ __device__ __forceinline__ void box_muller2(uint32_t a1, uint32_t b1, uint32_t a
     const f2 u2 = fma(make_float2(__uint2float_rn(a2 >> 9), __uint2float_rn(b2 >> 9)),
                       bc(0x1p-23f), bc(0x1p-24f));
     const f2 q = mul(bc(-2.0f), make_float2(logf(u1.x), logf(u1.y)));
-    const f2 r = mul(q, make_float2(rsqrtf(q.x), rsqrtf(q.y)));
+    const f2 r = mul(q, make_float2(rsqrt_n(q.x), rsqrt_n(q.y)));
     f2 s, c;
     sincospif(2.0f * u2.x, &s.x, &c.x);
     sincospif(2.0f * u2.y, &s.y, &c.y);

@@ -285,21 +285,22 @@ __device__ __forceinline__ void merit_split(const DevParams& P, const float4* re
 }
 
 // Three warps for the C = 1.5 model: thread 0 runs the velocity recurrence
-// (tyre forces; the steer's sin / cos and the rear force of every step are
-// precomputed by the whole block), thread 32 the pose recurrence from the
-// published velocities, warp 2 the track walk from the published positions.
-// BLK >= 96; buf holds 40 N + 8 bytes; prog two counters.
+// (tyre forces; the control factors of every step, vel_coef, are precomputed
+// by the whole block), thread 32 the pose recurrence from the published
+// velocities, warp 2 the track walk from the published positions.
+// BLK >= 96; buf holds 44 N + 15 bytes; prog two counters.
 __device__ __forceinline__ void merit_split3(const DevParams& P, const float4* rec,
                                              const State& x0, int s0, int N, const float2* Vw,
                                              float* buf, volatile int* prog, double* out,
                                              volatile int* done, unsigned* status) {
     const int tid = threadIdx.x;
     // buf is only 8-byte aligned in some callers: round up to 16 bytes for the
-    // float4 rows (the tape scratch has 44 (T + 2) >= 40 N + 8 bytes)
+    // float4 rows (the tape scratch has 44 (T + 2) >= 44 N + 15 bytes)
     float4* ctl = reinterpret_cast<float4*>((reinterpret_cast<uintptr_t>(buf) + 15) &
-                                            ~uintptr_t(15));  // (d, sin d, cos d, Fx) of step t
+                                            ~uintptr_t(15));  // (Bd, kx, ky, kr) of step t
     float4* vel = ctl + N;                                    // (v_x, v_y, r) of x_t
     float2* pos = reinterpret_cast<float2*>(vel + N);         // (X, Y) of x_{t+1}
+    float* bx = reinterpret_cast<float*>(pos + N);            // bx of step t
     if (tid == 0) {
         prog[0] = 0;
         prog[1] = 0;
@@ -309,7 +310,9 @@ __device__ __forceinline__ void merit_split3(const DevParams& P, const float4* r
         const float2 u = clamp2(P, Vw[t]);
         float sd, cd;
         sincos_half(u.x, &sd, &cd);
-        ctl[t] = make_float4(u.x, sd, cd, P.fx_gain * u.y);
+        const VelCoef k = vel_coef(P, u.x, sd, cd, u.y);
+        ctl[t] = make_float4(k.Bd, k.kx, k.ky, k.kr);
+        bx[t] = k.bx;
     }
     __syncthreads();
     if (tid == 0) {
@@ -321,7 +324,7 @@ __device__ __forceinline__ void merit_split3(const DevParams& P, const float4* r
                 prog[0] = t + 1;
             }
             const float4 c = ctl[t];
-            vel_step_fast(P, vx, vy, r, c.x, c.y, c.z, c.w);
+            vel_step_fast(P, vx, vy, r, VelCoef{c.x, c.y, c.z, c.w, bx[t]});
         }
     } else if (tid == 32) {
         float X = x0.X, Y = x0.Y, psi = x0.psi, cp = x0.cp, sp = x0.sp;

@@ -1,7 +1,7 @@
 """The atan polynomial of the rollout kernels is reproducible: the minimax fit
 (csrc/atan_minimax.py, Remez exchange for the absolute error of
 atan(a) = a p(a^2) on [0, 1]) regenerates the float32 literals that the
-scalar and the packed atan2 (device.cuh) share, its error equioscillates as a minimax error must (Chebyshev's
+scalar and the packed atan2 forms (device.cuh) share, its error equioscillates as a minimax error must (Chebyshev's
 alternation theorem: at least degree + 2 extrema of equal size and
 alternating sign), and the float32 coefficients stay within 2.2e-8."""
 import importlib.util
@@ -34,9 +34,9 @@ def test_fit_regenerates_the_kernel_coefficients():
     lit = _literals()
     assert len(lit) == 9
     assert A.float32_coefficients() == [float(np.float32(v)) for v in lit]
-    # the scalar and the packed atan2 use these constants; no source holds a copy
+    # the scalar and the two packed atan2 use these constants; no source holds a copy
     dev = open(os.path.join(CSRC, "device.cuh")).read()
-    assert dev.count("ATAN_P8") == 3          # defined, used by atan2_poly and atan2_2
+    assert dev.count("ATAN_P8") == 4          # defined, used by atan2_poly, atan2_2, atan2_2_lat
     for f in os.listdir(CSRC):
         if f.endswith((".cu", ".cuh")):
             assert open(os.path.join(CSRC, f)).read().count("%.9e" % lit[0]) == (f == "device.cuh")

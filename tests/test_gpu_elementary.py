@@ -3,8 +3,9 @@ evaluated on the GPU through smppi_debug_elementary on dense grids of their
 domains, against float64 (numpy) and against CUDA's own functions of the same
 float32 arguments.  Errors are in ulps of the float32 result.
 
-  * atan2 (octant reduction + the minimax polynomial), scalar and packed form,
-    for finite arguments with max(|x|, |y|) in [2^-126, 2^126) and at the
+  * atan2 (octant reduction + the minimax polynomial), scalar and packed form
+    (Horner, and the one-thread recurrences' Estrin form with the octant folded
+    into one FMA), for finite arguments with max(|x|, |y|) in [2^-126, 2^126) and at the
     special points (0, 0), (+-0, x), (y, 0): within 4 ulp (3.8 measured: up to
     3 from the reciprocal and the polynomial, 0.7 from the float32 pi/2 of the
     octant fold);
@@ -71,7 +72,7 @@ def _atan2_args(rng):
     return np.concatenate(ys).astype(np.float32), np.concatenate(xs).astype(np.float32)
 
 
-@pytest.mark.parametrize("fn,name", [(0, "scalar"), (1, "packed")])
+@pytest.mark.parametrize("fn,name", [(0, "scalar"), (1, "packed"), (8, "packed, Estrin + folded octant")])
 def test_atan2(S, fn, name):
     y, x, out, ref = _run(S, fn, *_atan2_args(np.random.default_rng(1)))
     exact = np.arctan2(y.astype(np.float64), x.astype(np.float64))
@@ -111,3 +112,23 @@ def test_sincos_half(S, fn_s, fn_c, name):
           % (name, es.max(), ec.max(), _ulp_err(s_ref, np.sin(x64)).max(),
              _ulp_err(c_ref, np.cos(x64)).max()))
     assert es.max() <= 2.0 and ec.max() <= 2.0
+
+
+def test_rsqrt_without_denormal_path_is_rsqrtf(S):
+    """The tyre and Box-Muller take 1/sqrt of arguments that are never denormal
+    (1 + z^2, (1 + cos t)/2, -2 ln u >= 1.2e-7) by rsqrt.approx.ftz: bit for bit
+    rsqrtf on every float in [1/2, 2) (both mantissa phases of the square root)
+    and on samples of every normal binade, with the special values."""
+    grid = np.arange(np.float32(0.5).view(np.uint32), np.float32(2.0).view(np.uint32),
+                     dtype=np.uint32).view(np.float32)
+    rng = np.random.default_rng(5)
+    bits = (rng.integers(1, 254, 2000000, dtype=np.uint32) << 23) | \
+        rng.integers(0, 1 << 23, 2000000, dtype=np.uint32)
+    x = np.concatenate([grid, bits.view(np.float32),
+                        np.array([np.inf, 1.17549435e-38, 3.4028235e38], np.float32)])
+    _, _, out, ref = _run(S, 9, x)
+    same = out.view(np.uint32) == ref.view(np.uint32)
+    print("rsqrt without denormal path: %d of %d arguments bit-equal to rsqrtf"
+          % (int(same.sum()), x.size))
+    assert np.all(same)
+
