@@ -387,24 +387,68 @@ struct ShieldTail {
     uint32_t ctr3_dist;     // counter word of the disturbance
 };
 
+// x_{n+1} = f(x_n, clamp(v_0)) + w_n (Eq. 26), w_n on (v_y, r) from the Philox
+// counter (0, 0, iter, ctr3); xn gets (v_x, v_y, r, X, Y, psi).
+__device__ __forceinline__ void closed_loop_next(const DevParams& P, const State& x0, float2 v0,
+                                                 uint32_t iter, uint32_t ctr3, float* xn) {
+    State x = x0;
+    model_step(P, x, clampf(v0.x, P.umin0, P.umax0), clampf(v0.y, P.umin1, P.umax1));
+    const uint4 r = philox10(make_uint4(0u, 0u, iter, ctr3), P);
+    const float2 z = box_muller(r.x, r.y);
+    xn[0] = x.vx;
+    xn[1] = fmaf(P.dsig0, z.x, x.vy);
+    xn[2] = fmaf(P.dsig1, z.y, x.r);
+    xn[3] = x.X;
+    xn[4] = x.Y;
+    xn[5] = x.psi;
+}
+
+// The closed-loop work that does not wait for the merit of V+: V <- shift(V+),
+// V_safe <- V+ and the next state from v_0 = V+_0, all right unless the shield
+// then repairs V+ (shield_tail redoes V_safe and the state in that case).  Run
+// by an idle warp during the first merit pass.
+struct TailSide {
+    const DevParams* P;
+    const float2* Vplus;   // shared
+    float2* Vs_out;        // global
+    float2* V2;            // global
+    State x0;
+    uint32_t iter, ctr3;
+    float* xn;             // shared, 6 floats
+    __device__ void operator()(int lane) const {
+        const int T = P->T;
+        for (int t = lane; t < T; t += 32) {
+            Vs_out[t] = Vplus[t];
+            V2[t] = Vplus[t + 1 < T ? t + 1 : T - 1];   // warm start: shift(V+)
+        }
+        if (lane == 0) closed_loop_next(*P, x0, Vplus[0], iter, ctr3, xn);
+    }
+};
+
 // The safety shield on V+ (Alg. 1 with Armijo backtracking, repair_in_block;
 // V_safe out) and the closed-loop step (x0 <- f(x0, v_0^safe) + w, V <- shift(V+),
 // Eq. 26) by one block of BLK threads.  smem_raw: the segment-pair table, whose
 // bulk copy completes on bar, then room for the repair's controls, gradient and
-// tape; Vplus: V+ in shared memory.
+// tape; Vplus: V+ in shared memory.  With the shield on, the closed-loop writes
+// for an unrepaired V+ run during the merit pass (TailSide); after a repair
+// V_safe and the state are written again from the repaired controls.
 template <int BLK, bool FAST>
 __device__ __forceinline__ void shield_tail(const DevParams& P, unsigned char* smem_raw,
                                             uint64_t* bar, const float2* Vplus, float* V,
                                             uint32_t iter, uint32_t n_upd, uint32_t* iter_dev,
                                             const ShieldTail& sh, unsigned* status) {
-    __shared__ int s_fail;
+    __shared__ int s_fail, s_iters;
+    __shared__ float s_xn[6];
     __shared__ RepairSmem rsm;
     const int tid = threadIdx.x, T = P.T;
     float4* rec = reinterpret_cast<float4*>(smem_raw);
     float2* Vw = reinterpret_cast<float2*>(rec + 3 * (P.n_track + 5));
     float2* G2 = Vw + T;
     float* tape_s = reinterpret_cast<float*>(G2 + T);
-    if (tid == 0) s_fail = 0;
+    if (tid == 0) {
+        s_fail = 0;
+        s_iters = 0;
+    }
     __syncthreads();
     if (!mbar_wait_bounded(bar, 0u)) s_fail = 1;
     __syncthreads();
@@ -418,27 +462,25 @@ __device__ __forceinline__ void shield_tail(const DevParams& P, unsigned char* s
     for (int t = tid; t < T; t += BLK) Vw[t] = Vplus[t];
     __syncthreads();
     const State x0 = make_state(sh.x0);
-    if (sh.n_repair > 0)
-        repair_in_block<BLK, FAST>(P, rec, x0, sh.seg0[0], Vw, G2, tape_s, sh.n_repair, 1, 0.0f,
-                                   sh.ck, sh.merit_out, nullptr, status, rsm);
     float2* Vs_out = reinterpret_cast<float2*>(sh.V_safe);
     float2* V2 = reinterpret_cast<float2*>(V);
-    for (int t = tid; t < T; t += BLK) {
-        Vs_out[t] = Vw[t];
-        V2[t] = Vplus[t + 1 < T ? t + 1 : T - 1];   // warm start: shift(V+)
+    if (sh.n_repair > 0) {
+        const TailSide side{&P, Vplus, Vs_out, V2, x0, iter, sh.ctr3_dist, s_xn};
+        repair_in_block<BLK, FAST>(P, rec, x0, sh.seg0[0], Vw, G2, tape_s, sh.n_repair, 1, 0.0f,
+                                   sh.ck, sh.merit_out, &s_iters, status, rsm, side);
+        if (s_iters != 0) {   // V+ was repaired: V_safe and the step from the new controls
+            for (int t = tid; t < T; t += BLK) Vs_out[t] = Vw[t];
+            if (tid == 0) closed_loop_next(P, x0, Vw[0], iter, sh.ctr3_dist, s_xn);
+        }
+    } else {
+        for (int t = tid; t < T; t += BLK) {
+            Vs_out[t] = Vw[t];
+            V2[t] = Vplus[t + 1 < T ? t + 1 : T - 1];   // warm start: shift(V+)
+        }
+        if (tid == 0) closed_loop_next(P, x0, Vw[0], iter, sh.ctr3_dist, s_xn);
     }
     if (tid == 0) {   // x0 <- f(x0, clamp(v_0^safe)) + w_n
-        State x = x0;
-        const float2 v0 = Vw[0];
-        model_step(P, x, clampf(v0.x, P.umin0, P.umax0), clampf(v0.y, P.umin1, P.umax1));
-        const uint4 r = philox10(make_uint4(0u, 0u, iter, sh.ctr3_dist), P);
-        const float2 z = box_muller(r.x, r.y);
-        sh.x0[0] = x.vx;
-        sh.x0[1] = fmaf(P.dsig0, z.x, x.vy);
-        sh.x0[2] = fmaf(P.dsig1, z.y, x.r);
-        sh.x0[3] = x.X;
-        sh.x0[4] = x.Y;
-        sh.x0[5] = x.psi;
+        for (int i = 0; i < 6; ++i) sh.x0[i] = s_xn[i];
         if (iter_dev) *iter_dev = n_upd + 1u;
     }
 }

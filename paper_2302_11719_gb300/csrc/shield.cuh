@@ -6,6 +6,7 @@
 #pragma once
 
 #include "kernels.cuh"
+#include <type_traits>
 
 namespace smppi {
 namespace {
@@ -151,15 +152,17 @@ __device__ __forceinline__ bool spin_until_geq(const volatile int* flag, int tar
 // The follower warp: positions pos[t - 1] = (X, Y) of x_t, t = 1..N, ready when
 // *prog >= t (published in chunks of MERIT_PUB).  For a chunk, lane l holds the
 // segment s - 1 + l of the window around the segment s where the chunk starts
-// and evaluates its squared distance to every position of the chunk; the
-// descent walks of the tracked projection are then read off ballots of "the
-// next segment is strictly closer", position after position: the walk from
-// window lane L moves forward to the first lane above L whose successor is not
-// closer, and stays at L when L + 1 is not closer and L - 1 is not closer
-// either.  The decode is one branch-free dependent chain per chunk, unrolled
-// so that it stays in registers.  A backward step or a walk that reaches the
-// window's last lane is finished one segment at a time by lane 0
-// (walk_seq_rec), for that position and the rest of the chunk.
+// and evaluates its squared distance to every position of the chunk.  For each
+// position every lane then forms its walk map: where the descent walk that
+// starts at lane l ends (forward to the first lane above l whose successor is
+// not strictly closer; at l when l + 1 is not closer and l - 1 is not closer
+// either; -1 for a backward step or a walk that reaches the window's last
+// lane).  The walk of the chunk is the composition of its positions' maps,
+// formed by a doubling scan (three rounds of shuffles for eight positions), so
+// the end lane of every position is known after three shuffle latencies
+// rather than after a chain of eight decodes.  From the first position whose
+// walk leaves the window, lane 0 finishes one segment at a time (walk_seq_rec)
+// for that position and the rest of the chunk.
 // The DCBF terms are summed as forward_cost sums them: float32 over blocks of
 // 16 steps, then each block's sum added to a float64 total in order.  With
 // chunks of 8 starting at t = 1 a block ends only at a chunk's last position,
@@ -193,7 +196,7 @@ __device__ __forceinline__ double merit_follow_warp(const DevParams& P, const fl
         // this lane's segment j (first half of record j + 1), loaded once per chunk
         const float4 nA = rec[3 * (j + 1)], nD = rec[3 * (j + 1) + 1], Dn = rec[3 * (j + 1) + 2];
         float dq[MERIT_PUB];
-        unsigned fw[MERIT_PUB], bw[MERIT_PUB];
+        int M[MERIT_PUB];
 #pragma unroll
         for (int q = 0; q < MERIT_PUB; ++q) {
             const float2 xy = pos[t0 - 1 + min(q, nq - 1)];
@@ -202,22 +205,36 @@ __device__ __forceinline__ double merit_follow_warp(const DevParams& P, const fl
             const float rx = fmaf(tt, nD.x, ex), ry = fmaf(tt, nD.z, ey);
             dq[q] = fmaf(rx, rx, ry * ry);
             const float dn = __shfl_down_sync(FULL, dq[q], 1);
-            fw[q] = __ballot_sync(FULL, lane < 31 && dn < dq[q]);   // bit l: d(l+1) < d(l)
-            bw[q] = __ballot_sync(FULL, lane < 31 && dq[q] < dn);   // bit l: d(l) < d(l+1)
+            const float dp = __shfl_up_sync(FULL, dq[q], 1);
+            const bool fwd = lane < 31 && dn < dq[q];            // d(l + 1) < d(l)
+            const unsigned fw = __ballot_sync(FULL, fwd);
+            const int Lf = __ffs(~fw & ~((2u << lane) - 1u)) - 1;
+            const bool back = lane == 0 || dp < dq[q];           // d(l - 1) < d(l) or unknown
+            M[q] = fwd ? ((Lf < 0 || Lf >= 31) ? -1 : Lf) : (back ? -1 : lane);
         }
-        // fast path: the positions whose walk stays inside the window, in order, up
-        // to qs = the first one that does not; each position's DCBF term of Eq. 17
-        // (C max(a, 0) equals forward_cost's conditional term exactly)
+        // M[q] <- the walk over positions 0..q from this lane (-1 once it leaves);
+        // q descending so that M[q - k] is still the previous round's
+#pragma unroll
+        for (int k = 1; k < MERIT_PUB; k <<= 1) {
+#pragma unroll
+            for (int q = MERIT_PUB - 1; q >= k; --q) {
+                const int src = M[q - k];
+                const int v = __shfl_sync(FULL, M[q], src & 31);
+                M[q] = src < 0 ? -1 : v;
+            }
+        }
+        // the walks start at lane 1 (segment s); qs = the first position that leaves
+        // the window; each kept position's DCBF term of Eq. 17 in order (C max(a, 0)
+        // equals forward_cost's conditional term exactly)
         int L = 1, qs = nq;
 #pragma unroll
         for (int q = 0; q < MERIT_PUB; ++q) {
-            const bool fwd = (fw[q] >> L) & 1u;
-            const int Lf = __ffs(~fw[q] & ~((2u << L) - 1u)) - 1;
-            const bool out = fwd ? (Lf < 0 || Lf >= 31) : (((bw[q] >> (L - 1)) & 1u) != 0u);
-            const bool go = q < qs && !out;
-            qs = (q < qs && out) ? q : qs;
-            L = (go && fwd) ? Lf : L;
-            const float h = P.w2 - __shfl_sync(FULL, dq[q], L);
+            const int Lq = __shfl_sync(FULL, M[q], 1);
+            const float dd = __shfl_sync(FULL, dq[q], Lq & 31);
+            const bool go = q < qs && Lq >= 0;
+            qs = (q < qs && Lq < 0) ? q : qs;
+            L = go ? Lq : L;
+            const float h = P.w2 - dd;
             const float a = cbf_arg(P, h_prev, h);
             Jf = go ? fmaf(P.C_cbf, fmaxf(a, 0.0f), Jf) : Jf;
             h_prev = go ? h : h_prev;
@@ -249,12 +266,13 @@ __device__ __forceinline__ double merit_follow_warp(const DevParams& P, const fl
 }
 
 // Two warps: thread 0 integrates the model (any parameters); warp 1 follows.
-// BLK >= 64; buf holds 8 N bytes.
-template <bool FAST>
+// BLK >= 64; buf holds 8 N bytes.  side(lane) runs on warp 2 meanwhile (BLK >= 96).
+template <bool FAST, class Side>
 __device__ __forceinline__ void merit_split(const DevParams& P, const float4* rec,
                                             const State& x0, int s0, int N, const float2* Vw,
                                             float* buf, volatile int* prog, double* out,
-                                            volatile int* done, unsigned* status) {
+                                            volatile int* done, unsigned* status,
+                                            const Side& side) {
     const int tid = threadIdx.x;
     float2* pos = reinterpret_cast<float2*>(buf);            // (X, Y) of x_{t+1}
     if (tid == 0) {
@@ -280,6 +298,8 @@ __device__ __forceinline__ void merit_split(const DevParams& P, const float4* re
             __threadfence_block();
             *done = 1;
         }
+    } else if ((tid >> 5) == 2) {
+        side(tid & 31);
     }
     __syncwarp();
 }
@@ -288,11 +308,14 @@ __device__ __forceinline__ void merit_split(const DevParams& P, const float4* re
 // (tyre forces; the control factors of every step, vel_coef, are precomputed
 // by the whole block), thread 32 the pose recurrence from the published
 // velocities, warp 2 the track walk from the published positions.
-// BLK >= 96; buf holds 44 N + 15 bytes; prog two counters.
+// BLK >= 96; buf holds 44 N + 15 bytes; prog two counters.  side(lane) runs on
+// warp 3 meanwhile (BLK >= 128).
+template <class Side>
 __device__ __forceinline__ void merit_split3(const DevParams& P, const float4* rec,
                                              const State& x0, int s0, int N, const float2* Vw,
                                              float* buf, volatile int* prog, double* out,
-                                             volatile int* done, unsigned* status) {
+                                             volatile int* done, unsigned* status,
+                                             const Side& side) {
     const int tid = threadIdx.x;
     // buf is only 8-byte aligned in some callers: round up to 16 bytes for the
     // float4 rows (the tape scratch has 44 (T + 2) >= 44 N + 15 bytes)
@@ -352,6 +375,8 @@ __device__ __forceinline__ void merit_split3(const DevParams& P, const float4* r
             __threadfence_block();
             *done = 1;
         }
+    } else if ((tid >> 5) == 3) {
+        side(tid & 31);
     }
     __syncwarp();
 }
@@ -446,6 +471,12 @@ __device__ void closed_loop_step(const DevParams& P, const ApplyArgs& ap, float2
 }
 
 
+// Work that a caller of repair_in_block hands to an otherwise idle warp during
+// the first merit pass (side(lane) on all lanes of that warp); NoSide: none.
+struct NoSide {
+    __device__ void operator()(int) const {}
+};
+
 // Shared-memory scratch of repair_in_block.
 struct RepairSmem {
     double P;
@@ -463,29 +494,34 @@ struct RepairSmem {
 // evaluated in parallel by the lanes of warp 0 (lane j: s 2^-j) and the
 // largest accepted step is taken: the same iterate as sequential backtracking.
 // The gradient comes from thread 0 (seq_cost_grad).  merit_row (optional):
-// n_iters + 1 merits; *iters_done: iterations run.  Returns the final merit.
-template <int BLK, bool FAST = false>
+// n_iters + 1 merits; *iters_done: iterations run (0: Vw is unchanged).  side:
+// run by an idle warp during the first merit pass (BLK >= 128).  Returns the
+// final merit.
+template <int BLK, bool FAST = false, class Side = NoSide>
 __device__ double repair_in_block(const DevParams& P, const float4* rec,
                                   const State& x0, int s0, float2* Vw, float2* G, float* tape_s,
                                   int n_iters, int mode, float delta, int ck, double* merit_row,
-                                  int* iters_done, unsigned* status, RepairSmem& sm) {
+                                  int* iters_done, unsigned* status, RepairSmem& sm,
+                                  const Side& side = Side()) {
+    static_assert(BLK >= 128 || std::is_same<Side, NoSide>::value, "side work needs a fourth warp");
     const int T = P.T, N = P.N_r;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = BLK / 32;
     const Tape tape{tape_s, 1, 0};
     // every thread waits (bounded) for the follower's completion flag before it
     // reads the merit, so that the branch on P below is taken by the whole block
-    auto merit = [&]() {
+    auto merit = [&](const auto& sd) {
         if (FAST && BLK >= 96)
-            merit_split3(P, rec, x0, s0, N, Vw, tape_s, sm.prog, &sm.P, &sm.done, status);
+            merit_split3(P, rec, x0, s0, N, Vw, tape_s, sm.prog, &sm.P, &sm.done, status, sd);
         else
-            merit_split<FAST>(P, rec, x0, s0, N, Vw, tape_s, sm.prog, &sm.P, &sm.done, status);
+            merit_split<FAST>(P, rec, x0, s0, N, Vw, tape_s, sm.prog, &sm.P, &sm.done, status,
+                              sd);
         __syncthreads();
         if (!spin_until_geq(&sm.done, 1) && tid == 0) atomicOr(status, SMPPI_DEV_TIMEOUT);
         __threadfence_block();
         __syncthreads();
     };
-    merit();
+    merit(side);
     double P0 = sm.P;
     int it = 0;
     bool stalled = false;
@@ -499,7 +535,7 @@ __device__ double repair_in_block(const DevParams& P, const float4* rec,
                 Vw[t] = clamp2(P, make_float2(fmaf(-delta, G[t].x, Vw[t].x),
                                               fmaf(-delta, G[t].y, Vw[t].y)));
             __syncthreads();
-            merit();
+            merit(NoSide());
             P0 = sm.P;
             continue;
         }
