@@ -689,8 +689,9 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_update_kernel(
 // One control update after a rollout launch that wrote block partials: the
 // merge of the partials into V+ (Eq. 10-11; the log-sum-exp rescaling
 // c_b = exp(-(m_b - m)/lambda) with m the smallest block minimum, the sums in
-// float64 in block order; blocks whose whole contribution c_b eta_b is below w_skip are
-// left out of the noise sum, which moves V+ by at most w_skip max|eps| each),
+// a fixed order in float32, the noise sum compensated; blocks whose whole
+// contribution c_b eta_b is below w_skip are left out of the noise sum, which
+// moves V+ by at most w_skip max|eps| each),
 // then the shield and the closed-loop step (shield_tail).  One block; the
 // track table is staged before the wait on the rollout launch.
 template <bool FAST>
@@ -701,11 +702,10 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_merge_shield_kernel(
     constexpr int NW = UPD_BLK / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
-    __shared__ double s_c[MERGE_MAX_BLOCKS];
+    __shared__ float s_c[MERGE_MAX_BLOCKS];
     __shared__ int l_b[MERGE_MAX_BLOCKS];
     __shared__ float vplus[2 * SMPPI_MAX_T];
     __shared__ float red_f[NW];
-    __shared__ double red_d[NW];
     __shared__ int w_cnt[NW];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int T2 = 2 * P.T;
@@ -721,14 +721,13 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_merge_shield_kernel(
     iter += n_upd;
     // every block's (m_b, eta_b, has_b) loaded at once into registers (one round trip)
     constexpr int PB = MERGE_MAX_BLOCKS / UPD_BLK;
-    float mb[PB];
-    double eb[PB];
+    float mb[PB], eb[PB];
     int hb[PB];
 #pragma unroll
     for (int u = 0; u < PB; ++u) {
         const int b = tid + u * UPD_BLK;
         mb[u] = b < nb ? __ldcg(&blk_min[b]) : 3.0e38f;
-        eb[u] = b < nb ? __ldcg(&part.eta[b]) : 0.0;
+        eb[u] = b < nb ? (float)__ldcg(&part.eta[b]) : 0.0f;
         hb[u] = b < nb ? __ldcg(&part.has[b]) : 0;
     }
     // m = min_b m_b
@@ -742,36 +741,33 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_merge_shield_kernel(
     m = red_f[0];
 #pragma unroll
     for (int w = 1; w < NW; ++w) m = fminf(m, red_f[w]);
-    // c_b (float32: its rounding rescales eta_b and A_b alike) and eta = sum c_b eta_b
-    // in float64 (fixed order: thread-strided, then the warps' sums in order)
-    double eta = 0.0;
+    // c_b (its rounding rescales eta_b and A_b alike) and eta = sum c_b eta_b, a
+    // sum of positive terms in a fixed tree (thread-strided, the warp's butterfly,
+    // then the warps in order; relative error below 12 ulp)
+    float eta = 0.0f;
 #pragma unroll
     for (int u = 0; u < PB; ++u) {
         const int b = tid + u * UPD_BLK;
         if (b < nb) {
-            const double c = (double)expf((m - mb[u]) * P.lam_inv);
-            const double ce = c * eb[u];
+            const float c = expf((m - mb[u]) * P.lam_inv);
+            const float ce = c * eb[u];
             eta += ce;
-            s_c[b] = (hb[u] && ce > (double)P.w_skip) ? c : 0.0;
+            s_c[b] = (hb[u] && ce > P.w_skip) ? c : 0.0f;
         }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) eta += __shfl_xor_sync(0xffffffffu, eta, o);
-    if (lane == 0) red_d[warp] = eta;
+    if (lane == 0) red_f[warp] = eta;
     __syncthreads();
-    if (tid == 0) {
-        double e = red_d[0];
+    float inv_eta = red_f[0];
 #pragma unroll
-        for (int w = 1; w < NW; ++w) e += red_d[w];
-        red_d[0] = 1.0 / e;          // one float64 division for the block
-    }
-    __syncthreads();
-    const double inv_eta = red_d[0];
+    for (int w = 1; w < NW; ++w) inv_eta += red_f[w];
+    inv_eta = 1.0f / inv_eta;
     // the blocks that enter the noise sum, in block order
     int nz = 0;
     for (int b0 = 0; b0 < nb; b0 += UPD_BLK) {
         const int b = b0 + tid;
-        const bool sel = b < nb && s_c[b] != 0.0;
+        const bool sel = b < nb && s_c[b] != 0.0f;
         const unsigned bal = __ballot_sync(0xffffffffu, sel);
         if (lane == 0) w_cnt[warp] = __popc(bal);
         __syncthreads();
@@ -781,19 +777,32 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_merge_shield_kernel(
         for (int w = 0; w < NW; ++w) nz += w_cnt[w];
         __syncthreads();
     }
+    // A_j = sum_b c_b A_b[j] in block order by the compensated dot product of
+    // Ogita, Rump and Oishi (Dot2: each product's rounding error from an FMA, each
+    // sum's from the two-sum, both carried in a second accumulator), as accurate
+    // as the sum in twice the float32 precision rounded once
     for (int j = tid; j < T2; j += UPD_BLK) {
-        double A = 0.0;
+        float A = 0.0f, cmp = 0.0f;
+        auto add = [&](float c, float v) {
+            const float t = __fmul_rn(c, v);
+            const float et = fmaf(c, v, -t);
+            const float sum = __fadd_rn(A, t);
+            const float bv = __fsub_rn(sum, A);
+            const float es = __fadd_rn(__fsub_rn(A, __fsub_rn(sum, bv)), __fsub_rn(t, bv));
+            cmp = __fadd_rn(cmp, __fadd_rn(es, et));
+            A = sum;
+        };
         int i = 0;
         for (; i + 8 <= nz; i += 8) {      // 8 independent loads in flight, summed in order
             float v[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) v[u] = __ldcg(&part.acc[(size_t)l_b[i + u] * T2 + j]);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) A = fma(s_c[l_b[i + u]], (double)v[u], A);
+            for (int u = 0; u < 8; ++u) add(s_c[l_b[i + u]], v[u]);
         }
-        for (; i < nz; ++i) A = fma(s_c[l_b[i]], (double)__ldcg(&part.acc[(size_t)l_b[i] * T2 + j]), A);
+        for (; i < nz; ++i) add(s_c[l_b[i]], __ldcg(&part.acc[(size_t)l_b[i] * T2 + j]));
         const float lo = (j & 1) ? P.umin1 : P.umin0, hi = (j & 1) ? P.umax1 : P.umax0;
-        const float v = (float)fma(A, inv_eta, (double)V[j]);
+        const float v = fmaf(__fadd_rn(A, cmp), inv_eta, V[j]);
         if (!isfinite(v)) atomicOr(status, SMPPI_DEV_NUMERIC);
         vplus[j] = clampf(v, lo, hi);
     }
