@@ -469,6 +469,9 @@ smppi_status smppi_create(const smppi_params* p, void* cuda_stream, smppi_handle
             h->dp.inv_len = (float)(1.0 / L);
         }
     }
+    // the segment-pair table is complete before any launch of this handle: the
+    // merge-and-shield kernel stages it before its wait on the rollout launch
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     if (e == cudaSuccess && !track_ok) {
         free_all(h);
         delete h;
