@@ -268,9 +268,10 @@ smppi_status smppi_apply(smppi_handle* h, float* x0, float* V, const float* V_ex
  * smppi_step, then smppi_repair (mode 1, n_repair iterations) of V^+ into
  * V_safe, then the closed-loop step (smppi_apply) with n = iter.
  *   host_buffers = 0: x0 [6], V [T x 2], V_safe [T x 2] are device arrays.
- *   host_buffers = 1: they are host arrays (pinned memory recommended); the
- *   update copies x0 and V in and x0, V and V_safe out and synchronises the
- *   stream before returning.
+ *   host_buffers = 1: they are host arrays (any host memory); the update
+ *   copies x0 and V in and x0, V, V_safe (and the merits) out in one copy each
+ *   way through a staging block of the handle and its pinned host mirror
+ *   (allocated on first use), and synchronises the stream before returning.
  *   merit_out [n_repair + 1] optional, device (or host when host_buffers = 1).
  */
 smppi_status smppi_shield_update(smppi_handle* h, float* x0, float* V, float* V_safe,

@@ -29,10 +29,10 @@ struct smppi_handle {
     unsigned* status = nullptr;
     uint32_t* iter_dev = nullptr;
     RepairWs rws{};
-    float* d_x0 = nullptr;           // staging for host-buffer updates
-    float* d_V = nullptr;
-    float* d_Vs = nullptr;
-    double* d_merit = nullptr;
+    // staging of host-buffer updates, one block each way: x0 (8 floats), V and
+    // V_safe (2T floats each), then merit_cap merits; h_io is its pinned mirror
+    unsigned char* d_io = nullptr;
+    unsigned char* h_io = nullptr;
     int merit_cap = 0;
     float* kappa = nullptr;          // curvature samples of the curvilinear state
     void* bfgs_ws = nullptr;         // BFGS repair workspace: counter + H slices (grown on use)
@@ -187,10 +187,11 @@ void free_all(smppi_handle* h) {
                     h->ticket,
                     h->status,
                     h->iter_dev,
-                    h->rws.tape, h->rws.Vw, h->rws.G, h->rws.seg0, h->d_x0, h->d_V, h->d_Vs,
-                    h->d_merit, h->bfgs_ws, h->kappa};
+                    h->rws.tape, h->rws.Vw, h->rws.G, h->rws.seg0, h->d_io,
+                    h->bfgs_ws, h->kappa};
     for (void* q : ptrs)
         if (q) cudaFree(q);
+    if (h->h_io) cudaFreeHost(h->h_io);
     if (h->cap) cudaStreamDestroy(h->cap);
 }
 
@@ -445,9 +446,6 @@ smppi_status smppi_create(const smppi_params* p, void* cuda_stream, smppi_handle
     ALLOC(h->rws.Vw, sizeof(float2) * (size_t)T * ms);
     ALLOC(h->rws.G, sizeof(float2) * (size_t)T * ms);
     ALLOC(h->rws.seg0, sizeof(int) * ms);
-    ALLOC(h->d_x0, sizeof(float) * 6);
-    ALLOC(h->d_V, sizeof(float) * 2 * T);
-    ALLOC(h->d_Vs, sizeof(float) * 2 * T);
 #undef ALLOC
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->status, 0, sizeof(unsigned), h->st);
@@ -673,30 +671,39 @@ smppi_status smppi_shield_update(smppi_handle* h, float* x0, float* V, float* V_
         if (!std::isfinite(x0[j])) return fail(h, SMPPI_ERR_ARG, "x0 must be finite");
     if (std::fabs(x0[3]) > 1e18f || std::fabs(x0[4]) > 1e18f)
         return fail(h, SMPPI_ERR_ARG, "x0 position beyond 1e18 m");
-    const size_t vb = sizeof(float) * 2 * h->p.T;
-    double* dm = nullptr;
-    if (merit_out && n_repair > 0) {
-        if (h->merit_cap < n_repair + 1) {
-            if (h->d_merit) cudaFree(h->d_merit);
-            h->d_merit = nullptr;
-            h->merit_cap = 0;
-            CU(h, cudaMalloc(&h->d_merit, sizeof(double) * (n_repair + 1)));
-            h->merit_cap = n_repair + 1;
-        }
-        dm = h->d_merit;
+    // one copy in (x0, V) and one copy out (x0, V, V_safe, merits) through the
+    // handle's staging block and its pinned mirror: each small copy costs a few
+    // microseconds of its own
+    const size_t vb = sizeof(float) * 2 * h->p.T, off_V = 32, off_Vs = off_V + vb,
+                 off_m = off_Vs + vb;
+    const int n_merit = (merit_out && n_repair > 0) ? n_repair + 1 : 0;
+    if (!h->d_io || h->merit_cap < n_merit) {
+        if (h->d_io) cudaFree(h->d_io);
+        if (h->h_io) cudaFreeHost(h->h_io);
+        h->d_io = h->h_io = nullptr;
+        h->merit_cap = 0;
+        const int cap = std::max(n_merit, 11);
+        const size_t bytes = off_m + sizeof(double) * cap;
+        CU(h, cudaMalloc(&h->d_io, bytes));
+        CU(h, cudaMallocHost(&h->h_io, bytes));
+        h->merit_cap = cap;
     }
-    CU(h, cudaMemcpyAsync(h->d_x0, x0, sizeof(float) * 6, cudaMemcpyHostToDevice, h->st));
-    CU(h, cudaMemcpyAsync(h->d_V, V, vb, cudaMemcpyHostToDevice, h->st));
-    smppi_status s = enqueue_shield(h, h->st, h->d_x0, h->d_V, h->d_Vs, iter, instance, n_repair,
-                                    dm, nullptr);
+    std::memcpy(h->h_io, x0, sizeof(float) * 6);
+    std::memcpy(h->h_io + off_V, V, vb);
+    CU(h, cudaMemcpyAsync(h->d_io, h->h_io, off_Vs, cudaMemcpyHostToDevice, h->st));
+    float* dx = reinterpret_cast<float*>(h->d_io);
+    float* dV = reinterpret_cast<float*>(h->d_io + off_V);
+    float* dVs = reinterpret_cast<float*>(h->d_io + off_Vs);
+    double* dm = n_merit ? reinterpret_cast<double*>(h->d_io + off_m) : nullptr;
+    smppi_status s = enqueue_shield(h, h->st, dx, dV, dVs, iter, instance, n_repair, dm, nullptr);
     if (s != SMPPI_OK) return s;
-    CU(h, cudaMemcpyAsync(x0, h->d_x0, sizeof(float) * 6, cudaMemcpyDeviceToHost, h->st));
-    CU(h, cudaMemcpyAsync(V, h->d_V, vb, cudaMemcpyDeviceToHost, h->st));
-    CU(h, cudaMemcpyAsync(V_safe, h->d_Vs, vb, cudaMemcpyDeviceToHost, h->st));
-    if (dm)
-        CU(h, cudaMemcpyAsync(merit_out, dm, sizeof(double) * (n_repair + 1),
-                              cudaMemcpyDeviceToHost, h->st));
+    CU(h, cudaMemcpyAsync(h->h_io, h->d_io, off_m + sizeof(double) * n_merit,
+                          cudaMemcpyDeviceToHost, h->st));
     CU(h, cudaStreamSynchronize(h->st));
+    std::memcpy(x0, h->h_io, sizeof(float) * 6);
+    std::memcpy(V, h->h_io + off_V, vb);
+    std::memcpy(V_safe, h->h_io + off_Vs, vb);
+    if (n_merit) std::memcpy(merit_out, h->h_io + off_m, sizeof(double) * n_merit);
     return SMPPI_OK;
 }
 
