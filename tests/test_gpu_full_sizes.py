@@ -2,6 +2,11 @@
 
   * the MPPI iteration at K = 65536 and 262144, T = 100: V+ against the
     oracle's V+ (the end-to-end update bound, and the maximum error printed);
+  * the whole Shield-MPPI update at the same sizes through the launch pair
+    bench.py times (rollouts that also write block partials, then one block
+    that merges them into V+, runs the shield and takes the closed-loop step):
+    the warm start shift(V+) within the update bound, V_safe within the repair
+    tolerance plus that bound, the executed step within 1e-4 relative;
   * the shield on 8192 near-boundary sequences, T = 100, 20 iterations, run in
     the launch shape of that size (one thread per sequence for the gradient
     repair, one warp per sequence for BFGS), compared with the oracle's repair
@@ -68,6 +73,36 @@ def test_update_error_full_size(S, orc, K):
           "here %.2e..%.2e)" % (K, es, e.max(), V_UPD, tol.min(), tol.max()))
     assert np.all(e <= tol)
     assert e.max() <= V_UPD
+
+
+@pytest.mark.parametrize("K", [65536, 262144])
+def test_shield_update_full_size(S, orc, K):
+    pr = I.throughput_problem(K, 100)
+    it, inst = 1, 0
+    ctl = S.Controller(pr.params, pr.track)
+    x0, V = ctl.tensor(pr.x0), ctl.tensor(pr.V)
+    Vs = torch.empty_like(V)
+    S.smppi_shield_update(ctl.h, x0, V, Vs, it, inst, 10)
+    st, _ = ctl.sync_status()
+    assert st in (S.OK, S.ERR_STALLED), st
+    Vg, Vsg = V.cpu().numpy().astype(np.float64), Vs.cpu().numpy()
+    xg = x0.cpu().numpy()
+    ctl.close()
+    m = orc.Model(pr.params, pr.track)
+    So, Vp = orc.mppi_step(m, pr.x0, pr.V, it, inst, nthreads=N_THREADS)
+    tol = _bound_top(orc, m, So, pr.V, Vp, it, inst, pr.params["lam"])
+    tol_sh = np.concatenate([tol[1:], tol[-1:]])
+    e_sh = np.abs(Vg - orc.shift(m, Vp))
+    Vso, mer, _, its = orc.repair(m, pr.x0, Vp.astype(np.float32), 10)
+    e_s = np.abs(Vsg.astype(np.float64) - Vso)
+    x1 = orc.apply(m, pr.x0, Vsg[0], it, inst)
+    ex = rel_err(xg, x1)
+    print("shield update K=%d T=100: max |shift(V+) err| %.2e (bound %.2e..%.2e), "
+          "max |V_safe err| %.2e (oracle repair iterations %d), rel next-state err %.2e"
+          % (K, e_sh.max(), tol.min(), tol.max(), e_s.max(), its, ex))
+    assert np.all(e_sh <= tol_sh) and e_sh.max() <= V_UPD
+    assert np.all(e_s <= V_REP + tol)
+    assert ex <= X_REL
 
 
 def _repair_sample(S, orc, mode):

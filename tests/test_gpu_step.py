@@ -214,7 +214,7 @@ def test_degenerate_updates(S, orc):
 
 
 def test_full_size_bench_launch(S, orc):
-    # K = 65536, T = 100 in the launch configuration bench.py times
+    # K = 65536, T = 100: the MPPI iteration alone (smppi_step: rollouts, then the update kernel)
     pr = I.throughput_problem(65536, 100)
     Sg, Vg, _ = run_step(S, pr, it=1)
     m = orc.Model(pr.params, pr.track)
