@@ -688,10 +688,10 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_update_kernel(
 
 // One control update after a rollout launch that wrote block partials: the
 // merge of the partials into V+ (Eq. 10-11; the log-sum-exp rescaling
-// c_b = exp(-(m_b - m)/lambda) with m the smallest block minimum, the sums in
-// a fixed order in float32, the noise sum compensated; blocks whose whole
-// contribution c_b eta_b is below w_skip are left out of the noise sum, which
-// moves V+ by at most w_skip max|eps| each),
+// c_b = exp(-(m_b - m)/lambda) with m the smallest block minimum; the
+// normaliser in float64, the noise sum in float32 compensated, both in a fixed
+// order; blocks whose whole contribution c_b eta_b is below w_skip are left out
+// of the noise sum, which moves V+ by at most w_skip max|eps| each),
 // then the shield and the closed-loop step (shield_tail).  One block; the
 // track table is staged before the wait on the rollout launch.
 template <bool FAST>
@@ -706,6 +706,7 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_merge_shield_kernel(
     __shared__ int l_b[MERGE_MAX_BLOCKS];
     __shared__ float vplus[2 * SMPPI_MAX_T];
     __shared__ float red_f[NW];
+    __shared__ double red_d[NW];
     __shared__ int w_cnt[NW];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int T2 = 2 * P.T;
@@ -721,13 +722,14 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_merge_shield_kernel(
     iter += n_upd;
     // every block's (m_b, eta_b, has_b) loaded at once into registers (one round trip)
     constexpr int PB = MERGE_MAX_BLOCKS / UPD_BLK;
-    float mb[PB], eb[PB];
+    float mb[PB];
+    double eb[PB];
     int hb[PB];
 #pragma unroll
     for (int u = 0; u < PB; ++u) {
         const int b = tid + u * UPD_BLK;
         mb[u] = b < nb ? __ldcg(&blk_min[b]) : 3.0e38f;
-        eb[u] = b < nb ? (float)__ldcg(&part.eta[b]) : 0.0f;
+        eb[u] = b < nb ? __ldcg(&part.eta[b]) : 0.0;
         hb[u] = b < nb ? __ldcg(&part.has[b]) : 0;
     }
     // m = min_b m_b
@@ -741,28 +743,32 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_merge_shield_kernel(
     m = red_f[0];
 #pragma unroll
     for (int w = 1; w < NW; ++w) m = fminf(m, red_f[w]);
-    // c_b (its rounding rescales eta_b and A_b alike) and eta = sum c_b eta_b, a
-    // sum of positive terms in a fixed tree (thread-strided, the warp's butterfly,
-    // then the warps in order; relative error below 12 ulp)
-    float eta = 0.0f;
+    // c_b (float32: its rounding rescales eta_b and A_b alike) and the normaliser
+    // eta = sum c_b eta_b and 1/eta in float64 (fixed order: thread-strided, the
+    // warp's butterfly, then the warps in order)
+    double eta = 0.0;
 #pragma unroll
     for (int u = 0; u < PB; ++u) {
         const int b = tid + u * UPD_BLK;
         if (b < nb) {
             const float c = expf((m - mb[u]) * P.lam_inv);
-            const float ce = c * eb[u];
+            const double ce = (double)c * eb[u];
             eta += ce;
-            s_c[b] = (hb[u] && ce > P.w_skip) ? c : 0.0f;
+            s_c[b] = (hb[u] && ce > (double)P.w_skip) ? c : 0.0f;
         }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) eta += __shfl_xor_sync(0xffffffffu, eta, o);
-    if (lane == 0) red_f[warp] = eta;
+    if (lane == 0) red_d[warp] = eta;
     __syncthreads();
-    float inv_eta = red_f[0];
+    if (tid == 0) {
+        double e = red_d[0];
 #pragma unroll
-    for (int w = 1; w < NW; ++w) inv_eta += red_f[w];
-    inv_eta = 1.0f / inv_eta;
+        for (int w = 1; w < NW; ++w) e += red_d[w];
+        red_d[0] = 1.0 / e;          // one float64 division for the block
+    }
+    __syncthreads();
+    const double inv_eta = red_d[0];
     // the blocks that enter the noise sum, in block order
     int nz = 0;
     for (int b0 = 0; b0 < nb; b0 += UPD_BLK) {
@@ -802,7 +808,7 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_merge_shield_kernel(
         }
         for (; i < nz; ++i) add(s_c[l_b[i]], __ldcg(&part.acc[(size_t)l_b[i] * T2 + j]));
         const float lo = (j & 1) ? P.umin1 : P.umin0, hi = (j & 1) ? P.umax1 : P.umax0;
-        const float v = fmaf(__fadd_rn(A, cmp), inv_eta, V[j]);
+        const float v = (float)fma((double)__fadd_rn(A, cmp), inv_eta, (double)V[j]);
         if (!isfinite(v)) atomicOr(status, SMPPI_DEV_NUMERIC);
         vplus[j] = clampf(v, lo, hi);
     }
