@@ -271,7 +271,9 @@ smppi_status smppi_apply(smppi_handle* h, float* x0, float* V, const float* V_ex
  *   host_buffers = 1: they are host arrays (any host memory); the update
  *   copies x0 and V in and x0, V, V_safe (and the merits) out in one copy each
  *   way through a staging block of the handle and its pinned host mirror
- *   (allocated on first use), and synchronises the stream before returning.
+ *   (allocated on first use), replays the copies and the launches from a CUDA
+ *   graph the handle keeps per (instance, n_repair, merits), and synchronises
+ *   the stream before returning.  Per-kernel timing does not cover these calls.
  *   merit_out [n_repair + 1] optional, device (or host when host_buffers = 1).
  */
 smppi_status smppi_shield_update(smppi_handle* h, float* x0, float* V, float* V_safe,

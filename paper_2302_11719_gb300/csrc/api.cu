@@ -34,6 +34,8 @@ struct smppi_handle {
     unsigned char* d_io = nullptr;
     unsigned char* h_io = nullptr;
     int merit_cap = 0;
+    cudaGraphExec_t io_exec = nullptr;   // copy in, the update, copy out (host-buffer updates)
+    std::string io_key;
     float* kappa = nullptr;          // curvature samples of the curvilinear state
     void* bfgs_ws = nullptr;         // BFGS repair workspace: counter + H slices (grown on use)
     size_t bfgs_ws_bytes = 0;
@@ -182,6 +184,7 @@ DevParams derive(const smppi_params& p) {
 
 void free_all(smppi_handle* h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->io_exec) cudaGraphExecDestroy(h->io_exec);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     void* ptrs[] = {h->rec, h->S_ws, h->blk_min, h->part_acc, h->part_eta, h->part_has,
                     h->ticket,
@@ -671,13 +674,17 @@ smppi_status smppi_shield_update(smppi_handle* h, float* x0, float* V, float* V_
         if (!std::isfinite(x0[j])) return fail(h, SMPPI_ERR_ARG, "x0 must be finite");
     if (std::fabs(x0[3]) > 1e18f || std::fabs(x0[4]) > 1e18f)
         return fail(h, SMPPI_ERR_ARG, "x0 position beyond 1e18 m");
-    // one copy in (x0, V) and one copy out (x0, V, V_safe, merits) through the
-    // handle's staging block and its pinned mirror: each small copy costs a few
-    // microseconds of its own
-    const size_t vb = sizeof(float) * 2 * h->p.T, off_V = 32, off_Vs = off_V + vb,
-                 off_m = off_Vs + vb;
+    // one copy in (x0, the iteration, V) and one copy out (x0, V, V_safe, merits)
+    // through the handle's staging block and its pinned mirror, the copies and the
+    // update's launches replayed from one CUDA graph per (instance, n_repair,
+    // merits): the iteration reaches the kernels through the staged word that
+    // they read as their device iteration counter
+    const size_t vb = sizeof(float) * 2 * h->p.T, off_iter = 24, off_V = 32,
+                 off_Vs = off_V + vb, off_m = off_Vs + vb;
     const int n_merit = (merit_out && n_repair > 0) ? n_repair + 1 : 0;
     if (!h->d_io || h->merit_cap < n_merit) {
+        if (h->io_exec) cudaGraphExecDestroy(h->io_exec);
+        h->io_exec = nullptr;
         if (h->d_io) cudaFree(h->d_io);
         if (h->h_io) cudaFreeHost(h->h_io);
         h->d_io = h->h_io = nullptr;
@@ -688,17 +695,42 @@ smppi_status smppi_shield_update(smppi_handle* h, float* x0, float* V, float* V_
         CU(h, cudaMallocHost(&h->h_io, bytes));
         h->merit_cap = cap;
     }
+    char key[64];
+    std::snprintf(key, sizeof(key), "%u %d %d", instance, n_repair, n_merit);
+    if (!h->io_exec || h->io_key != key) {
+        if (h->io_exec) cudaGraphExecDestroy(h->io_exec);
+        h->io_exec = nullptr;
+        float* dx = reinterpret_cast<float*>(h->d_io);
+        float* dV = reinterpret_cast<float*>(h->d_io + off_V);
+        float* dVs = reinterpret_cast<float*>(h->d_io + off_Vs);
+        double* dm = n_merit ? reinterpret_cast<double*>(h->d_io + off_m) : nullptr;
+        uint32_t* di = reinterpret_cast<uint32_t*>(h->d_io + off_iter);
+        cudaGraph_t g = nullptr;
+        CU(h, cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = cudaMemcpyAsync(h->d_io, h->h_io, off_Vs, cudaMemcpyHostToDevice, h->cap);
+        smppi_status s = SMPPI_OK;
+        if (e == cudaSuccess)
+            s = enqueue_shield(h, h->cap, dx, dV, dVs, 0u, instance, n_repair, dm, di);
+        if (e == cudaSuccess && s == SMPPI_OK)
+            e = cudaMemcpyAsync(h->h_io, h->d_io, off_m + sizeof(double) * n_merit,
+                                cudaMemcpyDeviceToHost, h->cap);
+        const cudaError_t e_end = cudaStreamEndCapture(h->cap, &g);
+        if (s != SMPPI_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (e == cudaSuccess) e = e_end;
+        if (e != cudaSuccess && g) cudaGraphDestroy(g);
+        CU(h, e);
+        e = cudaGraphInstantiate(&h->io_exec, g, 0);
+        cudaGraphDestroy(g);
+        CU(h, e);
+        h->io_key = key;
+    }
     std::memcpy(h->h_io, x0, sizeof(float) * 6);
+    std::memcpy(h->h_io + off_iter, &iter, sizeof(uint32_t));
     std::memcpy(h->h_io + off_V, V, vb);
-    CU(h, cudaMemcpyAsync(h->d_io, h->h_io, off_Vs, cudaMemcpyHostToDevice, h->st));
-    float* dx = reinterpret_cast<float*>(h->d_io);
-    float* dV = reinterpret_cast<float*>(h->d_io + off_V);
-    float* dVs = reinterpret_cast<float*>(h->d_io + off_Vs);
-    double* dm = n_merit ? reinterpret_cast<double*>(h->d_io + off_m) : nullptr;
-    smppi_status s = enqueue_shield(h, h->st, dx, dV, dVs, iter, instance, n_repair, dm, nullptr);
-    if (s != SMPPI_OK) return s;
-    CU(h, cudaMemcpyAsync(h->h_io, h->d_io, off_m + sizeof(double) * n_merit,
-                          cudaMemcpyDeviceToHost, h->st));
+    CU(h, cudaGraphLaunch(h->io_exec, h->st));
     CU(h, cudaStreamSynchronize(h->st));
     std::memcpy(x0, h->h_io, sizeof(float) * 6);
     std::memcpy(V, h->h_io + off_V, vb);
