@@ -149,6 +149,8 @@ __global__ void __launch_bounds__(REPB_BLK) repair_block_kernel(
     float2* Vw = reinterpret_cast<float2*>(rec + 3 * (n + 5));
     float2* G = Vw + T;
     float* tape_s = reinterpret_cast<float*>(G + T);
+    const GradWs gws =
+        grad_ws_at(reinterpret_cast<unsigned char*>(tape_s + (size_t)(T + 2) * NFIELD), T);
     __shared__ __align__(8) uint64_t bar;
     __shared__ RepairSmem sm;
     __shared__ float s_red[REPB_BLK / 32];
@@ -182,7 +184,7 @@ __global__ void __launch_bounds__(REPB_BLK) repair_block_kernel(
                                                    status);
     repair_in_block<REPB_BLK, FAST>(P, rec, x0, s0, Vw, G, tape_s, n_iters, mode, delta, ck,
                               merit_out ? merit_out + (size_t)q * (n_iters + 1) : nullptr,
-                              iters_out ? iters_out + q : nullptr, status, sm);
+                              iters_out ? iters_out + q : nullptr, status, sm, NoSide(), &gws);
     float2* vout = reinterpret_cast<float2*>(Vout) + (size_t)q * T;
     for (int t = tid; t < T; t += REPB_BLK) vout[t] = Vw[t];
     if (q == 0 && tid == 0 && ap.x0) closed_loop_step(P, ap, Vw[0]);
@@ -224,7 +226,7 @@ cudaError_t launch_repair(const DevParams& P, const float4* rec, const RepairWs&
                           unsigned* status, cudaStream_t st) {
     if (n_seq <= REPAIR_BLOCK_MAX_SEQ) {
         const size_t smem = rec_table_bytes(P.n_track) + (size_t)P.T * 16 +
-                            (size_t)(P.T + 2) * NFIELD * 4;
+                            (size_t)(P.T + 2) * NFIELD * 4 + grad_ws_bytes(P.T);
         auto kern = fast_model(P) ? repair_block_kernel<true> : repair_block_kernel<false>;
         cudaError_t e = ensure_smem((const void*)kern, smem);
         if (e != cudaSuccess) return e;

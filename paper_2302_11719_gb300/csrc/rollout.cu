@@ -436,7 +436,8 @@ template <int BLK, bool FAST>
 __device__ __forceinline__ void shield_tail(const DevParams& P, unsigned char* smem_raw,
                                             uint64_t* bar, const float2* Vplus, float* V,
                                             uint32_t iter, uint32_t n_upd, uint32_t* iter_dev,
-                                            const ShieldTail& sh, unsigned* status) {
+                                            const ShieldTail& sh, unsigned* status,
+                                            bool block_grad = false) {
     __shared__ int s_fail, s_iters;
     __shared__ float s_xn[6];
     __shared__ RepairSmem rsm;
@@ -445,6 +446,9 @@ __device__ __forceinline__ void shield_tail(const DevParams& P, unsigned char* s
     float2* Vw = reinterpret_cast<float2*>(rec + 3 * (P.n_track + 5));
     float2* G2 = Vw + T;
     float* tape_s = reinterpret_cast<float*>(G2 + T);
+    // the block gradient's workspace follows the tape scratch (block_grad only)
+    const GradWs gws =
+        grad_ws_at(reinterpret_cast<unsigned char*>(tape_s + (size_t)(T + 2) * NFIELD), T);
     if (tid == 0) {
         s_fail = 0;
         s_iters = 0;
@@ -467,7 +471,8 @@ __device__ __forceinline__ void shield_tail(const DevParams& P, unsigned char* s
     if (sh.n_repair > 0) {
         const TailSide side{&P, Vplus, Vs_out, V2, x0, iter, sh.ctr3_dist, s_xn};
         repair_in_block<BLK, FAST>(P, rec, x0, sh.seg0[0], Vw, G2, tape_s, sh.n_repair, 1, 0.0f,
-                                   sh.ck, sh.merit_out, &s_iters, status, rsm, side);
+                                   sh.ck, sh.merit_out, &s_iters, status, rsm, side,
+                                   block_grad ? &gws : nullptr);
         if (s_iters != 0) {   // V+ was repaired: V_safe and the step from the new controls
             for (int t = tid; t < T; t += BLK) Vs_out[t] = Vw[t];
             if (tid == 0) closed_loop_next(P, x0, Vw[0], iter, sh.ctr3_dist, s_xn);
@@ -813,7 +818,7 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_merge_shield_kernel(
         vplus[j] = clampf(v, lo, hi);
     }
     shield_tail<UPD_BLK, FAST>(P, smem_raw, &bar, reinterpret_cast<const float2*>(vplus), V, iter,
-                               n_upd, iter_dev, sh, status);
+                               n_upd, iter_dev, sh, status, true);
 }
 
 // Control noise exactly as the rollout kernels draw it (test access).
@@ -1063,7 +1068,7 @@ cudaError_t launch_merge_shield(const DevParams& P, int nb, const float* blk_min
                                 float* V_safe, int n_repair, int ck, double* merit_out,
                                 uint32_t ctr3_dist, cudaStream_t st) {
     const size_t smem = rec_table_bytes(P.n_track) + (size_t)P.T * 16 +
-                        (size_t)(P.T + 2) * NFIELD * 4;
+                        (size_t)(P.T + 2) * NFIELD * 4 + grad_ws_bytes(P.T);
     const ShieldTail sh{rec, seg0, x0, V_safe, n_repair, ck, merit_out, ctr3_dist};
     auto kern = (P.tyre15 && P.steer_small) ? mppi_merge_shield_kernel<true>
                                              : mppi_merge_shield_kernel<false>;

@@ -149,6 +149,16 @@ __device__ __forceinline__ bool spin_until_geq(const volatile int* flag, int tar
     return tries <= MERIT_WAIT_LIMIT;
 }
 
+// The trajectory a merit pass leaves for the block gradient (shared memory; a
+// null member stores nothing): ang[t] = (psi, cos psi, sin psi) of x_{t+1},
+// t = 0..N-1; sg[t] and hh[t] = the tracked segment and h = w^2 - e_y^2 of x_t,
+// t = 0..N.
+struct MeritTraj {
+    float4* ang = nullptr;
+    int* sg = nullptr;
+    float* hh = nullptr;
+};
+
 // The follower warp: positions pos[t - 1] = (X, Y) of x_t, t = 1..N, ready when
 // *prog >= t (published in chunks of MERIT_PUB).  For a chunk, lane l holds the
 // segment s - 1 + l of the window around the segment s where the chunk starts
@@ -167,11 +177,13 @@ __device__ __forceinline__ bool spin_until_geq(const volatile int* flag, int tar
 // 16 steps, then each block's sum added to a float64 total in order.  With
 // chunks of 8 starting at t = 1 a block ends only at a chunk's last position,
 // so the float64 add runs once per block, after that chunk.
+// With sg / hh (MeritTraj) lane 0 also stores each position's segment and h.
 // Returns J on every lane.
 __device__ __forceinline__ double merit_follow_warp(const DevParams& P, const float4* rec,
                                                     const State& x0, int s0, int N,
                                                     const float2* pos, volatile int* prog,
-                                                    unsigned* status) {
+                                                    unsigned* status, int* sg = nullptr,
+                                                    float* hh = nullptr) {
     static_assert(MERIT_PUB == 8, "the float64 adds assume chunks of 8 steps starting at t = 1");
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, n = P.n_track;
@@ -181,6 +193,10 @@ __device__ __forceinline__ double merit_follow_warp(const DevParams& P, const fl
     double J = (double)(0.0f * run_cost(P, x0.vx, d2));
     float Jf = 0.0f;
     bool timed_out = false;
+    if (sg && lane == 0) {
+        sg[0] = s0;
+        hh[0] = h_prev;
+    }
     for (int t0 = 1; t0 <= N; t0 += MERIT_PUB) {
         const int t1 = min(N, t0 + MERIT_PUB - 1), nq = t1 - t0 + 1;
         const bool ok = spin_until_geq(prog, t1);
@@ -197,6 +213,8 @@ __device__ __forceinline__ double merit_follow_warp(const DevParams& P, const fl
         const float4 nA = rec[3 * (j + 1)], nD = rec[3 * (j + 1) + 1], Dn = rec[3 * (j + 1) + 2];
         float dq[MERIT_PUB];
         int M[MERIT_PUB];
+        int jq[MERIT_PUB];     // end lane and h of each position (stored when sg is given)
+        float hq[MERIT_PUB];
 #pragma unroll
         for (int q = 0; q < MERIT_PUB; ++q) {
             const float2 xy = pos[t0 - 1 + min(q, nq - 1)];
@@ -238,6 +256,20 @@ __device__ __forceinline__ double merit_follow_warp(const DevParams& P, const fl
             const float a = cbf_arg(P, h_prev, h);
             Jf = go ? fmaf(P.C_cbf, fmaxf(a, 0.0f), Jf) : Jf;
             h_prev = go ? h : h_prev;
+            jq[q] = Lq;
+            hq[q] = h;
+        }
+        if (sg && lane == 0) {   // unrolled: jq and hq stay in registers
+#pragma unroll
+            for (int q = 0; q < MERIT_PUB; ++q) {
+                if (q < qs) {
+                    int sq = s - 1 + jq[q];
+                    if (sq < 0) sq += n;
+                    while (sq >= n) sq -= n;
+                    sg[t0 + q] = sq;
+                    hh[t0 + q] = hq[q];
+                }
+            }
         }
         int scur = s - 1 + L;
         if (scur < 0) scur += n;
@@ -254,6 +286,10 @@ __device__ __forceinline__ double merit_follow_warp(const DevParams& P, const fl
             const float a = cbf_arg(P, h_prev, h);
             Jf = fmaf(P.C_cbf, fmaxf(a, 0.0f), Jf);
             h_prev = h;
+            if (sg && lane == 0) {
+                sg[t0 + q] = scur;
+                hh[t0 + q] = h;
+            }
         }
         s = scur;
         if (nq == MERIT_PUB && ((t1 & 15) == 0)) {   // a block of 16 steps ends here
@@ -304,26 +340,45 @@ __device__ __forceinline__ void merit_split(const DevParams& P, const float4* re
     __syncwarp();
 }
 
+// The merit pass's rows in its buffer (only 8-byte aligned in some callers:
+// rounded up to 16 bytes for the float4 rows; the tape scratch has
+// 44 (T + 2) >= 44 N + 15 bytes): ctl[t] = (Bd, kx, ky, kr) and bx[t] of step t,
+// vel[t] = (v_x, v_y, r) of x_t, pos[t] = (X, Y) of x_{t+1}.
+struct MeritRows {
+    float4* ctl;
+    float4* vel;
+    float2* pos;
+    float* bx;
+};
+
+__device__ __forceinline__ MeritRows merit_rows(float* buf, int N) {
+    MeritRows m;
+    m.ctl = reinterpret_cast<float4*>((reinterpret_cast<uintptr_t>(buf) + 15) & ~uintptr_t(15));
+    m.vel = m.ctl + N;
+    m.pos = reinterpret_cast<float2*>(m.vel + N);
+    m.bx = reinterpret_cast<float*>(m.pos + N);
+    return m;
+}
+
 // Three warps for the C = 1.5 model: thread 0 runs the velocity recurrence
 // (tyre forces; the control factors of every step, vel_coef, are precomputed
 // by the whole block), thread 32 the pose recurrence from the published
 // velocities, warp 2 the track walk from the published positions.
-// BLK >= 96; buf holds 44 N + 15 bytes; prog two counters.  side(lane) runs on
-// warp 3 meanwhile (BLK >= 128).
+// BLK >= 96; buf holds 44 N + 15 bytes (merit_rows); prog two counters.  tr:
+// the trajectory kept for the block gradient (members may be null).
+// side(lane) runs on warp 3 meanwhile (BLK >= 128).
 template <class Side>
 __device__ __forceinline__ void merit_split3(const DevParams& P, const float4* rec,
                                              const State& x0, int s0, int N, const float2* Vw,
                                              float* buf, volatile int* prog, double* out,
                                              volatile int* done, unsigned* status,
-                                             const Side& side) {
+                                             const MeritTraj& tr, const Side& side) {
     const int tid = threadIdx.x;
-    // buf is only 8-byte aligned in some callers: round up to 16 bytes for the
-    // float4 rows (the tape scratch has 44 (T + 2) >= 44 N + 15 bytes)
-    float4* ctl = reinterpret_cast<float4*>((reinterpret_cast<uintptr_t>(buf) + 15) &
-                                            ~uintptr_t(15));  // (Bd, kx, ky, kr) of step t
-    float4* vel = ctl + N;                                    // (v_x, v_y, r) of x_t
-    float2* pos = reinterpret_cast<float2*>(vel + N);         // (X, Y) of x_{t+1}
-    float* bx = reinterpret_cast<float*>(pos + N);            // bx of step t
+    const MeritRows mr = merit_rows(buf, N);
+    float4* ctl = mr.ctl;
+    float4* vel = mr.vel;
+    float2* pos = mr.pos;
+    float* bx = mr.bx;
     if (tid == 0) {
         prog[0] = 0;
         prog[1] = 0;
@@ -363,13 +418,15 @@ __device__ __forceinline__ void merit_split3(const DevParams& P, const float4* r
             const float4 v = vel[t];
             pose_step_fast(P, v.x, v.y, v.z, X, Y, psi, cp, sp);
             pos[t] = make_float2(X, Y);
+            if (tr.ang) tr.ang[t] = make_float4(psi, cp, sp, 0.0f);
             if ((t + 1) % MERIT_PUB == 0 || t + 1 == N) {
                 __threadfence_block();
                 prog[1] = t + 1;
             }
         }
     } else if ((tid >> 5) == 2) {
-        const double J = merit_follow_warp(P, rec, x0, s0, N, pos, prog + 1, status);
+        const double J = merit_follow_warp(P, rec, x0, s0, N, pos, prog + 1, status, tr.sg,
+                                           tr.hh);
         if (tid == 64) {
             *out = J;
             __threadfence_block();
@@ -447,6 +504,131 @@ __device__ double seq_cost_grad(const DevParams& P, const float4* rec,
     return J;
 }
 
+// Shared-memory workspace of the block gradient: the trajectory a merit pass
+// keeps (MeritTraj) and five float4 of adjoint coefficients per step.
+struct GradWs {
+    MeritTraj tr;
+    float4* coef;
+};
+
+// Bytes of a GradWs for horizon T (with 16 bytes for alignment), and its
+// carving from the memory at p.
+__host__ __device__ constexpr size_t grad_ws_bytes(int T) {
+    return (size_t)T * 16 + (size_t)T * 80 + (size_t)(T + 1) * 8 + 16;
+}
+
+__device__ __forceinline__ GradWs grad_ws_at(unsigned char* p, int T) {
+    GradWs g;
+    g.tr.ang = reinterpret_cast<float4*>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
+    g.coef = g.tr.ang + T;
+    g.tr.sg = reinterpret_cast<int*>(g.coef + 5 * T);
+    g.tr.hh = reinterpret_cast<float*>(g.tr.sg + T + 1);
+    return g;
+}
+
+// Gradient G_t = dP/dv_t of the merit P (the CBF objective of Eq. 22: running-cost
+// weight 0, CBF weight 1) by the whole block, from the trajectory of Vw that the
+// last merit pass left (merit_rows of buf, gw.tr).  The adjoint of the Euler
+// step is linear in the adjoint: lambda_t = lambda_{t+1} + E_t' lambda_{t+1}
+// + d_t and g_t = B_t' lambda_{t+1}, with E_t, B_t the derivatives of
+// model_step at (x_t, u_t) scaled by dt (those of model_step_adjoint, collected
+// per step) and d_t the CBF penalties' derivative at x_t (add_direct).  Every
+// thread forms the coefficients of its steps; thread 0 then runs the recursion
+// over (v_x, v_y, r, X, Y, psi).  Writes G_t for t < N (0 for N <= t < T).
+// The stored segments are clamped to the track (a merit pass whose wait gave up
+// leaves them unset; the TIMEOUT bit reports that case).
+template <int BLK>
+__device__ void block_cost_grad(const DevParams& P, const float4* rec, const State& x0, int N,
+                                int T, const float2* Vw, float2* G, float* buf,
+                                const GradWs& gw) {
+    const int tid = threadIdx.x;
+    const MeritRows mr = merit_rows(buf, N);
+    const float dt = P.dt, wc = P.C_cbf;
+    for (int t = tid; t < N; t += BLK) {
+        const float4 v4 = mr.vel[t];
+        const float vx = v4.x, vy = v4.y, r = v4.z;
+        float X = x0.X, Y = x0.Y, cp = x0.cp, sp = x0.sp;
+        if (t > 0) {
+            const float2 p = mr.pos[t - 1];
+            const float4 a = gw.tr.ang[t - 1];
+            X = p.x;
+            Y = p.y;
+            cp = a.y;
+            sp = a.z;
+        }
+        const float2 v = Vw[t];
+        const float d = clampf(v.x, P.umin0, P.umax0);
+        const float yf = fmaf(P.lf, r, vy), yr = fmaf(-P.lr, r, vy);
+        const float bf = atan2_poly(yf, vx), br = atan2_poly(yr, vx);
+        float dphf, dphr;
+        const float Fyf = P.Fzf * tyre_shape(P, P.B * (d - bf), &dphf);
+        tyre_shape(P, P.B * (-br), &dphr);
+        float sd, cd;
+        if (P.steer_small) sincos_half(d, &sd, &cd);
+        else sincosf(d, &sd, &cd);
+        const float dX = vx * cp - vy * sp, dY = vx * sp + vy * cp;
+        // lateral-force adjoints Fyf_b = a1 g_vx + a2 g_vy + a3 g_r, Fyr_b = b2 g_vy + b3 g_r;
+        // through the tyres and the slip angles they reach v_x (q), v_y and r (p)
+        const float kf = P.Fzf * dphf * P.B, kr = P.Fzr * dphr * P.B;
+        const float nf = fmaf(vx, vx, yf * yf), nr = fmaf(vx, vx, yr * yr);
+        const float pf = nf > 0.0f ? -kf * vx / nf : 0.0f, qf = nf > 0.0f ? kf * yf / nf : 0.0f;
+        const float pr = nr > 0.0f ? -kr * vx / nr : 0.0f, qr = nr > 0.0f ? kr * yr / nr : 0.0f;
+        const float a1 = -sd * P.m_inv, a2 = cd * P.m_inv, a3 = P.lf * cd * P.Iz_inv;
+        const float b2 = P.m_inv, b3 = -P.lr * P.Iz_inv;
+        const bool in0 = v.x >= P.umin0 && v.x <= P.umax0, in1 = v.y >= P.umin1 && v.y <= P.umax1;
+        float4* c = gw.coef + 5 * t;
+        c[0] = make_float4(dt * (qf * a1), dt * (-r + qf * a2 + qr * b2), dt * (qf * a3 + qr * b3),
+                           dt * (r + pf * a1));
+        c[1] = make_float4(dt * (pf * a2 + pr * b2), dt * (pf * a3 + pr * b3),
+                           dt * (vy + P.lf * pf * a1),
+                           dt * (-vx + P.lf * pf * a2 - P.lr * pr * b2));
+        c[2] = make_float4(dt * (P.lf * pf * a3 - P.lr * pr * b3), dt * cp, dt * sp, dt * dX);
+        c[3] = make_float4(dt * dY, in0 ? dt * (-Fyf * cd * P.m_inv + kf * a1) : 0.0f,
+                           in0 ? dt * (-Fyf * sd * P.m_inv + kf * a2) : 0.0f,
+                           in0 ? dt * (-P.lf * Fyf * sd * P.Iz_inv + kf * a3) : 0.0f);
+        // d_t (t >= 1): the penalties of the pairs (t - 1, t) and (t, t + 1) through e_y^2
+        float ddX = 0.0f, ddY = 0.0f;
+        if (t > 0) {
+            const float h = gw.tr.hh[t];
+            float ch = 0.0f;
+            if (cbf_arg(P, gw.tr.hh[t - 1], h) > 0.0f) ch -= wc;
+            if (cbf_arg(P, h, gw.tr.hh[t + 1]) > 0.0f) ch += wc * P.one_m_alpha;
+            const float2 ro = rec_offset(rec, min(max(gw.tr.sg[t], 0), P.n_track - 1), X, Y);
+            ddX = -2.0f * ch * ro.x;
+            ddY = -2.0f * ch * ro.y;
+        }
+        c[4] = make_float4(in1 ? dt * P.fx_gain * P.m_inv : 0.0f, ddX, ddY, 0.0f);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float lvx = 0.0f, lvy = 0.0f, lr = 0.0f, lX = 0.0f, lY = 0.0f, lp = 0.0f;
+        if (N > 0 && cbf_arg(P, gw.tr.hh[N - 1], gw.tr.hh[N]) > 0.0f) {   // lambda_N = d_N
+            const float2 p = mr.pos[N - 1];
+            const float2 ro = rec_offset(rec, min(max(gw.tr.sg[N], 0), P.n_track - 1), p.x, p.y);
+            lX = 2.0f * wc * ro.x;
+            lY = 2.0f * wc * ro.y;
+        }
+#pragma unroll 4
+        for (int t = N - 1; t >= 0; --t) {
+            const float4* c = gw.coef + 5 * t;
+            const float4 c0 = c[0], c1 = c[1], c2 = c[2], c3 = c[3], c4 = c[4];
+            G[t] = make_float2(fmaf(c3.y, lvx, fmaf(c3.z, lvy, c3.w * lr)), c4.x * lvx);
+            const float nvx = lvx + (fmaf(c0.x, lvx, c0.y * lvy) + fmaf(c0.z, lr, fmaf(c2.y, lX, c2.z * lY)));
+            const float nvy = lvy + (fmaf(c0.w, lvx, c1.x * lvy) + fmaf(c1.y, lr, fmaf(c2.y, lY, -c2.z * lX)));
+            const float nr = lr + (fmaf(c1.z, lvx, c1.w * lvy) + fmaf(c2.x, lr, dt * lp));
+            const float np = lp + fmaf(c2.w, lY, -c3.x * lX);
+            lX += c4.y;
+            lY += c4.z;
+            lvx = nvx;
+            lvy = nvy;
+            lr = nr;
+            lp = np;
+        }
+        for (int t = N; t < T; ++t) G[t] = make_float2(0.0f, 0.0f);
+    }
+    __syncthreads();
+}
+
 // Closed-loop step (Alg. 2 ExecuteCommand + warm start, Eq. 26), one thread:
 // x0 <- f(x0, clamp(v_exec)) + w_n, V <- shift(V).
 __device__ void closed_loop_step(const DevParams& P, const ApplyArgs& ap, float2 v_exec) {
@@ -495,14 +677,16 @@ struct RepairSmem {
 // largest accepted step is taken: the same iterate as sequential backtracking.
 // The gradient comes from thread 0 (seq_cost_grad).  merit_row (optional):
 // n_iters + 1 merits; *iters_done: iterations run (0: Vw is unchanged).  side:
-// run by an idle warp during the first merit pass (BLK >= 128).  Returns the
+// run by an idle warp during the first merit pass (BLK >= 128).  gw (C = 1.5
+// model, BLK >= 128): the gradient is formed by the block (block_cost_grad) from
+// the trajectory the merit pass keeps there, instead of by thread 0.  Returns the
 // final merit.
 template <int BLK, bool FAST = false, class Side = NoSide>
 __device__ double repair_in_block(const DevParams& P, const float4* rec,
                                   const State& x0, int s0, float2* Vw, float2* G, float* tape_s,
                                   int n_iters, int mode, float delta, int ck, double* merit_row,
                                   int* iters_done, unsigned* status, RepairSmem& sm,
-                                  const Side& side = Side()) {
+                                  const Side& side = Side(), const GradWs* gw = nullptr) {
     static_assert(BLK >= 128 || std::is_same<Side, NoSide>::value, "side work needs a fourth warp");
     const int T = P.T, N = P.N_r;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -510,9 +694,15 @@ __device__ double repair_in_block(const DevParams& P, const float4* rec,
     const Tape tape{tape_s, 1, 0};
     // every thread waits (bounded) for the follower's completion flag before it
     // reads the merit, so that the branch on P below is taken by the whole block
-    auto merit = [&](const auto& sd) {
+    // the first merit pass keeps no trajectory (most updates need no repair and
+    // keeping it costs that pass about 2 us); a repair's gradient first runs a
+    // pass that keeps it
+    const bool block_grad = FAST && BLK >= 128 && gw != nullptr;
+    bool traj_ok = false;   // the kept trajectory is that of the current Vw
+    auto merit = [&](const auto& sd, bool keep) {
         if (FAST && BLK >= 96)
-            merit_split3(P, rec, x0, s0, N, Vw, tape_s, sm.prog, &sm.P, &sm.done, status, sd);
+            merit_split3(P, rec, x0, s0, N, Vw, tape_s, sm.prog, &sm.P, &sm.done, status,
+                         (block_grad && keep) ? gw->tr : MeritTraj{}, sd);
         else
             merit_split<FAST>(P, rec, x0, s0, N, Vw, tape_s, sm.prog, &sm.P, &sm.done, status,
                               sd);
@@ -521,21 +711,28 @@ __device__ double repair_in_block(const DevParams& P, const float4* rec,
         __threadfence_block();
         __syncthreads();
     };
-    merit(side);
+    merit(side, false);
     double P0 = sm.P;
     int it = 0;
     bool stalled = false;
     for (; it < n_iters; ++it) {
         if (tid == 0 && merit_row) merit_row[it] = P0;
         if (P0 == 0.0) break;
-        if (tid == 0) seq_cost_grad<FAST>(P, rec, x0, s0, N, T, Vw, G, 1, 0, 0.0f, 1.0f, ck, tape);
-        __syncthreads();
+        if (block_grad) {
+            if (!traj_ok) merit(NoSide(), true);   // keeps the trajectory of the current iterate
+            traj_ok = true;
+            block_cost_grad<BLK>(P, rec, x0, N, T, Vw, G, tape_s, *gw);
+        } else {
+            if (tid == 0)
+                seq_cost_grad<FAST>(P, rec, x0, s0, N, T, Vw, G, 1, 0, 0.0f, 1.0f, ck, tape);
+            __syncthreads();
+        }
         if (mode == 0) {
             for (int t = tid; t < N; t += BLK)
                 Vw[t] = clamp2(P, make_float2(fmaf(-delta, G[t].x, Vw[t].x),
                                               fmaf(-delta, G[t].y, Vw[t].y)));
             __syncthreads();
-            merit(NoSide());
+            merit(NoSide(), true);
             P0 = sm.P;
             continue;
         }
@@ -578,6 +775,7 @@ __device__ double repair_in_block(const DevParams& P, const float4* rec,
             Vw[t] = clamp2(P, make_float2(fmaf(-sa, G[t].x, Vw[t].x), fmaf(-sa, G[t].y, Vw[t].y)));
         __syncthreads();
         P0 = sm.P;
+        traj_ok = false;
     }
     if (tid == 0) {
         if (merit_row)
