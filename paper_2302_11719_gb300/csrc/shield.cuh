@@ -509,12 +509,13 @@ __device__ double seq_cost_grad(const DevParams& P, const float4* rec,
 struct GradWs {
     MeritTraj tr;
     float4* coef;
+    float2* vt;     // [T] the controls of the line search's first trial
 };
 
 // Bytes of a GradWs for horizon T (with 16 bytes for alignment), and its
 // carving from the memory at p.
 __host__ __device__ constexpr size_t grad_ws_bytes(int T) {
-    return (size_t)T * 16 + (size_t)T * 80 + (size_t)(T + 1) * 8 + 16;
+    return (size_t)T * 16 + (size_t)T * 80 + (size_t)(T + 1) * 8 + (size_t)T * 8 + 16;
 }
 
 __device__ __forceinline__ GradWs grad_ws_at(unsigned char* p, int T) {
@@ -523,6 +524,7 @@ __device__ __forceinline__ GradWs grad_ws_at(unsigned char* p, int T) {
     g.coef = g.tr.ang + T;
     g.tr.sg = reinterpret_cast<int*>(g.coef + 5 * T);
     g.tr.hh = reinterpret_cast<float*>(g.tr.sg + T + 1);
+    g.vt = reinterpret_cast<float2*>(g.tr.hh + T + 1);
     return g;
 }
 
@@ -662,6 +664,7 @@ struct NoSide {
 // Shared-memory scratch of repair_in_block.
 struct RepairSmem {
     double P;
+    double dec;        // the Armijo decrease term of the first trial (block_grad)
     int prog[2];       // progress counters of merit_split / merit_split3
     int done;          // set by the merit follower once P is written
     float red[32];
@@ -699,19 +702,19 @@ __device__ double repair_in_block(const DevParams& P, const float4* rec,
     // pass that keeps it
     const bool block_grad = FAST && BLK >= 128 && gw != nullptr;
     bool traj_ok = false;   // the kept trajectory is that of the current Vw
-    auto merit = [&](const auto& sd, bool keep) {
+    auto merit = [&](const auto& sd, bool keep, const float2* ctrl) {
         if (FAST && BLK >= 96)
-            merit_split3(P, rec, x0, s0, N, Vw, tape_s, sm.prog, &sm.P, &sm.done, status,
+            merit_split3(P, rec, x0, s0, N, ctrl, tape_s, sm.prog, &sm.P, &sm.done, status,
                          (block_grad && keep) ? gw->tr : MeritTraj{}, sd);
         else
-            merit_split<FAST>(P, rec, x0, s0, N, Vw, tape_s, sm.prog, &sm.P, &sm.done, status,
+            merit_split<FAST>(P, rec, x0, s0, N, ctrl, tape_s, sm.prog, &sm.P, &sm.done, status,
                               sd);
         __syncthreads();
         if (!spin_until_geq(&sm.done, 1) && tid == 0) atomicOr(status, SMPPI_DEV_TIMEOUT);
         __threadfence_block();
         __syncthreads();
     };
-    merit(side, false);
+    merit(side, false, Vw);
     double P0 = sm.P;
     int it = 0;
     bool stalled = false;
@@ -719,7 +722,7 @@ __device__ double repair_in_block(const DevParams& P, const float4* rec,
         if (tid == 0 && merit_row) merit_row[it] = P0;
         if (P0 == 0.0) break;
         if (block_grad) {
-            if (!traj_ok) merit(NoSide(), true);   // keeps the trajectory of the current iterate
+            if (!traj_ok) merit(NoSide(), true, Vw);   // keeps the trajectory of the current iterate
             traj_ok = true;
             block_cost_grad<BLK>(P, rec, x0, N, T, Vw, G, tape_s, *gw);
         } else {
@@ -732,7 +735,7 @@ __device__ double repair_in_block(const DevParams& P, const float4* rec,
                 Vw[t] = clamp2(P, make_float2(fmaf(-delta, G[t].x, Vw[t].x),
                                               fmaf(-delta, G[t].y, Vw[t].y)));
             __syncthreads();
-            merit(NoSide(), true);
+            merit(NoSide(), true, Vw);
             P0 = sm.P;
             continue;
         }
@@ -748,11 +751,49 @@ __device__ double repair_in_block(const DevParams& P, const float4* rec,
         for (int w = 1; w < NW; ++w) gm = fmaxf(gm, sm.red[w]);
         if (!(gm > 0.0f)) { stalled = true; break; }
         const float s_first = P.ls_s0 / gm;
+        int j0 = 0;   // the first trial the lanes evaluate
+        if (block_grad && P.ls_max > 0) {
+            // the full step s_first (accepted in about two of three iterations) by the
+            // three-warp merit pass on the trial controls, whose kept trajectory then
+            // serves the next gradient; only when it is rejected do the lanes try the
+            // shorter steps (the same iterate as sequential backtracking)
+            float2* Vt = gw->vt;
+            float dpart = 0.0f;
+            for (int t = tid; t < N; t += BLK) {
+                const float2 v = Vw[t], g = G[t];
+                const float2 u = clamp2(P, make_float2(fmaf(-s_first, g.x, v.x),
+                                                       fmaf(-s_first, g.y, v.y)));
+                Vt[t] = u;
+                dpart = fmaf(g.x, v.x - u.x, fmaf(g.y, v.y - u.y, dpart));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dpart += __shfl_xor_sync(0xffffffffu, dpart, o);
+            __syncthreads();   // every thread has read sm.red for |g|_inf
+            if (lane == 0) sm.red[warp] = dpart;
+            __syncthreads();
+            if (tid == 0) {
+                double dec = 0.0;
+                for (int w = 0; w < NW; ++w) dec += (double)sm.red[w];
+                sm.dec = dec;
+            }
+            merit(NoSide(), true, Vt);
+            const double Pt = sm.P;
+            if (Pt <= P0 - (double)P.ls_c * sm.dec) {
+                for (int t = tid; t < N; t += BLK) Vw[t] = Vt[t];
+                __syncthreads();
+                P0 = Pt;
+                traj_ok = true;
+                continue;
+            }
+            traj_ok = false;
+            j0 = 1;
+        }
         if (warp == 0) {
-            // lane j tries s_first 2^-j (j = lane, lane + 32, ...); keep the smallest accepted j
+            // lane j tries s_first 2^-j (j = j0 + lane, j0 + lane + 32, ...); keep the
+            // smallest accepted j
             int best = 0x7fffffff;
             double best_P = 0.0;
-            for (int j = lane; j < P.ls_max; j += 32) {
+            for (int j = j0 + lane; j < P.ls_max; j += 32) {
                 const float sj = ldexpf(s_first, -j);
                 double dec;
                 const double Pt = forward_cost<false, true, FAST>(P, rec, x0, s0, N, Vw, G, sj, 1,
