@@ -83,6 +83,7 @@ __global__ void __launch_bounds__(RB) batch_kernel(DevParams P0, BatchArgs a) {
     int* l_k = reinterpret_cast<int*>(tape_s + (size_t)(Tm + 2) * NFIELD);
     float* l_w = reinterpret_cast<float*>(l_k + RB * BATCH_PPT);
     float* acc_s = l_w + RB * BATCH_PPT;                       // [2 Tm]
+    const GradWs gws = grad_ws_at(reinterpret_cast<unsigned char*>(acc_s + 2 * Tm), Tm);
     __shared__ __align__(8) uint64_t bar;
     __shared__ RepairSmem rsm;
     __shared__ float red_f[NW];
@@ -310,7 +311,7 @@ __global__ void __launch_bounds__(RB) batch_kernel(DevParams P0, BatchArgs a) {
         State xr = make_state(a.x0 + 6 * i);
         if (a.n_repair > 0)
             repair_in_block<RB, FAST>(P, rec, xr, s0, Vw, G, tape_s, a.n_repair, 1, 0.0f, a.ck,
-                                nullptr, nullptr, a.status, rsm);
+                                nullptr, nullptr, a.status, rsm, NoSide(), &gws);
         float2* Vsafe = reinterpret_cast<float2*>(a.V_safe) + D.V_off;
         for (int t = tid; t < T; t += RB) Vsafe[t] = Vw[t];
         // ---- closed loop: x0 <- f(x0, v0_safe) + w (Eq. 26), V <- shift(V+) ----
@@ -432,7 +433,8 @@ smppi_status bfail(smppi_batch* b, smppi_status s, const std::string& m) {
 
 size_t batch_smem(int RB, int n_track_max, int T_max) {
     return rec_table_bytes(n_track_max) + (size_t)T_max * 32 + (size_t)T_max * 8 * 3 +
-           (size_t)(T_max + 2) * NFIELD * 4 + (size_t)RB * BATCH_PPT * 8 + (size_t)T_max * 2 * 4;
+           (size_t)(T_max + 2) * NFIELD * 4 + (size_t)RB * BATCH_PPT * 8 + (size_t)T_max * 2 * 4 +
+           grad_ws_bytes(T_max);
 }
 
 template <bool FAST>
