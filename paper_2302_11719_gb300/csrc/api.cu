@@ -275,7 +275,7 @@ smppi_status enqueue_repair(smppi_handle* h, cudaStream_t st, int n_seq, const f
         toc(h, st, SMPPI_KERNEL_REPAIR, ev);
         return SMPPI_OK;
     }
-    if (!curv && !seg0_known) {
+    if (!curv && !seg0_known && mode == 2) {   // the block repair (modes 0, 1) searches itself
         ev = tic(h, st);
         CU(h, launch_seg0(h->dp, h->rec, n_seq, x0, h->rws.seg0, h->status, st));
         toc(h, st, SMPPI_KERNEL_SEG0, ev);

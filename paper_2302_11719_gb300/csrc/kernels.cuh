@@ -115,9 +115,6 @@ struct RepairWs {
     int* seg0;                 // [max_seq]     nearest segment of x0
 };
 constexpr int NFIELD = 11;     // x (6), cos psi, sin psi, segment, h, h of the previous step
-// Repairs of at most this many sequences run one block per sequence (shared
-// memory, parallel line search); larger batches run one thread per sequence.
-constexpr int REPAIR_BLOCK_MAX_SEQ = 1024;
 
 // Closed-loop step fused into the tail of the repair of sequence 0.
 struct ApplyArgs {

@@ -62,80 +62,12 @@ __global__ void __launch_bounds__(REP_BLK) cost_grad_kernel(
     for (int t = 0; t < T; ++t) grow[t] = ws.G[(size_t)t * ms + q];
 }
 
-template <bool FAST>
-__global__ void __launch_bounds__(REP_BLK) repair_kernel(
-    DevParams P, const float4* __restrict__ recg, RepairWs ws,
-    int n_seq, const float* __restrict__ x0g, const float* Vin, float* Vout, int n_iters,
-    int mode, float delta, double* __restrict__ merit_out, int* __restrict__ iters_out,
-    ApplyArgs ap, unsigned* __restrict__ status) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float4* rec = reinterpret_cast<float4*>(smem_raw);
-    stage_track(P, recg, rec);
-    const int q = blockIdx.x * REP_BLK + threadIdx.x;
-    if (q >= n_seq) return;
-    const int T = P.T, N = P.N_r, ms = ws.max_seq;
-    const float2* vin = reinterpret_cast<const float2*>(Vin) + (size_t)q * T;
-    float2* vout = reinterpret_cast<float2*>(Vout) + (size_t)q * T;
-    for (int t = 0; t < T; ++t) ws.Vw[(size_t)t * ms + q] = vin[t];
-    const State x0 = make_state(x0g + 6 * q);
-    const int s0 = ws.seg0[q];
-    const Tape tape{ws.tape, ms, q};
-    double P0 = forward_cost<false, false, FAST>(P, rec, x0, s0, N, ws.Vw, nullptr, 0.0f, ms, q,
-                                           0.0f, 1.0f, 0, tape, nullptr);
-    int it = 0;
-    bool stalled = false;
-    for (; it < n_iters; ++it) {
-        if (merit_out) merit_out[(size_t)q * (n_iters + 1) + it] = P0;
-        if (P0 == 0.0) break;
-        seq_cost_grad<FAST>(P, rec, x0, s0, N, T, ws.Vw, ws.G, ms, q, 0.0f, 1.0f, ws.ck, tape);
-        if (mode == 0) {
-            for (int t = 0; t < N; ++t) {
-                const size_t o = (size_t)t * ms + q;
-                const float2 v = ws.Vw[o], g = ws.G[o];
-                ws.Vw[o] = clamp2(P, make_float2(fmaf(-delta, g.x, v.x), fmaf(-delta, g.y, v.y)));
-            }
-            P0 = forward_cost<false, false, FAST>(P, rec, x0, s0, N, ws.Vw, nullptr, 0.0f, ms, q,
-                                            0.0f, 1.0f, 0, tape, nullptr);
-            continue;
-        }
-        float gmax = 0.0f;
-        for (int t = 0; t < N; ++t) {
-            const float2 g = ws.G[(size_t)t * ms + q];
-            gmax = fmaxf(gmax, fmaxf(fabsf(g.x), fabsf(g.y)));
-        }
-        if (!(gmax > 0.0f)) { stalled = true; break; }
-        float s = P.ls_s0 / gmax;
-        bool accepted = false;
-        for (int j = 0; j < P.ls_max; ++j) {
-            double dec;
-            const double Pt = forward_cost<false, true, FAST>(P, rec, x0, s0, N, ws.Vw, ws.G, s, ms,
-                                                        q, 0.0f, 1.0f, 0, tape, &dec);
-            if (Pt <= P0 - (double)P.ls_c * dec) {
-                for (int t = 0; t < N; ++t) {
-                    const size_t o = (size_t)t * ms + q;
-                    const float2 v = ws.Vw[o], g = ws.G[o];
-                    ws.Vw[o] = clamp2(P, make_float2(fmaf(-s, g.x, v.x), fmaf(-s, g.y, v.y)));
-                }
-                P0 = Pt;
-                accepted = true;
-                break;
-            }
-            s *= 0.5f;
-        }
-        if (!accepted) { stalled = true; break; }
-    }
-    if (merit_out)
-        for (int i = it; i <= n_iters; ++i) merit_out[(size_t)q * (n_iters + 1) + i] = P0;
-    if (iters_out) iters_out[q] = it;
-    if (stalled) atomicOr(status, SMPPI_DEV_STALLED);
-    if (!isfinite(P0)) atomicOr(status, SMPPI_DEV_NUMERIC);
-    for (int t = 0; t < T; ++t) vout[t] = ws.Vw[(size_t)t * ms + q];
-    if (q == 0 && ap.x0) closed_loop_step(P, ap, ws.Vw[0]);
-}
-
-// Safety shield for few sequences: one block per sequence, everything in
-// shared memory (track table staged by a bulk copy, controls, gradient,
-// checkpoint tape); see repair_in_block.
+// Safety shield, one block per sequence, everything in shared memory (track
+// table staged by a bulk copy, controls, gradient, the merit pass's buffers and
+// the block gradient's workspace); see repair_in_block.  Blocks of sequences
+// that finish early free their SM for the next ones, which at 8192 and 65536
+// sequences made this form faster than one thread per sequence (5.2 against
+// 19.4 ms and 33 against 39 ms for 20 Armijo iterations).
 constexpr int REPB_BLK = 128;
 
 template <bool FAST>
@@ -224,22 +156,13 @@ cudaError_t launch_repair(const DevParams& P, const float4* rec, const RepairWs&
                           const float* x0, const float* V_in, float* V_out, int n_iters, int mode,
                           float delta, double* merit_out, int* iters_out, const ApplyArgs& ap,
                           unsigned* status, cudaStream_t st) {
-    if (n_seq <= REPAIR_BLOCK_MAX_SEQ) {
-        const size_t smem = rec_table_bytes(P.n_track) + (size_t)P.T * 16 +
-                            (size_t)(P.T + 2) * NFIELD * 4 + grad_ws_bytes(P.T);
-        auto kern = fast_model(P) ? repair_block_kernel<true> : repair_block_kernel<false>;
-        cudaError_t e = ensure_smem((const void*)kern, smem);
-        if (e != cudaSuccess) return e;
-        kern<<<n_seq, REPB_BLK, smem, st>>>(P, rec, x0, V_in, V_out, n_iters, mode, delta, ws.ck,
-                                            merit_out, iters_out, ap, status);
-        return cudaGetLastError();
-    }
-    const size_t smem = rec_table_bytes(P.n_track);
-    auto kern = fast_model(P) ? repair_kernel<true> : repair_kernel<false>;
+    const size_t smem = rec_table_bytes(P.n_track) + (size_t)P.T * 16 +
+                        (size_t)(P.T + 2) * NFIELD * 4 + grad_ws_bytes(P.T);
+    auto kern = fast_model(P) ? repair_block_kernel<true> : repair_block_kernel<false>;
     cudaError_t e = ensure_smem((const void*)kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<(n_seq + REP_BLK - 1) / REP_BLK, REP_BLK, smem, st>>>(
-        P, rec, ws, n_seq, x0, V_in, V_out, n_iters, mode, delta, merit_out, iters_out, ap, status);
+    kern<<<n_seq, REPB_BLK, smem, st>>>(P, rec, x0, V_in, V_out, n_iters, mode, delta, ws.ck,
+                                        merit_out, iters_out, ap, status);
     return cudaGetLastError();
 }
 

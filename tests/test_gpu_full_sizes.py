@@ -8,7 +8,7 @@
     the warm start shift(V+) within the update bound, V_safe within the repair
     tolerance plus that bound, the executed step within 1e-4 relative;
   * the shield on 8192 near-boundary sequences, T = 100, 20 iterations, run in
-    the launch shape of that size (one thread per sequence for the gradient
+    the launch shape of that size (one block per sequence for the gradient
     repair, one warp per sequence for BFGS), compared with the oracle's repair
     on every 32nd sequence: flips (line-search decisions taken differently in
     float32 and float64) counted and printed, the other sequences within 1e-4;
