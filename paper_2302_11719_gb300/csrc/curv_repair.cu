@@ -8,7 +8,9 @@
 //
 // Kernels:
 //   curv_repair_kernel       modes 0 and 1, one block per sequence: thread 0
-//                            runs the forward pass and the adjoint, the lanes of
+//                            runs the forward pass, the block forms the adjoint's
+//                            coefficients and thread 0 its recursion
+//                            (curv_block_grad), the lanes of
 //                            warp 0 evaluate the trial steps s, s/2, ... in
 //                            parallel and the largest accepted step is taken
 //                            (the same iterate as sequential backtracking);
@@ -219,6 +221,108 @@ __device__ double curv_merit_grad(const DevParams& P, const float* kt, const Sta
     return J;
 }
 
+// Gradient G of the merit (running-cost weight 0, CBF weight 1) of Vw by a
+// block of BLK threads: thread 0 runs the forward pass into the tape, every
+// thread forms the coefficients of its steps' adjoint map, and thread 0 runs
+// the recursion over (v_x, v_y, r, s, e_y, e_psi).  The adjoint of the Euler
+// step is linear in the adjoint, lambda_t = lambda_{t+1} + E_t' lambda_{t+1}
+// + d_t and g_t = B_t' lambda_{t+1}; E_t and B_t are the derivatives of
+// model_step_adjoint_curv at (x_t, u_t) scaled by dt, collected per step (the
+// velocity block as the Cartesian block gradient, the Frenet kinematics through
+// (s, e_y, e_psi)), d_t the CBF penalties' derivative at x_t.  coef: 7 float4
+// per step.  G_t = 0 for N <= t < T and outside the box.
+template <int BLK>
+__device__ void curv_block_grad(const DevParams& P, const float* kt, const State& x0, int N,
+                                int T, const float2* Vw, float2* G, float* tape, float4* coef) {
+    const int tid = threadIdx.x;
+    if (tid == 0)
+        curv_forward<true, false>(P, kt, x0, N, Vw, nullptr, 0.0f, tape, nullptr, 0.0f, 1.0f);
+    __syncthreads();
+    const float dt = P.dt, wc = P.C_cbf;
+    auto h_at = [&](int t) { return tape[(size_t)t * CR_NF + 8]; };
+    for (int t = tid; t < N; t += BLK) {
+        const State x = tape_state(tape, t);
+        const float2 v = Vw[t];
+        const float d = clampf(v.x, P.umin0, P.umax0);
+        // velocity part: v_x, v_y, r through the tyre forces (as the Cartesian model)
+        const float yf = fmaf(P.lf, x.r, x.vy), yr = fmaf(-P.lr, x.r, x.vy);
+        const float bf = atan2_poly(yf, x.vx), br = atan2_poly(yr, x.vx);
+        float dphf, dphr;
+        const float Fyf = P.Fzf * tyre_shape(P, P.B * (d - bf), &dphf);
+        tyre_shape(P, P.B * (-br), &dphr);
+        float sd, cd;
+        sincos_half(d, &sd, &cd);
+        const float kf = P.Fzf * dphf * P.B, kr = P.Fzr * dphr * P.B;
+        const float nf = fmaf(x.vx, x.vx, yf * yf), nr = fmaf(x.vx, x.vx, yr * yr);
+        const float pf = nf > 0.0f ? -kf * x.vx / nf : 0.0f, qf = nf > 0.0f ? kf * yf / nf : 0.0f;
+        const float pr = nr > 0.0f ? -kr * x.vx / nr : 0.0f, qr = nr > 0.0f ? kr * yr / nr : 0.0f;
+        const float a1 = -sd * P.m_inv, a2 = cd * P.m_inv, a3 = P.lf * cd * P.Iz_inv;
+        const float b2 = P.m_inv, b3 = -P.lr * P.Iz_inv;
+        const bool in0 = v.x >= P.umin0 && v.x <= P.umax0, in1 = v.y >= P.umin1 && v.y <= P.umax1;
+        // kinematics: s' = num / den, e_y' = eyd, e_psi' = r - kappa s'
+        const float cp = x.cp, sp = x.sp;
+        const float k = kappa_at(P, kt, x.X);
+        const float den_raw = fmaf(-k, x.Y, 1.0f);
+        const float den = fmaxf(den_raw, 0.1f), id = 1.0f / den;
+        const float num = x.vx * cp - x.vy * sp, eyd = x.vx * sp + x.vy * cp;
+        const float sdot = num * id;
+        const float g1 = den_raw > 0.1f ? 1.0f : 0.0f;   // the guard has no derivative
+        const float ks = kappa_slope(P, kt, x.X);
+        float4* c = coef + 7 * t;
+        c[0] = make_float4(dt * (qf * a1), dt * (-x.r + qf * a2 + qr * b2),
+                           dt * (qf * a3 + qr * b3), dt * (x.r + pf * a1));
+        c[1] = make_float4(dt * (pf * a2 + pr * b2), dt * (pf * a3 + pr * b3),
+                           dt * (x.vy + P.lf * pf * a1),
+                           dt * (-x.vx + P.lf * pf * a2 - P.lr * pr * b2));
+        c[2] = make_float4(dt * (P.lf * pf * a3 - P.lr * pr * b3), dt * cp * id, dt * sp,
+                           -dt * cp * k * id);
+        c[3] = make_float4(-dt * sp * id, dt * cp, dt * sp * k * id,
+                           dt * ks * g1 * x.Y * sdot * id);
+        c[4] = make_float4(dt * ks * (-sdot - g1 * x.Y * k * sdot * id), dt * g1 * k * sdot * id,
+                           -dt * g1 * k * k * sdot * id, -dt * eyd * id);
+        c[5] = make_float4(dt * num, dt * eyd * k * id,
+                           in0 ? dt * (-Fyf * cd * P.m_inv + kf * a1) : 0.0f,
+                           in0 ? dt * (-Fyf * sd * P.m_inv + kf * a2) : 0.0f);
+        float dey = 0.0f;   // d_t (t >= 1): the penalties of the pairs (t - 1, t) and (t, t + 1)
+        if (t > 0) {
+            const float w = (cbf_arg(P, h_at(t - 1), h_at(t)) > 0.0f ? -wc : 0.0f) +
+                            (cbf_arg(P, h_at(t), h_at(t + 1)) > 0.0f ? wc * P.one_m_alpha : 0.0f);
+            dey = w * (-2.0f * x.Y);
+        }
+        c[6] = make_float4(in0 ? dt * (-P.lf * Fyf * sd * P.Iz_inv + kf * a3) : 0.0f,
+                           in1 ? dt * P.fx_gain * P.m_inv : 0.0f, dey, 0.0f);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float lvx = 0.0f, lvy = 0.0f, lr = 0.0f, ls = 0.0f, ley = 0.0f, lep = 0.0f;
+        if (N > 0 && cbf_arg(P, h_at(N - 1), h_at(N)) > 0.0f)   // lambda_N = d_N
+            ley = -wc * (-2.0f * tape[(size_t)N * CR_NF + 4]);
+#pragma unroll 4
+        for (int t = N - 1; t >= 0; --t) {
+            const float4* c = coef + 7 * t;
+            const float4 c0 = c[0], c1 = c[1], c2 = c[2], c3 = c[3], c4 = c[4], c5 = c[5],
+                         c6 = c[6];
+            G[t] = make_float2(fmaf(c5.z, lvx, fmaf(c5.w, lvy, c6.x * lr)), c6.y * lvx);
+            const float nvx = lvx + (fmaf(c0.x, lvx, c0.y * lvy) + c0.z * lr +
+                                     fmaf(c2.y, ls, fmaf(c2.z, ley, c2.w * lep)));
+            const float nvy = lvy + (fmaf(c0.w, lvx, c1.x * lvy) + c1.y * lr +
+                                     fmaf(c3.x, ls, fmaf(c3.y, ley, c3.z * lep)));
+            const float nr = lr + (fmaf(c1.z, lvx, c1.w * lvy) + fmaf(c2.x, lr, dt * lep));
+            const float ns = ls + fmaf(c3.w, ls, c4.x * lep);
+            const float ney = ley + fmaf(c4.y, ls, c4.z * lep) + c6.z;
+            const float nep = lep + (fmaf(c4.w, ls, c5.x * ley) + c5.y * lep);
+            lvx = nvx;
+            lvy = nvy;
+            lr = nr;
+            ls = ns;
+            ley = ney;
+            lep = nep;
+        }
+        for (int t = N; t < T; ++t) G[t] = make_float2(0.0f, 0.0f);
+    }
+    __syncthreads();
+}
+
 // The merit of the curvilinear state from x0 for the BFGS solver (bfgs.cuh):
 // curv_forward and curv_merit_grad with the warp's full tape.
 struct CurvMerit {
@@ -265,6 +369,8 @@ __global__ void __launch_bounds__(CR_BLK) curv_repair_kernel(
     float2* G = Vw + T;
     float* kt = reinterpret_cast<float*>(G + T);
     float* tape = kt + ((n + 1 + 3) & ~3);
+    float4* coef = reinterpret_cast<float4*>(
+        (reinterpret_cast<uintptr_t>(tape + (size_t)(T + 1) * CR_NF) + 15) & ~uintptr_t(15));
     __shared__ CurvSmem sm;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NW = CR_BLK / 32;
@@ -283,8 +389,7 @@ __global__ void __launch_bounds__(CR_BLK) curv_repair_kernel(
     for (; it < n_iters; ++it) {
         if (tid == 0 && mrow) mrow[it] = P0;
         if (P0 == 0.0) break;
-        if (tid == 0) curv_merit_grad(P, kt, x0, N, T, Vw, G, tape);
-        __syncthreads();
+        curv_block_grad<CR_BLK>(P, kt, x0, N, T, Vw, G, tape, coef);
         if (mode == 0) {
             for (int t = tid; t < N; t += CR_BLK)
                 Vw[t] = clamp2(P, make_float2(fmaf(-delta, G[t].x, Vw[t].x),
@@ -394,7 +499,7 @@ cudaError_t launch_repair_curv(const DevParams& P, const float* kappa, int n_seq
                                int mode, float delta, double* merit_out, int* iters_out,
                                const ApplyArgs& ap, unsigned* status, cudaStream_t st) {
     const size_t smem = (size_t)P.T * 16 + (size_t)((P.n_track + 1 + 3) & ~3) * 4 +
-                        (size_t)(P.T + 1) * CR_NF * 4;
+                        (size_t)(P.T + 1) * CR_NF * 4 + 16 + (size_t)P.T * 7 * 16;
     cudaError_t e = ensure_smem((const void*)curv_repair_kernel, smem);
     if (e != cudaSuccess) return e;
     curv_repair_kernel<<<n_seq, CR_BLK, smem, st>>>(P, kappa, x0, V_in, V_out, n_iters, mode,
