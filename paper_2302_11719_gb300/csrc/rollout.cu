@@ -437,7 +437,9 @@ __device__ __forceinline__ void shield_tail(const DevParams& P, unsigned char* s
                                             uint64_t* bar, const float2* Vplus, float* V,
                                             uint32_t iter, uint32_t n_upd, uint32_t* iter_dev,
                                             const ShieldTail& sh, unsigned* status,
-                                            bool block_grad = false) {
+                                            bool block_grad = false,
+                                            const float* x0_in = nullptr,
+                                            const int* seg0_in = nullptr) {
     __shared__ int s_fail, s_iters;
     __shared__ float s_xn[6];
     __shared__ RepairSmem rsm;
@@ -465,12 +467,13 @@ __device__ __forceinline__ void shield_tail(const DevParams& P, unsigned char* s
     }
     for (int t = tid; t < T; t += BLK) Vw[t] = Vplus[t];
     __syncthreads();
-    const State x0 = make_state(sh.x0);
+    const State x0 = make_state(x0_in ? x0_in : sh.x0);   // x0_in: already loaded
     float2* Vs_out = reinterpret_cast<float2*>(sh.V_safe);
     float2* V2 = reinterpret_cast<float2*>(V);
     if (sh.n_repair > 0) {
         const TailSide side{&P, Vplus, Vs_out, V2, x0, iter, sh.ctr3_dist, s_xn};
-        repair_in_block<BLK, FAST>(P, rec, x0, sh.seg0[0], Vw, G2, tape_s, sh.n_repair, 1, 0.0f,
+        repair_in_block<BLK, FAST>(P, rec, x0, seg0_in ? *seg0_in : sh.seg0[0], Vw, G2, tape_s,
+                                   sh.n_repair, 1, 0.0f,
                                    sh.ck, sh.merit_out, &s_iters, status, rsm, side,
                                    block_grad ? &gws : nullptr);
         if (s_iters != 0) {   // V+ was repaired: V_safe and the step from the new controls
@@ -515,7 +518,7 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_update_kernel(
     __shared__ int l_k[UPD_LIST];
     __shared__ float l_w[UPD_LIST];
     __shared__ int w_cnt[NW];
-    __shared__ float acc_s[2 * SMPPI_MAX_T];
+    __shared__ __align__(16) float acc_s[2 * SMPPI_MAX_T];   // read as float2 by the shield
     __shared__ bool s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int K = P.K, T = P.T, T2 = 2 * T, npair = (T + 1) >> 1;
@@ -709,7 +712,7 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_merge_shield_kernel(
     __shared__ __align__(8) uint64_t bar;
     __shared__ float s_c[MERGE_MAX_BLOCKS];
     __shared__ int l_b[MERGE_MAX_BLOCKS];
-    __shared__ float vplus[2 * SMPPI_MAX_T];
+    __shared__ __align__(16) float vplus[2 * SMPPI_MAX_T];   // read as float2 by the shield
     __shared__ float red_f[NW];
     __shared__ double red_d[NW];
     __shared__ int w_cnt[NW];
@@ -737,6 +740,13 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_merge_shield_kernel(
         eb[u] = b < nb ? __ldcg(&part.eta[b]) : 0.0;
         hb[u] = b < nb ? __ldcg(&part.has[b]) : 0;
     }
+    // loaded in the same round trip and used only later: V (the first control of
+    // this thread), x0 and the start segment of the shield
+    const float v_pre = tid < T2 ? __ldcg(&V[tid]) : 0.0f;
+    float x0r[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) x0r[i] = __ldcg(&sh.x0[i]);
+    const int seg0r = __ldcg(sh.seg0);
     // m = min_b m_b
     float m = mb[0];
 #pragma unroll
@@ -813,12 +823,13 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_merge_shield_kernel(
         }
         for (; i < nz; ++i) add(s_c[l_b[i]], __ldcg(&part.acc[(size_t)l_b[i] * T2 + j]));
         const float lo = (j & 1) ? P.umin1 : P.umin0, hi = (j & 1) ? P.umax1 : P.umax0;
-        const float v = (float)fma((double)__fadd_rn(A, cmp), inv_eta, (double)V[j]);
+        const float vj = j == tid ? v_pre : V[j];
+        const float v = (float)fma((double)__fadd_rn(A, cmp), inv_eta, (double)vj);
         if (!isfinite(v)) atomicOr(status, SMPPI_DEV_NUMERIC);
         vplus[j] = clampf(v, lo, hi);
     }
     shield_tail<UPD_BLK, FAST>(P, smem_raw, &bar, reinterpret_cast<const float2*>(vplus), V, iter,
-                               n_upd, iter_dev, sh, status, true);
+                               n_upd, iter_dev, sh, status, true, x0r, &seg0r);
 }
 
 // Control noise exactly as the rollout kernels draw it (test access).

@@ -105,6 +105,36 @@ def test_shield_update_full_size(S, orc, K):
     assert ex <= X_REL
 
 
+@pytest.mark.parametrize("T,K", [(1, 1 << 19), (2, 1 << 19), (51, 65536), (255, 16384),
+                                 (256, 16384), (511, 8192), (512, 8192)])
+def test_shield_update_horizons(S, orc, T, K):
+    # the merge of the block partials at horizons from 1 to SMPPI_MAX_T (one
+    # control per thread up to 2T = 256, several beyond) and from 32 to 2048
+    # rollout blocks, against the oracle's V+ (the warm start shift(V+) within the
+    # update bound), and V_safe = V+ where no repair ran
+    pr = I.throughput_problem(K, T)
+    it, inst = 2, 1
+    ctl = S.Controller(pr.params, pr.track)
+    x0, V = ctl.tensor(pr.x0), ctl.tensor(pr.V)
+    Vs = torch.empty_like(V)
+    mer = torch.empty(11, dtype=torch.float64, device="cuda")
+    S.smppi_shield_update(ctl.h, x0, V, Vs, it, inst, 10, mer)
+    st, _ = ctl.sync_status()
+    assert st in (S.OK, S.ERR_STALLED), st
+    Vg, Vsg = V.cpu().numpy().astype(np.float64), Vs.cpu().numpy().astype(np.float64)
+    ctl.close()
+    m = orc.Model(pr.params, pr.track)
+    So, Vp = orc.mppi_step(m, pr.x0, pr.V, it, inst, nthreads=N_THREADS)
+    tol = _bound_top(orc, m, So, pr.V, Vp, it, inst, pr.params["lam"])
+    tol_sh = np.concatenate([tol[1:], tol[-1:]])
+    e_sh = np.abs(Vg - orc.shift(m, Vp))
+    print("shield update K=%d T=%d: max |shift(V+) err| %.2e (bound %.2e..%.2e)"
+          % (K, T, e_sh.max(), tol.min(), tol.max()))
+    assert np.all(e_sh <= tol_sh) and e_sh.max() <= V_UPD
+    if mer.cpu().numpy()[0] == 0.0:      # V+ already safe: V_safe is V+ itself
+        assert np.all(np.abs(Vsg - Vp) <= tol)
+
+
 def _repair_sample(S, orc, mode):
     sb = I.near_boundary_sequences(8192, 100, seed=0)
     n = sb.x0.shape[0]
