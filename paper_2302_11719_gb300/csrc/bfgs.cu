@@ -3,8 +3,9 @@
 // projected path, binding coordinates held, gradient-step restarts) is stated
 // with smppi_repair's mode 2 in smppi.h.
 //
-// One WARP per sequence: lane 0 computes the adjoint gradient (seq_cost_grad,
-// a serial chain), the lanes evaluate the line-search trials a = 1, 1/2, ...
+// One WARP per sequence: the warp computes the adjoint gradient (lane 0 the
+// forward pass into the tape and the recursion, the lanes the coefficients of
+// the steps' adjoint maps, tape_cost_grad), the lanes evaluate the line-search trials a = 1, 1/2, ...
 // in parallel (the largest accepted a is taken: the same iterate as
 // sequential backtracking), and the O(n^2) parts (H y, H_FF g_F, the rank-two
 // update, n = 2 N_r) are spread over the lanes.  A block holds a few warps
@@ -29,20 +30,28 @@
 namespace smppi {
 namespace {
 
-// The merit of the Cartesian state from x0 (nearest segment s0): forward_cost
-// and seq_cost_grad with the warp's tape (checkpoint interval ck).
+// The merit of the Cartesian state from x0 (nearest segment s0): forward_cost,
+// and its gradient from the warp's full tape by the warp (tape_cost_grad; the
+// C = 1.5, small-steer model) or by lane 0 alone (seq_cost_grad, checkpoint
+// interval ck).
 template <bool FAST>
 struct CartMerit {
     const float4* rec;
     State x0;
     int s0, ck;
     Tape tape;
+    float4* coef;   // 5 float4 per step
     __device__ __forceinline__ double merit(const DevParams& P, const float2* Vw) const {
         return forward_cost<false, false, FAST>(P, rec, x0, s0, P.N_r, Vw, nullptr, 0.0f, 1, 0, 0.0f,
                                                 1.0f, 0, tape, nullptr);
     }
     __device__ __forceinline__ void grad(const DevParams& P, const float2* Vw, float2* G) const {
-        seq_cost_grad<FAST>(P, rec, x0, s0, P.N_r, P.T, Vw, G, 1, 0, 0.0f, 1.0f, ck, tape);
+        const int lane = threadIdx.x & 31;
+        if (FAST)
+            tape_cost_grad<FAST>(P, rec, x0, s0, P.N_r, P.T, Vw, G, tape, coef, lane, 32,
+                                 []() { __syncwarp(); });
+        else if (lane == 0)
+            seq_cost_grad<FAST>(P, rec, x0, s0, P.N_r, P.T, Vw, G, 1, 0, 0.0f, 1.0f, ck, tape);
     }
     __device__ __forceinline__ double trial(const DevParams& P, const float2* Vw, const float2* G,
                                             const float2* Dn, float a, double* dec) const {
@@ -54,14 +63,18 @@ struct CartMerit {
 }  // namespace
 
 // Bytes of one warp's shared-memory region for horizon T (a multiple of 8, so
-// every warp's float2 arrays stay aligned): the solver's arrays and the tape,
-// padded to 16 bytes.
+// every warp's float2 arrays stay aligned): the solver's arrays, the tape
+// padded to 16 bytes, and the gradient's coefficients (5 float4 per step, at the
+// next 16-byte boundary).
+__host__ __device__ inline size_t bfgs_tape_bytes(int T) {
+    return (((size_t)(T + 2) * NFIELD * 4) + 15) & ~size_t(15);
+}
 __host__ __device__ inline size_t bfgs_warp_bytes(int T) {
-    return bfgs_array_bytes(T) + ((((size_t)(T + 2) * NFIELD * 4) + 15) & ~size_t(15));
+    return bfgs_array_bytes(T) + bfgs_tape_bytes(T) + (size_t)T * 80 + 16;
 }
 
 template <bool FAST>
-__global__ void __launch_bounds__(32 * BFGS_WPB_MAX) repair_bfgs_kernel(
+__global__ void __launch_bounds__(32 * BFGS_WPB_MAX, 2) repair_bfgs_kernel(
     DevParams P, const float4* __restrict__ recg, const float* __restrict__ x0g, const float* Vin,
     float* Vout, int n_seq, int n_iters, int ck, float* __restrict__ Hws,
     unsigned* __restrict__ next, double* __restrict__ merit_out, int* __restrict__ iters_out,
@@ -73,6 +86,9 @@ __global__ void __launch_bounds__(32 * BFGS_WPB_MAX) repair_bfgs_kernel(
     unsigned char* wbase = smem_raw + rec_table_bytes(nt) + (size_t)warp * bfgs_warp_bytes(T);
     const BfgsArrays a = bfgs_arrays(wbase, T);
     float* tape_s = reinterpret_cast<float*>(wbase + bfgs_array_bytes(T));
+    float4* coef = reinterpret_cast<float4*>(
+        (reinterpret_cast<uintptr_t>(wbase + bfgs_array_bytes(T) + bfgs_tape_bytes(T)) + 15) &
+        ~uintptr_t(15));
     float* H = Hws + ((size_t)blockIdx.x * wpb + warp) * n * n;
 
     for (int i = threadIdx.x; i < 3 * (nt + 5); i += blockDim.x) rec[i] = recg[i];
@@ -96,7 +112,7 @@ __global__ void __launch_bounds__(32 * BFGS_WPB_MAX) repair_bfgs_kernel(
         warp_argmin(bd, s0);
         s0 = seg_or_zero(s0, nt, lane == 0 ? status : nullptr);
         __syncwarp();
-        const CartMerit<FAST> f{rec, x0, s0, ck, Tape{tape_s, 1, 0}};
+        const CartMerit<FAST> f{rec, x0, s0, ck, Tape{tape_s, 1, 0}, coef};
         double P0;
         bool stalled;
         const int it = bfgs_solve(P, f, a, H, n_iters,

@@ -6,15 +6,17 @@
 // curv_repair.cu: curvilinear state); what differs between them is the merit,
 // supplied as an object with
 //   double merit(P, Vw)                         lane 0: P(Vw)
-//   void   grad(P, Vw, G)                       lane 0: G = dP/dV at Vw, 0 past N_r
-//                                               and for controls outside the box
+//   void   grad(P, Vw, G)                       all lanes: G = dP/dV at Vw, 0 past
+//                                               N_r and for controls outside the box
 //   double trial(P, Vw, G, Dn, a, &dec)         any lane: P(u), u = clip(Vw - a Dn),
 //                                               dec = G . (Vw - u)
 //
-// Lane 0 computes the gradient (a serial chain), the lanes evaluate the
-// line-search trials a = 1, 1/2, ... in parallel (the largest accepted a is
-// taken: the same iterate as sequential backtracking), and the O(n^2) parts
-// (H y, H_FF g_F, the rank-two update, n = 2 N_r) are spread over the lanes.
+// The warp computes the gradient (lane 0 the forward pass and the adjoint
+// recursion, the lanes the coefficients of the steps' adjoint maps), the lanes
+// evaluate the line-search trials a = 1, 1/2, ... in parallel (the largest
+// accepted a is taken: the same iterate as sequential backtracking), and the
+// O(n^2) parts (H y, H_FF g_F, the rank-two update, n = 2 N_r) are spread over
+// the lanes.
 //
 // H lives in the warp's slice of a global workspace, small enough to stay in
 // L2.  The update is evaluated in a form that is symmetric in (i, j) operation
@@ -30,6 +32,8 @@ namespace smppi {
 constexpr int BFGS_WPB_MAX = 4;                      // warps (sequences) per block
 constexpr size_t BFGS_WS_MAX = size_t(256) << 20;    // bytes of H slices at most
 constexpr int BFGS_ROWS = 8;                         // rows per lane per pass of a product
+constexpr int BFGS_COLS = 8;                         // columns of H read at once by a product
+constexpr int BFGS_UPD = 4;                          // rows of H read at once by the update
 
 namespace {
 
@@ -40,7 +44,10 @@ __device__ __forceinline__ double bfgs_warp_sum(double v) {
 }
 
 // out_i = sum_j H_ji x_j (= (H x)_i, H symmetric) for i < n, lanes over i;
-// with mask, only the flagged rows and columns (other rows give 0).
+// with mask, only the flagged rows and columns (other rows give 0).  The
+// columns are read BFGS_COLS at a time, all their loads issued before the
+// products, which are then added in column order (H is in global memory: one
+// column at a time would wait for each load in turn).
 __device__ __forceinline__ void warp_symv(const float* __restrict__ H, const float* x, int n,
                                           const unsigned char* mask, float* out) {
     const int lane = threadIdx.x & 31;
@@ -48,14 +55,28 @@ __device__ __forceinline__ void warp_symv(const float* __restrict__ H, const flo
         float acc[BFGS_ROWS];
 #pragma unroll
         for (int r = 0; r < BFGS_ROWS; ++r) acc[r] = 0.0f;
-        for (int j = 0; j < n; ++j) {
-            if (mask && !mask[j]) continue;          // the same j on every lane
-            const float xj = x[j];
-            const float* col = H + (size_t)j * n;
+        for (int j0 = 0; j0 < n; j0 += BFGS_COLS) {
+            float h[BFGS_COLS][BFGS_ROWS];
 #pragma unroll
-            for (int r = 0; r < BFGS_ROWS; ++r) {
-                const int i = i0 + 32 * r;
-                if (i < n) acc[r] = fmaf(col[i], xj, acc[r]);
+            for (int u = 0; u < BFGS_COLS; ++u) {
+                const int j = j0 + u;
+                const bool use = j < n && (!mask || mask[j]);   // the same j on every lane
+                const float* col = H + (size_t)j * n;
+#pragma unroll
+                for (int r = 0; r < BFGS_ROWS; ++r) {
+                    const int i = i0 + 32 * r;
+                    h[u][r] = (use && i < n) ? __ldcg(col + i) : 0.0f;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < BFGS_COLS; ++u) {
+                const int j = j0 + u;
+                if (j < n && (!mask || mask[j])) {
+                    const float xj = x[j];
+#pragma unroll
+                    for (int r = 0; r < BFGS_ROWS; ++r)
+                        if (i0 + 32 * r < n) acc[r] = fmaf(h[u][r], xj, acc[r]);
+                }
             }
         }
 #pragma unroll
@@ -122,7 +143,7 @@ __device__ __forceinline__ int bfgs_solve(const DevParams& P, const Merit& f, co
     for (; it < n_iters; ++it) {
         if (lane == 0 && mrow) mrow[it] = P0;
         if (P0 == 0.0) break;
-        if (lane == 0) f.grad(P, a.Vw, a.G);
+        f.grad(P, a.Vw, a.G);
         __syncwarp();
         // curvature pair of the last accepted step and the inverse update
         //   H <- (I - rho s y') H (I - rho y s') + rho s s'
@@ -143,7 +164,8 @@ __device__ __forceinline__ int bfgs_solve(const DevParams& P, const Merit& f, co
             if (sy > 1e-5 * sqrt(ss * yy)) {
                 if (!H_set) {
                     const float h0 = (float)(sy / yy);
-                    for (int k = lane; k < n * n; k += 32) H[k] = (k % (n + 1) == 0) ? h0 : 0.0f;
+                    for (int i = 0; i < n; ++i)
+                        for (int j = lane; j < n; j += 32) H[(size_t)i * n + j] = i == j ? h0 : 0.0f;
                     __syncwarp();
                     H_set = true;
                 }
@@ -153,12 +175,45 @@ __device__ __forceinline__ int bfgs_solve(const DevParams& P, const Merit& f, co
                 yHy = bfgs_warp_sum(yHy);
                 const float rho = (float)(1.0 / sy);
                 const float cs = (float)(yHy / (sy * sy) + 1.0 / sy);
-                for (int k = lane; k < n * n; k += 32) {
-                    const int i = k / n, j = k - i * n;
-                    const float si = sf[i], sj = sf[j];
-                    const float cross = __fadd_rn(__fmul_rn(si, a.Hy[j]), __fmul_rn(sj, a.Hy[i]));
-                    const float delta = __fsub_rn(__fmul_rn(cs, __fmul_rn(si, sj)), __fmul_rn(rho, cross));
-                    H[k] = __fadd_rn(H[k], delta);
+                // by column chunks of 32 BFGS_ROWS (s_j and (Hy)_j of a lane's columns held
+                // in registers) and BFGS_UPD rows at a time, all loads of H first
+                for (int c0 = lane; c0 < n; c0 += 32 * BFGS_ROWS) {
+                    float sj[BFGS_ROWS], hyj[BFGS_ROWS];
+#pragma unroll
+                    for (int u = 0; u < BFGS_ROWS; ++u) {
+                        const int j = c0 + 32 * u;
+                        sj[u] = j < n ? sf[j] : 0.0f;
+                        hyj[u] = j < n ? a.Hy[j] : 0.0f;
+                    }
+                    for (int i0 = 0; i0 < n; i0 += BFGS_UPD) {
+                        float hk[BFGS_UPD][BFGS_ROWS];
+#pragma unroll
+                        for (int v = 0; v < BFGS_UPD; ++v)
+#pragma unroll
+                            for (int u = 0; u < BFGS_ROWS; ++u) {
+                                const int i = i0 + v, j = c0 + 32 * u;
+                                hk[v][u] = (i < n && j < n) ? __ldcg(H + (size_t)i * n + j) : 0.0f;
+                            }
+#pragma unroll
+                        for (int v = 0; v < BFGS_UPD; ++v) {
+                            const int i = i0 + v;
+                            if (i < n) {
+                                const float si = sf[i], hyi = a.Hy[i];
+#pragma unroll
+                                for (int u = 0; u < BFGS_ROWS; ++u) {
+                                    const int j = c0 + 32 * u;
+                                    if (j < n) {
+                                        const float cross = __fadd_rn(__fmul_rn(si, hyj[u]),
+                                                                      __fmul_rn(sj[u], hyi));
+                                        const float delta =
+                                            __fsub_rn(__fmul_rn(cs, __fmul_rn(si, sj[u])),
+                                                      __fmul_rn(rho, cross));
+                                        H[(size_t)i * n + j] = __fadd_rn(hk[v][u], delta);
+                                    }
+                                }
+                            }
+                        }
+                    }
                 }
                 __syncwarp();
             }

@@ -230,17 +230,20 @@ __device__ double curv_merit_grad(const DevParams& P, const float* kt, const Sta
 // model_step_adjoint_curv at (x_t, u_t) scaled by dt, collected per step (the
 // velocity block as the Cartesian block gradient, the Frenet kinematics through
 // (s, e_y, e_psi)), d_t the CBF penalties' derivative at x_t.  coef: 7 float4
-// per step.  G_t = 0 for N <= t < T and outside the box.
-template <int BLK>
-__device__ void curv_block_grad(const DevParams& P, const float* kt, const State& x0, int N,
-                                int T, const float2* Vw, float2* G, float* tape, float4* coef) {
-    const int tid = threadIdx.x;
+// per step.  G_t = 0 for N <= t < T and outside the box.  The group is NT
+// threads of ranks 0..NT-1 synchronised by sync() (the block of the repair
+// kernel, the warp of the BFGS solver).
+template <class Sync>
+__device__ __forceinline__ void curv_group_grad(const DevParams& P, const float* kt,
+                                                const State& x0, int N, int T, const float2* Vw,
+                                                float2* G, float* tape, float4* coef, int tid,
+                                                int NT, const Sync& sync) {
     if (tid == 0)
         curv_forward<true, false>(P, kt, x0, N, Vw, nullptr, 0.0f, tape, nullptr, 0.0f, 1.0f);
-    __syncthreads();
+    sync();
     const float dt = P.dt, wc = P.C_cbf;
     auto h_at = [&](int t) { return tape[(size_t)t * CR_NF + 8]; };
-    for (int t = tid; t < N; t += BLK) {
+    for (int t = tid; t < N; t += NT) {
         const State x = tape_state(tape, t);
         const float2 v = Vw[t];
         const float d = clampf(v.x, P.umin0, P.umax0);
@@ -292,7 +295,7 @@ __device__ void curv_block_grad(const DevParams& P, const float* kt, const State
         c[6] = make_float4(in0 ? dt * (-P.lf * Fyf * sd * P.Iz_inv + kf * a3) : 0.0f,
                            in1 ? dt * P.fx_gain * P.m_inv : 0.0f, dey, 0.0f);
     }
-    __syncthreads();
+    sync();
     if (tid == 0) {
         float lvx = 0.0f, lvy = 0.0f, lr = 0.0f, ls = 0.0f, ley = 0.0f, lep = 0.0f;
         if (N > 0 && cbf_arg(P, h_at(N - 1), h_at(N)) > 0.0f)   // lambda_N = d_N
@@ -320,20 +323,30 @@ __device__ void curv_block_grad(const DevParams& P, const float* kt, const State
         }
         for (int t = N; t < T; ++t) G[t] = make_float2(0.0f, 0.0f);
     }
-    __syncthreads();
+    sync();
+}
+
+template <int BLK>
+__device__ void curv_block_grad(const DevParams& P, const float* kt, const State& x0, int N,
+                                int T, const float2* Vw, float2* G, float* tape, float4* coef) {
+    curv_group_grad(P, kt, x0, N, T, Vw, G, tape, coef, (int)threadIdx.x, BLK,
+                    []() { __syncthreads(); });
 }
 
 // The merit of the curvilinear state from x0 for the BFGS solver (bfgs.cuh):
-// curv_forward and curv_merit_grad with the warp's full tape.
+// curv_forward, and its gradient by the warp from the warp's full tape
+// (curv_group_grad; coef: 7 float4 per step).
 struct CurvMerit {
     const float* kt;
     State x0;
     float* tape;
+    float4* coef;
     __device__ __forceinline__ double merit(const DevParams& P, const float2* Vw) const {
         return curv_forward<false, false>(P, kt, x0, P.N_r, Vw, nullptr, 0.0f, nullptr, nullptr);
     }
     __device__ __forceinline__ void grad(const DevParams& P, const float2* Vw, float2* G) const {
-        curv_merit_grad(P, kt, x0, P.N_r, P.T, Vw, G, tape);
+        curv_group_grad(P, kt, x0, P.N_r, P.T, Vw, G, tape, coef, (int)(threadIdx.x & 31), 32,
+                        []() { __syncwarp(); });
     }
     __device__ __forceinline__ double trial(const DevParams& P, const float2* Vw, const float2* G,
                                             const float2* Dn, float a, double* dec) const {
@@ -344,10 +357,14 @@ struct CurvMerit {
 // Bytes of the staged curvature samples (n_track + 1 floats, padded to 16).
 __host__ __device__ inline size_t kappa_bytes(int n) { return (size_t)((n + 1 + 3) & ~3) * 4; }
 
-// Bytes of one warp's region of the BFGS kernel: the solver's arrays and a full
-// tape of T + 1 states, padded to 16 (a multiple of 8: float2 arrays stay aligned).
+// Bytes of one warp's region of the BFGS kernel: the solver's arrays, a full
+// tape of T + 1 states padded to 16, and the gradient's coefficients (7 float4 per
+// step, at the next 16-byte boundary); a multiple of 8, so float2 arrays stay aligned.
+__host__ __device__ inline size_t curv_bfgs_tape_bytes(int T) {
+    return ((size_t)(T + 1) * CR_NF * 4 + 15) & ~size_t(15);
+}
 __host__ __device__ inline size_t curv_bfgs_warp_bytes(int T) {
-    return bfgs_array_bytes(T) + (((size_t)(T + 1) * CR_NF * 4 + 15) & ~size_t(15));
+    return bfgs_array_bytes(T) + curv_bfgs_tape_bytes(T) + (size_t)T * 112 + 16;
 }
 
 struct CurvSmem {
@@ -511,7 +528,7 @@ cudaError_t launch_repair_curv(const DevParams& P, const float* kappa, int n_seq
 // BFGS repair (mode 2) on the curvilinear state: the solver of bfgs.cuh with
 // the curvilinear merit.  A block holds a few warps that share the staged
 // curvature samples; warps take sequences from an atomic counter.
-__global__ void __launch_bounds__(32 * BFGS_WPB_MAX) curv_repair_bfgs_kernel(
+__global__ void __launch_bounds__(32 * BFGS_WPB_MAX, 2) curv_repair_bfgs_kernel(
     DevParams P, const float* __restrict__ kappa, const float* __restrict__ x0g, const float* Vin,
     float* Vout, int n_seq, int n_iters, float* __restrict__ Hws, unsigned* __restrict__ next,
     double* __restrict__ merit_out, int* __restrict__ iters_out, ApplyArgs ap,
@@ -523,6 +540,9 @@ __global__ void __launch_bounds__(32 * BFGS_WPB_MAX) curv_repair_bfgs_kernel(
     unsigned char* wbase = smem_raw + kappa_bytes(nt) + (size_t)warp * curv_bfgs_warp_bytes(T);
     const BfgsArrays a = bfgs_arrays(wbase, T);
     float* tape = reinterpret_cast<float*>(wbase + bfgs_array_bytes(T));
+    float4* coef = reinterpret_cast<float4*>(
+        (reinterpret_cast<uintptr_t>(wbase + bfgs_array_bytes(T) + curv_bfgs_tape_bytes(T)) + 15) &
+        ~uintptr_t(15));
     float* H = Hws + ((size_t)blockIdx.x * wpb + warp) * n * n;
 
     for (int i = threadIdx.x; i <= nt; i += blockDim.x) kt[i] = kappa[i];
@@ -536,7 +556,7 @@ __global__ void __launch_bounds__(32 * BFGS_WPB_MAX) curv_repair_bfgs_kernel(
         const float2* vin = reinterpret_cast<const float2*>(Vin) + (size_t)q * T;
         for (int t = lane; t < T; t += 32) a.Vw[t] = vin[t];
         __syncwarp();
-        const CurvMerit f{kt, make_state(x0g + 6 * q), tape};
+        const CurvMerit f{kt, make_state(x0g + 6 * q), tape, coef};
         double P0;
         bool stalled;
         const int it = bfgs_solve(P, f, a, H, n_iters,

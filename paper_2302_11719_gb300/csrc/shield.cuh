@@ -528,6 +528,105 @@ __device__ __forceinline__ GradWs grad_ws_at(unsigned char* p, int T) {
     return g;
 }
 
+// Where the penalty part of step t >= 1 reads its inputs: h_{t-1}, h_t, h_{t+1}
+// and the tracked segment of x_t.
+struct PenIn {
+    float hm, h, hn;
+    int sg;
+};
+
+// Coefficients of the adjoint map of step t (5 float4; block_cost_grad states
+// the map) at the state x_t: velocity (vx, vy, r), position (X, Y), heading
+// (cp, sp) = (cos psi, sin psi); v the control of step t; for t >= 1 the
+// penalty part from pen() (a PenIn; the segment is clamped to the track: a
+// merit pass whose wait gave up leaves it unset, and the TIMEOUT bit reports
+// that case).
+template <class Pen>
+__device__ __forceinline__ void cart_grad_coef(const DevParams& P, const float4* rec, int t,
+                                               float vx, float vy, float r, float X, float Y,
+                                               float cp, float sp, float2 v, const Pen& pen,
+                                               float4* c) {
+    const float dt = P.dt, wc = P.C_cbf;
+    const float d = clampf(v.x, P.umin0, P.umax0);
+    const float yf = fmaf(P.lf, r, vy), yr = fmaf(-P.lr, r, vy);
+    const float bf = atan2_poly(yf, vx), br = atan2_poly(yr, vx);
+    float dphf, dphr;
+    const float Fyf = P.Fzf * tyre_shape(P, P.B * (d - bf), &dphf);
+    tyre_shape(P, P.B * (-br), &dphr);
+    float sd, cd;
+    if (P.steer_small) sincos_half(d, &sd, &cd);
+    else sincosf(d, &sd, &cd);
+    const float dX = vx * cp - vy * sp, dY = vx * sp + vy * cp;
+    // lateral-force adjoints Fyf_b = a1 g_vx + a2 g_vy + a3 g_r, Fyr_b = b2 g_vy + b3 g_r;
+    // through the tyres and the slip angles they reach v_x (q), v_y and r (p)
+    const float kf = P.Fzf * dphf * P.B, kr = P.Fzr * dphr * P.B;
+    const float nf = fmaf(vx, vx, yf * yf), nr = fmaf(vx, vx, yr * yr);
+    const float pf = nf > 0.0f ? -kf * vx / nf : 0.0f, qf = nf > 0.0f ? kf * yf / nf : 0.0f;
+    const float pr = nr > 0.0f ? -kr * vx / nr : 0.0f, qr = nr > 0.0f ? kr * yr / nr : 0.0f;
+    const float a1 = -sd * P.m_inv, a2 = cd * P.m_inv, a3 = P.lf * cd * P.Iz_inv;
+    const float b2 = P.m_inv, b3 = -P.lr * P.Iz_inv;
+    const bool in0 = v.x >= P.umin0 && v.x <= P.umax0, in1 = v.y >= P.umin1 && v.y <= P.umax1;
+    c[0] = make_float4(dt * (qf * a1), dt * (-r + qf * a2 + qr * b2), dt * (qf * a3 + qr * b3),
+                       dt * (r + pf * a1));
+    c[1] = make_float4(dt * (pf * a2 + pr * b2), dt * (pf * a3 + pr * b3),
+                       dt * (vy + P.lf * pf * a1), dt * (-vx + P.lf * pf * a2 - P.lr * pr * b2));
+    c[2] = make_float4(dt * (P.lf * pf * a3 - P.lr * pr * b3), dt * cp, dt * sp, dt * dX);
+    c[3] = make_float4(dt * dY, in0 ? dt * (-Fyf * cd * P.m_inv + kf * a1) : 0.0f,
+                       in0 ? dt * (-Fyf * sd * P.m_inv + kf * a2) : 0.0f,
+                       in0 ? dt * (-P.lf * Fyf * sd * P.Iz_inv + kf * a3) : 0.0f);
+    // d_t (t >= 1): the penalties of the pairs (t - 1, t) and (t, t + 1) through e_y^2
+    float ddX = 0.0f, ddY = 0.0f;
+    if (t > 0) {
+        const PenIn q = pen();
+        float ch = 0.0f;
+        if (cbf_arg(P, q.hm, q.h) > 0.0f) ch -= wc;
+        if (cbf_arg(P, q.h, q.hn) > 0.0f) ch += wc * P.one_m_alpha;
+        const float2 ro = rec_offset(rec, min(max(q.sg, 0), P.n_track - 1), X, Y);
+        ddX = -2.0f * ch * ro.x;
+        ddY = -2.0f * ch * ro.y;
+    }
+    c[4] = make_float4(in1 ? dt * P.fx_gain * P.m_inv : 0.0f, ddX, ddY, 0.0f);
+}
+
+// The recursion of the gradient on one thread: lambda_N = d_N (the penalty of
+// the last pair: hN() = (h_{N-1}, h_N), and where it is active xN() = (X, Y) of
+// x_N and its segment), then G_t and lambda_t for t = N - 1 .. 0 from the
+// coefficients; G_t = 0 for N <= t < T.
+template <class HN, class XN>
+__device__ __forceinline__ void cart_grad_recur(const DevParams& P, const float4* rec, int N,
+                                                int T, const float4* coef, float2* G,
+                                                const HN& hN, const XN& xN) {
+    const float dt = P.dt, wc = P.C_cbf;
+    float lvx = 0.0f, lvy = 0.0f, lr = 0.0f, lX = 0.0f, lY = 0.0f, lp = 0.0f;
+    if (N > 0) {
+        const float2 hh = hN();
+        if (cbf_arg(P, hh.x, hh.y) > 0.0f) {
+            const float3 p = xN();
+            const float2 ro = rec_offset(rec, min(max(__float_as_int(p.z), 0), P.n_track - 1),
+                                         p.x, p.y);
+            lX = 2.0f * wc * ro.x;
+            lY = 2.0f * wc * ro.y;
+        }
+    }
+#pragma unroll 4
+    for (int t = N - 1; t >= 0; --t) {
+        const float4* c = coef + 5 * t;
+        const float4 c0 = c[0], c1 = c[1], c2 = c[2], c3 = c[3], c4 = c[4];
+        G[t] = make_float2(fmaf(c3.y, lvx, fmaf(c3.z, lvy, c3.w * lr)), c4.x * lvx);
+        const float nvx = lvx + (fmaf(c0.x, lvx, c0.y * lvy) + fmaf(c0.z, lr, fmaf(c2.y, lX, c2.z * lY)));
+        const float nvy = lvy + (fmaf(c0.w, lvx, c1.x * lvy) + fmaf(c1.y, lr, fmaf(c2.y, lY, -c2.z * lX)));
+        const float nr = lr + (fmaf(c1.z, lvx, c1.w * lvy) + fmaf(c2.x, lr, dt * lp));
+        const float np = lp + fmaf(c2.w, lY, -c3.x * lX);
+        lX += c4.y;
+        lY += c4.z;
+        lvx = nvx;
+        lvy = nvy;
+        lr = nr;
+        lp = np;
+    }
+    for (int t = N; t < T; ++t) G[t] = make_float2(0.0f, 0.0f);
+}
+
 // Gradient G_t = dP/dv_t of the merit P (the CBF objective of Eq. 22: running-cost
 // weight 0, CBF weight 1) by the whole block, from the trajectory of Vw that the
 // last merit pass left (merit_rows of buf, gw.tr).  The adjoint of the Euler
@@ -545,10 +644,8 @@ __device__ void block_cost_grad(const DevParams& P, const float4* rec, const Sta
                                 const GradWs& gw) {
     const int tid = threadIdx.x;
     const MeritRows mr = merit_rows(buf, N);
-    const float dt = P.dt, wc = P.C_cbf;
     for (int t = tid; t < N; t += BLK) {
         const float4 v4 = mr.vel[t];
-        const float vx = v4.x, vy = v4.y, r = v4.z;
         float X = x0.X, Y = x0.Y, cp = x0.cp, sp = x0.sp;
         if (t > 0) {
             const float2 p = mr.pos[t - 1];
@@ -558,77 +655,54 @@ __device__ void block_cost_grad(const DevParams& P, const float4* rec, const Sta
             cp = a.y;
             sp = a.z;
         }
-        const float2 v = Vw[t];
-        const float d = clampf(v.x, P.umin0, P.umax0);
-        const float yf = fmaf(P.lf, r, vy), yr = fmaf(-P.lr, r, vy);
-        const float bf = atan2_poly(yf, vx), br = atan2_poly(yr, vx);
-        float dphf, dphr;
-        const float Fyf = P.Fzf * tyre_shape(P, P.B * (d - bf), &dphf);
-        tyre_shape(P, P.B * (-br), &dphr);
-        float sd, cd;
-        if (P.steer_small) sincos_half(d, &sd, &cd);
-        else sincosf(d, &sd, &cd);
-        const float dX = vx * cp - vy * sp, dY = vx * sp + vy * cp;
-        // lateral-force adjoints Fyf_b = a1 g_vx + a2 g_vy + a3 g_r, Fyr_b = b2 g_vy + b3 g_r;
-        // through the tyres and the slip angles they reach v_x (q), v_y and r (p)
-        const float kf = P.Fzf * dphf * P.B, kr = P.Fzr * dphr * P.B;
-        const float nf = fmaf(vx, vx, yf * yf), nr = fmaf(vx, vx, yr * yr);
-        const float pf = nf > 0.0f ? -kf * vx / nf : 0.0f, qf = nf > 0.0f ? kf * yf / nf : 0.0f;
-        const float pr = nr > 0.0f ? -kr * vx / nr : 0.0f, qr = nr > 0.0f ? kr * yr / nr : 0.0f;
-        const float a1 = -sd * P.m_inv, a2 = cd * P.m_inv, a3 = P.lf * cd * P.Iz_inv;
-        const float b2 = P.m_inv, b3 = -P.lr * P.Iz_inv;
-        const bool in0 = v.x >= P.umin0 && v.x <= P.umax0, in1 = v.y >= P.umin1 && v.y <= P.umax1;
-        float4* c = gw.coef + 5 * t;
-        c[0] = make_float4(dt * (qf * a1), dt * (-r + qf * a2 + qr * b2), dt * (qf * a3 + qr * b3),
-                           dt * (r + pf * a1));
-        c[1] = make_float4(dt * (pf * a2 + pr * b2), dt * (pf * a3 + pr * b3),
-                           dt * (vy + P.lf * pf * a1),
-                           dt * (-vx + P.lf * pf * a2 - P.lr * pr * b2));
-        c[2] = make_float4(dt * (P.lf * pf * a3 - P.lr * pr * b3), dt * cp, dt * sp, dt * dX);
-        c[3] = make_float4(dt * dY, in0 ? dt * (-Fyf * cd * P.m_inv + kf * a1) : 0.0f,
-                           in0 ? dt * (-Fyf * sd * P.m_inv + kf * a2) : 0.0f,
-                           in0 ? dt * (-P.lf * Fyf * sd * P.Iz_inv + kf * a3) : 0.0f);
-        // d_t (t >= 1): the penalties of the pairs (t - 1, t) and (t, t + 1) through e_y^2
-        float ddX = 0.0f, ddY = 0.0f;
-        if (t > 0) {
-            const float h = gw.tr.hh[t];
-            float ch = 0.0f;
-            if (cbf_arg(P, gw.tr.hh[t - 1], h) > 0.0f) ch -= wc;
-            if (cbf_arg(P, h, gw.tr.hh[t + 1]) > 0.0f) ch += wc * P.one_m_alpha;
-            const float2 ro = rec_offset(rec, min(max(gw.tr.sg[t], 0), P.n_track - 1), X, Y);
-            ddX = -2.0f * ch * ro.x;
-            ddY = -2.0f * ch * ro.y;
-        }
-        c[4] = make_float4(in1 ? dt * P.fx_gain * P.m_inv : 0.0f, ddX, ddY, 0.0f);
+        cart_grad_coef(P, rec, t, v4.x, v4.y, v4.z, X, Y, cp, sp, Vw[t],
+                       [&]() {
+                           return PenIn{gw.tr.hh[t - 1], gw.tr.hh[t], gw.tr.hh[t + 1],
+                                        gw.tr.sg[t]};
+                       },
+                       gw.coef + 5 * t);
     }
     __syncthreads();
-    if (tid == 0) {
-        float lvx = 0.0f, lvy = 0.0f, lr = 0.0f, lX = 0.0f, lY = 0.0f, lp = 0.0f;
-        if (N > 0 && cbf_arg(P, gw.tr.hh[N - 1], gw.tr.hh[N]) > 0.0f) {   // lambda_N = d_N
-            const float2 p = mr.pos[N - 1];
-            const float2 ro = rec_offset(rec, min(max(gw.tr.sg[N], 0), P.n_track - 1), p.x, p.y);
-            lX = 2.0f * wc * ro.x;
-            lY = 2.0f * wc * ro.y;
-        }
-#pragma unroll 4
-        for (int t = N - 1; t >= 0; --t) {
-            const float4* c = gw.coef + 5 * t;
-            const float4 c0 = c[0], c1 = c[1], c2 = c[2], c3 = c[3], c4 = c[4];
-            G[t] = make_float2(fmaf(c3.y, lvx, fmaf(c3.z, lvy, c3.w * lr)), c4.x * lvx);
-            const float nvx = lvx + (fmaf(c0.x, lvx, c0.y * lvy) + fmaf(c0.z, lr, fmaf(c2.y, lX, c2.z * lY)));
-            const float nvy = lvy + (fmaf(c0.w, lvx, c1.x * lvy) + fmaf(c1.y, lr, fmaf(c2.y, lY, -c2.z * lX)));
-            const float nr = lr + (fmaf(c1.z, lvx, c1.w * lvy) + fmaf(c2.x, lr, dt * lp));
-            const float np = lp + fmaf(c2.w, lY, -c3.x * lX);
-            lX += c4.y;
-            lY += c4.z;
-            lvx = nvx;
-            lvy = nvy;
-            lr = nr;
-            lp = np;
-        }
-        for (int t = N; t < T; ++t) G[t] = make_float2(0.0f, 0.0f);
-    }
+    if (tid == 0)
+        cart_grad_recur(
+            P, rec, N, T, gw.coef, G,
+            [&]() { return make_float2(gw.tr.hh[N - 1], gw.tr.hh[N]); },
+            [&]() {
+                const float2 p = mr.pos[N - 1];
+                return make_float3(p.x, p.y, __int_as_float(gw.tr.sg[N]));
+            });
     __syncthreads();
+}
+
+// The same gradient by a group of NT threads (rank 0..NT-1, synchronised by
+// sync()) from a full tape of the trajectory that rank 0 writes first
+// (forward_cost, every state): the warp of the BFGS solver.  coef: 5 float4
+// per step.
+template <bool FAST, class Sync>
+__device__ __forceinline__ void tape_cost_grad(const DevParams& P, const float4* rec,
+                                               const State& x0, int s0, int N, int T,
+                                               const float2* Vw, float2* G, const Tape& tape,
+                                               float4* coef, int rank, int NT, const Sync& sync) {
+    if (rank == 0)
+        forward_cost<true, false, FAST>(P, rec, x0, s0, N, Vw, nullptr, 0.0f, 1, 0, 0.0f, 1.0f,
+                                        0, tape, nullptr);
+    sync();
+    for (int t = rank; t < N; t += NT) {
+        const State x = {tape.at(t, 0), tape.at(t, 1), tape.at(t, 2), tape.at(t, 3),
+                         tape.at(t, 4), tape.at(t, 5), tape.at(t, 6), tape.at(t, 7)};
+        cart_grad_coef(P, rec, t, x.vx, x.vy, x.r, x.X, x.Y, x.cp, x.sp, Vw[t],
+                       [&]() {
+                           return PenIn{tape.at(t, 10), tape.at(t, 9), tape.at(t + 1, 9),
+                                        __float_as_int(tape.at(t, 8))};
+                       },
+                       coef + 5 * t);
+    }
+    sync();
+    if (rank == 0)
+        cart_grad_recur(
+            P, rec, N, T, coef, G, [&]() { return make_float2(tape.at(N, 10), tape.at(N, 9)); },
+            [&]() { return make_float3(tape.at(N, 3), tape.at(N, 4), tape.at(N, 8)); });
+    sync();
 }
 
 // Closed-loop step (Alg. 2 ExecuteCommand + warm start, Eq. 26), one thread:
