@@ -95,10 +95,11 @@ __device__ __forceinline__ f2 rollout2_curv(const DevParams& P, const float* kt,
     State2 x = broadcast(x0);
     if (DUMP) dump2(ta, tb, 0, x);
     f2 za0, za1, zb0, zb1;
-    noise_pair2(P, ka, kb, 0u, iter, ctr3, za0, za1, zb0, zb1);
+    const PhiloxPair ph = philox_pair_setup(P, ka, kb, iter, ctr3);
+    noise_pair2(P, ph, 0u, za0, za1, zb0, zb1);
     for (int p = 0; p < npair; ++p) {   // steps 2p and 2p + 1 (< T)
         f2 na0, na1, nb0, nb1;
-        if (p + 1 < npair) noise_pair2(P, ka, kb, (uint32_t)(p + 1), iter, ctr3, na0, na1, nb0, nb1);
+        if (p + 1 < npair) noise_pair2(P, ph, (uint32_t)(p + 1), na0, na1, nb0, nb1);
         f2 d, a;
         perturb2(P, Vp[4 * p], Vp[4 * p + 1], za0, za1, acc, d, a);
         model_step2_curv<DUMP>(P, kt, x, d, a);

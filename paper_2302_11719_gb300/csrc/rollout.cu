@@ -840,7 +840,11 @@ __global__ void debug_noise_kernel(DevParams P, uint32_t iter, uint32_t ctr3, in
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
         const int k = (int)(i / npair), p = (int)(i % npair);
-        const uint4 r = philox10(make_uint4((uint32_t)k, (uint32_t)p, iter, ctr3), P);
+        // the rollout kernels' form (first two rounds split), checked against the
+        // oracle's Philox word for word
+        uint4 r, r2;
+        x2::philox_pair_words(P, x2::philox_pair_setup(P, (uint32_t)k, (uint32_t)k, iter, ctr3),
+                              (uint32_t)p, r, r2);
         if (raw) {
             uint32_t* o = raw + i * 4;
             o[0] = r.x; o[1] = r.y; o[2] = r.z; o[3] = r.w;

@@ -125,13 +125,67 @@ __device__ __forceinline__ void box_muller2(uint32_t a1, uint32_t b1, uint32_t a
     z1 = mul(r, s);
 }
 
+// Philox4x32-10 of the counters (k, p, iter, ctr3) of two rollouts ka, kb for
+// successive p, with the parts of the first two rounds that do not depend on p
+// formed once (philox10 does the same rounds in full).  Round 0 maps the counter
+// to (G0 ^ p, G1, R0, R1): G0 = hi(M1 iter) ^ key0, G1 = lo(M1 iter),
+// R0 = hi(M0 k) ^ ctr3 ^ key1, R1 = lo(M0 k).  Round 1 then gives
+// (hi(M1 R0) ^ G1 ^ key0', lo(M1 R0), hi(M0 x) ^ R1 ^ key1', lo(M0 x)) with
+// x = G0 ^ p, the one product the two rollouts share; rounds 2-9 follow.
+struct PhiloxPair {
+    uint32_t g0;                 // hi(M1 iter) ^ key0 of round 0
+    uint32_t qa0, qa1, sa1;      // rollout a: round-1 words 0 and 1, R1 ^ key1 of round 1
+    uint32_t qb0, qb1, sb1;      // rollout b
+};
+
+__device__ __forceinline__ PhiloxPair philox_pair_setup(const DevParams& P, uint32_t ka,
+                                                        uint32_t kb, uint32_t iter,
+                                                        uint32_t ctr3) {
+    constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const unsigned long long gi = (unsigned long long)M1 * iter;
+    PhiloxPair s;
+    s.g0 = (uint32_t)(gi >> 32) ^ P.rk0[0];
+    const uint32_t g1 = (uint32_t)gi;
+    auto one = [&](uint32_t k, uint32_t& q0, uint32_t& q1, uint32_t& s1) {
+        const unsigned long long pk = (unsigned long long)M0 * k;
+        const uint32_t r0 = (uint32_t)(pk >> 32) ^ ctr3 ^ P.rk1[0], r1 = (uint32_t)pk;
+        const unsigned long long pr = (unsigned long long)M1 * r0;
+        q0 = (uint32_t)(pr >> 32) ^ g1 ^ P.rk0[1];
+        q1 = (uint32_t)pr;
+        s1 = r1 ^ P.rk1[1];
+    };
+    one(ka, s.qa0, s.qa1, s.sa1);
+    one(kb, s.qb0, s.qb1, s.sb1);
+    return s;
+}
+
+// Rounds 2-9 of Philox4x32-10 (round keys rk[2..9]).
+__device__ __forceinline__ uint4 philox_rounds_2_9(uint4 c, const DevParams& P) {
+#pragma unroll
+    for (int i = 2; i < 10; ++i) {
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ P.rk0[i], (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ P.rk1[i], (uint32_t)p0);
+    }
+    return c;
+}
+
+// The Philox words of counters (ka, p, iter, ctr3) and (kb, p, iter, ctr3).
+__device__ __forceinline__ void philox_pair_words(const DevParams& P, const PhiloxPair& ph,
+                                                  uint32_t p, uint4& ra, uint4& rb) {
+    const unsigned long long px = (unsigned long long)0xD2511F53u * (ph.g0 ^ p);
+    const uint32_t hx = (uint32_t)(px >> 32), lx = (uint32_t)px;
+    ra = philox_rounds_2_9(make_uint4(ph.qa0, ph.qa1, hx ^ ph.sa1, lx), P);
+    rb = philox_rounds_2_9(make_uint4(ph.qb0, ph.qb1, hx ^ ph.sb1, lx), P);
+}
+
 // Noise of steps 2p (zs0, zs1) and 2p + 1 (zt0, zt1) of rollouts ka, kb:
 // Philox counter (k, p, iter, ctr3), words 0-1 for step 2p, 2-3 for 2p + 1.
-__device__ __forceinline__ void noise_pair2(const DevParams& P, uint32_t ka, uint32_t kb,
-                                            uint32_t p, uint32_t iter, uint32_t ctr3, f2& zs0,
-                                            f2& zs1, f2& zt0, f2& zt1) {
-    const uint4 ra = philox10(make_uint4(ka, p, iter, ctr3), P);
-    const uint4 rb = philox10(make_uint4(kb, p, iter, ctr3), P);
+__device__ __forceinline__ void noise_pair2(const DevParams& P, const PhiloxPair& ph, uint32_t p,
+                                            f2& zs0, f2& zs1, f2& zt0, f2& zt1) {
+    uint4 ra, rb;
+    philox_pair_words(P, ph, p, ra, rb);
     box_muller2(ra.x, rb.x, ra.y, rb.y, zs0, zs1);
     box_muller2(ra.z, rb.z, ra.w, rb.w, zt0, zt1);
 }
@@ -200,10 +254,11 @@ __device__ __forceinline__ f2 rollout2(const DevParams& P, const float4* rec,
     bool fb = false;
     if (DUMP) dump2(ta, tb, 0, x);
     f2 za0, za1, zb0, zb1;
-    noise_pair2(P, ka, kb, 0u, iter, ctr3, za0, za1, zb0, zb1);
+    const PhiloxPair ph = philox_pair_setup(P, ka, kb, iter, ctr3);
+    noise_pair2(P, ph, 0u, za0, za1, zb0, zb1);
     {   // steps 0 and 1 (the cost of x_0 is already in acc)
         f2 na0, na1, nb0, nb1;
-        noise_pair2(P, ka, kb, 1u, iter, ctr3, na0, na1, nb0, nb1);
+        noise_pair2(P, ph, 1u, na0, na1, nb0, nb1);
         f2 d, a;
         perturb2(P, Vp[0], Vp[1], za0, za1, acc, d, a);
         model_step2<DUMP, false>(P, x, d, a, fb);
@@ -220,7 +275,7 @@ __device__ __forceinline__ f2 rollout2(const DevParams& P, const float4* rec,
     }
     for (int p = 1; p < nfull; ++p) {   // steps 2p, 2p + 1 < T
         f2 na0, na1, nb0, nb1;
-        noise_pair2(P, ka, kb, (uint32_t)(p + 1), iter, ctr3, na0, na1, nb0, nb1);
+        noise_pair2(P, ph, (uint32_t)(p + 1), na0, na1, nb0, nb1);
         const State2 x_in = x;
         const int sa_in = sa, sb_in = sb;
         const f2 hp_in = h_prev, acc_in = acc;
