@@ -240,7 +240,10 @@ smppi_status smppi_cost_grad(smppi_handle* h, int n_seq, const float* x0, const 
  *           (ls_max_halvings), accepted when g'(V - V') > 0 and
  *           P' <= P - ls_c g'(V - V'); if none is and d came from H, the search
  *           is repeated along the gradient step.  One warp per sequence (both
- *           state kinds); a mode-2 call that needs more workspace than the handle holds
+ *           state kinds).  When 2 n_iters (2 N_r + 1) <= (2 N_r)^2 the warp keeps
+ *           the curvature pairs since the last reset and applies H by the
+ *           two-loop recursion (the same H in exact arithmetic), otherwise H
+ *           itself.  A mode-2 call that needs more workspace than the handle holds
  *           allocates it (a work counter and (2 N_r)^2 floats per resident
  *           warp, about 256 MB at most).
  *   x0 [n_seq x 6]; V_in, V_out [n_seq x T x 2] (may alias);

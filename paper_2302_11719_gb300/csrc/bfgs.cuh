@@ -18,11 +18,15 @@
 // O(n^2) parts (H y, H_FF g_F, the rank-two update, n = 2 N_r) are spread over
 // the lanes.
 //
-// H lives in the warp's slice of a global workspace, small enough to stay in
-// L2.  The update is evaluated in a form that is symmetric in (i, j) operation
-// by operation (no fused multiply-add), so H stays exactly symmetric; products
-// with H then read it by columns, H[j][i] = H[i][j], so that the lanes' loads
-// of one j coalesce.
+// The warp's slice of a global workspace (n^2 floats) holds, when they fit
+// (2 n_iters (n + 1) <= n^2, as for any n_iters <= n/2 - 1), the curvature
+// pairs since the last restart and H's products are formed from them by the
+// two-loop recursion (lm_product; equal to the dense update's in exact
+// arithmetic, O(k n) instead of O(n^2) per iteration).  Otherwise it holds H
+// itself: the update is evaluated in a form that is symmetric in (i, j)
+// operation by operation (no fused multiply-add), so H stays exactly
+// symmetric; products with H then read it by columns, H[j][i] = H[i][j], so
+// that the lanes' loads of one j coalesce.
 #pragma once
 
 #include "shield.cuh"
@@ -88,6 +92,48 @@ __device__ __forceinline__ void warp_symv(const float* __restrict__ H, const flo
     __syncwarp();
 }
 
+__device__ __forceinline__ float bfgs_warp_sumf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Dn = P_F H P_F g for the H that k inverse updates with the stored pairs
+// (s_i, y_i, rho_i = 1/(y_i's_i)), oldest first, make of h0 I: the two-loop
+// recursion (equal to the dense update's product in exact arithmetic).  S, Y: k
+// rows of n floats; rho, alpha: k floats; q: n floats of scratch (shared); fr:
+// the free coordinates.  All lanes; the dot products by the warp's butterfly.
+__device__ __forceinline__ void lm_product(const float* S, const float* Y, const float* rho,
+                                           float* alpha, int k, float h0, int n, const float* g,
+                                           const unsigned char* fr, float* q, float* dn) {
+    const int lane = threadIdx.x & 31;
+    for (int j = lane; j < n; j += 32) q[j] = fr[j] ? g[j] : 0.0f;
+    __syncwarp();
+    for (int i = k - 1; i >= 0; --i) {
+        const float* si = S + (size_t)i * n;
+        const float* yi = Y + (size_t)i * n;
+        float d = 0.0f;
+        for (int j = lane; j < n; j += 32) d = fmaf(__ldcg(si + j), q[j], d);
+        const float a = rho[i] * bfgs_warp_sumf(d);
+        if (lane == 0) alpha[i] = a;
+        for (int j = lane; j < n; j += 32) q[j] = fmaf(-a, __ldcg(yi + j), q[j]);
+        __syncwarp();
+    }
+    for (int j = lane; j < n; j += 32) q[j] *= h0;
+    __syncwarp();
+    for (int i = 0; i < k; ++i) {
+        const float* si = S + (size_t)i * n;
+        const float* yi = Y + (size_t)i * n;
+        float d = 0.0f;
+        for (int j = lane; j < n; j += 32) d = fmaf(__ldcg(yi + j), q[j], d);
+        const float c = alpha[i] - rho[i] * bfgs_warp_sumf(d);
+        for (int j = lane; j < n; j += 32) q[j] = fmaf(c, __ldcg(si + j), q[j]);
+        __syncwarp();
+    }
+    for (int j = lane; j < n; j += 32) dn[j] = fr[j] ? q[j] : 0.0f;
+    __syncwarp();
+}
+
 // The warp's working arrays for horizon T: five float2 arrays of T, two float
 // arrays of 2T and 2T flag bytes (padded to 16 bytes).
 struct BfgsArrays {
@@ -139,6 +185,15 @@ __device__ __forceinline__ int bfgs_solve(const DevParams& P, const Merit& f, co
     if (lane == 0) P0 = f.merit(P, a.Vw);
     P0 = __shfl_sync(FULL, P0, 0);
     bool H_set = false, have_step = false, stalled = false;
+    // limited-memory form when the pairs fit in the H slice (at most n_iters of
+    // them): S, Y (n_iters rows of n), then rho and alpha (n_iters each)
+    const bool lm = (size_t)2 * n_iters * (n + 1) <= (size_t)n * n;
+    float* S_st = H;
+    float* Y_st = H + (size_t)n_iters * n;
+    float* rho_st = H + (size_t)2 * n_iters * n;
+    float* alpha_st = rho_st + n_iters;
+    int lm_k = 0;
+    float lm_h0 = 0.0f;
     int it = 0;
     for (; it < n_iters; ++it) {
         if (lane == 0 && mrow) mrow[it] = P0;
@@ -161,7 +216,20 @@ __device__ __forceinline__ int bfgs_solve(const DevParams& P, const Merit& f, co
             yy = bfgs_warp_sum(yy);
             ss = bfgs_warp_sum(ss);
             __syncwarp();
-            if (sy > 1e-5 * sqrt(ss * yy)) {
+            if (lm && sy > 1e-5 * sqrt(ss * yy)) {   // store the pair
+                if (!H_set) {
+                    lm_h0 = (float)(sy / yy);
+                    lm_k = 0;
+                    H_set = true;
+                }
+                for (int i = lane; i < n; i += 32) {
+                    S_st[(size_t)lm_k * n + i] = sf[i];
+                    Y_st[(size_t)lm_k * n + i] = a.Yv[i];
+                }
+                if (lane == 0) rho_st[lm_k] = (float)(1.0 / sy);
+                ++lm_k;
+                __syncwarp();
+            } else if (sy > 1e-5 * sqrt(ss * yy)) {
                 if (!H_set) {
                     const float h0 = (float)(sy / yy);
                     for (int i = 0; i < n; ++i)
@@ -233,7 +301,8 @@ __device__ __forceinline__ int bfgs_solve(const DevParams& P, const Merit& f, co
         const float s_first = P.ls_s0 / gm;
         // direction (negated): Dn = H_FF g_F, or the scaled gradient step
         if (H_set) {
-            warp_symv(H, gf, n, a.fr, dnf);
+            if (lm) lm_product(S_st, Y_st, rho_st, alpha_st, lm_k, lm_h0, n, gf, a.fr, a.Hy, dnf);
+            else warp_symv(H, gf, n, a.fr, dnf);
             double gHg = 0.0;
             for (int i = lane; i < n; i += 32) gHg += (double)gf[i] * dnf[i];
             gHg = bfgs_warp_sum(gHg);

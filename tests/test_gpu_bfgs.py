@@ -12,6 +12,8 @@ restarts along the gradient step) against the FP64 oracle's BFGS.
     shares with a small batch;
   * one iteration from a gradient-step start equals the oracle's mode-1
     iteration (the first BFGS step is the scaled gradient step);
+  * the dense-H form (more iterations than the stored-pair form holds) against
+    the oracle as well;
   * merits and iterations against the gradient repair are printed.
 """
 import numpy as np
@@ -64,6 +66,18 @@ def test_bfgs_near_boundary_batch(S, orc):
     print("near-boundary BFGS repair: %d flips of %d, worst |dV| %.2e" % (flips, n, worst))
     assert worst <= V_REP
     assert flips <= n // 8
+
+
+def test_bfgs_dense_form(S, orc):
+    # more iterations than the stored-pair form holds in the H slice
+    # (2 n_iters (n + 1) > n^2 with n = 2 N_r = 20, 10 iterations): H itself is
+    # updated, against the oracle's BFGS
+    sq = I.near_boundary_sequences(n_seq=64, T=10, seed=6)
+    flips, worst = repair_compare(S, orc, sq.params, sq.track, sq.x0, sq.V, 10, mode=2)
+    print("near-boundary BFGS repair, T=10, 10 iterations (dense H): %d flips of 64, worst "
+          "|dV| %.2e" % (flips, worst))
+    assert worst <= V_REP
+    assert flips <= 64 // 8
 
 
 def _bfgs_run(S, ctl, x0, V, n, n_iters):
