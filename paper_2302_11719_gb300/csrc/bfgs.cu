@@ -30,10 +30,11 @@
 namespace smppi {
 namespace {
 
-// The merit of the Cartesian state from x0 (nearest segment s0): forward_cost,
-// and its gradient from the warp's full tape by the warp (tape_cost_grad; the
-// C = 1.5, small-steer model) or by lane 0 alone (seq_cost_grad, checkpoint
-// interval ck).
+// The merit of the Cartesian state from x0 (nearest segment s0): forward_cost
+// (the merit and a kept trial leave their trajectory on the warp's full tape),
+// and its gradient from that tape by the warp (tape_cost_grad; the C = 1.5,
+// small-steer model) or by lane 0 alone (seq_cost_grad, checkpoint interval ck,
+// which writes its own tape).
 template <bool FAST>
 struct CartMerit {
     const float4* rec;
@@ -42,21 +43,23 @@ struct CartMerit {
     Tape tape;
     float4* coef;   // 5 float4 per step
     __device__ __forceinline__ double merit(const DevParams& P, const float2* Vw) const {
-        return forward_cost<false, false, FAST>(P, rec, x0, s0, P.N_r, Vw, nullptr, 0.0f, 1, 0, 0.0f,
-                                                1.0f, 0, tape, nullptr);
+        return forward_cost<true, false, FAST>(P, rec, x0, s0, P.N_r, Vw, nullptr, 0.0f, 1, 0, 0.0f,
+                                               1.0f, 0, tape, nullptr);
     }
-    __device__ __forceinline__ void grad(const DevParams& P, const float2* Vw, float2* G) const {
+    __device__ __forceinline__ void grad(const DevParams& P, const float2* Vw, float2* G,
+                                         bool have_tape) const {
         const int lane = threadIdx.x & 31;
         if (FAST)
             tape_cost_grad<FAST>(P, rec, x0, s0, P.N_r, P.T, Vw, G, tape, coef, lane, 32,
-                                 []() { __syncwarp(); });
+                                 []() { __syncwarp(); }, have_tape);
         else if (lane == 0)
             seq_cost_grad<FAST>(P, rec, x0, s0, P.N_r, P.T, Vw, G, 1, 0, 0.0f, 1.0f, ck, tape);
     }
     __device__ __forceinline__ double trial(const DevParams& P, const float2* Vw, const float2* G,
-                                            const float2* Dn, float a, double* dec) const {
-        return forward_cost<false, true, FAST>(P, rec, x0, s0, P.N_r, Vw, G, a, 1, 0, 0.0f, 1.0f, 0,
-                                               tape, dec, Dn);
+                                            const float2* Dn, float a, double* dec,
+                                            bool keep) const {
+        return forward_cost<true, true, FAST>(P, rec, x0, s0, P.N_r, Vw, G, a, 1, 0, 0.0f, 1.0f, 0,
+                                              keep ? tape : Tape{nullptr, 1, 0}, dec, Dn);
     }
 };
 

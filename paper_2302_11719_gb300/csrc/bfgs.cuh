@@ -6,10 +6,14 @@
 // curv_repair.cu: curvilinear state); what differs between them is the merit,
 // supplied as an object with
 //   double merit(P, Vw)                         lane 0: P(Vw)
-//   void   grad(P, Vw, G)                       all lanes: G = dP/dV at Vw, 0 past
+//   void   grad(P, Vw, G, have_tape)            all lanes: G = dP/dV at Vw, 0 past
 //                                               N_r and for controls outside the box
-//   double trial(P, Vw, G, Dn, a, &dec)         any lane: P(u), u = clip(Vw - a Dn),
-//                                               dec = G . (Vw - u)
+//                                               (have_tape: the warp's tape already
+//                                               holds Vw's trajectory)
+//   double trial(P, Vw, G, Dn, a, &dec, keep)   any lane: P(u), u = clip(Vw - a Dn),
+//                                               dec = G . (Vw - u); keep: leave u's
+//                                               trajectory on the warp's tape
+// merit() leaves Vw's trajectory on the tape too.
 //
 // The warp computes the gradient (lane 0 the forward pass and the adjoint
 // recursion, the lanes the coefficients of the steps' adjoint maps), the lanes
@@ -194,11 +198,14 @@ __device__ __forceinline__ int bfgs_solve(const DevParams& P, const Merit& f, co
     float* alpha_st = rho_st + n_iters;
     int lm_k = 0;
     float lm_h0 = 0.0f;
+    // the tape holds the current iterate's trajectory (left by the merit, or by
+    // the full-step trial of lane 0 when that step was taken)
+    bool traj_ok = true;
     int it = 0;
     for (; it < n_iters; ++it) {
         if (lane == 0 && mrow) mrow[it] = P0;
         if (P0 == 0.0) break;
-        f.grad(P, a.Vw, a.G);
+        f.grad(P, a.Vw, a.G, traj_ok);
         __syncwarp();
         // curvature pair of the last accepted step and the inverse update
         //   H <- (I - rho s y') H (I - rho y s') + rho s s'
@@ -322,7 +329,7 @@ __device__ __forceinline__ int bfgs_solve(const DevParams& P, const Merit& f, co
             double bp = 0.0;
             for (int j = lane; j < P.ls_max; j += 32) {
                 double dec;
-                const double Pt = f.trial(P, a.Vw, a.G, a.Dn, ldexpf(1.0f, -j), &dec);
+                const double Pt = f.trial(P, a.Vw, a.G, a.Dn, ldexpf(1.0f, -j), &dec, j == 0);
                 if (dec > 0.0 && Pt <= P0 - (double)P.ls_c * dec && j < best) {
                     best = j;
                     bp = Pt;
@@ -339,6 +346,7 @@ __device__ __forceinline__ int bfgs_solve(const DevParams& P, const Merit& f, co
             __syncwarp();
         }
         if (bj == 0x7fffffff) { stalled = true; break; }
+        traj_ok = bj == 0;   // the full step's trial trajectory is the new iterate's
         const float al = ldexpf(1.0f, -bj);
         for (int t = lane; t < N; t += 32) {
             const float2 v = a.Vw[t], dn = a.Dn[t];

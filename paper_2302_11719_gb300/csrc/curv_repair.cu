@@ -66,7 +66,7 @@ __device__ double curv_forward(const DevParams& P, const float* kt, const State&
     double dec = 0.0;
     float Jf = 0.0f, decf = 0.0f;
     const float wc = w_cbf * P.C_cbf;
-    if (STORE) tape_put(tape, 0, x, h_prev);
+    if (STORE && tape) tape_put(tape, 0, x, h_prev);
     for (int t = 0; t < N; ++t) {
         const float2 v = Vw[t];
         float2 u;
@@ -85,7 +85,7 @@ __device__ double curv_forward(const DevParams& P, const float* kt, const State&
         const float a = cbf_arg(P, h_prev, h);
         Jf = (a > 0.0f) ? fmaf(wc, a, Jf) : Jf;
         h_prev = h;
-        if (STORE) tape_put(tape, t + 1, x, h);
+        if (STORE && tape) tape_put(tape, t + 1, x, h);
         if (((t + 1) & 15) == 0) {
             J += (double)Jf;
             dec += (double)decf;
@@ -237,8 +237,8 @@ template <class Sync>
 __device__ __forceinline__ void curv_group_grad(const DevParams& P, const float* kt,
                                                 const State& x0, int N, int T, const float2* Vw,
                                                 float2* G, float* tape, float4* coef, int tid,
-                                                int NT, const Sync& sync) {
-    if (tid == 0)
+                                                int NT, const Sync& sync, bool have_tape = false) {
+    if (tid == 0 && !have_tape)   // have_tape: the tape already holds Vw's trajectory
         curv_forward<true, false>(P, kt, x0, N, Vw, nullptr, 0.0f, tape, nullptr, 0.0f, 1.0f);
     sync();
     const float dt = P.dt, wc = P.C_cbf;
@@ -334,23 +334,27 @@ __device__ void curv_block_grad(const DevParams& P, const float* kt, const State
 }
 
 // The merit of the curvilinear state from x0 for the BFGS solver (bfgs.cuh):
-// curv_forward, and its gradient by the warp from the warp's full tape
-// (curv_group_grad; coef: 7 float4 per step).
+// curv_forward (the merit and a kept trial leave their trajectory on the warp's
+// full tape), and its gradient by the warp from that tape (curv_group_grad;
+// coef: 7 float4 per step).
 struct CurvMerit {
     const float* kt;
     State x0;
     float* tape;
     float4* coef;
     __device__ __forceinline__ double merit(const DevParams& P, const float2* Vw) const {
-        return curv_forward<false, false>(P, kt, x0, P.N_r, Vw, nullptr, 0.0f, nullptr, nullptr);
+        return curv_forward<true, false>(P, kt, x0, P.N_r, Vw, nullptr, 0.0f, tape, nullptr);
     }
-    __device__ __forceinline__ void grad(const DevParams& P, const float2* Vw, float2* G) const {
+    __device__ __forceinline__ void grad(const DevParams& P, const float2* Vw, float2* G,
+                                         bool have_tape) const {
         curv_group_grad(P, kt, x0, P.N_r, P.T, Vw, G, tape, coef, (int)(threadIdx.x & 31), 32,
-                        []() { __syncwarp(); });
+                        []() { __syncwarp(); }, have_tape);
     }
     __device__ __forceinline__ double trial(const DevParams& P, const float2* Vw, const float2* G,
-                                            const float2* Dn, float a, double* dec) const {
-        return curv_forward<false, true>(P, kt, x0, P.N_r, Vw, G, a, nullptr, dec, 0.0f, 1.0f, Dn);
+                                            const float2* Dn, float a, double* dec,
+                                            bool keep) const {
+        return curv_forward<true, true>(P, kt, x0, P.N_r, Vw, G, a, keep ? tape : nullptr, dec,
+                                        0.0f, 1.0f, Dn);
     }
 };
 

@@ -53,8 +53,8 @@ __device__ __forceinline__ void add_direct(const DevParams& P, const float4* rec
 }
 
 // Forward rollout of u_t = clamp(Vw_t - step G_t) for N steps from x0 (segment s0).
-// Returns J in float64 and, when STORE, fills the tape (every state when
-// ck <= 0, else every ck-th).  dec_out (optional) = sum_t G_t . (Vw_t - u'_t)
+// Returns J in float64 and, when STORE (and the tape has a base), fills the tape
+// (every state when ck <= 0, else every ck-th).  dec_out (optional) = sum_t G_t . (Vw_t - u'_t)
 // where u'_t = clip(Vw_t - step Dn_t) (the Armijo decrease term), Dn = G when
 // no search direction is given (the gradient step).  The terms are
 // summed in float32 over blocks of 16 steps and the block sums in float64
@@ -77,7 +77,7 @@ __device__ double forward_cost(const DevParams& P, const float4* rec,
     float Jf = 0.0f, decf = 0.0f;
     const float wc = w_cbf * P.C_cbf;
     const bool full = ck <= 0;
-    if (STORE && N > 0) tape.put(0, x, s, h_prev, h_pp);
+    if (STORE && N > 0 && tape.base) tape.put(0, x, s, h_prev, h_pp);
     auto control = [&](int t) {
         const float2 v = Vw[(size_t)t * ms + seq];
         if (TRIAL) {
@@ -100,7 +100,7 @@ __device__ double forward_cost(const DevParams& P, const float4* rec,
         Jf = (a > 0.0f) ? fmaf(wc, a, Jf) : Jf;
         h_pp = h_prev;
         h_prev = h;
-        if (STORE && (full ? true : (t % ck == 0)) && (t < N || full))
+        if (STORE && tape.base && (full ? true : (t % ck == 0)) && (t < N || full))
             tape.put(full ? t : t / ck, xs, s, h_prev, h_pp);
         if ((t & 15) == 0) {
             J += (double)Jf;
@@ -676,14 +676,15 @@ __device__ void block_cost_grad(const DevParams& P, const float4* rec, const Sta
 
 // The same gradient by a group of NT threads (rank 0..NT-1, synchronised by
 // sync()) from a full tape of the trajectory that rank 0 writes first
-// (forward_cost, every state): the warp of the BFGS solver.  coef: 5 float4
-// per step.
+// (forward_cost, every state) unless have_tape says the tape already holds that
+// of Vw: the warp of the BFGS solver.  coef: 5 float4 per step.
 template <bool FAST, class Sync>
 __device__ __forceinline__ void tape_cost_grad(const DevParams& P, const float4* rec,
                                                const State& x0, int s0, int N, int T,
                                                const float2* Vw, float2* G, const Tape& tape,
-                                               float4* coef, int rank, int NT, const Sync& sync) {
-    if (rank == 0)
+                                               float4* coef, int rank, int NT, const Sync& sync,
+                                               bool have_tape = false) {
+    if (rank == 0 && !have_tape)
         forward_cost<true, false, FAST>(P, rec, x0, s0, N, Vw, nullptr, 0.0f, 1, 0, 0.0f, 1.0f,
                                         0, tape, nullptr);
     sync();
