@@ -328,9 +328,10 @@ __device__ __forceinline__ void curv_group_grad(const DevParams& P, const float*
 
 template <int BLK>
 __device__ void curv_block_grad(const DevParams& P, const float* kt, const State& x0, int N,
-                                int T, const float2* Vw, float2* G, float* tape, float4* coef) {
+                                int T, const float2* Vw, float2* G, float* tape, float4* coef,
+                                bool have_tape = false) {
     curv_group_grad(P, kt, x0, N, T, Vw, G, tape, coef, (int)threadIdx.x, BLK,
-                    []() { __syncthreads(); });
+                    []() { __syncthreads(); }, have_tape);
 }
 
 // The merit of the curvilinear state from x0 for the BFGS solver (bfgs.cuh):
@@ -376,6 +377,7 @@ struct CurvSmem {
     float red[CR_BLK / 32];
     float step;
     int ok;
+    int keep;
 };
 
 }  // namespace
@@ -402,24 +404,28 @@ __global__ void __launch_bounds__(CR_BLK) curv_repair_kernel(
     const State x0 = make_state(x0g + 6 * q);
     __syncthreads();
     double* mrow = merit_out ? merit_out + (size_t)q * (n_iters + 1) : nullptr;
-    if (tid == 0) sm.P = curv_forward<false, false>(P, kt, x0, N, Vw, nullptr, 0.0f, nullptr, nullptr);
+    // the merit passes and the line search's first trial leave their trajectory on
+    // the tape: the next gradient skips its forward pass when the tape holds Vw's
+    if (tid == 0) sm.P = curv_forward<true, false>(P, kt, x0, N, Vw, nullptr, 0.0f, tape, nullptr);
     __syncthreads();
     double P0 = sm.P;
+    bool traj_ok = true;
     int it = 0;
     bool stalled = false;
     for (; it < n_iters; ++it) {
         if (tid == 0 && mrow) mrow[it] = P0;
         if (P0 == 0.0) break;
-        curv_block_grad<CR_BLK>(P, kt, x0, N, T, Vw, G, tape, coef);
+        curv_block_grad<CR_BLK>(P, kt, x0, N, T, Vw, G, tape, coef, traj_ok);
         if (mode == 0) {
             for (int t = tid; t < N; t += CR_BLK)
                 Vw[t] = clamp2(P, make_float2(fmaf(-delta, G[t].x, Vw[t].x),
                                               fmaf(-delta, G[t].y, Vw[t].y)));
             __syncthreads();
             if (tid == 0)
-                sm.P = curv_forward<false, false>(P, kt, x0, N, Vw, nullptr, 0.0f, nullptr, nullptr);
+                sm.P = curv_forward<true, false>(P, kt, x0, N, Vw, nullptr, 0.0f, tape, nullptr);
             __syncthreads();
             P0 = sm.P;
+            traj_ok = true;
             continue;
         }
         float gm = 0.0f;
@@ -439,7 +445,8 @@ __global__ void __launch_bounds__(CR_BLK) curv_repair_kernel(
             for (int j = lane; j < P.ls_max; j += 32) {
                 const float sj = ldexpf(s_first, -j);
                 double dec;
-                const double Pt = curv_forward<false, true>(P, kt, x0, N, Vw, G, sj, nullptr, &dec);
+                const double Pt =
+                    curv_forward<true, true>(P, kt, x0, N, Vw, G, sj, j == 0 ? tape : nullptr, &dec);
                 if (Pt <= P0 - (double)P.ls_c * dec && j < best) { best = j; best_P = Pt; }
             }
             int bj = best;
@@ -449,10 +456,14 @@ __global__ void __launch_bounds__(CR_BLK) curv_repair_kernel(
                 sm.P = best_P;
                 sm.step = ldexpf(s_first, -bj);
             }
-            if (lane == 0) sm.ok = (bj != 0x7fffffff);
+            if (lane == 0) {
+                sm.ok = (bj != 0x7fffffff);
+                sm.keep = (bj == 0);   // the first trial's trajectory is the new iterate's
+            }
         }
         __syncthreads();
         if (!sm.ok) { stalled = true; break; }
+        traj_ok = sm.keep != 0;
         const float sa = sm.step;
         for (int t = tid; t < N; t += CR_BLK)
             Vw[t] = clamp2(P, make_float2(fmaf(-sa, G[t].x, Vw[t].x), fmaf(-sa, G[t].y, Vw[t].y)));
