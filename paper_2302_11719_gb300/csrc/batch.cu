@@ -69,7 +69,7 @@ constexpr int BATCH_MAXPS = 4;    // pair sets per thread (pairs <= 4 * RB)
 // FAST (C = 1.5, |steer| <= 1/2): a work item is 2 RB rollouts, two per
 // thread on the packed path (rollout2.cuh); otherwise RB, one per thread.
 template <int RB, bool FAST>
-__global__ void __launch_bounds__(RB) batch_kernel(DevParams P0, BatchArgs a) {
+__global__ void __launch_bounds__(RB, 1) batch_kernel(DevParams P0, BatchArgs a) {
     constexpr int NW = RB / 32;
     constexpr int CHUNK = FAST ? 2 * RB : RB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
