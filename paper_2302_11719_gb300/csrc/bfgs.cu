@@ -1,27 +1,14 @@
-// BFGS repair: the solver Sec. IV-B names for the local problem of Eq. 22, run
-// for a fixed number of iterations.  The variant (box projection, Armijo on the
-// projected path, binding coordinates held, gradient-step restarts) is stated
-// with smppi_repair's mode 2 in smppi.h.
-//
-// One WARP per sequence: the warp computes the adjoint gradient (lane 0 the
-// forward pass into the tape and the recursion, the lanes the coefficients of
-// the steps' adjoint maps, tape_cost_grad), the lanes evaluate the line-search trials a = 1, 1/2, ...
-// in parallel (the largest accepted a is taken: the same iterate as
-// sequential backtracking), and the O(n^2) parts (H y, H_FF g_F, the rank-two
-// update, n = 2 N_r) are spread over the lanes.  A block holds a few warps
-// that share the staged track table; warps take sequences from an atomic
-// counter, so the sequences that need many iterations do not hold up a fixed
-// share of the others.
-//
-// H of the sequence a warp works on lives in that warp's slice of a global
-// workspace, small enough to stay in L2.  The update is evaluated in a form
-// that is symmetric in (i, j) operation by operation (no fused multiply-add),
-// so H stays exactly symmetric; products with H then read it by columns,
-// H[j][i] = H[i][j], so that the lanes' loads of one j coalesce.
-// BFGS repair on the Cartesian state (smppi_repair mode 2; the solver and its
-// variant are in bfgs.cuh).  A block holds a few warps that share the staged
-// track table; warps take sequences from an atomic counter, so the sequences
-// that need many iterations do not hold up a fixed share of the others.
+// BFGS repair on the Cartesian state (smppi_repair mode 2): the solver Sec. IV-B
+// names for the local problem of Eq. 22, run for a fixed number of iterations;
+// the solver, its variant (box projection, Armijo on the projected path,
+// binding coordinates held, gradient-step restarts) and the forms of H are in
+// bfgs.cuh.  One WARP per sequence: the warp forms the adjoint gradient (lane 0
+// the forward pass into the warp's tape unless the merit or the full step's
+// trial left it there, the lanes the coefficients of the steps' adjoint maps,
+// lane 0 the recursion: tape_cost_grad), and the lanes evaluate the line-search
+// trials in parallel.  A block holds a few warps that share the staged track
+// table; warps take sequences from an atomic counter, so the sequences that
+// need many iterations do not hold up a fixed share of the others.
 #include <algorithm>
 
 #include "bfgs.cuh"
