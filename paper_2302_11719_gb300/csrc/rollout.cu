@@ -776,14 +776,21 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_merge_shield_kernel(
     for (int o = 16; o > 0; o >>= 1) eta += __shfl_xor_sync(0xffffffffu, eta, o);
     if (lane == 0) red_d[warp] = eta;
     __syncthreads();
-    if (tid == 0) {
+    // 1/eta, one float64 division for the block (the warps' sums in order): with
+    // fewer controls than threads a thread without a control forms it while the
+    // others sum the noise, else thread 0 first
+    __shared__ double s_inv;
+    const bool late = T2 < UPD_BLK;
+    auto form_inv = [&]() {
         double e = red_d[0];
 #pragma unroll
         for (int w = 1; w < NW; ++w) e += red_d[w];
-        red_d[0] = 1.0 / e;          // one float64 division for the block
+        s_inv = 1.0 / e;
+    };
+    if (!late) {
+        if (tid == 0) form_inv();
+        __syncthreads();
     }
-    __syncthreads();
-    const double inv_eta = red_d[0];
     // the blocks that enter the noise sum, in block order
     int nz = 0;
     for (int b0 = 0; b0 < nb; b0 += UPD_BLK) {
@@ -798,6 +805,15 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_merge_shield_kernel(
         for (int w = 0; w < NW; ++w) nz += w_cnt[w];
         __syncthreads();
     }
+    if (late && tid == UPD_BLK - 1) form_inv();
+    auto form = [&](int j, float A, float cmp) {
+        const float lo = (j & 1) ? P.umin1 : P.umin0, hi = (j & 1) ? P.umax1 : P.umax0;
+        const float vj = j == tid ? v_pre : V[j];
+        const float v = (float)fma((double)__fadd_rn(A, cmp), s_inv, (double)vj);
+        if (!isfinite(v)) atomicOr(status, SMPPI_DEV_NUMERIC);
+        vplus[j] = clampf(v, lo, hi);
+    };
+    float A_own = 0.0f, cmp_own = 0.0f;   // the sum of this thread's control (late)
     // A_j = sum_b c_b A_b[j] in block order by the compensated dot product of
     // Ogita, Rump and Oishi (Dot2: each product's rounding error from an FMA, each
     // sum's from the two-sum, both carried in a second accumulator), as accurate
@@ -822,11 +838,16 @@ __global__ void __launch_bounds__(UPD_BLK) mppi_merge_shield_kernel(
             for (int u = 0; u < 8; ++u) add(s_c[l_b[i + u]], v[u]);
         }
         for (; i < nz; ++i) add(s_c[l_b[i]], __ldcg(&part.acc[(size_t)l_b[i] * T2 + j]));
-        const float lo = (j & 1) ? P.umin1 : P.umin0, hi = (j & 1) ? P.umax1 : P.umax0;
-        const float vj = j == tid ? v_pre : V[j];
-        const float v = (float)fma((double)__fadd_rn(A, cmp), inv_eta, (double)vj);
-        if (!isfinite(v)) atomicOr(status, SMPPI_DEV_NUMERIC);
-        vplus[j] = clampf(v, lo, hi);
+        if (late) {
+            A_own = A;
+            cmp_own = cmp;
+        } else {
+            form(j, A, cmp);
+        }
+    }
+    if (late) {
+        __syncthreads();
+        if (tid < T2) form(tid, A_own, cmp_own);
     }
     shield_tail<UPD_BLK, FAST>(P, smem_raw, &bar, reinterpret_cast<const float2*>(vplus), V, iter,
                                n_upd, iter_dev, sh, status, true, x0r, &seg0r);
