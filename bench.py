@@ -50,7 +50,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 L2_FLUSH_BYTES = 256 << 20
 # DRAM traffic per rollout launch from the ncu capture in profiles/, valid only
 # for the kernel source it was taken on (hash of the files that define it).
-ROLLOUT_TRAFFIC = {"sources_sha": "7a04f74482f1e0b0", "bytes_per_launch": 140032}
+ROLLOUT_TRAFFIC = {"sources_sha": "69b15b31bd555004", "bytes_per_launch": 139776}
 
 
 def kernel_sha() -> str:
