@@ -15,12 +15,12 @@
 //                                               trajectory on the warp's tape
 // merit() leaves Vw's trajectory on the tape too.
 //
-// The warp computes the gradient (lane 0 the forward pass and the adjoint
-// recursion, the lanes the coefficients of the steps' adjoint maps), the lanes
-// evaluate the line-search trials a = 1, 1/2, ... in parallel (the largest
-// accepted a is taken: the same iterate as sequential backtracking), and the
-// O(n^2) parts (H y, H_FF g_F, the rank-two update, n = 2 N_r) are spread over
-// the lanes.
+// The warp computes the gradient (lane 0 the forward pass, unless the tape
+// already holds the iterate's trajectory, and the adjoint recursion; the lanes
+// the coefficients of the steps' adjoint maps), the lanes evaluate the
+// line-search trials a = 1, 1/2, ... in parallel (the largest accepted a is
+// taken: the same iterate as sequential backtracking), and the products with H
+// (n = 2 N_r) are spread over the lanes.
 //
 // The warp's slice of a global workspace (n^2 floats) holds, when they fit
 // (2 n_iters (n + 1) <= n^2, as for any n_iters <= n/2 - 1), the curvature
